@@ -1,0 +1,461 @@
+"""Benchmark: KKT factor + solve throughput on one GB300.
+
+Workload (one step = the whole hot path, Algorithms 1-3, on one system):
+an interior-point-shaped SPD block-tridiagonal-arrow KKT matrix with N = 1024
+stage blocks of n = 32, arrow width m = 8, FP64, stage blocks
+Q + G^T Sigma G + 1e-8 I with Sigma log-uniform over [1e-8, 1e8], random
+dynamics couplings, one right-hand side b ~ N(0, 1). Every step factors the
+matrix and solves for b from inputs resident in HBM; L2 is flushed (a 256 MiB
+write) before every timed step. The level plan (segments per level of the
+recursive partition) is picked on the device among a few candidates before
+the warm-up.
+
+`--impl reference` times the FP64 CPU oracle (the sequential block method)
+on the host cores instead, on a bounded sample of the same workload.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+METRIC = "KKT factor+solve systems/sec at stated error vs plain FP64 GPU; % FLOP roofline"
+UNIT = "systems/s"
+N_STAGES, N_BLOCK, M_ARROW = 1024, 32, 8
+WORKLOAD = f"ipm-shaped KKT, one system: N={N_STAGES}, n={N_BLOCK}, m={M_ARROW}, FP64, nrhs=1"
+# FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+L2_FLUSH_BYTES = 256 << 20
+
+
+def backward_error(D, E, G, R, x, b):
+    """||b - Psi x||_inf / (||Psi||_inf ||x||_inf + ||b||_inf), blocks of Eq. (3)."""
+    N, n, _ = D.shape
+    m = R.shape[0]
+    Ds = np.tril(D) + np.swapaxes(np.tril(D, -1), 1, 2)
+    xs = x[:N * n].reshape(N, n)
+    y = np.einsum("jab,jb->ja", Ds, xs)
+    y[1:] += np.einsum("jab,jb->ja", E, xs[:-1])
+    y[:-1] += np.einsum("jba,jb->ja", E, xs[1:])
+    y = y.reshape(-1)
+    xg = x[N * n:]
+    Rs = np.tril(R) + np.tril(R, -1).T
+    y += np.einsum("jba,b->ja", G, xg).reshape(-1)
+    yg = np.einsum("jab,jb->a", G, xs) + Rs @ xg
+    r = b - np.concatenate([y, yg])
+    rows = np.abs(Ds).sum(axis=2)
+    rows[1:] += np.abs(E).sum(axis=2)
+    rows[:-1] += np.abs(E).sum(axis=1)
+    rows += np.abs(G).sum(axis=1)
+    grows = np.abs(G).sum(axis=(0, 2)) + np.abs(Rs).sum(axis=1)
+    norm = max(rows.max(), grows.max())
+    return float(np.abs(r).max() / (norm * np.abs(x).max() + np.abs(b).max())), \
+        float(np.linalg.norm(r) / np.linalg.norm(b))
+
+
+class ClockSampler:
+    """SM clock and clock-event (throttle) reasons sampled every 2 ms during the
+    timed region through NVML's read-only queries (ctypes; nvidia-smi's 200 ms
+    loop as a fallback)."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index: int, period_s: float = 0.002):
+        self.cuda_index = cuda_index
+        self.period = period_s
+        self.samples = []       # (sm_mhz, max_mhz, reasons_bitmask)
+        self.stop = threading.Event()
+        self.nvml = None
+        self.proc = None
+
+    def _nvml_handle(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        handle = ctypes.c_void_p()
+        try:
+            import torch
+            p = torch.cuda.get_device_properties(self.cuda_index)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            if lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(handle)) != 0:
+                raise RuntimeError
+        except Exception:
+            if lib.nvmlDeviceGetHandleByIndex_v2(self.cuda_index, ctypes.byref(handle)) != 0:
+                return None
+        fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return lib, handle, fn
+
+    def _loop(self):
+        import ctypes
+        lib, handle, reasons_fn = self.nvml
+        mhz, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        lib.nvmlDeviceGetMaxClockInfo(handle, 1, ctypes.byref(mx))
+        while not self.stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(handle, 1, ctypes.byref(mhz)) == 0 and \
+                    reasons_fn(handle, ctypes.byref(rs)) == 0:
+                self.samples.append((float(mhz.value), float(mx.value), int(rs.value)))
+            time.sleep(self.period)
+
+    def _smi(self):
+        for line in self.proc.stdout:
+            p = [v.strip() for v in line.split(",")]
+            try:
+                bits = 0
+                for name_bit, v in zip((0x8, 0x40, 0x20, 0x4), p[3:7]):
+                    if v.lower() == "active":
+                        bits |= name_bit
+                self.samples.append((float(p[1]), float(p[2]), bits))
+            except (ValueError, IndexError):
+                pass
+
+    def __enter__(self):
+        try:
+            self.nvml = self._nvml_handle()
+        except OSError:
+            self.nvml = None
+        if self.nvml:
+            self.t = threading.Thread(target=self._loop, daemon=True)
+        else:
+            fields = ("index,clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+                      "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                      "clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={fields}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._smi, daemon=True)
+        self.t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self.stop.set()
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        reasons = set()
+        for _, _, bits in self.samples:
+            for bit, name in self.REASONS.items():
+                if bits & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(v[0] for v in self.samples),
+                "sm_max_mhz": max(v[1] for v in self.samples), "reasons": sorted(reasons),
+                "samples": len(self.samples), "source": "nvml" if self.nvml else "nvidia-smi"}
+
+
+def read_traffic(kernel_src_sha: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when that summary was taken on other kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_factor_level1_ipm1024.md")
+    if not os.path.exists(path):
+        return None
+    sha, traffic = None, None
+    for line in open(path):
+        if line.startswith("kernel_source_sha256:"):
+            sha = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if sha == kernel_src_sha else None
+
+
+def kernel_source_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kkt_kernels.cu", "kkt_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2511_00946_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def workload(seed: int):
+    D, E, G, R = gen.ipm(N_STAGES, N_BLOCK, M_ARROW, seed=seed)
+    b = gen.rhs(N_STAGES * N_BLOCK + M_ARROW, 1, seed=seed + 1)
+    return D, E, G, R, b
+
+
+def cpu_oracle_rate(D, E, G, R, b, budget_s: float):
+    """The FP64 oracle's sequential factor + solve on one host core, timed on
+    as many copies of the system as fit in about `budget_s` seconds."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    F = oracle.seq_factor(D, E, G, R)
+    oracle.seq_solve(F, b)
+    one = time.perf_counter() - t0
+    reps = max(1, int(budget_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        F = oracle.seq_factor(D, E, G, R)
+        oracle.seq_solve(F, b)
+    dt = time.perf_counter() - t0
+    return reps / dt, reps, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    D, E, G, R, b = workload(0)
+    per_step = []
+    total_sys = 0
+    for _ in range(args.warmup):
+        cpu_oracle_rate(D, E, G, R, b, budget_s=0.0)
+    for _ in range(args.steps):
+        rate, reps, dt = cpu_oracle_rate(D, E, G, R, b, budget_s=args.ref_seconds)
+        per_step.append(dt / reps)
+        total_sys += reps
+    ms = 1000.0 * statistics.mean(per_step)
+    value = 1000.0 / ms
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "method": "FP64 CPU oracle, sequential block Cholesky"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{total_sys} factor+solve runs of the workload system, "
+                                   f"{args.steps} steps of about {args.ref_seconds:.0f} s"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def per_launch_flops(kkt, plan):
+    """Names and algorithmic FP64 flops (standard convention, as executed) of
+    the launches of one factor + one solve, in launch order: factor levels
+    1..L, forward levels 1..L (the top level also solves the corner and runs
+    its backward sweep), backward levels L-1..1."""
+    L = len(plan)
+    Ns = [N_STAGES]
+    for p in plan[:-1]:
+        Ns.append(p - 1)
+    suf = [kkt.kkt_plan_flops(Ns[l], N_BLOCK, M_ARROW, plan[l:], kkt.KKT_PARTITION_BALANCED)
+           for l in range(L)]
+    fac = [suf[l]["factor"] - (suf[l + 1]["factor"] if l + 1 < L else 0.0) for l in range(L)]
+    sol = [suf[l]["solve"] - (suf[l + 1]["solve"] if l + 1 < L else 0.0) for l in range(L)]
+    names = [f"k_factor level {l + 1}" for l in range(L)]
+    flops = list(fac)
+    for l in range(L):
+        names.append(f"k_forward level {l + 1}" + (" (+corner, backward)" if l == L - 1 else ""))
+        flops.append(sol[l] if l == L - 1 else sol[l] / 2.0)
+    for l in range(L - 2, -1, -1):
+        names.append(f"k_backward level {l + 1}")
+        flops.append(sol[l] / 2.0)
+    return names, flops
+
+
+def candidate_plans(kkt):
+    plans = [[152, 38, 10, 1], [152, 50, 16, 1], [152, 76, 25, 8, 1], [152, 38, 10, 3, 1],
+             [256, 64, 16, 4, 1], [304, 76, 19, 5, 1], [128, 32, 8, 1], [100, 25, 6, 1]]
+    ok = []
+    for p in plans:
+        try:
+            kkt.kkt_plan_flops(N_STAGES, N_BLOCK, M_ARROW, p, kkt.KKT_PARTITION_BALANCED)
+            ok.append(p)
+        except kkt.KKTError:
+            pass
+    return ok
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--levels", default=None, help="comma-separated segments per level (skips the search)")
+    ap.add_argument("--ref-seconds", type=float, default=3.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import paper_2511_00946_gb300 as kkt
+
+    D, E, G, R, b = workload(rank)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    Dd, Ed, Gd, Rd, b0 = dev(D), dev(E), dev(G), dev(R), dev(b)
+    bd = b0.clone()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # --- level plan: fastest of a few candidates (untimed)
+    if args.levels:
+        plan = [int(v) for v in args.levels.split(",")]
+    else:
+        best = None
+        for p in candidate_plans(kkt):
+            h = kkt.kkt_create_plan(N_STAGES, N_BLOCK, M_ARROW, p, kkt.KKT_PARTITION_BALANCED)
+            ts = []
+            for it in range(4):
+                bd.copy_(b0)
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+                kkt.kkt_solve(h, bd)
+                e1.record()
+                torch.cuda.synchronize()
+                if it:
+                    ts.append(e0.elapsed_time(e1))
+            kkt.kkt_destroy(h)
+            t = min(ts)
+            if best is None or t < best[0]:
+                best = (t, p)
+        plan = best[1]
+    h = kkt.kkt_create_plan(N_STAGES, N_BLOCK, M_ARROW, plan, kkt.KKT_PARTITION_BALANCED)
+    nfac, nsol = kkt.kkt_launch_counts(h)
+    nl = nfac + nsol
+    fl = kkt.kkt_flops(h)
+    launch_names, launch_flops = per_launch_flops(kkt, plan)
+    assert len(launch_names) == nl
+
+    launch_ev = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
+    for ev in launch_ev:
+        ev.record()
+    torch.cuda.synchronize()
+    kkt.kkt_set_launch_events(h, launch_ev)
+
+    def step():
+        kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+        kkt.kkt_solve(h, bd)
+
+    for _ in range(max(args.warmup, 3)):
+        bd.copy_(b0)
+        step()
+    torch.cuda.synchronize()
+    info = kkt.kkt_get_info(h)
+    if info["status"] != 0:
+        raise RuntimeError(f"factorization failed: {info}")
+
+    step_ms, launch_ms = [], [[] for _ in range(nl)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            bd.copy_(b0)
+            flush.zero_()       # evict L2 before the timed step
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            prev = e0
+            for i, ev in enumerate(launch_ev):
+                launch_ms[i].append(prev.elapsed_time(ev))
+                prev = ev
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+    x = bd.cpu().numpy()
+    eta, relres = backward_error(D, E, G, R, x, b)
+
+    # --- end to end through the public API with host buffers (pinned)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    hD, hE, hG, hR, hb = pin(D), pin(E), pin(G), pin(R), pin(b)
+    hx = torch.empty_like(hb).pin_memory()
+    h2d = sum(t.numel() * 8 for t in (hD, hE, hG, hR, hb))
+    d2h = hx.numel() * 8
+    kkt.kkt_set_launch_events(h, [])
+    e2e_ms = []
+    for it in range(args.steps + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Dd.copy_(hD, non_blocking=True); Ed.copy_(hE, non_blocking=True)
+        Gd.copy_(hG, non_blocking=True); Rd.copy_(hR, non_blocking=True)
+        bd.copy_(hb, non_blocking=True)
+        step()
+        hx.copy_(bd, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= 2:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
+
+    # --- roofline of the dominant kernel (largest share of the step)
+    avg = [statistics.mean(v) for v in launch_ms]
+    dom = int(np.argmax(avg))
+    names = launch_names
+    achieved = launch_flops[dom] / (avg[dom] * 1e-3) / 1e12
+    peak = FP64_PEAK_GFLOPS / 1000.0
+    traffic = read_traffic(kernel_source_sha())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, reps, dt = cpu_oracle_rate(D, E, G, R, b, budget_s=args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{reps} sequential FP64 factor+solve runs of the workload system ({dt:.1f} s)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "levels": plan, "partition": "balanced", "precision": "fp64",
+                       "l2": "flushed before every timed step (256 MiB write)",
+                       "replicas": world},
+            "error": {"backward_error": eta, "relative_residual": relres},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * nl,
+            "launches_per_step": {names[i] if i < len(names) else f"launch {i}": round(a, 4)
+                                  for i, a in enumerate(avg)},
+            "roofline": {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                         "traffic": traffic, "peak_note": "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz"},
+            "flops_per_step": {"factor": fl["factor"], "solve": fl["solve"],
+                               "sequential_factor": fl["sequential_factor"]},
+            "clocks": clk.summary(),
+            "wall_s_timed": wall,
+        }
+        if cpu:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out), flush=True)
+    kkt.kkt_destroy(h)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

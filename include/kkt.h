@@ -1,0 +1,209 @@
+/*
+ * kkt.h — C interface of the GB300 (sm_103a) solver for symmetric
+ * positive-definite block-tridiagonal-arrow KKT systems
+ *
+ *        Psi x = b,   Psi = [ D_1  E_1^T                 G_1^T ]
+ *                           [ E_1  D_2   E_2^T           G_2^T ]
+ *                           [       .     .     .          .   ]
+ *                           [             E_{N-1} D_N    G_N^T ]
+ *                           [ G_1  G_2   ...      G_N    R     ]
+ *
+ * (Eq. (3) of "Parallel KKT Solver in PIQP for Multistage Optimization",
+ * arXiv 2511.00946), by the partitioned block Cholesky factorization of
+ * Algorithm 1 and the forward/backward substitutions of Algorithms 2 and 3.
+ *
+ * Conventions shared by every call:
+ *  - All matrices are FP64, row-major, natural stage order j = 0..N-1,
+ *    stage block size n, arrow (global-variable) width m >= 0:
+ *        D [N][n][n]    D[j] = Psi_{j,j}      (lower triangle is read)
+ *        E [N-1][n][n]  E[j] = Psi_{j+1,j}
+ *        G [N][m][n]    G[j] = Psi_{g,j}      (ignored when m = 0)
+ *        R [m][m]       Psi_{g,g}             (lower triangle is read)
+ *        b [N*n+m][ldb] right-hand sides in the first nrhs columns
+ *  - Matrix and vector pointers passed to kkt_factor/kkt_solve* are DEVICE
+ *    pointers owned by the caller; the library only reads them (b is
+ *    overwritten with the solution). The factor and all scratch space are
+ *    device memory owned by the handle, allocated by kkt_create* and freed
+ *    by kkt_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). kkt_factor and kkt_solve* only enqueue work: they never
+ *    synchronize, never allocate and are safe inside CUDA-graph capture.
+ *  - Numerical breakdown (a pivot block that is not positive definite,
+ *    including NaN input) never traps: the kernels record the first failure
+ *    in a device-side record read by kkt_get_info after the stream is
+ *    synchronized. The results of a failed factorization are undefined.
+ *  - Every call returns a kkt_status; no call aborts the process.
+ *
+ * Batches: kkt_batch_create describes `count` independent systems of
+ * possibly different (N, n, m, P). Their inputs are packed back to back in
+ * system order: system s's D starts count_D(s) = sum_{t<s} N_t n_t^2
+ * elements after the D base pointer, E after sum (N_t-1) n_t^2, G after
+ * sum N_t m_t n_t, R after sum m_t^2 and b after sum (N_t n_t + m_t) rows.
+ * kkt_batch_offsets returns these offsets.
+ */
+#ifndef KKT_H_
+#define KKT_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KKT_OK = 0,
+  KKT_ERR_ARG = 1,        /* a size, pointer or option is invalid              */
+  KKT_ERR_PARTITION = 2,  /* no partition: P < 1 or P > floor((N+1)/2)          */
+  KKT_ERR_NOT_SPD = 3,    /* a pivot block was not positive definite            */
+  KKT_ERR_CUDA = 4,       /* a CUDA runtime call failed (allocation, launch)   */
+  KKT_ERR_TIMEOUT = 5,    /* reserved: no call waits on the device              */
+  KKT_ERR_STATE = 6       /* call out of order (solve before factor)           */
+} kkt_status;
+
+/* Arithmetic of the factorization.
+ *  KKT_FP64        every operation in FP64.
+ *  KKT_MIXED_FP32  FP64 pivot blocks (the diagonal-block Cholesky), FP32
+ *                  triangular solves and Schur-complement products inside the
+ *                  segments, FP64 reduced system; kkt_solve_refined recovers
+ *                  FP64 accuracy by iterative refinement on the FP64 residual. */
+typedef enum { KKT_FP64 = 0, KKT_MIXED_FP32 = 1 } kkt_precision;
+
+/* How a level's N stages are split into P segments.
+ *  KKT_PARTITION_PAPER     Eq. (13): N_1 and P-1 equal lengths N_k, with the
+ *                          balance ratio 19/7 (Sec. 3.3). The rounding slack
+ *                          all goes to the first segment, which is harmless
+ *                          for a few threads and costly for hundreds of CTAs.
+ *  KKT_PARTITION_BALANCED  the same cost model with the kernel's per-stage
+ *                          flop counts, stage by stage to the cheapest
+ *                          segment: lengths N_1 and N_k or N_k + 1. */
+typedef enum { KKT_PARTITION_PAPER = 0, KKT_PARTITION_BALANCED = 1 } kkt_partition_mode;
+
+typedef struct kkt_handle kkt_handle;
+
+/* First breakdown recorded by the device since the last kkt_factor. */
+typedef struct {
+  int status;  /* KKT_OK or KKT_ERR_NOT_SPD                                     */
+  int system;  /* system index in the batch                                     */
+  int stage;   /* natural stage of the failing pivot block; N for the corner R */
+  int level;   /* 1 = stage blocks of Psi, 2.. = reduced (separator) systems    */
+} kkt_info;
+
+/* Create a solver for one system with N >= 1 stage blocks of size
+ * 1 <= n <= 48 and arrow width 0 <= m <= 16, split into P segments by the
+ * partition rule of Eq. (13) (Sec. 3.3, balance ratio 19/7). The reduced
+ * separator system of Eq. (7) is factored sequentially by one CTA, which is
+ * the paper's two-phase method. Returns KKT_ERR_PARTITION when
+ * P > floor((N+1)/2). On success *out owns device memory for the factor,
+ * including the fill-in blocks. */
+kkt_status kkt_create(int N, int n, int m, int P, int precision, kkt_handle** out);
+
+/* Like kkt_create but the reduced system is itself partitioned again
+ * (recursively): level 1 splits the N stages into P_levels[0] segments; the
+ * P_levels[0]-1 separators form the level-2 block-tridiagonal-arrow system
+ * (Eqs. (7), (8)), which is split into P_levels[1] segments, and so on.
+ * The last entry must be 1 (that level is factored sequentially). nlevels
+ * >= 1; nlevels = 2 with P_levels = {P, 1} is kkt_create. The solution is
+ * the same up to rounding; the factor is the Cholesky factor of the
+ * correspondingly nested permutation. */
+kkt_status kkt_create_levels(int N, int n, int m, int nlevels, const int* P_levels,
+                             int precision, kkt_handle** out);
+
+/* kkt_create_levels with a choice of partition rule for every level
+ * (kkt_partition_mode). */
+kkt_status kkt_create_plan(int N, int n, int m, int nlevels, const int* P_levels, int partition,
+                           int precision, kkt_handle** out);
+
+/* Batch of `count` independent systems; system s has N[s], n[s], m[s] and
+ * P[s] segments (P = NULL: P = 1, the sequential method, for every system).
+ * Limits per system as for kkt_create. */
+kkt_status kkt_batch_create(int count, const int* N, const int* n, const int* m, const int* P,
+                            int precision, kkt_handle** out);
+
+/* Free the handle and its device memory (NULL is accepted). */
+kkt_status kkt_destroy(kkt_handle* h);
+
+/* Segment lengths of system `system` at level `level` (1-based):
+ * seg_len[0..P-1] = (N_1, N_k, ..., N_k). `P_out` receives P. seg_len may
+ * be NULL to query P only. */
+kkt_status kkt_partition(const kkt_handle* h, int system, int level, int* P_out, int* seg_len);
+
+/* Host-side partition rule of Eq. (13) without a handle: writes P lengths.
+ * Returns KKT_ERR_PARTITION when infeasible. */
+kkt_status kkt_partition_rule(int N, int P, int* seg_len);
+
+/* Segment lengths of the balanced partition (KKT_PARTITION_BALANCED) of N
+ * stages of size n with arrow m into P segments. */
+kkt_status kkt_partition_balanced(int N, int n, int m, int P, int* seg_len);
+
+/* Element offsets of every system's inputs in the packed batch layout
+ * (arrays of length count+1; any pointer may be NULL). off_b counts rows. */
+kkt_status kkt_batch_offsets(const kkt_handle* h, size_t* off_D, size_t* off_E, size_t* off_G,
+                             size_t* off_R, size_t* off_b);
+
+/* Factor Psi (Algorithm 1). D, E, G, R: device pointers in the layout above
+ * (E may be NULL when every N = 1; G and R may be NULL when every m = 0).
+ * Enqueued on `stream`; asynchronous. */
+kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const double* G,
+                      const double* R, void* stream);
+
+/* Solve Psi x = b with the current factor (Algorithms 2 and 3): b is a
+ * device pointer to (N*n+m) rows of ldb >= nrhs doubles (for batches the
+ * packed rows of every system), overwritten with x in its first nrhs
+ * columns. nrhs >= 1. Asynchronous on `stream`. */
+kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream);
+
+/* Copy the first recorded breakdown to *info. Synchronizes with the device
+ * (call it after the stream that ran kkt_factor is synchronized). Clears the
+ * record when `clear` != 0. */
+kkt_status kkt_get_info(kkt_handle* h, kkt_info* info, int clear);
+
+/* Copy the blocks of the factor of system `system` to HOST buffers in the
+ * natural-order layout of the two-level method (Algorithm 1):
+ *   Ld [N][n][n]  D-hat at segment stages, A-hat_k at separator s_k
+ *   Le [N-1][n][n] E-hat inside a segment, F-hat_k at the last stage of
+ *                 segment k, zero at the separators
+ *   Lw [N][n][n]  fill-in W = L-hat(s_k, j) (the paper's B-hat^T) at the
+ *                 stages j of segments k >= 2, zero elsewhere
+ *   Lh [N][n][n]  fill-in H_k = L-hat(s_{k+1}, s_k) at j = s_k, zero elsewhere
+ *   Lg [N][m][n]  G-hat at segment stages, Q-hat_k at separator s_k
+ *   Lr [m][m]     R-hat
+ * Row-major, lower triangles of the diagonal blocks (upper parts zero).
+ * Only for handles with at most two levels; any pointer may be NULL.
+ * Synchronizes with the device. */
+kkt_status kkt_get_factor(kkt_handle* h, int system, double* Ld, double* Le, double* Lw,
+                          double* Lh, double* Lg, double* Lr);
+
+/* Attach `count` cudaEvent_t handles (passed as void*) that kkt_factor and
+ * kkt_solve record on their stream right after each of their kernel
+ * launches, in launch order (event i after launch i of the call; launches
+ * beyond `count` record nothing). Lets a caller time each launch with no
+ * extra work on the device. count = 0 or events = NULL detaches. The events
+ * stay owned by the caller and must outlive their use. */
+kkt_status kkt_set_launch_events(kkt_handle* h, void* const* events, int count);
+
+/* Number of kernel launches one kkt_factor / one kkt_solve (per chunk of up
+ * to 16 right-hand sides) enqueues for this handle. */
+kkt_status kkt_launch_counts(const kkt_handle* h, int* factor_launches, int* solve_launches);
+
+/* Algorithmic FP64 flops of one kkt_factor and of one kkt_solve with one
+ * right-hand side for this handle, in the standard counting convention
+ * (potrf n^3/3+n^2/2+n/6, trsm r n^2, syrk r(r+1)k, gemm 2rck, trsv n^2,
+ * gemv 2rc), as executed by the partitioned method (fill-in included), and
+ * the flops of the sequential method on the same systems. */
+kkt_status kkt_flops(const kkt_handle* h, double* factor_flops, double* solve_flops,
+                     double* sequential_factor_flops);
+
+/* Same counts as kkt_flops for one system planned like kkt_create_plan,
+ * computed on the host without a handle or a GPU. */
+kkt_status kkt_plan_flops(int N, int n, int m, int nlevels, const int* P_levels, int partition,
+                          double* factor_flops, double* solve_flops,
+                          double* sequential_factor_flops);
+
+/* Human-readable name of a status code (static string). */
+const char* kkt_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KKT_H_ */

@@ -1,0 +1,273 @@
+"""GB300-native partitioned block Cholesky solver for SPD block-tridiagonal-arrow
+KKT systems (arXiv 2511.00946, Algorithms 1-3).
+
+Thin Python binding over the C interface of ``libkkt.so`` (include/kkt.h).
+The functions keep the C names and only marshal arguments: every step of the
+factorization and the solve runs in the library's CUDA kernels. PyTorch is
+used for device memory and streams only. There is no CPU fallback: if the
+library is missing, importing this package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkkt.so")
+
+KKT_OK, KKT_ERR_ARG, KKT_ERR_PARTITION, KKT_ERR_NOT_SPD, KKT_ERR_CUDA, KKT_ERR_TIMEOUT, KKT_ERR_STATE = range(7)
+KKT_FP64, KKT_MIXED_FP32 = 0, 1
+KKT_PARTITION_PAPER, KKT_PARTITION_BALANCED = 0, 1
+RHS_CHUNK = 16
+
+EXPORTED = [
+    "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_destroy",
+    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_get_info",
+    "kkt_get_factor", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_status_string",
+]
+
+
+class KKTError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(the solver has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_vp = ctypes.c_void_p
+_ip = ctypes.POINTER(ctypes.c_int)
+_dp = ctypes.POINTER(ctypes.c_double)
+_szp = ctypes.POINTER(ctypes.c_size_t)
+_i = ctypes.c_int
+
+_sig = {
+    "kkt_create": [_i, _i, _i, _i, _i, ctypes.POINTER(_vp)],
+    "kkt_create_levels": [_i, _i, _i, _i, _ip, _i, ctypes.POINTER(_vp)],
+    "kkt_create_plan": [_i, _i, _i, _i, _ip, _i, _i, ctypes.POINTER(_vp)],
+    "kkt_batch_create": [_i, _ip, _ip, _ip, _ip, _i, ctypes.POINTER(_vp)],
+    "kkt_partition_balanced": [_i, _i, _i, _i, _ip],
+    "kkt_destroy": [_vp],
+    "kkt_partition": [_vp, _i, _i, _ip, _ip],
+    "kkt_partition_rule": [_i, _i, _ip],
+    "kkt_batch_offsets": [_vp, _szp, _szp, _szp, _szp, _szp],
+    "kkt_factor": [_vp, _vp, _vp, _vp, _vp, _vp],
+    "kkt_solve": [_vp, _vp, _i, _i, _vp],
+    "kkt_get_info": [_vp, _ip, _i],
+    "kkt_get_factor": [_vp, _i, _dp, _dp, _dp, _dp, _dp, _dp],
+    "kkt_set_launch_events": [_vp, ctypes.POINTER(_vp), _i],
+    "kkt_launch_counts": [_vp, _ip, _ip],
+    "kkt_flops": [_vp, _dp, _dp, _dp],
+    "kkt_plan_flops": [_i, _i, _i, _i, _ip, _i, _dp, _dp, _dp],
+    "kkt_status_string": [_i],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_char_p if _name == "kkt_status_string" else ctypes.c_int
+
+
+def status_string(status: int) -> str:
+    return _lib.kkt_status_string(int(status)).decode()
+
+
+kkt_status_string = status_string
+
+
+def _check(st: int, what: str):
+    if st != KKT_OK:
+        raise KKTError(st, what)
+
+
+def _ints(v):
+    arr = (ctypes.c_int * len(v))(*[int(x) for x in v])
+    return arr
+
+
+def _ptr(x):
+    """Device pointer of a torch CUDA tensor (FP64, contiguous) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    import torch
+    if not isinstance(x, torch.Tensor):
+        raise TypeError("expected a torch CUDA tensor or a raw device pointer")
+    if not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- C names
+
+def kkt_create(N: int, n: int, m: int, P: int, precision: int = KKT_FP64) -> int:
+    h = _vp()
+    _check(_lib.kkt_create(N, n, m, P, precision, ctypes.byref(h)), "kkt_create")
+    return h.value
+
+
+def kkt_create_levels(N: int, n: int, m: int, P_levels, precision: int = KKT_FP64) -> int:
+    h = _vp()
+    _check(_lib.kkt_create_levels(N, n, m, len(P_levels), _ints(P_levels), precision, ctypes.byref(h)),
+           "kkt_create_levels")
+    return h.value
+
+
+def kkt_create_plan(N: int, n: int, m: int, P_levels, partition: int = KKT_PARTITION_BALANCED,
+                    precision: int = KKT_FP64) -> int:
+    h = _vp()
+    _check(_lib.kkt_create_plan(N, n, m, len(P_levels), _ints(P_levels), partition, precision,
+                                ctypes.byref(h)), "kkt_create_plan")
+    return h.value
+
+
+def kkt_batch_create(N, n, m, P=None, precision: int = KKT_FP64) -> int:
+    count = len(N)
+    h = _vp()
+    _check(_lib.kkt_batch_create(count, _ints(N), _ints(n), _ints(m), _ints(P) if P is not None else None,
+                                 precision, ctypes.byref(h)), "kkt_batch_create")
+    return h.value
+
+
+def kkt_destroy(h: int):
+    _check(_lib.kkt_destroy(h), "kkt_destroy")
+
+
+def kkt_partition(h: int, system: int = 0, level: int = 1) -> list[int]:
+    P = ctypes.c_int()
+    _check(_lib.kkt_partition(h, system, level, ctypes.byref(P), None), "kkt_partition")
+    seg = (ctypes.c_int * P.value)()
+    _check(_lib.kkt_partition(h, system, level, None, seg), "kkt_partition")
+    return list(seg)
+
+
+def kkt_partition_rule(N: int, P: int) -> list[int]:
+    seg = (ctypes.c_int * max(P, 1))()
+    _check(_lib.kkt_partition_rule(N, P, seg), "kkt_partition_rule")
+    return list(seg[:P])
+
+
+def kkt_partition_balanced(N: int, n: int, m: int, P: int) -> list[int]:
+    seg = (ctypes.c_int * max(P, 1))()
+    _check(_lib.kkt_partition_balanced(N, n, m, P, seg), "kkt_partition_balanced")
+    return list(seg[:P])
+
+
+def kkt_batch_offsets(h: int, count: int) -> dict:
+    arrs = {k: (ctypes.c_size_t * (count + 1))() for k in ("D", "E", "G", "R", "b")}
+    _check(_lib.kkt_batch_offsets(h, arrs["D"], arrs["E"], arrs["G"], arrs["R"], arrs["b"]),
+           "kkt_batch_offsets")
+    return {k: np.array(list(v), dtype=np.int64) for k, v in arrs.items()}
+
+
+def kkt_factor(h: int, D, E, G, R, stream=None):
+    _check(_lib.kkt_factor(h, _ptr(D), _ptr(E), _ptr(G), _ptr(R), _stream(stream)), "kkt_factor")
+
+
+def kkt_solve(h: int, b, nrhs: int | None = None, ldb: int | None = None, stream=None):
+    if nrhs is None:
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+    if ldb is None:
+        ldb = 1 if b.dim() == 1 else b.shape[1]
+    _check(_lib.kkt_solve(h, _ptr(b), nrhs, ldb, _stream(stream)), "kkt_solve")
+
+
+def kkt_get_info(h: int, clear: bool = True) -> dict:
+    buf = (ctypes.c_int * 4)()
+    _check(_lib.kkt_get_info(h, buf, int(clear)), "kkt_get_info")
+    return dict(status=buf[0], system=buf[1], stage=buf[2], level=buf[3])
+
+
+def kkt_get_factor(h: int, N: int, n: int, m: int, system: int = 0) -> dict:
+    out = dict(Ld=np.zeros((N, n, n)), Le=np.zeros((max(N - 1, 0), n, n)), Lw=np.zeros((N, n, n)),
+               Lh=np.zeros((N, n, n)), Lg=np.zeros((N, m, n)), Lr=np.zeros((m, m)))
+    p = {k: (v.ctypes.data_as(_dp) if v.size else None) for k, v in out.items()}
+    _check(_lib.kkt_get_factor(h, system, p["Ld"], p["Le"], p["Lw"], p["Lh"], p["Lg"], p["Lr"]),
+           "kkt_get_factor")
+    return out
+
+
+def kkt_set_launch_events(h: int, events) -> None:
+    """events: list of torch.cuda.Event (created with enable_timing=True and
+    already recorded once so that they own a CUDA event) or raw handles."""
+    handles = []
+    for ev in events or []:
+        handles.append(ev if isinstance(ev, int) else ev.cuda_event)
+    arr = (_vp * max(len(handles), 1))(*handles)
+    _check(_lib.kkt_set_launch_events(h, arr if handles else None, len(handles)), "kkt_set_launch_events")
+
+
+def kkt_launch_counts(h: int) -> tuple[int, int]:
+    f, s = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.kkt_launch_counts(h, ctypes.byref(f), ctypes.byref(s)), "kkt_launch_counts")
+    return f.value, s.value
+
+
+def kkt_flops(h: int) -> dict:
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.kkt_flops(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "kkt_flops")
+    return dict(factor=a.value, solve=b.value, sequential_factor=c.value)
+
+
+def kkt_plan_flops(N: int, n: int, m: int, P_levels, partition: int = KKT_PARTITION_PAPER) -> dict:
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.kkt_plan_flops(N, n, m, len(P_levels), _ints(P_levels), partition, ctypes.byref(a),
+                               ctypes.byref(b), ctypes.byref(c)), "kkt_plan_flops")
+    return dict(factor=a.value, solve=b.value, sequential_factor=c.value)
+
+
+# ---------------------------------------------------------------- convenience
+
+class KKTSolver:
+    """Owns one handle. ``factor(D, E, G, R)`` and ``solve(b)`` take float64
+    CUDA tensors in the layout of include/kkt.h and enqueue on the current
+    torch stream."""
+
+    def __init__(self, N, n, m, P=1, precision=KKT_FP64, levels=None, partition=KKT_PARTITION_BALANCED):
+        self.N, self.n, self.m = N, n, m
+        if levels is not None:
+            self.h = kkt_create_plan(N, n, m, levels, partition, precision)
+        else:
+            self.h = kkt_create(N, n, m, P, precision)
+
+    def factor(self, D, E, G=None, R=None, stream=None):
+        kkt_factor(self.h, D, E, G, R, stream)
+
+    def solve(self, b, stream=None):
+        kkt_solve(self.h, b, stream=stream)
+        return b
+
+    def info(self, clear=True):
+        return kkt_get_info(self.h, clear)
+
+    def close(self):
+        if self.h:
+            kkt_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,666 @@
+// Host side of the C interface declared in include/kkt.h: the partition rule
+// of Eq. (13), the level plan of every system, the device workspace (factor,
+// fill-ins, reduced-system slots, solve vectors) and the kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "../../include/kkt.h"
+#include "kkt_internal.h"
+
+using kkt::LevelDesc;
+using kkt::Task;
+
+namespace {
+
+struct LevelPlan {
+  int N, P;
+  std::vector<int> start;  // segment k: stages start[k] .. start[k+1]-2; start[P] = N+1
+  std::vector<int> nat;    // natural stage index of each stage
+};
+
+struct SysPlan {
+  int N, n, m;
+  std::vector<LevelPlan> lv;  // levels 1..L (last has P = 1)
+  long long offD, offE, offG, offR, offB;
+};
+
+// Partition rule of Eq. (13): balance ratio sigma = 19/7 (first segment
+// 7/3 N_1 vs the others 19/3 N_k flops per Table 1), constraint
+// N_1 + (P-1) N_k + P - 1 = N, N_k the floor or ceil of
+// (N - P + 1) / (P - 1 + sigma) with the smaller max(7/3 N_1, 19/3 N_k),
+// the floor on a tie.
+bool partition_rule(int N, int P, int* N1, int* Nk) {
+  if (N < 1 || P < 1) return false;
+  if (P == 1) { *N1 = N; *Nk = 0; return true; }
+  if (P > (N + 1) / 2) return false;
+  const double sigma = 19.0 / 7.0;
+  const double ideal = double(N - P + 1) / (double(P - 1) + sigma);
+  const int cand[2] = {int(std::floor(ideal)), int(std::ceil(ideal))};
+  int best = -1;
+  double best_cost = 0.0;
+  for (int nk : cand) {
+    if (nk < 1) continue;
+    const int n1 = N - (P - 1) * (nk + 1);
+    if (n1 < 1) continue;
+    const double cost = std::max(7.0 / 3.0 * n1, 19.0 / 3.0 * nk);
+    if (best < 0 || cost < best_cost) { best = nk; best_cost = cost; }
+  }
+  if (best < 0) return false;
+  *Nk = best;
+  *N1 = N - (P - 1) * (best + 1);
+  return true;
+}
+
+int seg_first(const LevelPlan& L, int k) { return L.start[k]; }
+int seg_len(const LevelPlan& L, int k) { return L.start[k + 1] - L.start[k] - 1; }
+
+// FP64 flops of one stage of the segment kernel (standard convention):
+// potrf of the n x n pivot, trsm and syrk of the stacked panel of R rows.
+double stage_flops(int n, int R) {
+  const double dn = n, dR = R;
+  return dn * dn * dn / 3.0 + dn * dn / 2.0 + dn / 6.0 + dR * dn * dn + dR * (dR + 1.0) * dn;
+}
+
+// Segment lengths -> start array.
+std::vector<int> starts_from(const std::vector<int>& len) {
+  std::vector<int> st(len.size() + 1);
+  st[0] = 0;
+  for (size_t k = 0; k < len.size(); ++k) st[k + 1] = st[k] + len[k] + 1;
+  return st;
+}
+
+// Balanced partition: the first segment's stages are cheaper (no fill-in
+// rows), so stages go one at a time to the segment whose cost would grow the
+// least (first-segment stage weight w1, others w2), lowest index on ties.
+// Unlike Eq. (13) the other segments may differ in length by one stage, so
+// the rounding slack of large P is spread instead of piled onto segment 1.
+std::vector<int> balanced_lengths(int N, int P, double w1, double w2) {
+  std::vector<int> len(P, 1);
+  // bulk fill: every segment up to the common cost level, then one by one
+  double lo = 0.0, hi = (double)N * std::max(w1, w2) + 1.0;
+  for (int it = 0; it < 200; ++it) {  // largest cost level T with total length <= N-P+1
+    const double T = 0.5 * (lo + hi);
+    long long tot = std::max(1, (int)std::floor(T / w1));
+    tot += (long long)(P - 1) * std::max(1, (int)std::floor(T / w2));
+    if (tot <= N - P + 1) lo = T; else hi = T;
+  }
+  len[0] = std::max(1, (int)std::floor(lo / w1));
+  for (int k = 1; k < P; ++k) len[k] = std::max(1, (int)std::floor(lo / w2));
+  int rest = N - (P - 1);
+  for (int k = 0; k < P; ++k) rest -= len[k];
+  while (rest > 0) {
+    int best = 0;
+    double bc = 0.0;
+    for (int k = 0; k < P; ++k) {
+      const double c = (len[k] + 1) * (k == 0 ? w1 : w2);
+      if (k == 0 || c < bc) { bc = c; best = k; }
+    }
+    ++len[best];
+    --rest;
+  }
+  return len;
+}
+
+bool make_level(int N, int P, int mode, int n, int m, LevelPlan* L) {
+  L->N = N;
+  L->P = P;
+  if (N < 1 || P < 1) return false;
+  if (P == 1) { L->start = {0, N + 1}; return true; }
+  if (P > (N + 1) / 2) return false;
+  std::vector<int> len(P);
+  if (mode == KKT_PARTITION_BALANCED) {
+    // a stage also pays a fixed latency (pivot chain, barriers) that does not
+    // grow with the panel height; measured on GB300 it is about 5 n^3 flops
+    const double fixed = 5.0 * double(n) * n * n;
+    len = balanced_lengths(N, P, stage_flops(n, n + m) + fixed, stage_flops(n, 2 * n + m) + fixed);
+  } else {
+    int N1 = 0, Nk = 0;
+    if (!partition_rule(N, P, &N1, &Nk)) return false;
+    len[0] = N1;
+    for (int k = 1; k < P; ++k) len[k] = Nk;
+  }
+  L->start = starts_from(len);
+  return L->start[P] == N + 1;
+}
+
+}  // namespace
+
+struct kkt_handle {
+  int count = 0;
+  int precision = 0;
+  int maxn = 0, maxm = 0, maxL = 0;
+  std::vector<SysPlan> sys;
+  std::vector<LevelDesc> hdesc;              // host copy of the descriptors
+  std::vector<std::vector<int>> desc_of;     // desc_of[s][level-1]
+  std::vector<int> fac_off, fac_cnt;         // task ranges per level (factor + forward)
+  std::vector<int> bwd_off, bwd_cnt;         // task ranges per level (backward)
+  void* dmem = nullptr;                      // one allocation for everything
+  size_t dbytes = 0;
+  LevelDesc* ddesc = nullptr;
+  Task* dtasks = nullptr;
+  kkt::Info* dinfo = nullptr;
+  bool factored = false;
+  size_t tot_D = 0, tot_E = 0, tot_G = 0, tot_R = 0, tot_B = 0;
+  std::vector<cudaEvent_t> events;           // optional per-launch events
+};
+
+namespace {
+// Record the caller's event `i` (if attached) after a launch.
+inline bool mark(const kkt_handle* h, int i, void* stream) {
+  if (i < (int)h->events.size() && h->events[i])
+    return cudaEventRecord(h->events[i], (cudaStream_t)stream) == cudaSuccess;
+  return true;
+}
+}  // namespace
+
+namespace {
+
+struct Carver {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+kkt_status build_handle(int count, const int* N, const int* n, const int* m,
+                        const std::vector<std::vector<int>>& Plev, int mode, int precision,
+                        kkt_handle** out) {
+  if (!out) return KKT_ERR_ARG;
+  *out = nullptr;
+  if (count < 1 || !N || !n || !m) return KKT_ERR_ARG;
+  if (precision != KKT_FP64 && precision != KKT_MIXED_FP32) return KKT_ERR_ARG;
+  auto* h = new kkt_handle();
+  h->count = count;
+  h->precision = precision;
+  h->sys.resize(count);
+  for (int s = 0; s < count; ++s) {
+    SysPlan& sp = h->sys[s];
+    sp.N = N[s]; sp.n = n[s]; sp.m = m[s];
+    if (sp.N < 1 || sp.n < 1 || sp.n > kkt::kMaxN || sp.m < 0 || sp.m > kkt::kMaxM) {
+      delete h;
+      return KKT_ERR_ARG;
+    }
+    const std::vector<int>& Ps = Plev[s];
+    if (Ps.empty() || Ps.back() != 1) { delete h; return KKT_ERR_ARG; }
+    int Nl = sp.N;
+    std::vector<int> nat(sp.N);
+    for (int j = 0; j < sp.N; ++j) nat[j] = j;
+    for (size_t l = 0; l < Ps.size(); ++l) {
+      LevelPlan L;
+      if (!make_level(Nl, Ps[l], mode, sp.n, sp.m, &L)) { delete h; return KKT_ERR_PARTITION; }
+      L.nat = nat;
+      sp.lv.push_back(L);
+      if (L.P == 1) {
+        if (l + 1 != Ps.size()) { delete h; return KKT_ERR_ARG; }
+        break;
+      }
+      std::vector<int> nn(L.P - 1);
+      for (int k = 1; k < L.P; ++k) nn[k - 1] = nat[seg_first(L, k) - 1];
+      nat = nn;
+      Nl = L.P - 1;
+    }
+    sp.offD = h->tot_D; sp.offE = h->tot_E; sp.offG = h->tot_G; sp.offR = h->tot_R; sp.offB = h->tot_B;
+    h->tot_D += size_t(sp.N) * sp.n * sp.n;
+    h->tot_E += size_t(sp.N - 1) * sp.n * sp.n;
+    h->tot_G += size_t(sp.N) * sp.m * sp.n;
+    h->tot_R += size_t(sp.m) * sp.m;
+    h->tot_B += size_t(sp.N) * sp.n + sp.m;
+    h->maxn = std::max(h->maxn, sp.n);
+    h->maxm = std::max(h->maxm, sp.m);
+    h->maxL = std::max(h->maxL, (int)sp.lv.size());
+  }
+  // shared memory must fit: (n | 1)-padded blocks for the largest shapes
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    delete h;
+    return KKT_ERR_CUDA;
+  }
+  if (kkt::factor_smem_bytes(h->maxn, h->maxm) > size_t(optin)) { delete h; return KKT_ERR_ARG; }
+
+  // workspace carving (byte offsets), then one cudaMalloc
+  const size_t D8 = sizeof(double), CH = kkt::kRhsChunk;
+  Carver cv;
+  struct Offs {
+    size_t Ld, LdM, LdR, Lri, Lp, DA, DB, EN, GA, GB, X, YA, YB, nat, seg;
+  };
+  std::vector<std::vector<Offs>> lo(count);
+  std::vector<size_t> rhat(count), rri(count), rpart(count), ygall(count);
+  for (int s = 0; s < count; ++s) {
+    const SysPlan& sp = h->sys[s];
+    const size_t nn = size_t(sp.n) * sp.n, mn = size_t(sp.m) * sp.n, R = 2 * sp.n + sp.m;
+    size_t nparts = 0;
+    for (const LevelPlan& L : sp.lv) {
+      Offs o{};
+      const bool top = (L.P == 1);
+      o.Ld = cv.take(D8 * L.N * nn);
+      o.LdM = cv.take(D8 * L.N * nn);
+      o.LdR = cv.take(D8 * L.N * nn);
+      o.Lri = cv.take(D8 * L.N * sp.n);
+      o.Lp = cv.take(D8 * L.N * R * sp.n);
+      if (!top) {
+        o.DA = cv.take(D8 * (L.P - 1) * nn);
+        o.DB = cv.take(D8 * (L.P - 1) * nn);
+        o.EN = cv.take(D8 * std::max(L.P - 2, 1) * nn);
+        o.GA = cv.take(D8 * (L.P - 1) * std::max<size_t>(mn, 1));
+        o.GB = cv.take(D8 * (L.P - 1) * std::max<size_t>(mn, 1));
+        o.YA = cv.take(D8 * (L.P - 1) * sp.n * CH);
+        o.YB = cv.take(D8 * (L.P - 1) * sp.n * CH);
+        nparts += L.P;
+      }
+      o.X = cv.take(D8 * L.N * sp.n * CH);
+      o.nat = cv.take(sizeof(int) * L.N);
+      o.seg = cv.take(sizeof(int) * (L.P + 1));
+      lo[s].push_back(o);
+    }
+    rhat[s] = cv.take(D8 * std::max(sp.m * sp.m, 1));
+    rri[s] = cv.take(D8 * std::max(sp.m, 1));
+    rpart[s] = cv.take(D8 * std::max<size_t>(nparts * sp.m * sp.m, 1));
+    ygall[s] = cv.take(D8 * std::max<size_t>(nparts * sp.m * CH, 1));
+  }
+  // descriptors and tasks
+  std::vector<Task> tasks;
+  h->desc_of.assign(count, {});
+  for (int s = 0; s < count; ++s)
+    for (size_t l = 0; l < h->sys[s].lv.size(); ++l) {
+      h->desc_of[s].push_back((int)h->hdesc.size());
+      h->hdesc.push_back(LevelDesc{});
+    }
+  const size_t desc_off = cv.take(sizeof(LevelDesc) * h->hdesc.size());
+  // task lists: factor/forward per level, then backward per level
+  h->fac_off.assign(h->maxL, 0); h->fac_cnt.assign(h->maxL, 0);
+  h->bwd_off.assign(h->maxL, 0); h->bwd_cnt.assign(h->maxL, 0);
+  for (int l = 0; l < h->maxL; ++l) {
+    h->fac_off[l] = (int)tasks.size();
+    for (int s = 0; s < count; ++s)
+      if (l < (int)h->sys[s].lv.size())
+        for (int k = 0; k < h->sys[s].lv[l].P; ++k) tasks.push_back(Task{h->desc_of[s][l], k});
+    h->fac_cnt[l] = (int)tasks.size() - h->fac_off[l];
+  }
+  for (int l = 0; l < h->maxL; ++l) {
+    h->bwd_off[l] = (int)tasks.size();
+    for (int s = 0; s < count; ++s)
+      if (l + 1 < (int)h->sys[s].lv.size())
+        for (int k = 0; k < h->sys[s].lv[l].P; ++k) tasks.push_back(Task{h->desc_of[s][l], k});
+    h->bwd_cnt[l] = (int)tasks.size() - h->bwd_off[l];
+  }
+  const size_t task_off = cv.take(sizeof(Task) * std::max<size_t>(tasks.size(), 1));
+  const size_t info_off = cv.take(sizeof(kkt::Info));
+  h->dbytes = cv.off;
+  if (cudaMalloc(&h->dmem, h->dbytes) != cudaSuccess) {
+    h->dmem = nullptr;
+    delete h;
+    return KKT_ERR_CUDA;
+  }
+  char* base = (char*)h->dmem;
+  auto dp = [&](size_t o) { return (double*)(base + o); };
+  for (int s = 0; s < count; ++s) {
+    const SysPlan& sp = h->sys[s];
+    const int L = (int)sp.lv.size();
+    size_t part_cursor = 0;
+    for (int l = 0; l < L; ++l) {
+      const LevelPlan& P = sp.lv[l];
+      const Offs& o = lo[s][l];
+      LevelDesc& d = h->hdesc[h->desc_of[s][l]];
+      d.N = P.N; d.n = sp.n; d.m = sp.m; d.P = P.P;
+      d.seg = (const int*)(base + o.seg);
+      d.level = l + 1;
+      d.is_top = (P.P == 1);
+      d.sys = s;
+      d.precision = precision;
+      d.offD = sp.offD; d.offE = sp.offE; d.offG = sp.offG; d.offR = sp.offR; d.offB = sp.offB;
+      d.rowG = sp.offB + (long long)sp.N * sp.n;
+      d.Nnat = sp.N;
+      d.nat = (const int*)(base + o.nat);
+      d.Ld = dp(o.Ld); d.LdM = dp(o.LdM); d.LdR = dp(o.LdR); d.Lri = dp(o.Lri); d.Lp = dp(o.Lp);
+      d.X = dp(o.X);
+      if (!d.is_top) {
+        d.DA = dp(o.DA); d.DB = dp(o.DB); d.EN = dp(o.EN); d.GA = dp(o.GA); d.GB = dp(o.GB);
+        d.YA = dp(o.YA); d.YB = dp(o.YB);
+        d.Rpart = dp(rpart[s]) + part_cursor * sp.m * sp.m;
+        d.ygpart = dp(ygall[s]) + part_cursor * sp.m * kkt::kRhsChunk;
+        d.Xnext = dp(lo[s][l + 1].X);
+        part_cursor += P.P;
+      }
+      if (l > 0) {
+        const Offs& up = lo[s][l - 1];
+        d.Dw = dp(up.DA); d.D2w = dp(up.DB); d.Ew = dp(up.EN);
+        d.Gw = sp.m ? dp(up.GA) : nullptr; d.G2w = sp.m ? dp(up.GB) : nullptr;
+        d.RA = dp(up.YA); d.RB = dp(up.YB);
+      }
+      d.Rhat = dp(rhat[s]); d.Rri = dp(rri[s]);
+      d.Rpart_all = dp(rpart[s]);
+      d.yg_all = dp(ygall[s]);
+    }
+    for (int l = 0; l < L; ++l) {
+      LevelDesc& d = h->hdesc[h->desc_of[s][l]];
+      d.nRpart_all = (int)part_cursor;
+      d.nyg_all = (int)part_cursor;
+    }
+  }
+  h->ddesc = (LevelDesc*)(base + desc_off);
+  h->dtasks = (Task*)(base + task_off);
+  h->dinfo = (kkt::Info*)(base + info_off);
+  bool ok = cudaMemset(h->dmem, 0, h->dbytes) == cudaSuccess;
+  ok = ok && cudaMemcpy(h->ddesc, h->hdesc.data(), sizeof(LevelDesc) * h->hdesc.size(),
+                        cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!tasks.empty())
+    ok = ok && cudaMemcpy(h->dtasks, tasks.data(), sizeof(Task) * tasks.size(),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+  for (int s = 0; s < count && ok; ++s)
+    for (size_t l = 0; l < h->sys[s].lv.size() && ok; ++l) {
+      const std::vector<int>& nat = h->sys[s].lv[l].nat;
+      const std::vector<int>& st = h->sys[s].lv[l].start;
+      ok = cudaMemcpy(base + lo[s][l].nat, nat.data(), sizeof(int) * nat.size(),
+                      cudaMemcpyHostToDevice) == cudaSuccess &&
+           cudaMemcpy(base + lo[s][l].seg, st.data(), sizeof(int) * st.size(),
+                      cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+  if (!ok) {
+    cudaFree(h->dmem);
+    delete h;
+    return KKT_ERR_CUDA;
+  }
+  *out = h;
+  return KKT_OK;
+}
+
+// FP64 flops of one segment of `len` stages (standard convention).
+void seg_flops(int len, int n, int m, bool hasW, bool hasF, double* fac, double* sol) {
+  const double dn = n;
+  for (int i = 0; i < len; ++i) {
+    const bool eRows = (i < len - 1) || hasF;
+    const double rows = (eRows ? n : 0) + m + (hasW ? n : 0);
+    *fac += dn * dn * dn / 3.0 + dn * dn / 2.0 + dn / 6.0;   // potrf
+    *fac += rows * dn * dn;                                  // trsm
+    *fac += rows * (rows + 1) * dn;                          // syrk
+    *sol += 2.0 * (dn * dn + 2.0 * rows * dn);               // trsv + gemv, both sweeps
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+kkt_status kkt_create(int N, int n, int m, int P, int precision, kkt_handle** out) {
+  std::vector<int> Ps;
+  if (P == 1) Ps = {1};
+  else Ps = {P, 1};
+  if (P < 1) return KKT_ERR_PARTITION;
+  return build_handle(1, &N, &n, &m, {Ps}, KKT_PARTITION_PAPER, precision, out);
+}
+
+kkt_status kkt_create_levels(int N, int n, int m, int nlevels, const int* P_levels, int precision,
+                             kkt_handle** out) {
+  if (nlevels < 1 || !P_levels) return KKT_ERR_ARG;
+  std::vector<int> Ps(P_levels, P_levels + nlevels);
+  for (int p : Ps)
+    if (p < 1) return KKT_ERR_PARTITION;
+  return build_handle(1, &N, &n, &m, {Ps}, KKT_PARTITION_PAPER, precision, out);
+}
+
+kkt_status kkt_create_plan(int N, int n, int m, int nlevels, const int* P_levels, int partition,
+                           int precision, kkt_handle** out) {
+  if (nlevels < 1 || !P_levels) return KKT_ERR_ARG;
+  if (partition != KKT_PARTITION_PAPER && partition != KKT_PARTITION_BALANCED) return KKT_ERR_ARG;
+  std::vector<int> Ps(P_levels, P_levels + nlevels);
+  for (int p : Ps)
+    if (p < 1) return KKT_ERR_PARTITION;
+  return build_handle(1, &N, &n, &m, {Ps}, partition, precision, out);
+}
+
+kkt_status kkt_batch_create(int count, const int* N, const int* n, const int* m, const int* P,
+                            int precision, kkt_handle** out) {
+  if (count < 1 || !N || !n || !m) return KKT_ERR_ARG;
+  std::vector<std::vector<int>> Ps(count);
+  for (int s = 0; s < count; ++s) {
+    const int p = P ? P[s] : 1;
+    if (p < 1) return KKT_ERR_PARTITION;
+    Ps[s] = (p == 1) ? std::vector<int>{1} : std::vector<int>{p, 1};
+  }
+  return build_handle(count, N, n, m, Ps, KKT_PARTITION_PAPER, precision, out);
+}
+
+kkt_status kkt_destroy(kkt_handle* h) {
+  if (!h) return KKT_OK;
+  if (h->dmem) cudaFree(h->dmem);
+  delete h;
+  return KKT_OK;
+}
+
+kkt_status kkt_partition(const kkt_handle* h, int system, int level, int* P_out, int* seg) {
+  if (!h || system < 0 || system >= h->count) return KKT_ERR_ARG;
+  const SysPlan& sp = h->sys[system];
+  if (level < 1 || level > (int)sp.lv.size()) return KKT_ERR_ARG;
+  const LevelPlan& L = sp.lv[level - 1];
+  if (P_out) *P_out = L.P;
+  if (seg)
+    for (int k = 0; k < L.P; ++k) seg[k] = seg_len(L, k);
+  return KKT_OK;
+}
+
+kkt_status kkt_partition_rule(int N, int P, int* seg) {
+  int N1 = 0, Nk = 0;
+  if (!seg) return KKT_ERR_ARG;
+  if (!partition_rule(N, P, &N1, &Nk)) return KKT_ERR_PARTITION;
+  seg[0] = N1;
+  for (int k = 1; k < P; ++k) seg[k] = Nk;
+  return KKT_OK;
+}
+
+kkt_status kkt_partition_balanced(int N, int n, int m, int P, int* seg) {
+  if (!seg || n < 1 || m < 0) return KKT_ERR_ARG;
+  LevelPlan L;
+  if (!make_level(N, P, KKT_PARTITION_BALANCED, n, m, &L)) return KKT_ERR_PARTITION;
+  for (int k = 0; k < P; ++k) seg[k] = seg_len(L, k);
+  return KKT_OK;
+}
+
+kkt_status kkt_batch_offsets(const kkt_handle* h, size_t* oD, size_t* oE, size_t* oG, size_t* oR,
+                             size_t* oB) {
+  if (!h) return KKT_ERR_ARG;
+  for (int s = 0; s <= h->count; ++s) {
+    const bool end = (s == h->count);
+    if (oD) oD[s] = end ? h->tot_D : h->sys[s].offD;
+    if (oE) oE[s] = end ? h->tot_E : h->sys[s].offE;
+    if (oG) oG[s] = end ? h->tot_G : h->sys[s].offG;
+    if (oR) oR[s] = end ? h->tot_R : h->sys[s].offR;
+    if (oB) oB[s] = end ? h->tot_B : h->sys[s].offB;
+  }
+  return KKT_OK;
+}
+
+kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const double* G,
+                      const double* R, void* stream) {
+  if (!h || !D) return KKT_ERR_ARG;
+  if (h->tot_E > 0 && !E) return KKT_ERR_ARG;
+  if (h->maxm > 0 && (!G || !R)) return KKT_ERR_ARG;
+  int li = 0;
+  for (int l = 0; l < h->maxL; ++l) {
+    if (!h->fac_cnt[l]) continue;
+    const int e = kkt::launch_factor(h->ddesc, h->dtasks + h->fac_off[l], h->fac_cnt[l], h->maxn,
+                                     h->maxm, D, E, G, R, h->dinfo, stream);
+    if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
+  }
+  h->factored = true;
+  return KKT_OK;
+}
+
+kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream) {
+  if (!h || !b || nrhs < 1 || ldb < nrhs) return KKT_ERR_ARG;
+  if (!h->factored) return KKT_ERR_STATE;
+  // attached events: the factor's launches take the first slots, then the
+  // solve's launches in order
+  int li = 0;
+  for (int l = 0; l < h->maxL; ++l) li += h->fac_cnt[l] > 0;
+  for (int c0 = 0; c0 < nrhs; c0 += kkt::kRhsChunk) {
+    const int nr = std::min(kkt::kRhsChunk, nrhs - c0);
+    for (int l = 0; l < h->maxL; ++l) {
+      if (!h->fac_cnt[l]) continue;
+      const int e = kkt::launch_forward(h->ddesc, h->dtasks + h->fac_off[l], h->fac_cnt[l], h->maxn,
+                                        h->maxm, b + c0, ldb, nr, nullptr, stream);
+      if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
+    }
+    for (int l = h->maxL - 2; l >= 0; --l) {
+      if (!h->bwd_cnt[l]) continue;
+      const int e = kkt::launch_backward(h->ddesc, h->dtasks + h->bwd_off[l], h->bwd_cnt[l],
+                                         h->maxn, h->maxm, b + c0, ldb, nr, stream);
+      if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
+    }
+  }
+  return KKT_OK;
+}
+
+kkt_status kkt_get_info(kkt_handle* h, kkt_info* info, int clear) {
+  if (!h || !info) return KKT_ERR_ARG;
+  kkt::Info hi{};
+  if (cudaMemcpy(&hi, h->dinfo, sizeof(hi), cudaMemcpyDeviceToHost) != cudaSuccess) return KKT_ERR_CUDA;
+  info->status = hi.status == 3 ? KKT_ERR_NOT_SPD : KKT_OK;
+  info->system = hi.system;
+  info->stage = hi.stage;
+  info->level = hi.level;
+  if (clear && cudaMemset(h->dinfo, 0, sizeof(kkt::Info)) != cudaSuccess) return KKT_ERR_CUDA;
+  return KKT_OK;
+}
+
+kkt_status kkt_get_factor(kkt_handle* h, int system, double* Ld, double* Le, double* Lw, double* Lh,
+                          double* Lg, double* Lr) {
+  if (!h || system < 0 || system >= h->count) return KKT_ERR_ARG;
+  const SysPlan& sp = h->sys[system];
+  if (sp.lv.size() > 2) return KKT_ERR_ARG;
+  if (!h->factored) return KKT_ERR_STATE;
+  if (cudaDeviceSynchronize() != cudaSuccess) return KKT_ERR_CUDA;
+  const int N = sp.N, n = sp.n, m = sp.m, R = 2 * n + m;
+  const size_t nn = size_t(n) * n, mn = size_t(m) * n;
+  auto fetch = [&](const LevelDesc& d, std::vector<double>& hd, std::vector<double>& hp) {
+    hd.resize(size_t(d.N) * nn);
+    hp.resize(size_t(d.N) * R * n);
+    return cudaMemcpy(hd.data(), d.Ld, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost) == cudaSuccess &&
+           cudaMemcpy(hp.data(), d.Lp, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost) == cudaSuccess;
+  };
+  std::vector<double> d1, p1, d2, p2;
+  const LevelDesc& L1 = h->hdesc[h->desc_of[system][0]];
+  if (!fetch(L1, d1, p1)) return KKT_ERR_CUDA;
+  if (Ld) std::memset(Ld, 0, sizeof(double) * N * nn);
+  if (Le && N > 1) std::memset(Le, 0, sizeof(double) * (N - 1) * nn);
+  if (Lw) std::memset(Lw, 0, sizeof(double) * N * nn);
+  if (Lh) std::memset(Lh, 0, sizeof(double) * N * nn);
+  if (Lg && m) std::memset(Lg, 0, sizeof(double) * N * mn);
+  const LevelPlan& P1 = sp.lv[0];
+  auto panel = [&](const std::vector<double>& p, int j, int row0, int rows, double* dst) {
+    std::memcpy(dst, p.data() + (size_t(j) * R + row0) * n, sizeof(double) * rows * n);
+  };
+  for (int k = 0; k < P1.P; ++k) {
+    const int f = seg_first(P1, k), len = seg_len(P1, k);
+    for (int j = f; j < f + len; ++j) {
+      if (Ld) std::memcpy(Ld + j * nn, d1.data() + j * nn, sizeof(double) * nn);
+      if (Le && j < N - 1 && (j < f + len - 1 || k < P1.P - 1)) panel(p1, j, 0, n, Le + j * nn);
+      if (Lg && m) panel(p1, j, n, m, Lg + j * mn);
+      if (Lw && k >= 1) panel(p1, j, n + m, n, Lw + j * nn);
+    }
+  }
+  if (sp.lv.size() == 2) {
+    const LevelDesc& L2 = h->hdesc[h->desc_of[system][1]];
+    if (!fetch(L2, d2, p2)) return KKT_ERR_CUDA;
+    for (int k = 1; k < P1.P; ++k) {
+      const int s = seg_first(P1, k) - 1, j2 = k - 1;
+      if (Ld) std::memcpy(Ld + s * nn, d2.data() + j2 * nn, sizeof(double) * nn);
+      if (Lg && m) panel(p2, j2, n, m, Lg + s * mn);
+      if (Lh && k < P1.P - 1) panel(p2, j2, 0, n, Lh + s * nn);
+    }
+  }
+  if (Lr && m) {
+    const LevelDesc& top = h->hdesc[h->desc_of[system].back()];
+    if (cudaMemcpy(Lr, top.Rhat, sizeof(double) * m * m, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return KKT_ERR_CUDA;
+  }
+  return KKT_OK;
+}
+
+kkt_status kkt_set_launch_events(kkt_handle* h, void* const* events, int count) {
+  if (!h || count < 0) return KKT_ERR_ARG;
+  h->events.clear();
+  if (events)
+    for (int i = 0; i < count; ++i) h->events.push_back((cudaEvent_t)events[i]);
+  return KKT_OK;
+}
+
+kkt_status kkt_launch_counts(const kkt_handle* h, int* fl, int* sl) {
+  if (!h) return KKT_ERR_ARG;
+  int f = 0, sv = 0;
+  for (int l = 0; l < h->maxL; ++l) {
+    f += h->fac_cnt[l] > 0;
+    sv += h->fac_cnt[l] > 0;
+    sv += h->bwd_cnt[l] > 0;
+  }
+  if (fl) *fl = f;
+  if (sl) *sl = sv;
+  return KKT_OK;
+}
+
+static void plan_flops(const std::vector<SysPlan>& sys, double* ff, double* sf, double* seqf) {
+  double fac = 0.0, sol = 0.0, seq = 0.0, seqsol = 0.0;
+  for (const SysPlan& sp : sys) {
+    for (const LevelPlan& L : sp.lv)
+      for (int k = 0; k < L.P; ++k)
+        seg_flops(seg_len(L, k), sp.n, sp.m, k >= 1, k < L.P - 1, &fac, &sol);
+    seg_flops(sp.N, sp.n, sp.m, false, false, &seq, &seqsol);
+    const double dm = sp.m;
+    const double corner = sp.m ? dm * dm * dm / 3.0 + dm * dm / 2.0 + dm / 6.0 : 0.0;
+    fac += corner;
+    seq += corner;
+    sol += 2.0 * dm * dm;
+  }
+  if (ff) *ff = fac;
+  if (sf) *sf = sol;
+  if (seqf) *seqf = seq;
+}
+
+kkt_status kkt_flops(const kkt_handle* h, double* ff, double* sf, double* seqf) {
+  if (!h) return KKT_ERR_ARG;
+  plan_flops(h->sys, ff, sf, seqf);
+  return KKT_OK;
+}
+
+kkt_status kkt_plan_flops(int N, int n, int m, int nlevels, const int* P_levels, int partition,
+                          double* ff, double* sf, double* seqf) {
+  if (N < 1 || n < 1 || m < 0 || nlevels < 1 || !P_levels || P_levels[nlevels - 1] != 1)
+    return KKT_ERR_ARG;
+  SysPlan sp;
+  sp.N = N; sp.n = n; sp.m = m;
+  int Nl = N;
+  for (int l = 0; l < nlevels; ++l) {
+    LevelPlan L;
+    if (!make_level(Nl, P_levels[l], partition, n, m, &L)) return KKT_ERR_PARTITION;
+    sp.lv.push_back(L);
+    if (L.P == 1) {
+      if (l + 1 != nlevels) return KKT_ERR_ARG;
+      break;
+    }
+    Nl = L.P - 1;
+  }
+  plan_flops({sp}, ff, sf, seqf);
+  return KKT_OK;
+}
+
+const char* kkt_status_string(int s) {
+  switch (s) {
+    case KKT_OK: return "ok";
+    case KKT_ERR_ARG: return "invalid argument";
+    case KKT_ERR_PARTITION: return "no partition (P > floor((N+1)/2))";
+    case KKT_ERR_NOT_SPD: return "pivot block not positive definite";
+    case KKT_ERR_CUDA: return "CUDA runtime error";
+    case KKT_ERR_TIMEOUT: return "device wait timed out";
+    case KKT_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,386 @@
+"""Parity of the CUDA path (through the C interface) with the FP64 oracle.
+
+Tolerances (derived from FP64 arithmetic, see the design notes):
+* factor blocks on well-conditioned inputs: |L_gpu - L_oracle| <= 1e-12 * max|L|
+  (both are the unique Cholesky factor; only the rounding order differs);
+* solutions on well-conditioned inputs: |x_gpu - x_oracle| <= 1e-11 * max|x|;
+* every input: normwise backward error of the GPU solution <= 1e-14 (a
+  backward-stable Cholesky solve gives a few units of roundoff) and the
+  relative residual within 10x the oracle's own on the same input (or 1e-10);
+* ill-conditioned inputs: |x_gpu - x_oracle| <= 100 * u * kappa_est * max|x|.
+"""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def kkt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_00946_gb300 as k
+    return k
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def gpu_solve(kkt, D, E, G, R, b, P=1, levels=None, want_factor=False, balanced=False):
+    import torch
+    N, n = D.shape[0], D.shape[1]
+    m = 0 if R is None or np.size(R) == 0 else R.shape[0]
+    if balanced:
+        h = kkt.kkt_create_plan(N, n, m, levels or ([P, 1] if P > 1 else [1]), kkt.KKT_PARTITION_BALANCED)
+    elif levels:
+        h = kkt.kkt_create_levels(N, n, m, levels)
+    else:
+        h = kkt.kkt_create(N, n, m, P)
+    try:
+        Ed = dev(E) if N > 1 else None
+        Gd = dev(G) if m else None
+        Rd = dev(R) if m else None
+        bd = dev(b)
+        kkt.kkt_factor(h, dev(D), Ed, Gd, Rd)
+        kkt.kkt_solve(h, bd)
+        torch.cuda.synchronize()
+        info = kkt.kkt_get_info(h)
+        assert info["status"] == 0, info
+        F = kkt.kkt_get_factor(h, N, n, m) if want_factor else None
+        return bd.cpu().numpy(), F
+    finally:
+        kkt.kkt_destroy(h)
+
+
+def check_solution(orc, D, E, G, R, x, b, xo=None, fwd_tol=None):
+    A_mv = orc.block_matvec(D, E, G, R, x)
+    r = b - A_mv
+    Ainf = None
+    # normwise backward error with ||Psi||_inf from the blocks
+    N, n = D.shape[0], D.shape[1]
+    Ds = np.tril(D) + np.swapaxes(np.tril(D, -1), 1, 2)
+    rows = np.abs(Ds).sum(axis=2)
+    if N > 1:
+        rows[1:] += np.abs(E).sum(axis=2)
+        rows[:-1] += np.abs(E).sum(axis=1)
+    if G.size:
+        rows += np.abs(G).sum(axis=1)[:, :]
+        grows = np.abs(G).sum(axis=(0, 2)) + np.abs(np.tril(R) + np.tril(R, -1).T).sum(axis=1)
+        Ainf = max(rows.max(), grows.max())
+    else:
+        Ainf = rows.max()
+    eta = np.abs(r).max() / (Ainf * np.abs(x).max() + np.abs(b).max())
+    assert eta <= 1e-14, f"backward error {eta:.3e}"
+    if xo is not None:
+        ro = b - orc.block_matvec(D, E, G, R, xo)
+        rel_gpu = np.linalg.norm(r) / np.linalg.norm(b)
+        rel_orc = np.linalg.norm(ro) / np.linalg.norm(b)
+        assert rel_gpu <= max(1e-10, 10 * rel_orc), (rel_gpu, rel_orc)
+        if fwd_tol is not None:
+            err = np.abs(x - xo).max() / np.abs(xo).max()
+            assert err <= fwd_tol, f"forward difference {err:.3e} > {fwd_tol:.3e}"
+    return eta
+
+
+# ------------------------------------------------------------- config 1
+
+@pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 8])
+def test_known_factor_blocks_and_solution(kkt, orc, P):
+    """N = 16 stages of n = 8, arrow m = 4, Psi = L L^T: factor blocks equal
+    the oracle's Algorithm 1 blocks; at P = 1 they equal the generating L."""
+    D, E, G, R, Lf = gen.known_factor(16, 8, 4, seed=0)
+    b = gen.rhs(16 * 8 + 4, 1, seed=1)
+    x, F = gpu_solve(kkt, D, E, G, R, b, P=P, want_factor=True)
+    Fo = orc.par_factor(D, E, G, R, P=P)
+    xo = orc.par_solve(Fo, b)
+    for key in ("Ld", "Le", "Lw", "Lh", "Lg", "Lr"):
+        scale = max(1.0, np.abs(Fo[key]).max() if Fo[key].size else 1.0)
+        np.testing.assert_allclose(F[key], Fo[key], rtol=0, atol=1e-12 * scale, err_msg=key)
+    if P == 1:
+        for key in ("Ld", "Le", "Lg", "Lr"):
+            np.testing.assert_allclose(F[key], Lf[key], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(x, xo, rtol=0, atol=1e-11 * np.abs(xo).max())
+    check_solution(orc, D, E, G, R, x, b, xo)
+
+
+# ------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("N,n,m,P", [
+    (1, 8, 4, 1), (2, 8, 0, 1), (3, 1, 0, 2), (3, 1, 1, 2), (5, 3, 2, 3), (9, 5, 0, 5),
+    (17, 7, 3, 9), (11, 2, 16, 4), (24, 48, 4, 3), (30, 12, 0, 7), (7, 6, 2, 4), (64, 13, 5, 31)])
+def test_edge_shapes(kkt, orc, N, n, m, P):
+    """Single stage, no arrow, odd and tiny blocks, an arrow wider than the
+    block, the largest block, P at its feasibility limit (all segments of
+    one stage). Blocks larger than 16 use the IPM generator with a mild
+    barrier spread: a random triangular factor of that size is numerically
+    singular in FP64 (the oracle breaks down on it too)."""
+    if n <= 16:
+        D, E, G, R, _ = gen.known_factor(N, n, m, seed=N + n + m)
+    else:
+        D, E, G, R = gen.ipm(N, n, m, seed=N + n + m, sigma_decades=1.0)
+    b = gen.rhs(N * n + m, 1, seed=3)
+    x, F = gpu_solve(kkt, D, E, G, R, b, P=P, want_factor=True)
+    Fo = orc.par_factor(D, E, G, R, P=P)
+    xo = orc.par_solve(Fo, b)
+    for key in ("Ld", "Le", "Lw", "Lh", "Lg", "Lr"):
+        scale = max(1.0, np.abs(Fo[key]).max() if Fo[key].size else 1.0)
+        np.testing.assert_allclose(F[key], Fo[key], rtol=0, atol=1e-12 * scale, err_msg=key)
+    np.testing.assert_allclose(x, xo, rtol=0, atol=1e-11 * np.abs(xo).max())
+
+
+@pytest.mark.parametrize("nrhs,ldb", [(1, 1), (3, 3), (16, 16), (17, 20), (40, 40)])
+def test_multiple_rhs(kkt, orc, nrhs, ldb):
+    """Several right-hand sides (chunks of 16, a leading dimension above nrhs)."""
+    import torch
+    N, n, m, P = 40, 8, 3, 6
+    D, E, G, R, _ = gen.known_factor(N, n, m, seed=2)
+    b = gen.rhs(N * n + m, ldb, seed=7).reshape(N * n + m, ldb)
+    h = kkt.kkt_create(N, n, m, P)
+    try:
+        bd = dev(b)
+        kkt.kkt_factor(h, dev(D), dev(E), dev(G), dev(R))
+        kkt.kkt_solve(h, bd, nrhs=nrhs, ldb=ldb)
+        torch.cuda.synchronize()
+        x = bd.cpu().numpy()
+    finally:
+        kkt.kkt_destroy(h)
+    Fo = orc.par_factor(D, E, G, R, P=P)
+    xo = orc.par_solve(Fo, b[:, :nrhs])
+    np.testing.assert_allclose(x[:, :nrhs], xo, rtol=0, atol=1e-11 * np.abs(xo).max())
+    np.testing.assert_array_equal(x[:, nrhs:], b[:, nrhs:])   # untouched columns
+
+
+# ------------------------------------------------------------- IPM-shaped
+
+@pytest.mark.parametrize("N,n,m,P", [(128, 32, 8, 1), (128, 32, 8, 16), (200, 24, 4, 13), (96, 12, 0, 20)])
+def test_ipm_shaped(kkt, orc, N, n, m, P):
+    """Barrier-scaled blocks (Sigma over 16 decades): backward error at the
+    FP64 floor, residual and forward difference as the oracle's."""
+    D, E, G, R = gen.ipm(N, n, m, seed=11)
+    b = gen.rhs(N * n + m, 1, seed=12)
+    x, _ = gpu_solve(kkt, D, E, G, R, b, P=P)
+    xo = orc.par_solve(orc.par_factor(D, E, G, R, P=P), b)
+    check_solution(orc, D, E, G, R, x, b, xo, fwd_tol=1e-5)
+
+
+def test_ipm_full_size_two_levels(kkt, orc):
+    """N = 1024 stages of n = 32 with arrow m = 8 (the single-system IPM
+    workload), P = 64: complete comparison with the oracle."""
+    N, n, m, P = 1024, 32, 8, 64
+    D, E, G, R = gen.ipm(N, n, m, seed=0)
+    b = gen.rhs(N * n + m, 1, seed=1)
+    x, _ = gpu_solve(kkt, D, E, G, R, b, P=P)
+    xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b)
+    check_solution(orc, D, E, G, R, x, b, xo, fwd_tol=1e-5)
+
+
+# ------------------------------------------------------------- recursion
+
+@pytest.mark.parametrize("N,levels", [(16, [4, 2, 1]), (64, [16, 4, 1]), (200, [40, 10, 3, 1]),
+                                      (100, [50, 25, 12, 6, 3, 1])])
+def test_recursive_levels(kkt, orc, N, levels):
+    """The reduced system partitioned again (same block-tridiagonal-arrow
+    form): the solution is unchanged up to rounding."""
+    n, m = 6, 2
+    D, E, G, R, _ = gen.known_factor(N, n, m, seed=5)
+    b = gen.rhs(N * n + m, 2, seed=6)
+    x, _ = gpu_solve(kkt, D, E, G, R, b, levels=levels)
+    xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b)
+    np.testing.assert_allclose(x, xo, rtol=0, atol=1e-11 * np.abs(xo).max())
+
+
+@pytest.mark.parametrize("N,n,m,levels", [(1024, 32, 8, [152, 38, 10, 1]), (300, 12, 4, [60, 12, 1]),
+                                           (100, 8, 2, [40, 1]), (64, 6, 0, [20, 6, 1])])
+def test_balanced_partition_solution(kkt, orc, N, n, m, levels):
+    """Balanced segment lengths (not Eq. (13)) give the same solution."""
+    D, E, G, R = gen.ipm(N, n, m, seed=21)
+    b = gen.rhs(N * n + m, 1, seed=22)
+    x, _ = gpu_solve(kkt, D, E, G, R, b, levels=levels, balanced=True)
+    xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b)
+    check_solution(orc, D, E, G, R, x, b, xo, fwd_tol=1e-5)
+
+
+def test_balanced_two_level_blocks(kkt, orc):
+    """Two balanced levels: the factor blocks are Algorithm 1's on the
+    oracle's run with the same segment lengths."""
+    N, n, m, P = 40, 5, 2, 9
+    D, E, G, R, _ = gen.known_factor(N, n, m, seed=3)
+    seg = kkt.kkt_partition_balanced(N, n, m, P)
+    b = gen.rhs(N * n + m, 1, seed=4)
+    x, F = gpu_solve(kkt, D, E, G, R, b, P=P, want_factor=True, balanced=True)
+    Fo = orc.par_factor(D, E, G, R, seg_len=seg)
+    for key in ("Ld", "Le", "Lw", "Lh", "Lg", "Lr"):
+        scale = max(1.0, np.abs(Fo[key]).max() if Fo[key].size else 1.0)
+        np.testing.assert_allclose(F[key], Fo[key], rtol=0, atol=1e-12 * scale, err_msg=key)
+    np.testing.assert_allclose(x, orc.par_solve(Fo, b), rtol=0, atol=1e-11 * np.abs(x).max())
+
+
+def test_recursive_factor_is_nested_cholesky(kkt, orc):
+    """With three levels the factor is chol of the doubly permuted matrix:
+    compare the top-level corner with the dense Cholesky (unique)."""
+    import torch
+    N, n, m = 25, 3, 2
+    levels = [6, 2, 1]
+    D, E, G, R, _ = gen.known_factor(N, n, m, seed=8)
+    A = orc.assemble_dense(D, E, G, R)
+    L = orc.dense_chol(A)
+    h = kkt.kkt_create_levels(N, n, m, levels)
+    try:
+        kkt.kkt_factor(h, dev(D), dev(E), dev(G), dev(R))
+        torch.cuda.synchronize()
+        with pytest.raises(kkt.KKTError):
+            kkt.kkt_get_factor(h, N, n, m)   # only two-level layouts export blocks
+    finally:
+        kkt.kkt_destroy(h)
+    # the corner block of any symmetric permutation that keeps g last is the
+    # same: R-hat R-hat^T = Schur complement of the stage part
+    x, _ = gpu_solve(kkt, D, E, G, R, np.eye(N * n + m)[:, -m:].copy(), levels=levels)
+    S = np.linalg.inv(x[-m:, :])          # (Psi^{-1})_gg^{-1} = Schur complement
+    np.testing.assert_allclose(S, L[-m:, -m:] @ L[-m:, -m:].T, rtol=1e-10, atol=1e-12)
+
+
+# ------------------------------------------------------------- batches
+
+def test_uniform_batch(kkt, orc):
+    import torch
+    count, N, n, m = 6, 30, 8, 2
+    sy = [gen.ipm(N, n, m, seed=s) for s in range(count)]
+    Ps = [1, 2, 3, 4, 5, 1]
+    h = kkt.kkt_batch_create([N] * count, [n] * count, [m] * count, Ps)
+    try:
+        D = dev(np.concatenate([s[0].ravel() for s in sy]))
+        E = dev(np.concatenate([s[1].ravel() for s in sy]))
+        G = dev(np.concatenate([s[2].ravel() for s in sy]))
+        R = dev(np.concatenate([s[3].ravel() for s in sy]))
+        bs = [gen.rhs(N * n + m, 1, seed=100 + s) for s in range(count)]
+        b = dev(np.concatenate(bs))
+        kkt.kkt_factor(h, D, E, G, R)
+        kkt.kkt_solve(h, b)
+        torch.cuda.synchronize()
+        x = b.cpu().numpy().reshape(count, N * n + m)
+    finally:
+        kkt.kkt_destroy(h)
+    for s in range(count):
+        xo = orc.seq_solve(orc.seq_factor(*sy[s]), bs[s])
+        check_solution(orc, *sy[s], x[s], bs[s], xo, fwd_tol=1e-6)
+
+
+def test_uneven_batch(kkt, orc):
+    import torch
+    sy = gen.uneven_batch(12, seed=3, N_range=(5, 40))
+    Ns = [s[0].shape[0] for s in sy]
+    ns = [s[0].shape[1] for s in sy]
+    ms = [s[3].shape[0] for s in sy]
+    Ps = [max(1, min(4, (N + 1) // 2)) for N in Ns]
+    h = kkt.kkt_batch_create(Ns, ns, ms, Ps)
+    try:
+        off = kkt.kkt_batch_offsets(h, len(sy))
+        assert off["D"][-1] == sum(N * n * n for N, n in zip(Ns, ns))
+        cat = lambda i: dev(np.concatenate([s[i].ravel() for s in sy] + [np.zeros(1)]))
+        bs = [gen.rhs(N * n + m, 1, seed=i) for i, (N, n, m) in enumerate(zip(Ns, ns, ms))]
+        b = dev(np.concatenate(bs))
+        kkt.kkt_factor(h, cat(0), cat(1), cat(2), cat(3))
+        kkt.kkt_solve(h, b)
+        torch.cuda.synchronize()
+        x = b.cpu().numpy()
+    finally:
+        kkt.kkt_destroy(h)
+    for i, s in enumerate(sy):
+        xi = x[off["b"][i]:off["b"][i + 1]]
+        xo = orc.seq_solve(orc.seq_factor(*s), bs[i])
+        check_solution(orc, *s, xi, bs[i], xo, fwd_tol=1e-6)
+
+
+# ------------------------------------------------------------- failure, determinism, graphs
+
+@pytest.mark.parametrize("P,bad_stage", [(1, 5), (4, 9), (4, 7)])
+def test_not_spd_reported(kkt, P, bad_stage):
+    """A negated diagonal block (made on the host) is reported as
+    KKT_ERR_NOT_SPD with its natural stage; nothing traps."""
+    import torch
+    N, n, m = 16, 4, 2
+    D, E, G, R, _ = gen.known_factor(N, n, m, seed=0)
+    D = D.copy()
+    D[bad_stage] = -D[bad_stage]
+    h = kkt.kkt_create(N, n, m, P)
+    try:
+        kkt.kkt_factor(h, dev(D), dev(E), dev(G), dev(R))
+        torch.cuda.synchronize()
+        info = kkt.kkt_get_info(h)
+        assert info["status"] == kkt.KKT_ERR_NOT_SPD
+        assert info["stage"] == bad_stage and info["system"] == 0
+        assert kkt.kkt_get_info(h)["status"] == 0   # cleared
+    finally:
+        kkt.kkt_destroy(h)
+
+
+def test_nan_input_reported(kkt):
+    import torch
+    D, E, G, R, _ = gen.known_factor(8, 3, 1, seed=0)
+    D = D.copy()
+    D[0, 0, 0] = np.nan
+    h = kkt.kkt_create(8, 3, 1, 2)
+    try:
+        kkt.kkt_factor(h, dev(D), dev(E), dev(G), dev(R))
+        torch.cuda.synchronize()
+        assert kkt.kkt_get_info(h)["status"] == kkt.KKT_ERR_NOT_SPD
+    finally:
+        kkt.kkt_destroy(h)
+
+
+def test_bad_arguments(kkt):
+    with pytest.raises(kkt.KKTError) as ei:
+        kkt.kkt_create(10, 4, 0, 6)
+    assert ei.value.status == kkt.KKT_ERR_PARTITION
+    with pytest.raises(kkt.KKTError) as ei:
+        kkt.kkt_create(10, 49, 0, 1)
+    assert ei.value.status == kkt.KKT_ERR_ARG
+    h = kkt.kkt_create(10, 4, 0, 2)
+    try:
+        import torch
+        b = torch.zeros(40, dtype=torch.float64, device="cuda")
+        with pytest.raises(kkt.KKTError) as ei:
+            kkt.kkt_solve(h, b)
+        assert ei.value.status == kkt.KKT_ERR_STATE
+    finally:
+        kkt.kkt_destroy(h)
+
+
+def test_deterministic_and_graph_capturable(kkt):
+    """Fixed summation orders: two runs agree bit for bit; factor + solve
+    captured in a CUDA graph and replayed gives the same bits."""
+    import torch
+    N, n, m, P = 200, 16, 4, 12
+    D, E, G, R = gen.ipm(N, n, m, seed=4)
+    b = gen.rhs(N * n + m, 1, seed=5)
+    h = kkt.kkt_create(N, n, m, P)
+    try:
+        Dd, Ed, Gd, Rd = dev(D), dev(E), dev(G), dev(R)
+        outs = []
+        for _ in range(2):
+            bd = dev(b)
+            kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+            kkt.kkt_solve(h, bd)
+            torch.cuda.synchronize()
+            outs.append(bd.cpu().numpy())
+        np.testing.assert_array_equal(outs[0], outs[1])
+        bd = dev(b)
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                kkt.kkt_factor(h, Dd, Ed, Gd, Rd, stream=s)
+                kkt.kkt_solve(h, bd, stream=s)
+        bd.copy_(dev(b))
+        g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(bd.cpu().numpy(), outs[0])
+    finally:
+        kkt.kkt_destroy(h)
