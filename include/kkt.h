@@ -57,7 +57,8 @@ typedef enum {
   KKT_ERR_NOT_SPD = 3,    /* a pivot block was not positive definite            */
   KKT_ERR_CUDA = 4,       /* a CUDA runtime call failed (allocation, launch)   */
   KKT_ERR_TIMEOUT = 5,    /* reserved: no call waits on the device              */
-  KKT_ERR_STATE = 6       /* call out of order (solve before factor)           */
+  KKT_ERR_STATE = 6,      /* call out of order (solve before factor)           */
+  KKT_ERR_CAPACITY = 7    /* problem larger than a fixed-size buffer allows     */
 } kkt_status;
 
 /* Arithmetic of the factorization.
@@ -198,6 +199,37 @@ kkt_status kkt_flops(const kkt_handle* h, double* factor_flops, double* solve_fl
 kkt_status kkt_plan_flops(int N, int n, int m, int nlevels, const int* P_levels, int partition,
                           double* factor_flops, double* solve_flops,
                           double* sequential_factor_flops);
+
+/* Factor and solve ONE system without allocating any memory (the paper has
+ * no counterpart: this serves callers that cannot allocate device memory
+ * where they solve, e.g. code inside a CUDA-graph capture region or a
+ * real-time loop that must not touch an allocator, or a plugin whose host
+ * owns all allocations). Same method as kkt_create(N, n, m, P, KKT_FP64)
+ * followed by kkt_factor and kkt_solve, with the same results.
+ *  - D, E, G, R, b: device pointers as for kkt_factor / kkt_solve; b is
+ *    overwritten with the solution. `info`: optional device pointer to 4
+ *    ints that receive the kkt_info record of a breakdown (zeroed first by
+ *    this call; status KKT_ERR_NOT_SPD = 3 on breakdown), NULL to skip.
+ *  - The factor and every scratch table live in one library-owned,
+ *    statically sized device array of 16 MiB that each GPU loading the
+ *    library holds until the process exits. A shape whose factor and tables
+ *    need more (roughly 6 n^2 + 2 m n doubles per stage; for example
+ *    N = 256, n = 32, m = 8 fits, N = 1024, n = 32 does not), or N > 16384
+ *    or P > 1024, returns KKT_ERR_CAPACITY before any work is enqueued.
+ *  - The first call on a device (with that device current) looks up the
+ *    array's device address with cudaGetSymbolAddress; make that first call
+ *    before any stream capture. Each call copies a few small tables from
+ *    host memory with cudaMemcpyAsync (pageable, so it synchronizes with
+ *    `stream` first) and clears the breakdown record with cudaMemsetAsync.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind. Calls whose work overlaps on the GPU (other streams, other
+ *    host threads, other processes' contexts excluded) race on it and give
+ *    undefined results: serialize them, e.g. on one stream.
+ * Returns KKT_ERR_ARG for invalid sizes or pointers, KKT_ERR_PARTITION when
+ * P > floor((N+1)/2). */
+kkt_status kkt_solve_noalloc(int N, int n, int m, int P, const double* D, const double* E,
+                             const double* G, const double* R, double* b, int nrhs, int ldb,
+                             int* info, void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* kkt_status_string(int status);

@@ -17,7 +17,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libkkt.so")
 
-KKT_OK, KKT_ERR_ARG, KKT_ERR_PARTITION, KKT_ERR_NOT_SPD, KKT_ERR_CUDA, KKT_ERR_TIMEOUT, KKT_ERR_STATE = range(7)
+(KKT_OK, KKT_ERR_ARG, KKT_ERR_PARTITION, KKT_ERR_NOT_SPD, KKT_ERR_CUDA, KKT_ERR_TIMEOUT, KKT_ERR_STATE,
+ KKT_ERR_CAPACITY) = range(8)
 KKT_FP64, KKT_MIXED_FP32 = 0, 1
 KKT_PARTITION_PAPER, KKT_PARTITION_BALANCED = 0, 1
 RHS_CHUNK = 16
@@ -25,7 +26,7 @@ RHS_CHUNK = 16
 EXPORTED = [
     "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_destroy",
     "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_get_info",
-    "kkt_get_factor", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_status_string",
+    "kkt_get_factor", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
 ]
 
 
@@ -65,6 +66,7 @@ _sig = {
     "kkt_launch_counts": [_vp, _ip, _ip],
     "kkt_flops": [_vp, _dp, _dp, _dp],
     "kkt_plan_flops": [_i, _i, _i, _i, _ip, _i, _dp, _dp, _dp],
+    "kkt_solve_noalloc": [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp, _vp],
     "kkt_status_string": [_i],
 }
 for _name, _args in _sig.items():
@@ -229,6 +231,24 @@ def kkt_plan_flops(N: int, n: int, m: int, P_levels, partition: int = KKT_PARTIT
     _check(_lib.kkt_plan_flops(N, n, m, len(P_levels), _ints(P_levels), partition, ctypes.byref(a),
                                ctypes.byref(b), ctypes.byref(c)), "kkt_plan_flops")
     return dict(factor=a.value, solve=b.value, sequential_factor=c.value)
+
+
+def kkt_solve_noalloc(N: int, n: int, m: int, P: int, D, E, G, R, b, nrhs: int | None = None,
+                      ldb: int | None = None, info=None, stream=None):
+    """Factor and solve one system in the library's fixed device buffer (no
+    allocation; see include/kkt.h). `info`: optional int32 CUDA tensor of 4."""
+    if nrhs is None:
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+    if ldb is None:
+        ldb = 1 if b.dim() == 1 else b.shape[1]
+    ip = None
+    if info is not None:
+        import torch
+        if not (info.is_cuda and info.dtype == torch.int32 and info.numel() >= 4):
+            raise TypeError("info must be an int32 CUDA tensor of 4 elements")
+        ip = info.data_ptr()
+    _check(_lib.kkt_solve_noalloc(N, n, m, P, _ptr(D), _ptr(E), _ptr(G), _ptr(R), _ptr(b), nrhs, ldb, ip,
+                                  _stream(stream)), "kkt_solve_noalloc")
 
 
 # ---------------------------------------------------------------- convenience

@@ -659,6 +659,7 @@ const char* kkt_status_string(int s) {
     case KKT_ERR_CUDA: return "CUDA runtime error";
     case KKT_ERR_TIMEOUT: return "device wait timed out";
     case KKT_ERR_STATE: return "call out of order";
+    case KKT_ERR_CAPACITY: return "problem exceeds the fixed buffer capacity";
     default: return "unknown status";
   }
 }
