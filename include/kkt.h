@@ -62,12 +62,18 @@ typedef enum {
 } kkt_status;
 
 /* Arithmetic of the factorization.
- *  KKT_FP64        every operation in FP64.
- *  KKT_MIXED_FP32  FP64 pivot blocks (the diagonal-block Cholesky), FP32
- *                  triangular solves and Schur-complement products inside the
- *                  segments, FP64 reduced system; kkt_solve_refined recovers
- *                  FP64 accuracy by iterative refinement on the FP64 residual. */
-typedef enum { KKT_FP64 = 0, KKT_MIXED_FP32 = 1 } kkt_precision;
+ *  KKT_FP64            every operation in FP64.
+ *  KKT_MIXED_FP32      level-1 segments (the stage blocks of Psi): FP64 pivot
+ *                      blocks (the diagonal-block Cholesky) and FP64 Schur
+ *                      accumulators, FP32 panel triangular solves and FP32
+ *                      Schur-complement dot products, and an FP32 copy of the
+ *                      factor for the substitutions; the reduced separator
+ *                      systems (levels >= 2) and the corner stay FP64.
+ *                      kkt_solve then returns an unrefined solution;
+ *                      kkt_solve_refined recovers FP64 accuracy by iterative
+ *                      refinement on the FP64 residual.
+ *  KKT_MIXED_FP32_ALL  the same arithmetic on every level. */
+typedef enum { KKT_FP64 = 0, KKT_MIXED_FP32 = 1, KKT_MIXED_FP32_ALL = 2 } kkt_precision;
 
 /* How a level's N stages are split into P segments.
  *  KKT_PARTITION_PAPER     Eq. (13): N_1 and P-1 equal lengths N_k, with the
@@ -152,6 +158,26 @@ kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const dou
  * packed rows of every system), overwritten with x in its first nrhs
  * columns. nrhs >= 1. Asynchronous on `stream`. */
 kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream);
+
+/* Mixed-precision iterative refinement: x = Psi^{-1} b by x_0 = 0,
+ * c <- b; then `sweeps` times: c <- (L-hat L-hat^T)^{-1} c with the current
+ * factor (FP32 substitutions on mixed levels), x <- x + c, c <- b - Psi x in
+ * FP64 with the blocks of Eq. (3), eta = ||c||_inf / (||Psi||_inf ||x||_inf +
+ * ||b||_inf) over the system's right-hand sides together. A system whose eta
+ * is <= tol stops (its remaining sweeps return at once on the device: no
+ * host synchronization, capturable in a CUDA graph). D, E, G, R must be the
+ * matrix that was factored; b (read-only) and x (written) are device
+ * pointers with leading dimensions ldb, ldx >= nrhs. 1 <= sweeps <= 16.
+ * Works with any precision (with KKT_FP64 one sweep is a plain solve plus a
+ * residual check). */
+kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, const double* G,
+                             const double* R, const double* b, int ldb, double* x, int ldx, int nrhs,
+                             int sweeps, double tol, void* stream);
+
+/* eta of every system after sweep `sweep` (0-based) of the last
+ * kkt_solve_refined (last right-hand-side chunk); eta[count]. Synchronizes.
+ * Values after a system converged are those of its converging sweep. */
+kkt_status kkt_refine_eta(kkt_handle* h, int sweep, double* eta);
 
 /* Copy the first recorded breakdown to *info. Synchronizes with the device
  * (call it after the stream that ran kkt_factor is synchronized). Clears the

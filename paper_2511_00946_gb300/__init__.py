@@ -19,13 +19,13 @@ LIB_PATH = os.path.join(_HERE, "_build", "libkkt.so")
 
 (KKT_OK, KKT_ERR_ARG, KKT_ERR_PARTITION, KKT_ERR_NOT_SPD, KKT_ERR_CUDA, KKT_ERR_TIMEOUT, KKT_ERR_STATE,
  KKT_ERR_CAPACITY) = range(8)
-KKT_FP64, KKT_MIXED_FP32 = 0, 1
+KKT_FP64, KKT_MIXED_FP32, KKT_MIXED_FP32_ALL = 0, 1, 2
 KKT_PARTITION_PAPER, KKT_PARTITION_BALANCED = 0, 1
 RHS_CHUNK = 16
 
 EXPORTED = [
     "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_destroy",
-    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_get_info",
+    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_solve_refined", "kkt_refine_eta", "kkt_get_info",
     "kkt_get_factor", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
 ]
 
@@ -60,6 +60,8 @@ _sig = {
     "kkt_batch_offsets": [_vp, _szp, _szp, _szp, _szp, _szp],
     "kkt_factor": [_vp, _vp, _vp, _vp, _vp, _vp],
     "kkt_solve": [_vp, _vp, _i, _i, _vp],
+    "kkt_solve_refined": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i, _i, _i, ctypes.c_double, _vp],
+    "kkt_refine_eta": [_vp, _i, _dp],
     "kkt_get_info": [_vp, _ip, _i],
     "kkt_get_factor": [_vp, _i, _dp, _dp, _dp, _dp, _dp, _dp],
     "kkt_set_launch_events": [_vp, ctypes.POINTER(_vp), _i],
@@ -139,6 +141,7 @@ def kkt_create_plan(N: int, n: int, m: int, P_levels, partition: int = KKT_PARTI
 
 
 def kkt_batch_create(N, n, m, P=None, precision: int = KKT_FP64) -> int:
+    """Batch of independent systems (packed inputs, see kkt_batch_offsets)."""
     count = len(N)
     h = _vp()
     _check(_lib.kkt_batch_create(count, _ints(N), _ints(n), _ints(m), _ints(P) if P is not None else None,
@@ -187,6 +190,26 @@ def kkt_solve(h: int, b, nrhs: int | None = None, ldb: int | None = None, stream
     if ldb is None:
         ldb = 1 if b.dim() == 1 else b.shape[1]
     _check(_lib.kkt_solve(h, _ptr(b), nrhs, ldb, _stream(stream)), "kkt_solve")
+
+
+def kkt_solve_refined(h: int, D, E, G, R, b, x, nrhs: int | None = None, ldb: int | None = None,
+                      ldx: int | None = None, sweeps: int = 3, tol: float = 1e-15, stream=None):
+    """Iterative refinement with the current (mixed or FP64) factor; b is
+    read-only, x receives the solution (see include/kkt.h)."""
+    if nrhs is None:
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+    if ldb is None:
+        ldb = 1 if b.dim() == 1 else b.shape[1]
+    if ldx is None:
+        ldx = 1 if x.dim() == 1 else x.shape[1]
+    _check(_lib.kkt_solve_refined(h, _ptr(D), _ptr(E), _ptr(G), _ptr(R), _ptr(b), ldb, _ptr(x), ldx, nrhs,
+                                  sweeps, float(tol), _stream(stream)), "kkt_solve_refined")
+
+
+def kkt_refine_eta(h: int, sweep: int, count: int = 1) -> np.ndarray:
+    out = np.zeros(count)
+    _check(_lib.kkt_refine_eta(h, sweep, out.ctypes.data_as(_dp)), "kkt_refine_eta")
+    return out
 
 
 def kkt_get_info(h: int, clear: bool = True) -> dict:

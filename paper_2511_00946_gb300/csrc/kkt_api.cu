@@ -19,6 +19,7 @@ namespace {
 
 struct LevelPlan {
   int N, P;
+  int mixed = 0;           // FP32 panel arithmetic in this level's segments
   std::vector<int> start;  // segment k: stages start[k] .. start[k+1]-2; start[P] = N+1
   std::vector<int> nat;    // natural stage index of each stage
 };
@@ -147,7 +148,19 @@ struct kkt_handle {
   bool factored = false;
   size_t tot_D = 0, tot_E = 0, tot_G = 0, tot_R = 0, tot_B = 0;
   std::vector<cudaEvent_t> events;           // optional per-launch events
+  // iterative refinement
+  std::vector<kkt::ResTask> hres;
+  kkt::ResTask* dres = nullptr;
+  int* dsys_desc = nullptr;                  // level-1 descriptor of each system
+  int* dpart0 = nullptr;                     // first residual task of each system
+  double* dcorr = nullptr;                   // correction / residual vectors [tot_B][chunk]
+  double* dparts = nullptr;                  // residual partials
+  int* dconv = nullptr;                      // per-system convergence flags
+  double* deta = nullptr;                    // eta history [kMaxSweeps][count]
+  std::vector<int> level_mixed;              // per level index (all systems alike)
 };
+
+constexpr int kMaxSweeps = 16;
 
 namespace {
 // Record the caller's event `i` (if attached) after a launch.
@@ -175,7 +188,8 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
   if (!out) return KKT_ERR_ARG;
   *out = nullptr;
   if (count < 1 || !N || !n || !m) return KKT_ERR_ARG;
-  if (precision != KKT_FP64 && precision != KKT_MIXED_FP32) return KKT_ERR_ARG;
+  if (precision != KKT_FP64 && precision != KKT_MIXED_FP32 && precision != KKT_MIXED_FP32_ALL)
+    return KKT_ERR_ARG;
   auto* h = new kkt_handle();
   h->count = count;
   h->precision = precision;
@@ -196,6 +210,7 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       LevelPlan L;
       if (!make_level(Nl, Ps[l], mode, sp.n, sp.m, &L)) { delete h; return KKT_ERR_PARTITION; }
       L.nat = nat;
+      L.mixed = (precision == KKT_MIXED_FP32_ALL) || (precision == KKT_MIXED_FP32 && l == 0);
       sp.lv.push_back(L);
       if (L.P == 1) {
         if (l + 1 != Ps.size()) { delete h; return KKT_ERR_ARG; }
@@ -223,13 +238,17 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
     delete h;
     return KKT_ERR_CUDA;
   }
-  if (kkt::factor_smem_bytes(h->maxn, h->maxm) > size_t(optin)) { delete h; return KKT_ERR_ARG; }
+  if (kkt::factor_smem_bytes(h->maxn, h->maxm, 0) > size_t(optin)) { delete h; return KKT_ERR_ARG; }
+  h->level_mixed.assign(h->maxL, 0);
+  for (const SysPlan& sp : h->sys)
+    for (size_t l = 0; l < sp.lv.size(); ++l) h->level_mixed[l] = sp.lv[l].mixed;
 
   // workspace carving (byte offsets), then one cudaMalloc
   const size_t D8 = sizeof(double), CH = kkt::kRhsChunk;
   Carver cv;
   struct Offs {
     size_t Ld, LdM, LdR, Lri, Lp, DA, DB, EN, GA, GB, X, YA, YB, nat, seg;
+    size_t LdMf, LdRf, Lrif, Lpf;
   };
   std::vector<std::vector<Offs>> lo(count);
   std::vector<size_t> rhat(count), rri(count), rpart(count), ygall(count);
@@ -245,6 +264,12 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       o.LdR = cv.take(D8 * L.N * nn);
       o.Lri = cv.take(D8 * L.N * sp.n);
       o.Lp = cv.take(D8 * L.N * R * sp.n);
+      if (L.mixed) {
+        o.LdMf = cv.take(4 * L.N * nn);
+        o.LdRf = cv.take(4 * L.N * nn);
+        o.Lrif = cv.take(4 * L.N * sp.n);
+        o.Lpf = cv.take(4 * L.N * R * sp.n);
+      }
       if (!top) {
         o.DA = cv.take(D8 * (L.P - 1) * nn);
         o.DB = cv.take(D8 * (L.P - 1) * nn);
@@ -292,6 +317,21 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
     h->bwd_cnt[l] = (int)tasks.size() - h->bwd_off[l];
   }
   const size_t task_off = cv.take(sizeof(Task) * std::max<size_t>(tasks.size(), 1));
+  // refinement: residual tasks (chunks of kResChunk stages per system)
+  std::vector<int> sys_desc(count), part0(count);
+  for (int s = 0; s < count; ++s) {
+    sys_desc[s] = h->desc_of[s][0];
+    part0[s] = (int)h->hres.size();
+    const int np = (h->sys[s].N + kkt::kResChunk - 1) / kkt::kResChunk;
+    for (int p = 0; p < np; ++p)
+      h->hres.push_back(kkt::ResTask{h->desc_of[s][0], p * kkt::kResChunk, p, np});
+  }
+  const size_t res_off = cv.take(sizeof(kkt::ResTask) * h->hres.size());
+  const size_t sysd_off = cv.take(sizeof(int) * count), part0_off = cv.take(sizeof(int) * count);
+  const size_t corr_off = cv.take(sizeof(double) * h->tot_B * kkt::kRhsChunk);
+  const size_t parts_off = cv.take(sizeof(double) * h->hres.size() * kkt::kResPartDoubles);
+  const size_t conv_off = cv.take(sizeof(int) * count);
+  const size_t eta_off = cv.take(sizeof(double) * count * kMaxSweeps);
   const size_t info_off = cv.take(sizeof(kkt::Info));
   h->dbytes = cv.off;
   if (cudaMalloc(&h->dmem, h->dbytes) != cudaSuccess) {
@@ -319,7 +359,12 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       d.rowG = sp.offB + (long long)sp.N * sp.n;
       d.Nnat = sp.N;
       d.nat = (const int*)(base + o.nat);
-      d.Ld = dp(o.Ld); d.LdM = dp(o.LdM); d.LdR = dp(o.LdR); d.Lri = dp(o.Lri); d.Lp = dp(o.Lp);
+      d.Ld = dp(o.Ld); d.LdM = dp(o.LdM); d.LdR = dp(o.LdR);
+      d.mixed = P.mixed;
+      if (P.mixed) {
+        d.LdMf = (float*)(base + o.LdMf); d.LdRf = (float*)(base + o.LdRf);
+        d.Lrif = (float*)(base + o.Lrif); d.Lpf = (float*)(base + o.Lpf);
+      } d.Lri = dp(o.Lri); d.Lp = dp(o.Lp);
       d.X = dp(o.X);
       if (!d.is_top) {
         d.DA = dp(o.DA); d.DB = dp(o.DB); d.EN = dp(o.EN); d.GA = dp(o.GA); d.GB = dp(o.GB);
@@ -345,6 +390,13 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       d.nyg_all = (int)part_cursor;
     }
   }
+  h->dres = (kkt::ResTask*)(base + res_off);
+  h->dsys_desc = (int*)(base + sysd_off);
+  h->dpart0 = (int*)(base + part0_off);
+  h->dcorr = (double*)(base + corr_off);
+  h->dparts = (double*)(base + parts_off);
+  h->dconv = (int*)(base + conv_off);
+  h->deta = (double*)(base + eta_off);
   h->ddesc = (LevelDesc*)(base + desc_off);
   h->dtasks = (Task*)(base + task_off);
   h->dinfo = (kkt::Info*)(base + info_off);
@@ -354,6 +406,12 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
   if (!tasks.empty())
     ok = ok && cudaMemcpy(h->dtasks, tasks.data(), sizeof(Task) * tasks.size(),
                           cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(h->dres, h->hres.data(), sizeof(kkt::ResTask) * h->hres.size(),
+                        cudaMemcpyHostToDevice) == cudaSuccess;
+  ok = ok && cudaMemcpy(h->dsys_desc, sys_desc.data(), sizeof(int) * count, cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
+  ok = ok && cudaMemcpy(h->dpart0, part0.data(), sizeof(int) * count, cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
   for (int s = 0; s < count && ok; ++s)
     for (size_t l = 0; l < h->sys[s].lv.size() && ok; ++l) {
       const std::vector<int>& nat = h->sys[s].lv[l].nat;
@@ -486,12 +544,32 @@ kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const dou
   for (int l = 0; l < h->maxL; ++l) {
     if (!h->fac_cnt[l]) continue;
     const int e = kkt::launch_factor(h->ddesc, h->dtasks + h->fac_off[l], h->fac_cnt[l], h->maxn,
-                                     h->maxm, D, E, G, R, h->dinfo, stream);
+                                     h->maxm, h->level_mixed[l], D, E, G, R, h->dinfo, stream);
     if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
   }
   h->factored = true;
   return KKT_OK;
 }
+
+namespace {
+// One forward/backward sweep over every level for up to kRhsChunk columns.
+kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* skip, void* stream,
+                       int* li) {
+  for (int l = 0; l < h->maxL; ++l) {
+    if (!h->fac_cnt[l]) continue;
+    const int e = kkt::launch_forward(h->ddesc, h->dtasks + h->fac_off[l], h->fac_cnt[l], h->maxn,
+                                      h->maxm, h->level_mixed[l], b, ldb, nr, skip, stream);
+    if (e || (li && !mark(h, (*li)++, stream))) return KKT_ERR_CUDA;
+  }
+  for (int l = h->maxL - 2; l >= 0; --l) {
+    if (!h->bwd_cnt[l]) continue;
+    const int e = kkt::launch_backward(h->ddesc, h->dtasks + h->bwd_off[l], h->bwd_cnt[l], h->maxn,
+                                       h->maxm, h->level_mixed[l], b, ldb, nr, skip, stream);
+    if (e || (li && !mark(h, (*li)++, stream))) return KKT_ERR_CUDA;
+  }
+  return KKT_OK;
+}
+}  // namespace
 
 kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream) {
   if (!h || !b || nrhs < 1 || ldb < nrhs) return KKT_ERR_ARG;
@@ -502,19 +580,53 @@ kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream) 
   for (int l = 0; l < h->maxL; ++l) li += h->fac_cnt[l] > 0;
   for (int c0 = 0; c0 < nrhs; c0 += kkt::kRhsChunk) {
     const int nr = std::min(kkt::kRhsChunk, nrhs - c0);
-    for (int l = 0; l < h->maxL; ++l) {
-      if (!h->fac_cnt[l]) continue;
-      const int e = kkt::launch_forward(h->ddesc, h->dtasks + h->fac_off[l], h->fac_cnt[l], h->maxn,
-                                        h->maxm, b + c0, ldb, nr, nullptr, stream);
-      if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
-    }
-    for (int l = h->maxL - 2; l >= 0; --l) {
-      if (!h->bwd_cnt[l]) continue;
-      const int e = kkt::launch_backward(h->ddesc, h->dtasks + h->bwd_off[l], h->bwd_cnt[l],
-                                         h->maxn, h->maxm, b + c0, ldb, nr, stream);
-      if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
+    const kkt_status st = solve_chunk(h, b + c0, ldb, nr, nullptr, stream, &li);
+    if (st != KKT_OK) return st;
+  }
+  return KKT_OK;
+}
+
+kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, const double* G,
+                             const double* R, const double* b, int ldb, double* x, int ldx, int nrhs,
+                             int sweeps, double tol, void* stream) {
+  if (!h || !D || !b || !x || nrhs < 1 || ldb < nrhs || ldx < nrhs || sweeps < 1 ||
+      sweeps > kMaxSweeps)
+    return KKT_ERR_ARG;
+  if (h->tot_E > 0 && !E) return KKT_ERR_ARG;
+  if (h->maxm > 0 && (!G || !R)) return KKT_ERR_ARG;
+  if (!h->factored) return KKT_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int CH = kkt::kRhsChunk, nres = (int)h->hres.size();
+  for (int c0 = 0; c0 < nrhs; c0 += CH) {
+    const int nr = std::min(CH, nrhs - c0);
+    // x = 0, c = b (this chunk's columns), flags cleared
+    if (cudaMemset2DAsync(x + c0, sizeof(double) * ldx, 0, sizeof(double) * nr, h->tot_B, st) != cudaSuccess ||
+        cudaMemcpy2DAsync(h->dcorr, sizeof(double) * CH, b + c0, sizeof(double) * ldb, sizeof(double) * nr,
+                          h->tot_B, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(h->dconv, 0, sizeof(int) * h->count, st) != cudaSuccess)
+      return KKT_ERR_CUDA;
+    for (int sw = 0; sw < sweeps; ++sw) {
+      // correction c <- Psi~^{-1} c with the (mixed) factor, then x += c,
+      // c <- b - Psi x in FP64, eta and the per-system flags
+      kkt_status s2 = solve_chunk(h, h->dcorr, CH, nr, h->dconv, stream, nullptr);
+      if (s2 != KKT_OK) return s2;
+      if (kkt::launch_axpy(h->ddesc, h->dres, nres, x + c0, ldx, h->dcorr, nr, h->dconv, stream) ||
+          kkt::launch_residual(h->ddesc, h->dres, nres, h->maxn, D, E, G, b + c0, ldb, x + c0, ldx,
+                               h->dcorr, nr, h->dparts, h->dconv, stream) ||
+          kkt::launch_residual_final(h->ddesc, h->dsys_desc, h->dpart0, h->count, G, R, b + c0, ldb,
+                                     x + c0, ldx, h->dcorr, nr, h->dparts, tol,
+                                     h->deta + (size_t)sw * h->count, h->dconv, stream))
+        return KKT_ERR_CUDA;
     }
   }
+  return KKT_OK;
+}
+
+kkt_status kkt_refine_eta(kkt_handle* h, int sweep, double* eta) {
+  if (!h || !eta || sweep < 0 || sweep >= kMaxSweeps) return KKT_ERR_ARG;
+  if (cudaMemcpy(eta, h->deta + (size_t)sweep * h->count, sizeof(double) * h->count,
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return KKT_ERR_CUDA;
   return KKT_OK;
 }
 

@@ -68,6 +68,13 @@ struct LevelDesc {
   double* Lp;
   double* LdM;
   double* LdR;  // D-hat with its rows divided by their diagonal (backward substitution)
+  // mixed precision: the factor in FP32 for the correction solves, and
+  // whether this level's segments run their panel trsm/syrk in FP32
+  int mixed;
+  float* LdMf;
+  float* LdRf;
+  float* Lrif;
+  float* Lpf;
   // slots for the next level (null at the top), indexed by next-level stage
   double* DA;  // [P-1][n][n]  A~_{k}   written by segment k   (index k-1)
   double* DB;  // [P-1][n][n]  -F^_k F^_k^T  by segment k       (index k)
@@ -90,8 +97,6 @@ struct LevelDesc {
   int nRpart_all;
   double* yg_all;     // every level's yg partials, contiguous [..][m][chunk]
   int nyg_all;
-  // mixed precision: FP32 copies of the factor used by the refinement solve
-  float* Lp32;
 };
 
 struct Task {
@@ -104,13 +109,15 @@ struct Info {
   int status, system, stage, level;
 };
 
-// Shared-memory layouts (in doubles), identical on host and device. Square
-// buffers are sized for q = max(n, m) because the corner (m x m) reuses them.
-// Odd leading dimensions keep row- and column-wise FP64 accesses conflict-free.
+// Shared-memory layouts, byte offsets, identical on host and device. Square
+// FP64 buffers are sized for q = max(n, m) because the corner (m x m) reuses
+// them. zb = bytes per panel element (8: FP64 path, 4: mixed). Odd leading
+// dimensions keep row- and column-wise accesses free of bank conflicts.
 struct FacLayout {
-  int q, R, ldD, ldZ, ldT, oDfac, oM, oRinv, oZ, oT, total;
+  int q, R, ldD, ldZ, ldT, oDfac, oM, oRinv, oRinvZ, oZ, oT, total;
 };
-__host__ __device__ inline FacLayout fac_layout(int n, int m) {
+__host__ __device__ inline int kkt_align16(int b) { return (b + 15) & ~15; }
+__host__ __device__ inline FacLayout fac_layout(int n, int m, int zb) {
   FacLayout L;
   L.q = n > m ? n : m;
   L.R = 2 * n + m;
@@ -118,17 +125,18 @@ __host__ __device__ inline FacLayout fac_layout(int n, int m) {
   L.ldZ = n | 1;
   L.ldT = L.R | 1;
   L.oDfac = 0;
-  L.oM = L.oDfac + L.q * L.ldD;
-  L.oRinv = L.oM + n * L.ldD;
-  L.oZ = L.oRinv + ((L.q + 1) & ~1);
-  L.oT = L.oZ + L.R * L.ldZ;
-  L.total = L.oT + L.R * L.ldT;
+  L.oM = L.oDfac + kkt_align16(8 * L.q * L.ldD);
+  L.oRinv = L.oM + kkt_align16(zb * n * L.ldD);
+  L.oRinvZ = L.oRinv + kkt_align16(8 * L.q);
+  L.oZ = L.oRinvZ + kkt_align16(zb * L.q);
+  L.oT = L.oZ + kkt_align16(zb * L.R * L.ldZ);
+  L.total = L.oT + kkt_align16(8 * L.R * L.ldT);
   return L;
 }
 struct SolLayout {
   int q, R, ldL, ldZ, ldV, oL, oRinv, oZ, oV, oT, total;
 };
-__host__ __device__ inline SolLayout sol_layout(int n, int m) {
+__host__ __device__ inline SolLayout sol_layout(int n, int m, int sb) {
   SolLayout L;
   L.q = n > m ? n : m;
   L.R = 2 * n + m;
@@ -136,23 +144,53 @@ __host__ __device__ inline SolLayout sol_layout(int n, int m) {
   L.ldZ = n | 1;
   L.ldV = kRhsChunk | 1;
   L.oL = 0;
-  L.oRinv = L.oL + L.q * L.ldL;
-  L.oZ = L.oRinv + ((L.q + 1) & ~1);
-  L.oV = L.oZ + L.R * L.ldZ;
-  L.oT = L.oV + L.R * L.ldV;
-  L.total = L.oT + L.q * L.ldV;
+  L.oRinv = L.oL + kkt_align16(sb * L.q * L.ldL);
+  L.oZ = L.oRinv + kkt_align16(sb * L.q);
+  L.oV = L.oZ + kkt_align16(sb * L.R * L.ldZ);
+  L.oT = L.oV + kkt_align16(sb * L.R * L.ldV);
+  L.total = L.oT + kkt_align16(sb * L.q * L.ldV);
   return L;
 }
 
+// Residual pass of iterative refinement: one CTA per chunk of kResChunk
+// stages of one system.
+constexpr int kResChunk = 8;
+struct ResTask {
+  int desc;   // level-1 descriptor of the system
+  int j0;     // first stage of the chunk
+  int part;   // index of this chunk's partial-result slot within the system
+  int nparts; // chunks of the system
+};
+// per-chunk partial results: g-rows (m x chunk) then max|r|, max|x|, max|b|,
+// max row sum of |Psi| (chunk columns each)
+constexpr int kResPartDoubles = kMaxM * kRhsChunk + 4 * kRhsChunk;
+
 // Kernel launchers (kkt_kernels.cu). Each returns the cudaError_t of the launch.
-int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm,
+// `mixed`: FP32 panel arithmetic in the factor; `single`: FP32 substitution
+// with the FP32 factor copy (mixed levels only); `skip`: per-system flags
+// (null = never skip), a set flag makes the system's CTAs return at once.
+int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
                   void* stream);
-int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, double* b,
-                   int ldb, int nrhs, const double* R, void* stream);
-int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, double* b,
-                    int ldb, int nrhs, void* stream);
-size_t factor_smem_bytes(int maxn, int maxm);
-size_t solve_smem_bytes(int maxn, int maxm);
+int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
+                   double* b, int ldb, int nrhs, const int* skip, void* stream);
+int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
+                    double* b, int ldb, int nrhs, const int* skip, void* stream);
+// x += c (stage rows per residual task, g rows by each system's first task)
+int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int ldx, const double* c,
+                int nr, const int* skip, void* stream);
+// c = b - Psi x over the stage rows of each task (+ partials for the g rows
+// and the norms); c has leading dimension kRhsChunk
+int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, int maxn, const double* D,
+                    const double* E, const double* G, const double* b, int ldb, const double* x,
+                    int ldx, double* c, int nr, double* parts, const int* skip, void* stream);
+// g rows of c, eta per system, converged[s] = (eta <= tol)
+int launch_residual_final(const LevelDesc* d, const int* sys_desc, const int* part0, int count,
+                          const double* G, const double* R, const double* b, int ldb, const double* x,
+                          int ldx, double* c, int nr, const double* parts, double tol, double* eta_out,
+                          int* converged, void* stream);
+size_t factor_smem_bytes(int maxn, int maxm, int mixed);
+size_t solve_smem_bytes(int maxn, int maxm, int single);
+size_t residual_smem_bytes(int maxn);
 
 }  // namespace kkt

@@ -1,15 +1,21 @@
 // Kernels of the partitioned block Cholesky factorization and solve of an SPD
-// block-tridiagonal-arrow KKT matrix (arXiv 2511.00946, Algorithms 1-3).
+// block-tridiagonal-arrow KKT matrix (arXiv 2511.00946, Algorithms 1-3), and
+// of the FP64 residual used by mixed-precision iterative refinement.
 //
-// One CTA per segment task (kFactorThreads / kSolveThreads threads). Per stage the CTA keeps the pivot
-// block, the stacked panel Z = [E; G; W] and the Schur accumulator T in
-// shared memory (row-major, odd leading dimensions so that row- and
-// column-wise accesses of FP64 words are free of bank conflicts) and runs
+// One CTA per segment task. Per stage the CTA keeps the pivot block, the
+// stacked panel Z = [E; G; W] and the Schur accumulator T in shared memory
+// (row-major, odd leading dimensions: row- and column-wise accesses are free
+// of bank conflicts) and runs
 //   potrf(D)  ->  Z <- Z D-hat^{-T}  ->  T -= Z Z^T (lower triangle)
 // with every thread on the element loops. FP64 is the scarce resource on this
-// part (about 1/70 of the FP32 rate), so the loops are laid out to issue FP64
-// instructions from full warps only: lower triangles are enumerated linearly
-// instead of with a masked square.
+// part: one FP64 warp-instruction occupies a sub-partition's FP64 pipe for
+// about 64-76 cycles whether 1 or 32 lanes are active, and FP32 runs about
+// 70x faster. So the loops issue FP64 instructions from full warps only
+// (lower triangles are enumerated linearly instead of masked squares), and
+// the mixed variant (TZ = float) keeps only the pivot Cholesky and the
+// Schur accumulator in FP64: the panel trsm and the dot products of the
+// syrk run in FP32 and each dot product is subtracted from the FP64
+// accumulator once.
 #include <cuda_runtime.h>
 
 #include "kkt_internal.h"
@@ -42,7 +48,8 @@ __device__ void record_breakdown(Info* info, int sys, int stage, int level) {
 // dst (rows x cols, smem, ld) <- A (+ B) from global row-major [rows][cols],
 // or the transpose of A (+ B) given as [cols][rows] when `trans`. A null A
 // loads zeros. Coalesced over the global array.
-__device__ void load_blk(double* dst, int ld, const double* A, const double* B, int rows, int cols,
+template <typename T>
+__device__ void load_blk(T* dst, int ld, const double* A, const double* B, int rows, int cols,
                          bool trans) {
   const int tot = rows * cols;
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
@@ -52,132 +59,216 @@ __device__ void load_blk(double* dst, int ld, const double* A, const double* B, 
     double v = 0.0;
     if (A) v = A[e];
     if (B) v += B[e];
-    dst[r * ld + c] = v;
+    dst[r * ld + c] = (T)v;
   }
 }
 
 // global row-major [rows][cols] <- src (smem), or the transpose when `trans`
 // (dst is then [cols][rows]). `lower` writes zeros above the diagonal.
-__device__ void store_blk(double* dst, const double* src, int ld, int rows, int cols, bool trans,
+template <typename TD, typename TS>
+__device__ void store_blk(TD* dst, const TS* src, int ld, int rows, int cols, bool trans,
                           bool lower) {
   const int tot = rows * cols;
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
     int r, c;
     if (trans) { c = e / rows; r = e - c * rows; }
     else { r = e / cols; c = e - r * cols; }
-    double v = src[r * ld + c];
-    if (lower && c > r) v = 0.0;
-    dst[e] = v;
+    TS v = src[r * ld + c];
+    if (lower && c > r) v = TS(0);
+    dst[e] = (TD)v;
   }
 }
 
-// smem -> smem copy of a rows x cols block (lower triangle only when `lower`).
-__device__ void copy_blk(double* dst, int ldd, const double* src, int lds, int rows, int cols) {
+// smem -> smem copy of a rows x cols block (with conversion)
+template <typename TD, typename TS>
+__device__ void copy_blk(TD* dst, int ldd, const TS* src, int lds, int rows, int cols) {
   for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
     const int r = e / cols, c = e - r * cols;
-    dst[r * ldd + c] = src[r * lds + c];
+    dst[r * ldd + c] = (TD)src[r * lds + c];
   }
 }
 
-// 1/sqrt(d) for a pivot d > 0 in about five dependent FP64 operations instead
-// of a square root and a division (each several hundred cycles on this part).
+// 1/sqrt(d) for a pivot d > 0 in four dependent FP64 operations instead of a
+// square root and a division (each several hundred cycles on this part).
 // The exponent is split off with integer operations so that d' = d 4^-k lies
-// in [1, 4); a single-precision hardware estimate r ~ 1/sqrt(d') (relative
-// error below 2^-21) is refined by one step of Halley's method for
+// in [1, 4); the single-precision hardware estimate r ~ 1/sqrt(d') (relative
+// error below 2^-21) is formed from d' and converted back with bit
+// manipulation only, then refined by one step of Halley's method for
 // f(r) = r^-2 - d': with e = 1 - d' r^2, r <- r (1 + e/2 + 3 e^2 / 8), which
 // leaves an error of order e^3 (below 2^-62), so the result is within a few
-// units in the last place; finally r 2^-k. Returns NaN when d is not a
-// positive finite normal number.
+// units in the last place; finally r 2^-k. Falls back to 1/sqrt for
+// subnormal or huge d and returns NaN when d is not positive.
 __device__ __forceinline__ double pivot_rsqrt(double d) {
   const long long bits = __double_as_longlong(d);
   const int ex = (int)((bits >> 52) & 0x7ff) - 1023;
-  if (!(d > 0.0) || ex <= -1022 || ex >= 1023) return (d > 0.0 && d < 1e300) ? 1.0 / sqrt(d) : __longlong_as_double(0x7ff8000000000000LL);
-  const int k = ex >> 1;  // floor(ex / 2)
-  const double dp = __longlong_as_double(bits - ((long long)(2 * k) << 52));
-  double r = (double)rsqrtf((float)dp);
+  if (!(d > 0.0) || ex <= -1022 || ex >= 1023)
+    return (d > 0.0 && d < 1e300) ? 1.0 / sqrt(d) : __longlong_as_double(0x7ff8000000000000LL);
+  const int k = ex >> 1;                                   // floor(ex / 2)
+  const long long dbits = bits - ((long long)(2 * k) << 52);  // d' in [1, 4)
+  const double dp = __longlong_as_double(dbits);
+  // d' truncated to single precision (exponent 0 or 1, top 23 mantissa bits)
+  const int fbits = ((int)((dbits >> 52) & 0x7ff) - 1023 + 127) << 23 | (int)((dbits >> 29) & 0x7fffff);
+  const int rb = __float_as_int(rsqrtf(__int_as_float(fbits)));  // in (0.5, 1]: normal
+  double r = __longlong_as_double((long long)(((rb >> 23) & 0xff) - 127 + 1023) << 52 |
+                                  (long long)(rb & 0x7fffff) << 29);
   const double e = fma(-dp * r, r, 1.0);
   r = fma(r * e, fma(0.375, e, 0.5), r);
   return __longlong_as_double(__double_as_longlong(r) - ((long long)k << 52));
 }
 
-// In-place lower Cholesky of A (n x n). Writes rinv[j] = 1 / L_jj; on a pivot
-// that is not positive, sets *bad (first column + 1) and carries on (NaNs
-// propagate; no trap). Right-looking: per column a scalar pivot, a column
-// scaling and a rank-1 update of the trailing lower triangle.
-__device__ void potrf_sm(double* A, int ld, int n, double* rinv, int* bad) {
-  const int tid = threadIdx.x;
-  for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      const double d = A[j * ld + j];
-      if (!(d > 0.0) && *bad == 0) *bad = j + 1;
-      const double r = pivot_rsqrt(d);
-      A[j * ld + j] = d * r;
-      rinv[j] = r;
-    }
-    __syncthreads();
-    const double r = rinv[j];
-    const int w = n - 1 - j;
-    for (int e = tid; e < w; e += blockDim.x) A[(j + 1 + e) * ld + j] *= r;
-    __syncthreads();
-    const int ntri = w * (w + 1) / 2;
-    for (int e = tid; e < ntri; e += blockDim.x) {
-      int a, b;
-      tri_rc(e, a, b);
-      const int i = j + 1 + a, k = j + 1 + b;
-      A[i * ld + k] = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
-    }
-    __syncthreads();
-  }
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// M[c][j] = L[c][j] / L[j][j] for c > j (strict lower triangle).
-__device__ void scaled_cols(double* M, const double* L, int ld, int n, const double* rinv) {
+// In-place lower Cholesky of A (n x n, FP64) by the first kPotrfThreads
+// threads (one warp per FP64 sub-pipe), synchronized with a named barrier;
+// the CTA's other threads wait at the closing __syncthreads. Writes
+// rinv[j] = 1 / L_jj. On a pivot that is not positive it sets *bad (first
+// column + 1) and carries on (NaNs propagate; no trap).
+// Right-looking, two barriers per column. Each thread owns a fixed list of
+// strictly-lower elements (i, k), ordered by k descending so that the
+// trailing triangle of column j is the prefix of length (n-1-j)(n-j)/2 for
+// every j; the thread that updates the next diagonal element computes its
+// pivot at once (look-ahead), overlapping it with the other updates.
+constexpr int kPotrfThreads = 128;
+constexpr int kPotrfPer = (kMaxN * (kMaxN - 1) / 2 + kPotrfThreads - 1) / kPotrfThreads;
+
+__device__ void potrf_sm(double* A, int ld, int n, double* rinv, int* bad) {
+  const int tid = threadIdx.x;
+  if (tid < kPotrfThreads) {
+    int pi[kPotrfPer], pk[kPotrfPer];
+    const int npairs = n * (n - 1) / 2;
+#pragma unroll
+    for (int t = 0; t < kPotrfPer; ++t) {
+      const int e = tid + t * kPotrfThreads;
+      if (e < npairs) {
+        int a, b;
+        tri_rc(e, a, b);
+        pk[t] = n - 1 - a;
+        pi[t] = pk[t] + b;
+      } else {
+        pk[t] = pi[t] = 0;
+      }
+    }
+    if (tid == 0) {
+      const double d = A[0];
+      if (!(d > 0.0) && *bad == 0) *bad = 1;
+      const double r = pivot_rsqrt(d);
+      A[0] = d * r;
+      rinv[0] = r;
+    }
+    group_bar(1, kPotrfThreads);
+    for (int j = 0; j < n; ++j) {
+      const double r = rinv[j];
+      for (int i = j + 1 + tid; i < n; i += kPotrfThreads) A[i * ld + j] *= r;
+      group_bar(1, kPotrfThreads);
+      const int cnt = (n - 1 - j) * (n - j) / 2;
+#pragma unroll
+      for (int t = 0; t < kPotrfPer; ++t) {
+        if (tid + t * kPotrfThreads < cnt) {
+          const int i = pi[t], k = pk[t];
+          const double v = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
+          if (i == j + 1 && k == j + 1) {  // next pivot: compute it now
+            if (!(v > 0.0) && *bad == 0) *bad = j + 2;
+            const double rr = pivot_rsqrt(v);
+            A[i * ld + k] = v * rr;
+            rinv[j + 1] = rr;
+          } else {
+            A[i * ld + k] = v;
+          }
+        }
+      }
+      group_bar(1, kPotrfThreads);
+    }
+  }
+  __syncthreads();
+}
+
+// M[c][j] = L[c][j] / L[j][j] for c > j (strict lower triangle), rounded to TM.
+template <typename TM>
+__device__ void scaled_cols(TM* M, const double* L, int ld, int n, const double* rinv) {
   const int ntri = (n - 1) * n / 2;
   for (int e = threadIdx.x; e < ntri; e += blockDim.x) {
     int a, b;
     tri_rc(e, a, b);
     const int c = a + 1, j = b;
-    M[c * ld + j] = L[c * ld + j] * rinv[j];
+    M[c * ld + j] = (TM)(L[c * ld + j] * rinv[j]);
   }
 }
 
-// Z[r0:r1) <- Z[r0:r1) L^{-T}: column sweep with the pre-scaled columns M
-// (x_j = b_j / L_jj; b_c -= x_j L_cj = b_j M_cj), then the diagonal scaling.
+// Z[r0:r1) <- Z[r0:r1) L^{-T} with the pre-scaled columns M (M_cj = L_cj /
+// L_jj): for each row, u_c = z_c - sum_{k<c} u_k M_ck and x_c = u_c / L_cc.
+// FP64: column sweep (every thread on every column, FP64 from full warps),
+// thread t owning row r0 + t % rows and every (blockDim/rows)-th column.
 __device__ void trsm_panel(double* Z, int ldz, int r0, int r1, const double* M, int ldm, int n,
                            const double* rinv) {
   const int rows = r1 - r0;
+  const int per = blockDim.x / rows;  // threads per row (>= 1: rows <= 2 kMaxN + kMaxM)
+  const int rr = threadIdx.x % rows, cc = threadIdx.x / rows;
+  const bool act = cc < per;
+  double* zr = Z + (r0 + rr) * ldz;
   for (int j = 0; j < n - 1; ++j) {
-    const int w = n - 1 - j, tot = rows * w;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int rr = e / w, c = j + 1 + (e - rr * w);
-      double* zr = Z + (r0 + rr) * ldz;
-      zr[c] = fma(-zr[j], M[c * ldm + j], zr[c]);
+    if (act) {
+      const double zj = zr[j];
+      for (int c = j + 1 + cc; c < n; c += per) zr[c] = fma(-zj, M[c * ldm + j], zr[c]);
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < rows * n; e += blockDim.x) {
-    const int rr = e / n, c = e - rr * n;
-    Z[(r0 + rr) * ldz + c] *= rinv[c];
+  if (act)
+    for (int c = cc; c < n; c += per) zr[c] *= rinv[c];
+  __syncthreads();
+}
+
+// FP32: one thread per panel row runs the whole substitution in order (no
+// barriers; FP32 issue is cheap), four partial sums per dot product.
+__device__ void trsm_panel(float* Z, int ldz, int r0, int r1, const float* M, int ldm, int n,
+                           const float* rinv) {
+  const int rows = r1 - r0;
+  for (int rr = threadIdx.x; rr < rows; rr += blockDim.x) {
+    float* z = Z + (r0 + rr) * ldz;
+    for (int c = 1; c < n; ++c) {
+      const float* mc = M + c * ldm;
+      float s0 = z[c], s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      int k = 0;
+      for (; k + 3 < c; k += 4) {
+        s0 = fmaf(-mc[k], z[k], s0);
+        s1 = fmaf(-mc[k + 1], z[k + 1], s1);
+        s2 = fmaf(-mc[k + 2], z[k + 2], s2);
+        s3 = fmaf(-mc[k + 3], z[k + 3], s3);
+      }
+      for (; k < c; ++k) s0 = fmaf(-mc[k], z[k], s0);
+      z[c] = (s0 + s1) + (s2 + s3);
+    }
+    for (int c = 0; c < n; ++c) z[c] *= rinv[c];
   }
   __syncthreads();
 }
 
-// T[i][j] -= sum_t Z[i][t] Z[j][t] for r0 <= j <= i < r1.
-__device__ void syrk_panel(double* T, int ldt, const double* Z, int ldz, int r0, int r1, int n) {
+// T[i][j] -= sum_t Z[i][t] Z[j][t] for r0 <= j <= i < r1. The dot product is
+// formed in TZ (FP64, or FP32 in the mixed variant) and subtracted from the
+// FP64 accumulator once.
+template <typename TZ>
+__device__ void syrk_panel(double* T, int ldt, const TZ* Z, int ldz, int r0, int r1, int n) {
   const int w = r1 - r0, ntri = w * (w + 1) / 2;
+  int a = 0, b = 0;
+  if ((int)threadIdx.x < ntri) tri_rc(threadIdx.x, a, b);
   for (int e = threadIdx.x; e < ntri; e += blockDim.x) {
-    int a, b;
-    tri_rc(e, a, b);
-    const double* zi = Z + (r0 + a) * ldz;
-    const double* zj = Z + (r0 + b) * ldz;
-    double s0 = 0.0, s1 = 0.0;
+    if (e != (int)threadIdx.x) {  // advance (a, b) by blockDim along the rows
+      b += blockDim.x;
+      while (b > a) { b -= a + 1; ++a; }
+    }
+    const TZ* zi = Z + (r0 + a) * ldz;
+    const TZ* zj = Z + (r0 + b) * ldz;
+    TZ s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     int t = 0;
-    for (; t + 1 < n; t += 2) {
+    for (; t + 3 < n; t += 4) {
       s0 = fma(zi[t], zj[t], s0);
       s1 = fma(zi[t + 1], zj[t + 1], s1);
+      s2 = fma(zi[t + 2], zj[t + 2], s2);
+      s3 = fma(zi[t + 3], zj[t + 3], s3);
     }
-    if (t < n) s0 = fma(zi[t], zj[t], s0);
-    T[(r0 + a) * ldt + (r0 + b)] -= s0 + s1;
+    for (; t < n; ++t) s0 = fma(zi[t], zj[t], s0);
+    T[(r0 + a) * ldt + (r0 + b)] -= (double)((s0 + s1) + (s2 + s3));
   }
   __syncthreads();
 }
@@ -199,25 +290,32 @@ __device__ __forceinline__ SegGeom seg_geom(const LevelDesc& d, int k) {
 // Factorization: Algorithm 1 for one segment (parallel phase); the top level
 // (P = 1) is the sequential phase on the reduced system and also factors the
 // corner R-hat = chol(R + sum of every R~_k partial).
+// TZ = double: every operation in FP64. TZ = float: FP64 pivots and Schur
+// accumulator, FP32 panel (trsm and dot products), FP32 factor copy written
+// for the correction solves.
 // ---------------------------------------------------------------------------
+template <typename TZ>
 __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __restrict__ descs,
-                                                     const Task* __restrict__ tasks,
-                                                     const double* __restrict__ uD,
-                                                     const double* __restrict__ uE,
-                                                     const double* __restrict__ uG,
-                                                     const double* __restrict__ uR, Info* info) {
-  extern __shared__ double sm[];
+                                                           const Task* __restrict__ tasks,
+                                                           const double* __restrict__ uD,
+                                                           const double* __restrict__ uE,
+                                                           const double* __restrict__ uG,
+                                                           const double* __restrict__ uR,
+                                                           Info* info) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
   const Task tk = tasks[blockIdx.x];
   const LevelDesc& d = descs[tk.desc];
+  constexpr bool mixed = sizeof(TZ) == 4;
   const int n = d.n, m = d.m, R = 2 * n + m;
-  const FacLayout lay = fac_layout(n, m);
+  const FacLayout lay = fac_layout(n, m, (int)sizeof(TZ));
   const int ldD = odd(n), ldZ = lay.ldZ, ldT = lay.ldT;
-  double* Dfac = sm + lay.oDfac;
-  double* M = sm + lay.oM;
-  double* rinv = sm + lay.oRinv;
-  double* Z = sm + lay.oZ;
-  double* T = sm + lay.oT;
+  double* Dfac = (double*)(smraw + lay.oDfac);
+  TZ* M = (TZ*)(smraw + lay.oM);
+  double* rinv = (double*)(smraw + lay.oRinv);
+  TZ* rinvZ = (TZ*)(smraw + lay.oRinvZ);
+  TZ* Z = (TZ*)(smraw + lay.oZ);
+  double* T = (double*)(smraw + lay.oT);
   const int oG = n, oW = n + m;  // panel row offsets
   const SegGeom g = seg_geom(d, tk.seg);
   const int s = g.f - 1;  // separator of this segment (k >= 1)
@@ -231,16 +329,16 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
   const double* G2 = d.level == 1 ? nullptr : d.G2w;
   auto Dp = [&](const double* b, int j) { return b ? b + (size_t)j * nn : nullptr; };
   auto Gp = [&](const double* b, int j) { return b ? b + (size_t)j * mn : nullptr; };
+  const double* none = nullptr;
 
   if (threadIdx.x == 0) bad = 0;
-  // zero T (accumulators start at zero unless initialised below)
   for (int e = threadIdx.x; e < R * ldT; e += blockDim.x) T[e] = 0.0;
   __syncthreads();
   load_blk(Dfac, ldD, Dp(Din, g.f), Dp(D2, g.f), n, n, false);
-  if (g.len > 1 || g.hasF) load_blk(Z, ldZ, Dp(Ein, g.f), nullptr, n, n, false);
+  if (g.len > 1 || g.hasF) load_blk(Z, ldZ, Dp(Ein, g.f), none, n, n, false);
   if (m) load_blk(Z + oG * ldZ, ldZ, Gp(Gin, g.f), Gp(G2, g.f), m, n, false);
   if (g.hasW) {
-    load_blk(Z + oW * ldZ, ldZ, Dp(Ein, s), nullptr, n, n, true);              // W_1 = B_k = E[s]^T
+    load_blk(Z + oW * ldZ, ldZ, Dp(Ein, s), none, n, n, true);                 // W_1 = B_k = E[s]^T
     load_blk(T + oW * ldT + oW, ldT, Dp(Din, s), Dp(D2, s), n, n, false);       // A_k
     if (m) load_blk(T + oW * ldT + oG, ldT, Gp(Gin, s), Gp(G2, s), n, m, true);  // Q_k^T
   }
@@ -258,23 +356,36 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
     potrf_sm(Dfac, ldD, n, rinv, &bad);
     if (bad && threadIdx.x == 0) { record_breakdown(info, d.sys, d.nat[j], d.level); bad = 0; }
     scaled_cols(M, Dfac, ldD, n, rinv);
+    for (int e = threadIdx.x; e < n; e += blockDim.x) rinvZ[e] = (TZ)rinv[e];
     __syncthreads();
-    trsm_panel(Z, ldZ, r0, r1, M, ldD, n, rinv);
+    trsm_panel(Z, ldZ, r0, r1, M, ldD, n, rinvZ);
     // factor blocks of this stage
     store_blk(d.Ld + (size_t)j * nn, Dfac, ldD, n, n, false, true);
-    store_blk(d.LdM + (size_t)j * nn, M, ldD, n, n, false, true);
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // rows divided by their diagonal
-      const int r = e / n, c = e - r * n;
-      d.LdR[(size_t)j * nn + e] = c < r ? Dfac[r * ldD + c] * rinv[r] : 0.0;
-    }
-    for (int e = threadIdx.x; e < n; e += blockDim.x) d.Lri[(size_t)j * n + e] = rinv[e];
     {
       double* P = d.Lp + (size_t)j * R * n;
+      float* Pf = mixed ? d.Lpf + (size_t)j * R * n : nullptr;
       for (int e = threadIdx.x; e < R * n; e += blockDim.x) {
         const int r = e / n, c = e - r * n;
-        P[e] = (r >= r0 && r < r1) ? Z[r * ldZ + c] : 0.0;
+        const TZ v = (r >= r0 && r < r1) ? Z[r * ldZ + c] : TZ(0);
+        P[e] = (double)v;
+        if (mixed) Pf[e] = (float)v;
       }
     }
+    if (mixed) {
+      store_blk(d.LdMf + (size_t)j * nn, M, ldD, n, n, false, true);
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // rows divided by their diagonal
+        const int r = e / n, c = e - r * n;
+        d.LdRf[(size_t)j * nn + e] = c < r ? (float)(Dfac[r * ldD + c] * rinv[r]) : 0.0f;
+      }
+      for (int e = threadIdx.x; e < n; e += blockDim.x) d.Lrif[(size_t)j * n + e] = (float)rinv[e];
+    } else {
+      store_blk(d.LdM + (size_t)j * nn, M, ldD, n, n, false, true);
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        d.LdR[(size_t)j * nn + e] = c < r ? Dfac[r * ldD + c] * rinv[r] : 0.0;
+      }
+    }
+    for (int e = threadIdx.x; e < n; e += blockDim.x) d.Lri[(size_t)j * n + e] = rinv[e];
     syrk_panel(T, ldT, Z, ldZ, r0, r1, n);
     if (i + 1 < g.len) {
       // rotate: the updated blocks become the next stage's inputs
@@ -282,15 +393,15 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
       if (m) copy_blk(Z + oG * ldZ, ldZ, T + oG * ldT, ldT, m, n);             // G_{i+1}
       if (g.hasW) copy_blk(Z + oW * ldZ, ldZ, T + oW * ldT, ldT, n, n);        // W_{i+1}
       __syncthreads();
-      if ((i + 1 < g.len - 1) || g.hasF) load_blk(Z, ldZ, Dp(Ein, j + 1), nullptr, n, n, false);
+      if ((i + 1 < g.len - 1) || g.hasF) load_blk(Z, ldZ, Dp(Ein, j + 1), none, n, n, false);
       if (i + 2 < g.len) {
         load_blk(T, ldT, Dp(Din, j + 2), Dp(D2, j + 2), n, n, false);
         if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, j + 2), Gp(G2, j + 2), m, n, false);
       } else {
-        load_blk(T, ldT, nullptr, nullptr, n, n, false);
-        if (m) load_blk(T + oG * ldT, ldT, nullptr, nullptr, m, n, false);
+        load_blk(T, ldT, none, none, n, n, false);
+        if (m) load_blk(T + oG * ldT, ldT, none, none, m, n, false);
       }
-      if (g.hasW) load_blk(T + oW * ldT, ldT, nullptr, nullptr, n, n, false);  // W_{i+2} <- 0
+      if (g.hasW) load_blk(T + oW * ldT, ldT, none, none, n, n, false);        // W_{i+2} <- 0
       __syncthreads();
     }
   }
@@ -328,7 +439,9 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
 }
 
 // ---------------------------------------------------------------------------
-// Solve
+// Solve. TS = double: FP64 factor and vectors. TS = float: the FP32 factor
+// copy of a mixed level and FP32 vectors (the correction solves of iterative
+// refinement). Global vectors are FP64 in both cases.
 // ---------------------------------------------------------------------------
 
 // rhs / solution rows of stage j at this level: the caller's b at level 1
@@ -346,28 +459,30 @@ __device__ __forceinline__ VecView level_vec(const LevelDesc& d, double* b, int 
 }
 
 // dst (rows x nr, smem ld) <- src rows (global, stride lds) (+ src2, stride kRhsChunk)
-__device__ void load_vec(double* dst, int ldd, const double* src, int lds, const double* src2,
-                         int rows, int nr) {
+template <typename TS>
+__device__ void load_vec(TS* dst, int ldd, const double* src, int lds, const double* src2, int rows,
+                         int nr) {
   for (int e = threadIdx.x; e < rows * nr; e += blockDim.x) {
     const int r = e / nr, c = e - r * nr;
     double v = src ? src[(size_t)r * lds + c] : 0.0;
     if (src2) v += src2[(size_t)r * kRhsChunk + c];
-    dst[r * ldd + c] = v;
+    dst[r * ldd + c] = (TS)v;
   }
 }
 
-__device__ void store_vec(double* dst, int ldd, const double* src, int lds, int rows, int nr) {
+template <typename TS>
+__device__ void store_vec(double* dst, int ldd, const TS* src, int lds, int rows, int nr) {
   for (int e = threadIdx.x; e < rows * nr; e += blockDim.x) {
     const int r = e / nr, c = e - r * nr;
-    dst[(size_t)r * ldd + c] = src[r * lds + c];
+    dst[(size_t)r * ldd + c] = (double)src[r * lds + c];
   }
 }
 
 // t <- L^{-1} t for L = M diag(1/rinv) (M: the columns of L divided by their
 // diagonal, strict lower part used), nr columns: t_i -= M_ij t_j for the
 // unscaled t_j, then t_j *= rinv_j.
-__device__ void trsv_lower(double* t, int ldt, const double* M, int ldl, const double* rinv, int n,
-                           int nr) {
+template <typename TS>
+__device__ void trsv_lower(TS* t, int ldt, const TS* M, int ldl, const TS* rinv, int n, int nr) {
   for (int j = 0; j < n - 1; ++j) {
     const int w = n - 1 - j, tot = w * nr;
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
@@ -386,8 +501,8 @@ __device__ void trsv_lower(double* t, int ldt, const double* M, int ldl, const d
 // t <- L^{-T} t with MR, the rows of L divided by their diagonal: x_j =
 // t_j rinv_j once t_j is final, and t_i -= L_ji x_j = MR_ji t_j (unscaled t_j)
 // for i < j.
-__device__ void trsv_upper(double* t, int ldt, const double* M, int ldl, const double* rinv, int n,
-                           int nr) {
+template <typename TS>
+__device__ void trsv_upper(TS* t, int ldt, const TS* M, int ldl, const TS* rinv, int n, int nr) {
   for (int j = n - 1; j > 0; --j) {
     for (int e = threadIdx.x; e < j * nr; e += blockDim.x) {
       const int i = e / nr, c = e - i * nr;
@@ -402,37 +517,52 @@ __device__ void trsv_upper(double* t, int ldt, const double* M, int ldl, const d
   __syncthreads();
 }
 
+template <typename TS>
 struct SolveSmem {
-  double *L, *rinv, *Z, *V, *t;
+  TS *L, *rinv, *Z, *V, *t;
   int ldL, ldZ, ldV;
 };
 
-__device__ __forceinline__ SolveSmem solve_smem(double* sm, int n, int m) {
-  SolveSmem S;
-  const SolLayout L = sol_layout(n, m);
+template <typename TS>
+__device__ __forceinline__ SolveSmem<TS> solve_smem(unsigned char* sm, int n, int m) {
+  SolveSmem<TS> S;
+  const SolLayout L = sol_layout(n, m, (int)sizeof(TS));
   S.ldL = odd(n);
   S.ldZ = L.ldZ;
   S.ldV = L.ldV;
-  S.L = sm + L.oL;
-  S.rinv = sm + L.oRinv;
-  S.Z = sm + L.oZ;
-  S.V = sm + L.oV;
-  S.t = sm + L.oT;
+  S.L = (TS*)(sm + L.oL);
+  S.rinv = (TS*)(sm + L.oRinv);
+  S.Z = (TS*)(sm + L.oZ);
+  S.V = (TS*)(sm + L.oV);
+  S.t = (TS*)(sm + L.oT);
   return S;
+}
+
+template <typename TS>
+struct FactorView {
+  const TS *M, *MR, *ri, *P;
+};
+__device__ __forceinline__ FactorView<double> factor_view(const LevelDesc& d, double) {
+  return FactorView<double>{d.LdM, d.LdR, d.Lri, d.Lp};
+}
+__device__ __forceinline__ FactorView<float> factor_view(const LevelDesc& d, float) {
+  return FactorView<float>{d.LdMf, d.LdRf, d.Lrif, d.Lpf};
 }
 
 // load the factor blocks of stage j (D-hat with its columns (forward) or rows
 // (backward) divided by the diagonal, 1/diag, panel rows [r0, r1))
-__device__ void load_stage_factor(const SolveSmem& S, const LevelDesc& d, int j, int r0, int r1,
+template <typename TS>
+__device__ void load_stage_factor(const SolveSmem<TS>& S, const LevelDesc& d, int j, int r0, int r1,
                                   bool backward) {
   const int n = d.n, R = 2 * n + d.m;
-  const double* Lg = (backward ? d.LdR : d.LdM) + (size_t)j * n * n;
+  const FactorView<TS> F = factor_view(d, TS(0));
+  const TS* Lg = (backward ? F.MR : F.M) + (size_t)j * n * n;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int r = e / n, c = e - r * n;
     S.L[r * S.ldL + c] = Lg[e];
   }
-  for (int e = threadIdx.x; e < n; e += blockDim.x) S.rinv[e] = d.Lri[(size_t)j * n + e];
-  const double* P = d.Lp + (size_t)j * R * n;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) S.rinv[e] = F.ri[(size_t)j * n + e];
+  const TS* P = F.P + (size_t)j * R * n;
   for (int e = threadIdx.x + r0 * n; e < r1 * n; e += blockDim.x) {
     const int r = e / n, c = e - r * n;
     S.Z[r * S.ldZ + c] = P[e];
@@ -442,7 +572,8 @@ __device__ void load_stage_factor(const SolveSmem& S, const LevelDesc& d, int j,
 // Backward substitution over the stages of one segment (Algorithm 3,
 // parallel phase; for the top level the whole sequential sweep). On entry
 // S.V holds [x_next (E rows); x_g (G rows); x_sep (W rows)].
-__device__ void backward_segment(const SolveSmem& S, const LevelDesc& d, const SegGeom& g,
+template <typename TS>
+__device__ void backward_segment(const SolveSmem<TS>& S, const LevelDesc& d, const SegGeom& g,
                                  double* b, int ldb, int nr) {
   const int n = d.n, m = d.m;
   for (int i = g.len - 1; i >= 0; --i) {
@@ -455,7 +586,7 @@ __device__ void backward_segment(const SolveSmem& S, const LevelDesc& d, const S
     // t = y_j - Z^T v over the active panel rows
     for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
       const int c2 = e / nr, c = e - c2 * nr;
-      double acc = y.p[(size_t)c2 * y.ld + c];
+      TS acc = (TS)y.p[(size_t)c2 * y.ld + c];
       for (int r = r0; r < r1; ++r) acc = fma(-S.Z[r * S.ldZ + c2], S.V[r * S.ldV + c], acc);
       S.t[c2 * S.ldV + c] = acc;
     }
@@ -472,29 +603,31 @@ __device__ void backward_segment(const SolveSmem& S, const LevelDesc& d, const S
 
 // Forward substitution (Algorithm 2) for one segment; the top level (P = 1)
 // also solves the corner and runs its own backward sweep (Algorithm 3,
-// sequential phase).
+// sequential phase). `skip`: per-system flags; a set flag returns at once.
+template <typename TS>
 __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __restrict__ descs,
-                                                      const Task* __restrict__ tasks, double* b,
-                                                      int ldb, int nr) {
-  extern __shared__ double sm[];
+                                                           const Task* __restrict__ tasks, double* b,
+                                                           int ldb, int nr, const int* skip) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const Task tk = tasks[blockIdx.x];
   const LevelDesc& d = descs[tk.desc];
+  if (skip && skip[d.sys]) return;
   const int n = d.n, m = d.m;
-  const SolveSmem S = solve_smem(sm, n, m);
+  const SolveSmem<TS> S = solve_smem<TS>(smraw, n, m);
   const int oG = n, oW = n + m;
   const SegGeom g = seg_geom(d, tk.seg);
   const int k = tk.seg;
-  auto rhs = [&](int j, double* dst) {  // this level's right-hand side of stage j
+  auto rhs = [&](int j, TS* dst) {  // this level's right-hand side of stage j
     if (d.level == 1) {
       const VecView v = level_vec(d, b, ldb, j);
-      load_vec(dst, S.ldV, v.p, v.ld, nullptr, n, nr);
+      load_vec(dst, S.ldV, v.p, v.ld, (const double*)nullptr, n, nr);
     } else {
       load_vec(dst, S.ldV, d.RA + (size_t)j * n * kRhsChunk, kRhsChunk,
                d.RB + (size_t)j * n * kRhsChunk, n, nr);
     }
   };
   // V_G <- 0, V_W <- rhs of the separator, t <- rhs of the first stage
-  for (int e = threadIdx.x; e < (2 * n + m) * S.ldV; e += blockDim.x) S.V[e] = 0.0;
+  for (int e = threadIdx.x; e < (2 * n + m) * S.ldV; e += blockDim.x) S.V[e] = TS(0);
   __syncthreads();
   if (g.hasW) rhs(g.f - 1, S.V + oW * S.ldV);
   rhs(g.f, S.t);
@@ -512,7 +645,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
     // [V_E; V_G; V_W] -= Z y over the active panel rows
     for (int e = threadIdx.x; e < (r1 - r0) * nr; e += blockDim.x) {
       const int r = r0 + e / nr, c = e - (e / nr) * nr;
-      double acc = 0.0;
+      TS acc = 0;
       for (int t2 = 0; t2 < n; ++t2) acc = fma(S.Z[r * S.ldZ + t2], S.t[t2 * S.ldV + c], acc);
       S.V[r * S.ldV + c] -= acc;
     }
@@ -521,7 +654,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
       for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
         const int r = e / nr, c = e - r * nr;
         S.t[r * S.ldV + c] = S.V[r * S.ldV + c];
-        S.V[r * S.ldV + c] = 0.0;
+        S.V[r * S.ldV + c] = TS(0);
       }
       __syncthreads();
     }
@@ -536,25 +669,25 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
   // x_g = R-hat^{-T} y_g, written to the caller's b; then the backward sweep.
   if (m) {
     double* bg = b + (size_t)d.rowG * ldb;
-    double* gv = S.t;
+    TS* gv = S.t;
     const int ldR = odd(m);
     for (int e = threadIdx.x; e < m * nr; e += blockDim.x) {
       const int r = e / nr, c = e - r * nr;
       double v = bg[(size_t)r * ldb + c];
       for (int p = 0; p < d.nyg_all; ++p) v += d.yg_all[((size_t)p * m + r) * kRhsChunk + c];
-      v += S.V[(oG + r) * S.ldV + c];
-      gv[r * S.ldV + c] = v;
+      v += (double)S.V[(oG + r) * S.ldV + c];
+      gv[r * S.ldV + c] = (TS)v;
     }
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {  // R-hat, columns scaled
       const int r = e / m, c = e - r * m;
-      S.L[r * ldR + c] = d.Rhat[e] * d.Rri[c];
+      S.L[r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[c]);
     }
-    for (int e = threadIdx.x; e < m; e += blockDim.x) S.rinv[e] = d.Rri[e];
+    for (int e = threadIdx.x; e < m; e += blockDim.x) S.rinv[e] = (TS)d.Rri[e];
     __syncthreads();
     trsv_lower(gv, S.ldV, S.L, ldR, S.rinv, m, nr);
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {  // R-hat, rows scaled
       const int r = e / m, c = e - r * m;
-      S.L[r * ldR + c] = d.Rhat[e] * d.Rri[r];
+      S.L[r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[r]);
     }
     __syncthreads();
     trsv_upper(gv, S.ldV, S.L, ldR, S.rinv, m, nr);
@@ -563,7 +696,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
   // V <- [0; x_g; -] for the backward sweep of the top level
   for (int e = threadIdx.x; e < (2 * n + m) * S.ldV; e += blockDim.x) {
     const int r = e / S.ldV;
-    if (r < oG || r >= oW) S.V[e] = 0.0;
+    if (r < oG || r >= oW) S.V[e] = TS(0);
     else S.V[e] = S.t[(r - oG) * S.ldV + (e - r * S.ldV)];
   }
   __syncthreads();
@@ -573,24 +706,27 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
 // Backward substitution (Algorithm 3, parallel phase) for one segment below
 // the top level: needs x_g (already in b), the separator solutions of the
 // next level (x at s_k and s_{k+1}), and this level's y.
+template <typename TS>
 __global__ void __launch_bounds__(kSolveThreads) k_backward(const LevelDesc* __restrict__ descs,
-                                                       const Task* __restrict__ tasks, double* b,
-                                                       int ldb, int nr) {
-  extern __shared__ double sm[];
+                                                            const Task* __restrict__ tasks, double* b,
+                                                            int ldb, int nr, const int* skip) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const Task tk = tasks[blockIdx.x];
   const LevelDesc& d = descs[tk.desc];
+  if (skip && skip[d.sys]) return;
   const int n = d.n, m = d.m;
-  const SolveSmem S = solve_smem(sm, n, m);
+  const SolveSmem<TS> S = solve_smem<TS>(smraw, n, m);
   const int oG = n, oW = n + m;
   const SegGeom g = seg_geom(d, tk.seg);
   const int k = tk.seg;
-  for (int e = threadIdx.x; e < (2 * n + m) * S.ldV; e += blockDim.x) S.V[e] = 0.0;
+  const double* none = nullptr;
+  for (int e = threadIdx.x; e < (2 * n + m) * S.ldV; e += blockDim.x) S.V[e] = TS(0);
   __syncthreads();
-  if (g.hasF) load_vec(S.V, S.ldV, d.Xnext + (size_t)k * n * kRhsChunk, kRhsChunk, nullptr, n, nr);
-  if (m) load_vec(S.V + oG * S.ldV, S.ldV, b + (size_t)d.rowG * ldb, ldb, nullptr, m, nr);
+  if (g.hasF) load_vec(S.V, S.ldV, d.Xnext + (size_t)k * n * kRhsChunk, kRhsChunk, none, n, nr);
+  if (m) load_vec(S.V + oG * S.ldV, S.ldV, b + (size_t)d.rowG * ldb, ldb, none, m, nr);
   if (g.hasW) {
-    load_vec(S.V + oW * S.ldV, S.ldV, d.Xnext + (size_t)(k - 1) * n * kRhsChunk, kRhsChunk, nullptr,
-             n, nr);
+    load_vec(S.V + oW * S.ldV, S.ldV, d.Xnext + (size_t)(k - 1) * n * kRhsChunk, kRhsChunk, none, n,
+             nr);
     __syncthreads();
     const VecView xs = level_vec(d, b, ldb, g.f - 1);  // this level's copy of x at s_k
     store_vec(xs.p, xs.ld, S.V + oW * S.ldV, S.ldV, n, nr);
@@ -599,46 +735,291 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(const LevelDesc* __r
   backward_segment(S, d, g, b, ldb, nr);
 }
 
-}  // namespace
+// ---------------------------------------------------------------------------
+// Iterative refinement support (FP64): x += c; c = b - Psi x with the blocks
+// of Eq. (3) (lower triangles of D and R read); eta = ||c||_inf /
+// (||Psi||_inf ||x||_inf + ||b||_inf), maxima taken over all right-hand
+// sides of the system together.
+// ---------------------------------------------------------------------------
 
-size_t factor_smem_bytes(int n, int m) { return (size_t)fac_layout(n, m).total * sizeof(double); }
-
-size_t solve_smem_bytes(int n, int m) { return (size_t)sol_layout(n, m).total * sizeof(double); }
-
-static int set_smem(const void* fn, size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  return (int)e;
+// x += c over the stage rows of one chunk; each system's first chunk also
+// does the g rows. c has leading dimension kRhsChunk.
+__global__ void k_axpy(const LevelDesc* __restrict__ descs, const ResTask* __restrict__ tasks,
+                       double* x, int ldx, const double* c, int nr, const int* skip) {
+  const ResTask tk = tasks[blockIdx.x];
+  const LevelDesc& d = descs[tk.desc];
+  if (skip && skip[d.sys]) return;
+  const int j1 = min(tk.j0 + kResChunk, d.N);
+  const long long row0 = d.offB + (long long)tk.j0 * d.n;
+  const int rows = (j1 - tk.j0) * d.n;
+  for (int e = threadIdx.x; e < rows * nr; e += blockDim.x) {
+    const int r = e / nr, col = e - r * nr;
+    x[(size_t)(row0 + r) * ldx + col] += c[(size_t)(row0 + r) * kRhsChunk + col];
+  }
+  if (tk.part == 0)
+    for (int e = threadIdx.x; e < d.m * nr; e += blockDim.x) {
+      const int r = e / nr, col = e - r * nr;
+      x[(size_t)(d.rowG + r) * ldx + col] += c[(size_t)(d.rowG + r) * kRhsChunk + col];
+    }
 }
 
-int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm,
+// c = b - Psi x for the stage rows of one chunk. The g rows are finished by
+// k_residual_final from the partials written here: sum_j G_j x_j over the
+// chunk, the largest |r|, |x|, |b| and |Psi| row sum, and the chunk's |G|
+// column sums for the g rows of ||Psi||_inf.
+__global__ void k_residual(const LevelDesc* __restrict__ descs, const ResTask* __restrict__ tasks,
+                           const double* __restrict__ uD, const double* __restrict__ uE,
+                           const double* __restrict__ uG, const double* __restrict__ b, int ldb,
+                           const double* __restrict__ x, int ldx, double* c, int nr, double* parts,
+                           const int* skip) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const ResTask tk = tasks[blockIdx.x];
+  const LevelDesc& d = descs[tk.desc];
+  if (skip && skip[d.sys]) return;
+  const int n = d.n, m = d.m, N = d.N;
+  const int j1 = min(tk.j0 + kResChunk, N);
+  const int ld = odd(n);
+  double* Ds = (double*)smraw;           // D_j      n x n
+  double* Ep = Ds + n * ld;              // E_{j-1}  n x n
+  double* En = Ep + n * ld;              // E_j      n x n
+  double* Gs = En + n * ld;              // G_j      m x n
+  double* xv = Gs + kMaxM * ld;          // x_{j-1}, x_j, x_{j+1}: 3 n x kRhsChunk
+  double* xg = xv + 3 * n * kRhsChunk;   // x_g      m x kRhsChunk
+  double* red = xg + kMaxM * kRhsChunk;  // reductions [4][blockDim]
+  const size_t nn = (size_t)n * n, mn = (size_t)m * n;
+  const double* D = uD + d.offD;
+  const double* E = uE ? uE + d.offE : nullptr;
+  const double* G = m ? uG + d.offG : nullptr;
+  const double* none = nullptr;
+  double* part = parts + (size_t)blockIdx.x * kResPartDoubles;
+  double* pg = part;  // g partials m x kRhsChunk
+  double mr = 0.0, mx = 0.0, mb = 0.0, mrow = 0.0;
+  double gabs[kMaxM];
+  for (int q = 0; q < kMaxM; ++q) gabs[q] = 0.0;
+  for (int e = threadIdx.x; e < m * kRhsChunk; e += blockDim.x) pg[e] = 0.0;
+  for (int e = threadIdx.x; e < m * nr; e += blockDim.x) {
+    const int r = e / nr, col = e - r * nr;
+    xg[r * kRhsChunk + col] = x[(size_t)(d.rowG + r) * ldx + col];
+  }
+  for (int j = tk.j0; j < j1; ++j) {
+    __syncthreads();
+    load_blk(Ds, ld, D + (size_t)j * nn, none, n, n, false);
+    load_blk(Ep, ld, (j > 0 && E) ? E + (size_t)(j - 1) * nn : none, none, n, n, false);
+    load_blk(En, ld, (j < N - 1 && E) ? E + (size_t)j * nn : none, none, n, n, false);
+    if (m) load_blk(Gs, ld, G + (size_t)j * mn, none, m, n, false);
+    for (int e = threadIdx.x; e < 3 * n * nr; e += blockDim.x) {
+      const int q = e / (n * nr), rem = e - q * n * nr, r = rem / nr, col = rem - r * nr;
+      const int jj = j - 1 + q;
+      xv[(q * n + r) * kRhsChunk + col] =
+          (jj >= 0 && jj < N) ? x[(size_t)(d.offB + (long long)jj * n + r) * ldx + col] : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
+      const int i = e / nr, col = e - i * nr;
+      double acc = 0.0, rs = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const double a = k <= i ? Ds[i * ld + k] : Ds[k * ld + i];  // lower triangle read
+        acc = fma(a, xv[(n + k) * kRhsChunk + col], acc);
+        acc = fma(Ep[i * ld + k], xv[k * kRhsChunk + col], acc);
+        acc = fma(En[k * ld + i], xv[(2 * n + k) * kRhsChunk + col], acc);
+        if (col == 0) rs += fabs(a) + fabs(Ep[i * ld + k]) + fabs(En[k * ld + i]);
+      }
+      for (int q = 0; q < m; ++q) {
+        acc = fma(Gs[q * ld + i], xg[q * kRhsChunk + col], acc);
+        if (col == 0) rs += fabs(Gs[q * ld + i]);
+      }
+      const size_t row = (size_t)(d.offB + (long long)j * n + i);
+      const double bv = b[row * ldb + col];
+      const double r = bv - acc;
+      c[row * kRhsChunk + col] = r;
+      mr = fmax(mr, fabs(r));
+      mb = fmax(mb, fabs(bv));
+      mx = fmax(mx, fabs(xv[(n + i) * kRhsChunk + col]));
+      mrow = fmax(mrow, rs);
+    }
+    // g partial: pg[q][col] += sum_i G_j[q][i] x_j[i][col]; |G| sums per g row
+    for (int e = threadIdx.x; e < m * nr; e += blockDim.x) {
+      const int q = e / nr, col = e - q * nr;
+      double acc = 0.0, ga = 0.0;
+      for (int i = 0; i < n; ++i) {
+        acc = fma(Gs[q * ld + i], xv[(n + i) * kRhsChunk + col], acc);
+        if (col == 0) ga += fabs(Gs[q * ld + i]);
+      }
+      pg[q * kRhsChunk + col] += acc;
+      if (col == 0) gabs[q] += ga;
+    }
+  }
+  double* rmr = red;
+  double* rmx = red + blockDim.x;
+  double* rmb = red + 2 * blockDim.x;
+  double* rrow = red + 3 * blockDim.x;
+  __syncthreads();
+  rmr[threadIdx.x] = mr; rmx[threadIdx.x] = mx; rmb[threadIdx.x] = mb; rrow[threadIdx.x] = mrow;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      rmr[threadIdx.x] = fmax(rmr[threadIdx.x], rmr[threadIdx.x + w]);
+      rmx[threadIdx.x] = fmax(rmx[threadIdx.x], rmx[threadIdx.x + w]);
+      rmb[threadIdx.x] = fmax(rmb[threadIdx.x], rmb[threadIdx.x + w]);
+      rrow[threadIdx.x] = fmax(rrow[threadIdx.x], rrow[threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  double* pm = part + kMaxM * kRhsChunk;
+  if (threadIdx.x == 0) { pm[0] = rmr[0]; pm[1] = rmx[0]; pm[2] = rmb[0]; pm[3] = rrow[0]; }
+  // the thread that handled (q, col 0) holds the |G| sums of g row q
+  for (int e = threadIdx.x; e < m * nr; e += blockDim.x) {
+    const int q = e / nr, col = e - q * nr;
+    if (col == 0) pm[4 + q] = gabs[q];
+  }
+}
+
+// Finish the g rows of one system from the chunk partials, then eta and the
+// convergence flag.
+__global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int* __restrict__ sys_desc,
+                                 const int* __restrict__ part0, const double* __restrict__ uG,
+                                 const double* __restrict__ uR, const double* __restrict__ b, int ldb,
+                                 const double* __restrict__ x, int ldx, double* c, int nr,
+                                 const double* __restrict__ parts, double tol, double* eta_out,
+                                 int* converged) {
+  __shared__ double red[4][256];
+  __shared__ double gsum[kMaxM];
+  const int s = blockIdx.x;
+  const LevelDesc& d = descs[sys_desc[s]];
+  if (converged && converged[s]) return;
+  const int m = d.m;
+  const int p0 = part0[s], np = (d.N + kResChunk - 1) / kResChunk;
+  const double* R = m ? uR + d.offR : nullptr;
+  double mr = 0.0, mx = 0.0, mb = 0.0, mrow = 0.0;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const double* pm = parts + (size_t)(p0 + p) * kResPartDoubles + kMaxM * kRhsChunk;
+    mr = fmax(mr, pm[0]); mx = fmax(mx, pm[1]); mb = fmax(mb, pm[2]); mrow = fmax(mrow, pm[3]);
+  }
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    double ga = 0.0;
+    for (int p = 0; p < np; ++p) ga += parts[(size_t)(p0 + p) * kResPartDoubles + kMaxM * kRhsChunk + 4 + q];
+    for (int k = 0; k < m; ++k) ga += fabs(k <= q ? R[q * m + k] : R[k * m + q]);
+    gsum[q] = ga;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * nr; e += blockDim.x) {
+    const int q = e / nr, col = e - q * nr;
+    double acc = 0.0;
+    for (int p = 0; p < np; ++p) acc += parts[(size_t)(p0 + p) * kResPartDoubles + q * kRhsChunk + col];
+    for (int k = 0; k < m; ++k)
+      acc = fma(k <= q ? R[q * m + k] : R[k * m + q], x[(size_t)(d.rowG + k) * ldx + col], acc);
+    const size_t row = (size_t)(d.rowG + q);
+    const double bv = b[row * ldb + col];
+    const double r = bv - acc;
+    c[row * kRhsChunk + col] = r;
+    mr = fmax(mr, fabs(r));
+    mb = fmax(mb, fabs(bv));
+    mx = fmax(mx, fabs(x[row * ldx + col]));
+  }
+  for (int q = threadIdx.x; q < m; q += blockDim.x) mrow = fmax(mrow, gsum[q]);
+  red[0][threadIdx.x] = mr; red[1][threadIdx.x] = mx; red[2][threadIdx.x] = mb; red[3][threadIdx.x] = mrow;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = fmax(red[q][threadIdx.x], red[q][threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double eta = red[0][0] / (red[3][0] * red[1][0] + red[2][0]);
+    eta_out[s] = eta;
+    if (converged && eta <= tol) converged[s] = 1;
+  }
+}
+
+int set_smem(const void* fn, size_t bytes) {
+  return (int)cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+size_t factor_smem_bytes(int n, int m, int mixed) {
+  return (size_t)fac_layout(n, m, mixed ? 4 : 8).total;
+}
+
+size_t solve_smem_bytes(int n, int m, int single) {
+  return (size_t)sol_layout(n, m, single ? 4 : 8).total;
+}
+
+size_t residual_smem_bytes(int n) {
+  const int ld = n | 1;
+  return sizeof(double) * ((size_t)3 * n * ld + (size_t)kMaxM * ld + 3 * (size_t)n * kRhsChunk +
+                           (size_t)kMaxM * kRhsChunk + 4 * 256);
+}
+
+int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
                   void* stream) {
   if (ntasks <= 0) return 0;
-  const size_t sm = factor_smem_bytes(maxn, maxm);
-  int e = set_smem((const void*)k_factor, sm);
+  const size_t sm = factor_smem_bytes(maxn, maxm, mixed);
+  const void* fn = mixed ? (const void*)k_factor<float> : (const void*)k_factor<double>;
+  int e = set_smem(fn, sm);
   if (e) return e;
-  k_factor<<<ntasks, kFactorThreads, sm, (cudaStream_t)stream>>>(d, t, D, E, G, R, info);
+  if (mixed)
+    k_factor<float><<<ntasks, kFactorThreads, sm, (cudaStream_t)stream>>>(d, t, D, E, G, R, info);
+  else
+    k_factor<double><<<ntasks, kFactorThreads, sm, (cudaStream_t)stream>>>(d, t, D, E, G, R, info);
   return (int)cudaGetLastError();
 }
 
-int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, double* b,
-                   int ldb, int nrhs, const double* R, void* stream) {
-  (void)R;
+int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
+                   double* b, int ldb, int nrhs, const int* skip, void* stream) {
   if (ntasks <= 0) return 0;
-  const size_t sm = solve_smem_bytes(maxn, maxm);
-  int e = set_smem((const void*)k_forward, sm);
+  const size_t sm = solve_smem_bytes(maxn, maxm, single);
+  const void* fn = single ? (const void*)k_forward<float> : (const void*)k_forward<double>;
+  int e = set_smem(fn, sm);
   if (e) return e;
-  k_forward<<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs);
+  if (single)
+    k_forward<float><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip);
+  else
+    k_forward<double><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip);
   return (int)cudaGetLastError();
 }
 
-int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, double* b,
-                    int ldb, int nrhs, void* stream) {
+int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
+                    double* b, int ldb, int nrhs, const int* skip, void* stream) {
   if (ntasks <= 0) return 0;
-  const size_t sm = solve_smem_bytes(maxn, maxm);
-  int e = set_smem((const void*)k_backward, sm);
+  const size_t sm = solve_smem_bytes(maxn, maxm, single);
+  const void* fn = single ? (const void*)k_backward<float> : (const void*)k_backward<double>;
+  int e = set_smem(fn, sm);
   if (e) return e;
-  k_backward<<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs);
+  if (single)
+    k_backward<float><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip);
+  else
+    k_backward<double><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip);
+  return (int)cudaGetLastError();
+}
+
+int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int ldx, const double* c,
+                int nr, const int* skip, void* stream) {
+  if (ntasks <= 0) return 0;
+  k_axpy<<<ntasks, 256, 0, (cudaStream_t)stream>>>(d, t, x, ldx, c, nr, skip);
+  return (int)cudaGetLastError();
+}
+
+int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, int maxn, const double* D,
+                    const double* E, const double* G, const double* b, int ldb, const double* x,
+                    int ldx, double* c, int nr, double* parts, const int* skip, void* stream) {
+  if (ntasks <= 0) return 0;
+  const size_t sm = residual_smem_bytes(maxn);
+  int e = set_smem((const void*)k_residual, sm);
+  if (e) return e;
+  k_residual<<<ntasks, 256, sm, (cudaStream_t)stream>>>(d, t, D, E, G, b, ldb, x, ldx, c, nr, parts,
+                                                        skip);
+  return (int)cudaGetLastError();
+}
+
+int launch_residual_final(const LevelDesc* d, const int* sys_desc, const int* part0, int count,
+                          const double* G, const double* R, const double* b, int ldb, const double* x,
+                          int ldx, double* c, int nr, const double* parts, double tol, double* eta_out,
+                          int* converged, void* stream) {
+  if (count <= 0) return 0;
+  k_residual_final<<<count, 256, 0, (cudaStream_t)stream>>>(d, sys_desc, part0, G, R, b, ldb, x, ldx, c,
+                                                            nr, parts, tol, eta_out, converged);
   return (int)cudaGetLastError();
 }
 

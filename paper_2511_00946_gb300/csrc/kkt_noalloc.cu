@@ -93,7 +93,7 @@ extern "C" kkt_status kkt_solve_noalloc(int N, int n, int m, int P, const double
   const size_t oSeg1 = cv.take(sizeof(int) * (P + 1)), oSeg2 = cv.take(sizeof(int) * 2);
   const size_t oInfo = cv.take(sizeof(kkt::Info));
   if (cv.off > kNoallocBytes) return KKT_ERR_CAPACITY;
-  if (kkt::factor_smem_bytes(n, m) > 227 * 1024) return KKT_ERR_ARG;
+  if (kkt::factor_smem_bytes(n, m, 0) > 227 * 1024) return KKT_ERR_ARG;
 
   std::lock_guard<std::mutex> lock(g_mu);
   int dev = 0;
@@ -174,15 +174,15 @@ extern "C" kkt_status kkt_solve_noalloc(int N, int n, int m, int P, const double
 
   const kkt::LevelDesc* ddesc = (const kkt::LevelDesc*)(base + oDesc);
   const kkt::Task* dtask = (const kkt::Task*)(base + oTask);
-  if (kkt::launch_factor(ddesc, dtask, P, n, m, D, E, G, R, dinfo, stream)) return KKT_ERR_CUDA;
-  if (two && kkt::launch_factor(ddesc, dtask + P, 1, n, m, D, E, G, R, dinfo, stream)) return KKT_ERR_CUDA;
+  if (kkt::launch_factor(ddesc, dtask, P, n, m, 0, D, E, G, R, dinfo, stream)) return KKT_ERR_CUDA;
+  if (two && kkt::launch_factor(ddesc, dtask + P, 1, n, m, 0, D, E, G, R, dinfo, stream)) return KKT_ERR_CUDA;
   for (int c0 = 0; c0 < nrhs; c0 += kkt::kRhsChunk) {
     const int nr = nrhs - c0 < kkt::kRhsChunk ? nrhs - c0 : kkt::kRhsChunk;
-    if (kkt::launch_forward(ddesc, dtask, P, n, m, b + c0, ldb, nr, nullptr, stream)) return KKT_ERR_CUDA;
+    if (kkt::launch_forward(ddesc, dtask, P, n, m, 0, b + c0, ldb, nr, nullptr, stream)) return KKT_ERR_CUDA;
     if (two) {
-      if (kkt::launch_forward(ddesc, dtask + P, 1, n, m, b + c0, ldb, nr, nullptr, stream))
+      if (kkt::launch_forward(ddesc, dtask + P, 1, n, m, 0, b + c0, ldb, nr, nullptr, stream))
         return KKT_ERR_CUDA;
-      if (kkt::launch_backward(ddesc, dtask + P + 1, P, n, m, b + c0, ldb, nr, stream))
+      if (kkt::launch_backward(ddesc, dtask + P + 1, P, n, m, 0, b + c0, ldb, nr, nullptr, stream))
         return KKT_ERR_CUDA;
     }
   }

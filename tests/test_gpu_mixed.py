@@ -1,0 +1,158 @@
+"""Mixed precision (FP64 pivots and Schur accumulators, FP32 panel trsm and
+Schur dot products, FP32 substitutions) with FP64 iterative refinement,
+through the C interface, against the FP64 oracle.
+
+The gate is the FP64 one: after refinement the normwise backward error is
+<= 1e-14 and the solution agrees with the oracle's to the accuracy the
+conditioning allows; the unrefined (raw FP32-factor) error is reported and
+bounded loosely.
+"""
+import numpy as np
+import pytest
+
+import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kkt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_00946_gb300 as k
+    return k
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def eta(orc, D, E, G, R, x, b):
+    r = b - orc.block_matvec(D, E, G, R, x)
+    A = orc.assemble_dense(D, E, G, R) if D.shape[0] * D.shape[1] <= 4000 else None
+    if A is not None:
+        nrm = np.abs(A).sum(axis=1).max()
+    else:
+        Ds = np.tril(D) + np.swapaxes(np.tril(D, -1), 1, 2)
+        rows = np.abs(Ds).sum(axis=2)
+        rows[1:] += np.abs(E).sum(axis=2)
+        rows[:-1] += np.abs(E).sum(axis=1)
+        if G.size:
+            rows += np.abs(G).sum(axis=1)
+        nrm = rows.max()
+        if G.size:
+            nrm = max(nrm, (np.abs(G).sum(axis=(0, 2)) + np.abs(np.tril(R) + np.tril(R, -1).T).sum(axis=1)).max())
+    return np.abs(r).max() / (nrm * np.abs(x).max() + np.abs(b).max())
+
+
+def run(kkt, D, E, G, R, b, levels, precision, sweeps, tol=1e-15):
+    import torch
+    N, n, _ = D.shape
+    m = R.shape[0]
+    h = kkt.kkt_create_plan(N, n, m, levels, kkt.KKT_PARTITION_BALANCED, precision)
+    try:
+        Dd, Ed, Gd, Rd = dev(D), dev(E), dev(G) if m else None, dev(R) if m else None
+        kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+        bd = dev(b)
+        xd = torch.zeros_like(bd)
+        kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, bd, xd, sweeps=sweeps, tol=tol)
+        raw = dev(b)
+        kkt.kkt_solve(h, raw)          # the unrefined solution with the same factor
+        torch.cuda.synchronize()
+        assert kkt.kkt_get_info(h)["status"] == 0
+        etas = [float(kkt.kkt_refine_eta(h, s)[0]) for s in range(sweeps)]
+        np.testing.assert_array_equal(bd.cpu().numpy(), b)   # b is read-only
+        return xd.cpu().numpy(), raw.cpu().numpy(), etas
+    finally:
+        kkt.kkt_destroy(h)
+
+
+@pytest.mark.parametrize("name,N,n,m,levels,kind", [
+    ("ipm n32 m8", 256, 32, 8, [16, 1], "ipm8"),
+    ("ipm n32 m8 deep", 512, 32, 8, [64, 16, 4, 1], "ipm8"),
+    ("ipm n12 m0", 150, 12, 0, [1], "ipm6"),
+    ("ipm n24 m4", 120, 24, 4, [8, 1], "ipm6"),
+    ("ipm n48 m4", 60, 48, 4, [6, 1], "ipm6"),
+    ("raceline n6 m2", 2048, 6, 2, [64, 8, 1], "race"),
+])
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_refinement_reaches_fp64(kkt, orc, name, N, n, m, levels, kind, precision):
+    if kind == "race":
+        D, E, G, R = gen.raceline(N, n, m, seed=3)
+    else:
+        D, E, G, R = gen.ipm(N, n, m, seed=3, sigma_decades=8.0 if kind == "ipm8" else 6.0)
+    b = gen.rhs(N * n + m, 1, seed=4)
+    x, raw, etas = run(kkt, D, E, G, R, b, levels, precision, sweeps=10, tol=0.0)
+    e = eta(orc, D, E, G, R, x, b)
+    assert e <= 1e-14, (name, e, etas)
+    assert etas[-1] <= 1e-14, etas
+    e_raw = eta(orc, D, E, G, R, raw, b)
+    assert e_raw <= 1e-5, e_raw                 # raw FP32-factor solve: loose bound, reported
+    xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b)
+    ro = b - orc.block_matvec(D, E, G, R, xo)
+    r = b - orc.block_matvec(D, E, G, R, x)
+    assert np.linalg.norm(r) <= max(1e-10 * np.linalg.norm(b), 10 * np.linalg.norm(ro))
+    assert np.abs(x - xo).max() <= 1e-5 * np.abs(xo).max()
+
+
+def test_refinement_multiple_rhs_and_early_stop(kkt, orc):
+    """17 right-hand sides (two chunks); once converged the remaining sweeps
+    leave x unchanged on the device."""
+    import torch
+    N, n, m = 128, 16, 4
+    D, E, G, R = gen.ipm(N, n, m, seed=8)
+    b = gen.rhs(N * n + m, 17, seed=9)
+    h = kkt.kkt_create_plan(N, n, m, [8, 1], kkt.KKT_PARTITION_BALANCED, kkt.KKT_MIXED_FP32)
+    try:
+        Dd, Ed, Gd, Rd, bd = dev(D), dev(E), dev(G), dev(R), dev(b)
+        kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+        x8 = torch.zeros_like(bd)
+        kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, bd, x8, sweeps=8, tol=1e-13)
+        x3 = torch.zeros_like(bd)
+        kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, bd, x3, sweeps=3, tol=1e-13)
+        torch.cuda.synchronize()
+        x8, x3 = x8.cpu().numpy(), x3.cpu().numpy()
+    finally:
+        kkt.kkt_destroy(h)
+    np.testing.assert_array_equal(x8, x3)          # converged within 3 sweeps, then stopped
+    for c in range(17):
+        assert eta(orc, D, E, G, R, x8[:, c], b[:, c]) <= 1e-13
+
+
+def test_fp64_handle_refinement(kkt, orc):
+    """With an FP64 factor one correction sweep is the plain solve plus a
+    residual check, and refinement keeps the backward error at the floor."""
+    N, n, m = 200, 24, 4
+    D, E, G, R = gen.ipm(N, n, m, seed=12)
+    b = gen.rhs(N * n + m, 1, seed=13)
+    x, raw, etas = run(kkt, D, E, G, R, b, [13, 1], 0, sweeps=2)
+    np.testing.assert_allclose(x, raw, rtol=0, atol=1e-9 * np.abs(raw).max())
+    assert eta(orc, D, E, G, R, x, b) <= 1e-14
+
+
+def test_mixed_uneven_batch(kkt, orc):
+    import torch
+    sy = gen.uneven_batch(10, seed=5, N_range=(20, 60))
+    Ns = [s[0].shape[0] for s in sy]
+    ns = [s[0].shape[1] for s in sy]
+    ms = [s[3].shape[0] for s in sy]
+    h = kkt.kkt_batch_create(Ns, ns, ms, None, kkt.KKT_MIXED_FP32)
+    try:
+        off = kkt.kkt_batch_offsets(h, len(sy))
+        cat = lambda i: dev(np.concatenate([s[i].ravel() for s in sy] + [np.zeros(1)]))
+        bs = [gen.rhs(N * n + m, 1, seed=i) for i, (N, n, m) in enumerate(zip(Ns, ns, ms))]
+        Dd, Ed, Gd, Rd = cat(0), cat(1), cat(2), cat(3)
+        b = dev(np.concatenate(bs))
+        x = torch.zeros_like(b)
+        kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+        kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, b, x, sweeps=6, tol=1e-15)
+        torch.cuda.synchronize()
+        x = x.cpu().numpy()
+        etas = kkt.kkt_refine_eta(h, 5, len(sy))
+    finally:
+        kkt.kkt_destroy(h)
+    for i, s in enumerate(sy):
+        xi = x[off["b"][i]:off["b"][i + 1]]
+        assert eta(orc, *s, xi, bs[i]) <= 1e-14, (i, etas)
