@@ -174,6 +174,25 @@ kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, co
                              const double* R, const double* b, int ldb, double* x, int ldx, int nrhs,
                              int sweeps, double tol, void* stream);
 
+/* Adjoint of the solve, for a loss L(x) with x = Psi^{-1} b: given x (the
+ * solution, ldx) and xbar = dL/dx (ldxb), writes bbar = dL/db = Psi^{-1} xbar
+ * (ldbb) with the current factor (refined with `sweeps` sweeps of
+ * kkt_solve_refined when the factor is mixed; D, E, G, R are then required)
+ * and the gradients with respect to the stored blocks, in the layout of the
+ * inputs (dPsi = -bbar x^T restricted to the blocks, summed over the nrhs
+ * columns; a symmetric pair of entries is one parameter):
+ *   dD_j[r][c] = -(bbar_r x_c + bbar_c x_r) for r > c, -bbar_r x_r for r = c,
+ *                0 above the diagonal (the upper triangle is not read)
+ *   dE_j = -(bbar_{j+1} x_j^T + x_{j+1} bbar_j^T)
+ *   dG_j = -(bbar_g x_j^T + x_g bbar_j^T)
+ *   dR   like dD on the g rows.
+ * All pointers are device pointers; dE may be NULL when every N = 1, dG and
+ * dR when every m = 0. Asynchronous on `stream`. */
+kkt_status kkt_solve_adjoint(kkt_handle* h, const double* D, const double* E, const double* G,
+                             const double* R, const double* x, int ldx, const double* xbar, int ldxb,
+                             double* bbar, int ldbb, int nrhs, double* dD, double* dE, double* dG,
+                             double* dR, int sweeps, void* stream);
+
 /* eta of every system after sweep `sweep` (0-based) of the last
  * kkt_solve_refined (last right-hand-side chunk); eta[count]. Synchronizes.
  * Values after a system converged are those of its converging sweep. */

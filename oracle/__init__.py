@@ -341,3 +341,31 @@ def block_matvec(D, E, G, R, x):
         out[:N * n] += np.einsum("jba,br->jar", G, xg).reshape(N * n, -1)
         out[N * n:] = np.einsum("jab,jbr->ar", G, Xs) + Rs @ xg
     return out.reshape(x.shape)
+
+
+def adjoint(D, E, G, R, x, xbar):
+    """Adjoint of x = Psi^{-1} b (definition): bbar = Psi^{-1} xbar (Psi is
+    symmetric) with the O2 solve, and dL/dPsi = -bbar x^T restricted to the
+    stored blocks, a symmetric pair of entries counted as one parameter
+    (dD, dR lower-triangular), summed over the columns of x."""
+    D = _f64(D)
+    N, n, _ = D.shape
+    m = 0 if R is None or np.size(R) == 0 else np.asarray(R).shape[0]
+    bbar = seq_solve(seq_factor(D, E, G, R), xbar)
+    X = np.asarray(x, dtype=np.float64).reshape(x.shape[0], -1)
+    B = bbar.reshape(bbar.shape[0], -1)
+    Xs, Bs = X[:N * n].reshape(N, n, -1), B[:N * n].reshape(N, n, -1)
+    full = -np.einsum("jrq,jcq->jrc", Bs, Xs)
+    dD = np.tril(full + np.swapaxes(full, 1, 2))
+    idx = np.arange(n)
+    dD[:, idx, idx] = full[:, idx, idx]
+    dE = -(np.einsum("jrq,jcq->jrc", Bs[1:], Xs[:-1]) + np.einsum("jrq,jcq->jrc", Xs[1:], Bs[:-1]))
+    dG = np.zeros((N, m, n))
+    dR = np.zeros((m, m))
+    if m:
+        xg, bg = X[N * n:], B[N * n:]
+        dG = -(np.einsum("rq,jcq->jrc", bg, Xs) + np.einsum("rq,jcq->jrc", xg, Bs))
+        fr = -bg @ xg.T
+        dR = np.tril(fr + fr.T)
+        dR[np.arange(m), np.arange(m)] = np.diag(fr)
+    return bbar, dD, dE, dG, dR

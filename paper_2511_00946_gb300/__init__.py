@@ -25,7 +25,8 @@ RHS_CHUNK = 16
 
 EXPORTED = [
     "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_destroy",
-    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_solve_refined", "kkt_refine_eta", "kkt_get_info",
+    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta",
+    "kkt_get_info",
     "kkt_get_factor", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
 ]
 
@@ -62,6 +63,7 @@ _sig = {
     "kkt_solve": [_vp, _vp, _i, _i, _vp],
     "kkt_solve_refined": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i, _i, _i, ctypes.c_double, _vp],
     "kkt_refine_eta": [_vp, _i, _dp],
+    "kkt_solve_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _vp, _vp, _i, _vp],
     "kkt_get_info": [_vp, _ip, _i],
     "kkt_get_factor": [_vp, _i, _dp, _dp, _dp, _dp, _dp, _dp],
     "kkt_set_launch_events": [_vp, ctypes.POINTER(_vp), _i],
@@ -206,6 +208,17 @@ def kkt_solve_refined(h: int, D, E, G, R, b, x, nrhs: int | None = None, ldb: in
                                   sweeps, float(tol), _stream(stream)), "kkt_solve_refined")
 
 
+def kkt_solve_adjoint(h: int, x, xbar, bbar, dD, dE, dG, dR, D=None, E=None, G=None, R=None,
+                      sweeps: int = 4, stream=None):
+    """bbar = Psi^{-1} xbar and the block gradients of a loss with x = Psi^{-1} b
+    (see include/kkt.h); x, xbar, bbar are (rows,) or (rows, nrhs) tensors."""
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    ld = lambda t: 1 if t.dim() == 1 else t.shape[1]
+    _check(_lib.kkt_solve_adjoint(h, _ptr(D), _ptr(E), _ptr(G), _ptr(R), _ptr(x), ld(x), _ptr(xbar), ld(xbar),
+                                  _ptr(bbar), ld(bbar), nrhs, _ptr(dD), _ptr(dE), _ptr(dG), _ptr(dR), sweeps,
+                                  _stream(stream)), "kkt_solve_adjoint")
+
+
 def kkt_refine_eta(h: int, sweep: int, count: int = 1) -> np.ndarray:
     out = np.zeros(count)
     _check(_lib.kkt_refine_eta(h, sweep, out.ctypes.data_as(_dp)), "kkt_refine_eta")
@@ -274,6 +287,59 @@ def kkt_solve_noalloc(N: int, n: int, m: int, P: int, D, E, G, R, b, nrhs: int |
                                   _stream(stream)), "kkt_solve_noalloc")
 
 
+# ---------------------------------------------------------------- differentiable solve
+
+def _autograd_function():
+    import torch
+
+    class KKTSolveFunction(torch.autograd.Function):
+        """x = Psi^{-1} b through the solver's handle: forward = kkt_factor +
+        kkt_solve (kkt_solve_refined for a mixed handle), backward =
+        kkt_solve_adjoint with the stored factor. The handle must not be
+        refactored between the forward and the backward pass."""
+
+        @staticmethod
+        def forward(ctx, D, E, G, R, b, solver):
+            kkt_factor(solver.h, D, E, G, R)
+            x = torch.empty_like(b)
+            if solver.mixed:
+                kkt_solve_refined(solver.h, D, E, G, R, b, x, sweeps=solver.sweeps, tol=0.0)
+            else:
+                x.copy_(b)
+                kkt_solve(solver.h, x)
+            ctx.save_for_backward(D, E, G, R, x)
+            ctx.solver = solver
+            return x
+
+        @staticmethod
+        def backward(ctx, xbar):
+            D, E, G, R, x = ctx.saved_tensors
+            solver = ctx.solver
+            xbar = xbar.contiguous()
+            bbar = torch.empty_like(x)
+            dD = torch.empty_like(D)
+            dE = torch.empty_like(E) if E is not None else None
+            dG = torch.empty_like(G) if G is not None else None
+            dR = torch.empty_like(R) if R is not None else None
+            kkt_solve_adjoint(solver.h, x, xbar, bbar, dD, dE, dG, dR, D, E, G, R, sweeps=solver.sweeps)
+            return dD, dE, dG, dR, bbar, None
+
+    return KKTSolveFunction
+
+
+_KKTSolveFunction = None
+
+
+def kkt_solve_differentiable(solver, D, E, G, R, b):
+    """x = Psi^{-1} b, differentiable with respect to D, E, G, R and b (FP64
+    CUDA tensors in the layout of include/kkt.h; the upper triangles of D and
+    R are not read and receive zero gradient)."""
+    global _KKTSolveFunction
+    if _KKTSolveFunction is None:
+        _KKTSolveFunction = _autograd_function()
+    return _KKTSolveFunction.apply(D, E, G, R, b, solver)
+
+
 # ---------------------------------------------------------------- convenience
 
 class KKTSolver:
@@ -281,8 +347,11 @@ class KKTSolver:
     CUDA tensors in the layout of include/kkt.h and enqueue on the current
     torch stream."""
 
-    def __init__(self, N, n, m, P=1, precision=KKT_FP64, levels=None, partition=KKT_PARTITION_BALANCED):
+    def __init__(self, N, n, m, P=1, precision=KKT_FP64, levels=None, partition=KKT_PARTITION_BALANCED,
+                 sweeps=4):
         self.N, self.n, self.m = N, n, m
+        self.mixed = precision != KKT_FP64
+        self.sweeps = sweeps
         if levels is not None:
             self.h = kkt_create_plan(N, n, m, levels, partition, precision)
         else:

@@ -622,6 +622,36 @@ kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, co
   return KKT_OK;
 }
 
+kkt_status kkt_solve_adjoint(kkt_handle* h, const double* D, const double* E, const double* G,
+                             const double* R, const double* x, int ldx, const double* xbar, int ldxb,
+                             double* bbar, int ldbb, int nrhs, double* dD, double* dE, double* dG,
+                             double* dR, int sweeps, void* stream) {
+  if (!h || !x || !xbar || !bbar || nrhs < 1 || ldx < nrhs || ldxb < nrhs || ldbb < nrhs || !dD)
+    return KKT_ERR_ARG;
+  if (h->tot_E > 0 && !dE) return KKT_ERR_ARG;
+  if (h->maxm > 0 && (!dG || !dR)) return KKT_ERR_ARG;
+  if (!h->factored) return KKT_ERR_STATE;
+  bool mixed = false;
+  for (int v : h->level_mixed) mixed = mixed || v;
+  // bbar = Psi^{-1} xbar (Psi is symmetric): the same factor; refined when it is mixed
+  if (mixed) {
+    if (!D || (h->tot_E > 0 && !E) || (h->maxm > 0 && (!G || !R))) return KKT_ERR_ARG;
+    const kkt_status st = kkt_solve_refined(h, D, E, G, R, xbar, ldxb, bbar, ldbb, nrhs,
+                                            sweeps < 1 ? 4 : sweeps, 0.0, stream);
+    if (st != KKT_OK) return st;
+  } else {
+    if (cudaMemcpy2DAsync(bbar, sizeof(double) * ldbb, xbar, sizeof(double) * ldxb, sizeof(double) * nrhs,
+                          h->tot_B, cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess)
+      return KKT_ERR_CUDA;
+    const kkt_status st = kkt_solve(h, bbar, nrhs, ldbb, stream);
+    if (st != KKT_OK) return st;
+  }
+  if (kkt::launch_adjoint_grad(h->ddesc, h->dres, (int)h->hres.size(), x, ldx, bbar, ldbb, nrhs, dD, dE,
+                               dG, dR, stream))
+    return KKT_ERR_CUDA;
+  return KKT_OK;
+}
+
 kkt_status kkt_refine_eta(kkt_handle* h, int sweep, double* eta) {
   if (!h || !eta || sweep < 0 || sweep >= kMaxSweeps) return KKT_ERR_ARG;
   if (cudaMemcpy(eta, h->deta + (size_t)sweep * h->count, sizeof(double) * h->count,

@@ -189,6 +189,10 @@ int launch_residual_final(const LevelDesc* d, const int* sys_desc, const int* pa
                           const double* G, const double* R, const double* b, int ldb, const double* x,
                           int ldx, double* c, int nr, const double* parts, double tol, double* eta_out,
                           int* converged, void* stream);
+// adjoint block gradients (symmetric-entry convention) per residual task
+int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const double* x, int ldx,
+                        const double* xb, int ldxb, int nr, double* dD, double* dE, double* dG,
+                        double* dR, void* stream);
 size_t factor_smem_bytes(int maxn, int maxm, int mixed);
 size_t solve_smem_bytes(int maxn, int maxm, int single);
 size_t residual_smem_bytes(int maxn);

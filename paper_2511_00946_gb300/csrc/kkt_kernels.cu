@@ -931,6 +931,61 @@ __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int*
   }
 }
 
+// Gradients of a loss L(x), x = Psi^{-1} b, with respect to the stored
+// blocks, given x and bbar = Psi^{-1} xbar (xbar = dL/dx): dPsi = -bbar x^T
+// restricted to the blocks, each symmetric pair of entries perturbed
+// together, summed over the right-hand sides:
+//   dD_j[r][c] = -(bbar_r x_c + bbar_c x_r) (r > c), -bbar_r x_r (r = c), 0 above
+//   dE_j       = -(bbar_{j+1} x_j^T + x_{j+1} bbar_j^T)
+//   dG_j       = -(bbar_g x_j^T + x_g bbar_j^T),   dR like dD on the g rows.
+__global__ void k_adjoint_grad(const LevelDesc* __restrict__ descs, const ResTask* __restrict__ tasks,
+                               const double* __restrict__ x, int ldx, const double* __restrict__ xb,
+                               int ldxb, int nr, double* dD, double* dE, double* dG, double* dR) {
+  const ResTask tk = tasks[blockIdx.x];
+  const LevelDesc& d = descs[tk.desc];
+  const int n = d.n, m = d.m, N = d.N;
+  const int j1 = min(tk.j0 + kResChunk, N);
+  const size_t nn = (size_t)n * n, mn = (size_t)m * n;
+  auto xr = [&](long long row, int c) { return x[(size_t)row * ldx + c]; };
+  auto br = [&](long long row, int c) { return xb[(size_t)row * ldxb + c]; };
+  for (int j = tk.j0; j < j1; ++j) {
+    const long long rj = d.offB + (long long)j * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int r = e / n, c = e - r * n;
+      double v = 0.0;
+      if (c < r)
+        for (int q = 0; q < nr; ++q) v -= br(rj + r, q) * xr(rj + c, q) + br(rj + c, q) * xr(rj + r, q);
+      else if (c == r)
+        for (int q = 0; q < nr; ++q) v -= br(rj + r, q) * xr(rj + r, q);
+      dD[d.offD + (size_t)j * nn + e] = v;
+    }
+    if (j < N - 1)
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        double v = 0.0;
+        for (int q = 0; q < nr; ++q) v -= br(rj + n + r, q) * xr(rj + c, q) + xr(rj + n + r, q) * br(rj + c, q);
+        dE[d.offE + (size_t)j * nn + e] = v;
+      }
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+      const int r = e / n, c = e - r * n;
+      double v = 0.0;
+      for (int q = 0; q < nr; ++q) v -= br(d.rowG + r, q) * xr(rj + c, q) + xr(d.rowG + r, q) * br(rj + c, q);
+      dG[d.offG + (size_t)j * mn + e] = v;
+    }
+  }
+  if (tk.part == 0)
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int r = e / m, c = e - r * m;
+      double v = 0.0;
+      if (c < r)
+        for (int q = 0; q < nr; ++q)
+          v -= br(d.rowG + r, q) * xr(d.rowG + c, q) + br(d.rowG + c, q) * xr(d.rowG + r, q);
+      else if (c == r)
+        for (int q = 0; q < nr; ++q) v -= br(d.rowG + r, q) * xr(d.rowG + r, q);
+      dR[d.offR + e] = v;
+    }
+}
+
 int set_smem(const void* fn, size_t bytes) {
   return (int)cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
@@ -998,6 +1053,14 @@ int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int
                 int nr, const int* skip, void* stream) {
   if (ntasks <= 0) return 0;
   k_axpy<<<ntasks, 256, 0, (cudaStream_t)stream>>>(d, t, x, ldx, c, nr, skip);
+  return (int)cudaGetLastError();
+}
+
+int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const double* x, int ldx,
+                        const double* xb, int ldxb, int nr, double* dD, double* dE, double* dG,
+                        double* dR, void* stream) {
+  if (ntasks <= 0) return 0;
+  k_adjoint_grad<<<ntasks, 256, 0, (cudaStream_t)stream>>>(d, t, x, ldx, xb, ldxb, nr, dD, dE, dG, dR);
   return (int)cudaGetLastError();
 }
 

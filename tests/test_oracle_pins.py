@@ -243,3 +243,45 @@ def test_batch_matches_single(orc):
     for s in range(5):
         xs = orc.seq_solve(orc.seq_factor(*sysl[s]), b[s])
         np.testing.assert_array_equal(x[s], xs)
+
+
+def test_adjoint_matches_central_differences(orc):
+    """The oracle adjoint (bbar = Psi^{-1} xbar, dPsi = -bbar x^T on the
+    symmetric block parameters) against central differences of
+    L = 1/2 ||Psi^{-1} b||^2 computed with the O2 solve."""
+    N, n, m = 6, 3, 2
+    D, E, G, R, _ = gen.known_factor(N, n, m, seed=4)
+    b = gen.rhs(N * n + m, 1, seed=5)
+
+    def loss(D, E, G, R, b):
+        x = orc.seq_solve(orc.seq_factor(D, E, G, R), b)
+        return 0.5 * float(x @ x), x
+
+    L0, x = loss(D, E, G, R, b)
+    bbar, dD, dE, dG, dR = orc.adjoint(D, E, G, R, x, x)
+    h = 1e-6
+    rng = np.random.default_rng(0)
+
+    def fd(arr_idx, pos):
+        args = [D.copy(), E.copy(), G.copy(), R.copy(), b.copy()]
+        args[arr_idx][pos] += h
+        lp, _ = loss(*args)
+        args[arr_idx][pos] -= 2 * h
+        lm, _ = loss(*args)
+        return (lp - lm) / (2 * h)
+
+    for _ in range(12):
+        j, r = rng.integers(N), rng.integers(n)
+        c = rng.integers(r + 1)                       # lower triangle of D
+        assert fd(0, (j, r, c)) == pytest.approx(dD[j, r, c], rel=1e-6, abs=1e-9)
+        j, r, c = rng.integers(N - 1), rng.integers(n), rng.integers(n)
+        assert fd(1, (j, r, c)) == pytest.approx(dE[j, r, c], rel=1e-6, abs=1e-9)
+        j, r, c = rng.integers(N), rng.integers(m), rng.integers(n)
+        assert fd(2, (j, r, c)) == pytest.approx(dG[j, r, c], rel=1e-6, abs=1e-9)
+        r = rng.integers(m)
+        c = rng.integers(r + 1)
+        assert fd(3, (r, c)) == pytest.approx(dR[r, c], rel=1e-6, abs=1e-9)
+        i = rng.integers(N * n + m)
+        assert fd(4, (i,)) == pytest.approx(bbar[i], rel=1e-6, abs=1e-9)
+    # the upper triangles are not parameters
+    assert np.all(np.triu(dD, 1) == 0) and np.all(np.triu(dR, 1) == 0)
