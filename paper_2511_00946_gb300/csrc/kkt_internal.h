@@ -114,7 +114,7 @@ struct Info {
 // them. zb = bytes per panel element (8: FP64 path, 4: mixed). Odd leading
 // dimensions keep row- and column-wise accesses free of bank conflicts.
 struct FacLayout {
-  int q, R, ldD, ldZ, ldT, oDfac, oM, oRinv, oRinvZ, oZ, oT, total;
+  int q, R, ldD, ldZ, ldT, oDfac, oM, oRinv, oRinvZ, oZ, oT, oTab, total;
 };
 __host__ __device__ inline int kkt_align16(int b) { return (b + 15) & ~15; }
 __host__ __device__ inline FacLayout fac_layout(int n, int m, int zb) {
@@ -130,11 +130,14 @@ __host__ __device__ inline FacLayout fac_layout(int n, int m, int zb) {
   L.oRinvZ = L.oRinv + kkt_align16(8 * L.q);
   L.oZ = L.oRinvZ + kkt_align16(zb * L.q);
   L.oT = L.oZ + kkt_align16(zb * L.R * L.ldZ);
-  L.total = L.oT + kkt_align16(8 * L.R * L.ldT);
+  L.oTab = L.oT + kkt_align16(8 * L.R * L.ldT);  // potrf element table, q(q-1)/2 ints
+  L.total = L.oTab + kkt_align16(4 * (L.q * (L.q - 1) / 2 + 1));
   return L;
 }
+// The substitution kernels double-buffer the factor blocks (L, rinv, Z) so
+// that the next stage's blocks stream in while the current stage is solved.
 struct SolLayout {
-  int q, R, ldL, ldZ, ldV, oL, oRinv, oZ, oV, oT, total;
+  int q, R, ldL, ldZ, ldV, oL[2], oRinv[2], oZ[2], oV, oT, total;
 };
 __host__ __device__ inline SolLayout sol_layout(int n, int m, int sb) {
   SolLayout L;
@@ -143,10 +146,16 @@ __host__ __device__ inline SolLayout sol_layout(int n, int m, int sb) {
   L.ldL = L.q | 1;
   L.ldZ = n | 1;
   L.ldV = kRhsChunk | 1;
-  L.oL = 0;
-  L.oRinv = L.oL + kkt_align16(sb * L.q * L.ldL);
-  L.oZ = L.oRinv + kkt_align16(sb * L.q);
-  L.oV = L.oZ + kkt_align16(sb * L.R * L.ldZ);
+  int o = 0;
+  for (int b = 0; b < 2; ++b) {
+    L.oL[b] = o;
+    o += kkt_align16(sb * L.q * L.ldL);
+    L.oRinv[b] = o;
+    o += kkt_align16(sb * L.q);
+    L.oZ[b] = o;
+    o += kkt_align16(sb * L.R * L.ldZ);
+  }
+  L.oV = o;
   L.oT = L.oV + kkt_align16(sb * L.R * L.ldV);
   L.total = L.oT + kkt_align16(sb * L.q * L.ldV);
   return L;

@@ -48,18 +48,24 @@ __device__ void record_breakdown(Info* info, int sys, int stage, int level) {
 // dst (rows x cols, smem, ld) <- A (+ B) from global row-major [rows][cols],
 // or the transpose of A (+ B) given as [cols][rows] when `trans`. A null A
 // loads zeros. Coalesced over the global array.
+// The three source cases are separate loops: a predicated-off FP64 add still
+// holds the FP64 pipe on this part.
 template <typename T>
 __device__ void load_blk(T* dst, int ld, const double* A, const double* B, int rows, int cols,
                          bool trans) {
   const int tot = rows * cols;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+  auto at = [&](int e) {
     int r, c;
     if (trans) { c = e / rows; r = e - c * rows; }
     else { r = e / cols; c = e - r * cols; }
-    double v = 0.0;
-    if (A) v = A[e];
-    if (B) v += B[e];
-    dst[r * ld + c] = (T)v;
+    return r * ld + c;
+  };
+  if (A && B) {
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) dst[at(e)] = (T)(A[e] + B[e]);
+  } else if (A) {
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) dst[at(e)] = (T)A[e];
+  } else {
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) dst[at(e)] = T(0);
   }
 }
 
@@ -98,17 +104,42 @@ __device__ void copy_blk(TD* dst, int ldd, const TS* src, int lds, int rows, int
 // leaves an error of order e^3 (below 2^-62), so the result is within a few
 // units in the last place; finally r 2^-k. Falls back to 1/sqrt for
 // subnormal or huge d and returns NaN when d is not positive.
+// Rare path of pivot_rsqrt (zero, negative, NaN, subnormal or huge pivots),
+// kept out of line.
+__device__ __noinline__ double pivot_rsqrt_slow(double d) {
+  return (d > 0.0 && d < 1e300) ? 1.0 / sqrt(d) : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// True unless d is a positive finite number (integer test on the bits: an
+// FP64 comparison would occupy the scarce FP64 pipe).
+__device__ __forceinline__ bool not_positive(double d) {
+  const long long bits = __double_as_longlong(d);
+  return bits <= 0 || bits >= 0x7ff0000000000000LL;
+}
+
+// 1/sqrt(d) for a pivot d > 0 in four dependent FP64 operations instead of a
+// square root and a division (each several hundred cycles on this part).
+// The exponent is split off with integer operations so that d' = d 4^-k lies
+// in [1, 4); the single-precision hardware estimate r ~ 1/sqrt(d') (relative
+// error below 2^-21) is formed from d' and converted back with bit
+// manipulation only, then refined by one step of Halley's method for
+// f(r) = r^-2 - d': with e = 1 - d' r^2, r <- r (1 + e/2 + 3 e^2 / 8), which
+// leaves an error of order e^3 (below 2^-62), so the result is within a few
+// units in the last place; finally r 2^-k. Zero, negative, NaN, subnormal or
+// huge d take an out-of-line path (NaN when d is not positive). The range
+// tests are integer tests: FP64 comparisons would occupy the FP64 pipe.
 __device__ __forceinline__ double pivot_rsqrt(double d) {
   const long long bits = __double_as_longlong(d);
-  const int ex = (int)((bits >> 52) & 0x7ff) - 1023;
-  if (!(d > 0.0) || ex <= -1022 || ex >= 1023)
-    return (d > 0.0 && d < 1e300) ? 1.0 / sqrt(d) : __longlong_as_double(0x7ff8000000000000LL);
-  const int k = ex >> 1;                                   // floor(ex / 2)
+  const int ef = (int)((bits >> 52) & 0x7ff);  // biased exponent; sign handled by bits > 0
+  if (bits <= 0 || ef <= 1 || ef >= 2046) return pivot_rsqrt_slow(d);
+  const int k = (ef - 1023) >> 1;                            // floor(ex / 2)
   const long long dbits = bits - ((long long)(2 * k) << 52);  // d' in [1, 4)
   const double dp = __longlong_as_double(dbits);
   // d' truncated to single precision (exponent 0 or 1, top 23 mantissa bits)
   const int fbits = ((int)((dbits >> 52) & 0x7ff) - 1023 + 127) << 23 | (int)((dbits >> 29) & 0x7fffff);
-  const int rb = __float_as_int(rsqrtf(__int_as_float(fbits)));  // in (0.5, 1]: normal
+  float rf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__int_as_float(fbits)));
+  const int rb = __float_as_int(rf);  // in (0.5, 1]: normal
   double r = __longlong_as_double((long long)(((rb >> 23) & 0xff) - 127 + 1023) << 52 |
                                   (long long)(rb & 0x7fffff) << 29);
   const double e = fma(-dp * r, r, 1.0);
@@ -120,62 +151,78 @@ __device__ __forceinline__ void group_bar(int id, int nthreads) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// In-place lower Cholesky of A (n x n, FP64) by the first kPotrfThreads
-// threads (one warp per FP64 sub-pipe), synchronized with a named barrier;
-// the CTA's other threads wait at the closing __syncthreads. Writes
-// rinv[j] = 1 / L_jj. On a pivot that is not positive it sets *bad (first
-// column + 1) and carries on (NaNs propagate; no trap).
-// Right-looking, two barriers per column. Each thread owns a fixed list of
-// strictly-lower elements (i, k), ordered by k descending so that the
-// trailing triangle of column j is the prefix of length (n-1-j)(n-j)/2 for
-// every j; the thread that updates the next diagonal element computes its
-// pivot at once (look-ahead), overlapping it with the other updates.
-constexpr int kPotrfThreads = 128;
-constexpr int kPotrfPer = (kMaxN * (kMaxN - 1) / 2 + kPotrfThreads - 1) / kPotrfThreads;
+// Element table of the trailing updates of an n x n Cholesky: the pairs
+// (i, k) with 2 <= k <= i < n ordered by k descending (packed i << 16 | k),
+// so that the updates applied by column j form the prefix of length
+// (n-2-j)(n-1-j)/2. Built once per CTA (it depends on n only).
+__device__ void potrf_table(int* tab, int n) {
+  const int np = (n - 2) * (n - 1) / 2;
+  for (int e = threadIdx.x; e < np; e += blockDim.x) {
+    int a, b;
+    tri_rc(e, a, b);
+    const int k = n - 1 - a;
+    tab[e] = (k + b) << 16 | k;
+  }
+}
 
-__device__ void potrf_sm(double* A, int ld, int n, double* rinv, int* bad) {
-  const int tid = threadIdx.x;
-  if (tid < kPotrfThreads) {
-    int pi[kPotrfPer], pk[kPotrfPer];
-    const int npairs = n * (n - 1) / 2;
-#pragma unroll
-    for (int t = 0; t < kPotrfPer; ++t) {
-      const int e = tid + t * kPotrfThreads;
-      if (e < npairs) {
-        int a, b;
-        tri_rc(e, a, b);
-        pk[t] = n - 1 - a;
-        pi[t] = pk[t] + b;
-      } else {
-        pk[t] = pi[t] = 0;
-      }
-    }
-    if (tid == 0) {
-      const double d = A[0];
-      if (!(d > 0.0) && *bad == 0) *bad = 1;
-      const double r = pivot_rsqrt(d);
+// In-place lower Cholesky of A (n x n, FP64, n <= 64) by the first four warps
+// (one per FP64 sub-pipe); the CTA's other threads wait at the closing
+// __syncthreads. Writes rinv[j] = 1 / L_jj. On a pivot that is not positive
+// it sets *bad (first column + 1) and carries on (NaNs propagate; no trap).
+// Right-looking with a one-column look-ahead and one barrier per column: in
+// the phase of column j (final and scaled), warp 0 alone updates column j+1,
+// computes its pivot from the register holding the diagonal and scales it,
+// so the serial pivot chain runs on a sub-pipe of its own, while warps 1-3
+// walk the prefix of the element table `tab` for the trailing columns. Every
+// loop has a runtime trip count: on this part a predicated-off FP64
+// instruction still holds the FP64 pipe, so no FP64 work is issued for
+// inactive elements.
+constexpr int kPotrfThreads = 128;
+constexpr int kPotrfUpd = kPotrfThreads - 32;  // threads of warps 1-3
+
+__device__ void potrf_sm(double* A, int ld, int n, double* rinv, const int* tab, int* bad) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < 32) {
+    // column 0: pivot and scaling by warp 0
+    const double d = A[0];
+    const double r = pivot_rsqrt(d);
+    if (lane == 0) {
+      if (not_positive(d) && *bad == 0) *bad = 1;
       A[0] = d * r;
       rinv[0] = r;
     }
+    for (int i = 1 + lane; i < n; i += 32) A[i * ld] *= r;
+  }
+  if (tid < kPotrfThreads) {
     group_bar(1, kPotrfThreads);
-    for (int j = 0; j < n; ++j) {
-      const double r = rinv[j];
-      for (int i = j + 1 + tid; i < n; i += kPotrfThreads) A[i * ld + j] *= r;
-      group_bar(1, kPotrfThreads);
-      const int cnt = (n - 1 - j) * (n - j) / 2;
-#pragma unroll
-      for (int t = 0; t < kPotrfPer; ++t) {
-        if (tid + t * kPotrfThreads < cnt) {
-          const int i = pi[t], k = pk[t];
-          const double v = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
-          if (i == j + 1 && k == j + 1) {  // next pivot: compute it now
-            if (!(v > 0.0) && *bad == 0) *bad = j + 2;
-            const double rr = pivot_rsqrt(v);
-            A[i * ld + k] = v * rr;
-            rinv[j + 1] = rr;
-          } else {
-            A[i * ld + k] = v;
-          }
+    for (int j = 0; j + 1 < n; ++j) {
+      if (tid < 32) {
+        // look-ahead: column j+1 updated, pivoted and scaled by warp 0
+        const double lj = A[(j + 1) * ld + j];
+        const int i0 = j + 1 + lane, i1 = i0 + 32;
+        const bool two = j + 33 < n;  // warp-uniform: a second row per lane
+        double v0 = 0.0, v1 = 0.0;
+        if (i0 < n) v0 = fma(-A[i0 * ld + j], lj, A[i0 * ld + j + 1]);
+        if (two) {
+          if (i1 < n) v1 = fma(-A[i1 * ld + j], lj, A[i1 * ld + j + 1]);
+        }
+        double r = 0.0;
+        if (lane == 0) {  // v0 is the diagonal element (j+1, j+1)
+          if (not_positive(v0) && *bad == 0) *bad = j + 2;
+          r = pivot_rsqrt(v0);
+          A[(j + 1) * ld + j + 1] = v0 * r;
+          rinv[j + 1] = r;
+        }
+        r = __shfl_sync(0xffffffffu, r, 0);
+        if (lane > 0 && i0 < n) A[i0 * ld + j + 1] = v0 * r;
+        if (two) {
+          if (i1 < n) A[i1 * ld + j + 1] = v1 * r;
+        }
+      } else {
+        const int cnt = (n - 2 - j) * (n - 1 - j) / 2;
+        for (int e = tid - 32; e < cnt; e += kPotrfUpd) {
+          const int p = tab[e], i = p >> 16, k = p & 0xffff;
+          A[i * ld + k] = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
         }
       }
       group_bar(1, kPotrfThreads);
@@ -316,6 +363,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
   TZ* rinvZ = (TZ*)(smraw + lay.oRinvZ);
   TZ* Z = (TZ*)(smraw + lay.oZ);
   double* T = (double*)(smraw + lay.oT);
+  int* tab = (int*)(smraw + lay.oTab);
   const int oG = n, oW = n + m;  // panel row offsets
   const SegGeom g = seg_geom(d, tk.seg);
   const int s = g.f - 1;  // separator of this segment (k >= 1)
@@ -333,6 +381,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
 
   if (threadIdx.x == 0) bad = 0;
   for (int e = threadIdx.x; e < R * ldT; e += blockDim.x) T[e] = 0.0;
+  potrf_table(tab, n);
   __syncthreads();
   load_blk(Dfac, ldD, Dp(Din, g.f), Dp(D2, g.f), n, n, false);
   if (g.len > 1 || g.hasF) load_blk(Z, ldZ, Dp(Ein, g.f), none, n, n, false);
@@ -353,7 +402,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
     const bool eRows = (i < g.len - 1) || g.hasF;
     const int r0 = eRows ? 0 : n;
     const int r1 = n + m + (g.hasW ? n : 0);
-    potrf_sm(Dfac, ldD, n, rinv, &bad);
+    potrf_sm(Dfac, ldD, n, rinv, tab, &bad);
     if (bad && threadIdx.x == 0) { record_breakdown(info, d.sys, d.nat[j], d.level); bad = 0; }
     scaled_cols(M, Dfac, ldD, n, rinv);
     for (int e = threadIdx.x; e < n; e += blockDim.x) rinvZ[e] = (TZ)rinv[e];
@@ -371,20 +420,22 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
         if (mixed) Pf[e] = (float)v;
       }
     }
-    if (mixed) {
-      store_blk(d.LdMf + (size_t)j * nn, M, ldD, n, n, false, true);
-      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {  // rows divided by their diagonal
-        const int r = e / n, c = e - r * n;
-        d.LdRf[(size_t)j * nn + e] = c < r ? (float)(Dfac[r * ldD + c] * rinv[r]) : 0.0f;
-      }
-      for (int e = threadIdx.x; e < n; e += blockDim.x) d.Lrif[(size_t)j * n + e] = (float)rinv[e];
-    } else {
-      store_blk(d.LdM + (size_t)j * nn, M, ldD, n, n, false, true);
-      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int r = e / n, c = e - r * n;
-        d.LdR[(size_t)j * nn + e] = c < r ? Dfac[r * ldD + c] * rinv[r] : 0.0;
-      }
+    // D-hat with its rows divided by their diagonal (backward substitution):
+    // the strict lower triangle is computed, the rest zero-filled, so that no
+    // FP64 multiply is issued for the upper half
+    TZ* LdRj = mixed ? (TZ*)(d.LdRf + (size_t)j * nn) : (TZ*)(d.LdR + (size_t)j * nn);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) LdRj[e] = TZ(0);
+    store_blk(mixed ? (TZ*)(d.LdMf + (size_t)j * nn) : (TZ*)(d.LdM + (size_t)j * nn), M, ldD, n, n,
+              false, true);
+    __syncthreads();
+    for (int e = threadIdx.x; e < (n - 1) * n / 2; e += blockDim.x) {
+      int a, b;
+      tri_rc(e, a, b);
+      const int r = a + 1, c = b;
+      LdRj[r * n + c] = (TZ)(Dfac[r * ldD + c] * rinv[r]);
     }
+    if (mixed)
+      for (int e = threadIdx.x; e < n; e += blockDim.x) d.Lrif[(size_t)j * n + e] = (float)rinv[e];
     for (int e = threadIdx.x; e < n; e += blockDim.x) d.Lri[(size_t)j * n + e] = rinv[e];
     syrk_panel(T, ldT, Z, ldZ, r0, r1, n);
     if (i + 1 < g.len) {
@@ -430,8 +481,9 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
       v += T[(oG + r) * ldT + oG + c];
       Rs[r * ldR + c] = v;
     }
+    potrf_table(tab, m);
     __syncthreads();
-    potrf_sm(Rs, ldR, m, rinv, &bad);
+    potrf_sm(Rs, ldR, m, rinv, tab, &bad);
     if (bad && threadIdx.x == 0) record_breakdown(info, d.sys, d.Nnat, d.level);
     store_blk(d.Rhat, Rs, ldR, m, m, false, true);
     for (int e = threadIdx.x; e < m; e += blockDim.x) d.Rri[e] = rinv[e];
@@ -462,11 +514,16 @@ __device__ __forceinline__ VecView level_vec(const LevelDesc& d, double* b, int 
 template <typename TS>
 __device__ void load_vec(TS* dst, int ldd, const double* src, int lds, const double* src2, int rows,
                          int nr) {
-  for (int e = threadIdx.x; e < rows * nr; e += blockDim.x) {
-    const int r = e / nr, c = e - r * nr;
-    double v = src ? src[(size_t)r * lds + c] : 0.0;
-    if (src2) v += src2[(size_t)r * kRhsChunk + c];
-    dst[r * ldd + c] = (TS)v;
+  if (src2) {
+    for (int e = threadIdx.x; e < rows * nr; e += blockDim.x) {
+      const int r = e / nr, c = e - r * nr;
+      dst[r * ldd + c] = (TS)(src[(size_t)r * lds + c] + src2[(size_t)r * kRhsChunk + c]);
+    }
+  } else {
+    for (int e = threadIdx.x; e < rows * nr; e += blockDim.x) {
+      const int r = e / nr, c = e - r * nr;
+      dst[r * ldd + c] = (TS)src[(size_t)r * lds + c];
+    }
   }
 }
 
@@ -478,48 +535,99 @@ __device__ void store_vec(double* dst, int ldd, const TS* src, int lds, int rows
   }
 }
 
-// t <- L^{-1} t for L = M diag(1/rinv) (M: the columns of L divided by their
-// diagonal, strict lower part used), nr columns: t_i -= M_ij t_j for the
-// unscaled t_j, then t_j *= rinv_j.
-template <typename TS>
-__device__ void trsv_lower(TS* t, int ldt, const TS* M, int ldl, const TS* rinv, int n, int nr) {
-  for (int j = 0; j < n - 1; ++j) {
-    const int w = n - 1 - j, tot = w * nr;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int a = e / nr, c = e - a * nr, i = j + 1 + a;
-      t[i * ldt + c] = fma(-M[i * ldl + j], t[j * ldt + c], t[i * ldt + c]);
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
-    const int r = e / nr, c = e - r * nr;
-    t[r * ldt + c] *= rinv[r];
-  }
-  __syncthreads();
-}
+__device__ __forceinline__ double shfl_idx(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float shfl_idx(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 
-// t <- L^{-T} t with MR, the rows of L divided by their diagonal: x_j =
-// t_j rinv_j once t_j is final, and t_i -= L_ji x_j = MR_ji t_j (unscaled t_j)
-// for i < j.
+// Asynchronous global -> shared copy of one 4- or 8-byte element (no
+// register staging; completes at cp_async_wait).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// t <- L^{-1} t (forward) or t <- L^{-T} t (backward) for nr columns, one
+// warp per column (warp-synchronous: shuffles, no block barriers). Rows i
+// and i + 32 of a column live in lane i. Forward uses M (columns of L divided
+// by their diagonal): u_i -= M_ij u_j, x = u * rinv. Backward uses MR (rows
+// of L divided by their diagonal): u_i -= MR_ji u_j for i < j, x = u * rinv.
+// Ends with a block barrier.
 template <typename TS>
-__device__ void trsv_upper(TS* t, int ldt, const TS* M, int ldl, const TS* rinv, int n, int nr) {
-  for (int j = n - 1; j > 0; --j) {
-    for (int e = threadIdx.x; e < j * nr; e += blockDim.x) {
-      const int i = e / nr, c = e - i * nr;
-      t[i * ldt + c] = fma(-M[j * ldl + i], t[j * ldt + c], t[i * ldt + c]);
+__device__ void trsv_warp(TS* t, int ldt, const TS* M, int ldl, const TS* rinv, int n, int nr,
+                          bool backward) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int i0 = lane, i1 = lane + 32;
+  for (int c = warp; c < nr; c += nw) {
+    TS u0 = i0 < n ? t[i0 * ldt + c] : TS(0);
+    if (n <= 32) {  // one row per lane (warp-uniform branch: no predicated FP64 slots)
+      const int ir = i0 < n ? i0 : n - 1;  // clamp the multiplier row of idle lanes
+      if (!backward) {
+        int j = 0;
+        for (; j + 4 < n; j += 4) {  // multipliers of four steps loaded ahead
+          const TS m0 = M[ir * ldl + j], m1 = M[ir * ldl + j + 1], m2 = M[ir * ldl + j + 2],
+                   m3 = M[ir * ldl + j + 3];
+          TS uj = shfl_idx(u0, j);
+          if (i0 > j) u0 = fma(-m0, uj, u0);
+          uj = shfl_idx(u0, j + 1);
+          if (i0 > j + 1) u0 = fma(-m1, uj, u0);
+          uj = shfl_idx(u0, j + 2);
+          if (i0 > j + 2) u0 = fma(-m2, uj, u0);
+          uj = shfl_idx(u0, j + 3);
+          if (i0 > j + 3) u0 = fma(-m3, uj, u0);
+        }
+        for (; j < n - 1; ++j) {
+          const TS uj = shfl_idx(u0, j);
+          if (i0 > j) u0 = fma(-M[ir * ldl + j], uj, u0);
+        }
+      } else {
+        int j = n - 1;
+        for (; j - 3 > 0; j -= 4) {
+          const TS m0 = M[j * ldl + ir], m1 = M[(j - 1) * ldl + ir], m2 = M[(j - 2) * ldl + ir],
+                   m3 = M[(j - 3) * ldl + ir];
+          TS uj = shfl_idx(u0, j);
+          if (i0 < j) u0 = fma(-m0, uj, u0);
+          uj = shfl_idx(u0, j - 1);
+          if (i0 < j - 1) u0 = fma(-m1, uj, u0);
+          uj = shfl_idx(u0, j - 2);
+          if (i0 < j - 2) u0 = fma(-m2, uj, u0);
+          uj = shfl_idx(u0, j - 3);
+          if (i0 < j - 3) u0 = fma(-m3, uj, u0);
+        }
+        for (; j > 0; --j) {
+          const TS uj = shfl_idx(u0, j);
+          if (i0 < j) u0 = fma(-M[j * ldl + ir], uj, u0);
+        }
+      }
+    } else {
+      TS u1 = i1 < n ? t[i1 * ldt + c] : TS(0);
+      if (!backward) {
+        for (int j = 0; j < n - 1; ++j) {
+          const TS uj = shfl_idx(j < 32 ? u0 : u1, j & 31);
+          if (i0 > j) u0 = fma(-M[i0 * ldl + j], uj, u0);
+          if (i1 > j && i1 < n) u1 = fma(-M[i1 * ldl + j], uj, u1);
+        }
+      } else {
+        for (int j = n - 1; j > 0; --j) {
+          const TS uj = shfl_idx(j < 32 ? u0 : u1, j & 31);
+          if (i0 < j) u0 = fma(-M[j * ldl + i0], uj, u0);
+          if (i1 < j) u1 = fma(-M[j * ldl + i1], uj, u1);
+        }
+      }
+      if (i1 < n) t[i1 * ldt + c] = u1 * rinv[i1];
     }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
-    const int r = e / nr, c = e - r * nr;
-    t[r * ldt + c] *= rinv[r];
+    if (i0 < n) t[i0 * ldt + c] = u0 * rinv[i0];
   }
   __syncthreads();
 }
 
 template <typename TS>
 struct SolveSmem {
-  TS *L, *rinv, *Z, *V, *t;
+  TS *L[2], *rinv[2], *Z[2], *V, *t;
   int ldL, ldZ, ldV;
 };
 
@@ -530,9 +638,11 @@ __device__ __forceinline__ SolveSmem<TS> solve_smem(unsigned char* sm, int n, in
   S.ldL = odd(n);
   S.ldZ = L.ldZ;
   S.ldV = L.ldV;
-  S.L = (TS*)(sm + L.oL);
-  S.rinv = (TS*)(sm + L.oRinv);
-  S.Z = (TS*)(sm + L.oZ);
+  for (int q = 0; q < 2; ++q) {
+    S.L[q] = (TS*)(sm + L.oL[q]);
+    S.rinv[q] = (TS*)(sm + L.oRinv[q]);
+    S.Z[q] = (TS*)(sm + L.oZ[q]);
+  }
   S.V = (TS*)(sm + L.oV);
   S.t = (TS*)(sm + L.oT);
   return S;
@@ -549,56 +659,91 @@ __device__ __forceinline__ FactorView<float> factor_view(const LevelDesc& d, flo
   return FactorView<float>{d.LdMf, d.LdRf, d.Lrif, d.Lpf};
 }
 
-// load the factor blocks of stage j (D-hat with its columns (forward) or rows
-// (backward) divided by the diagonal, 1/diag, panel rows [r0, r1))
+// Start the asynchronous load of the factor blocks of stage j into buffer q
+// (D-hat with its columns (forward) or rows (backward) divided by the
+// diagonal, 1/diag, panel rows [r0, r1)).
 template <typename TS>
-__device__ void load_stage_factor(const SolveSmem<TS>& S, const LevelDesc& d, int j, int r0, int r1,
-                                  bool backward) {
+__device__ void prefetch_stage_factor(const SolveSmem<TS>& S, int q, const LevelDesc& d, int j, int r0,
+                                      int r1, bool backward) {
   const int n = d.n, R = 2 * n + d.m;
   const FactorView<TS> F = factor_view(d, TS(0));
   const TS* Lg = (backward ? F.MR : F.M) + (size_t)j * n * n;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int r = e / n, c = e - r * n;
-    S.L[r * S.ldL + c] = Lg[e];
+    cp_async_elem(S.L[q] + r * S.ldL + c, Lg + e);
   }
-  for (int e = threadIdx.x; e < n; e += blockDim.x) S.rinv[e] = F.ri[(size_t)j * n + e];
+  for (int e = threadIdx.x; e < n; e += blockDim.x) cp_async_elem(S.rinv[q] + e, F.ri + (size_t)j * n + e);
   const TS* P = F.P + (size_t)j * R * n;
   for (int e = threadIdx.x + r0 * n; e < r1 * n; e += blockDim.x) {
     const int r = e / n, c = e - r * n;
-    S.Z[r * S.ldZ + c] = P[e];
+    cp_async_elem(S.Z[q] + r * S.ldZ + c, P + e);
   }
+  cp_async_commit();
+}
+
+__device__ __forceinline__ void stage_rows(const SegGeom& g, int i, int n, int m, int& r0, int& r1) {
+  const bool eRows = (i < g.len - 1) || g.hasF;
+  r0 = eRows ? 0 : n;
+  r1 = n + m + (g.hasW ? n : 0);
 }
 
 // Backward substitution over the stages of one segment (Algorithm 3,
 // parallel phase; for the top level the whole sequential sweep). On entry
-// S.V holds [x_next (E rows); x_g (G rows); x_sep (W rows)].
+// S.V holds [x_next (E rows); x_g (G rows); x_sep (W rows)]. The factor
+// blocks of the next stage stream in while the current one is solved.
 template <typename TS>
 __device__ void backward_segment(const SolveSmem<TS>& S, const LevelDesc& d, const SegGeom& g,
                                  double* b, int ldb, int nr) {
   const int n = d.n, m = d.m;
+  int r0, r1;
+  stage_rows(g, g.len - 1, n, m, r0, r1);
+  prefetch_stage_factor(S, 0, d, g.f + g.len - 1, r0, r1, true);
   for (int i = g.len - 1; i >= 0; --i) {
-    const int j = g.f + i;
-    const bool eRows = (i < g.len - 1) || g.hasF;
-    const int r0 = eRows ? 0 : n, r1 = n + m + (g.hasW ? n : 0);
-    load_stage_factor(S, d, j, r0, r1, true);
+    const int j = g.f + i, q = (g.len - 1 - i) & 1;
+    stage_rows(g, i, n, m, r0, r1);
     const VecView y = level_vec(d, b, ldb, j);
+    cp_async_wait_all();
     __syncthreads();
-    // t = y_j - Z^T v over the active panel rows
-    for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
-      const int c2 = e / nr, c = e - c2 * nr;
-      TS acc = (TS)y.p[(size_t)c2 * y.ld + c];
-      for (int r = r0; r < r1; ++r) acc = fma(-S.Z[r * S.ldZ + c2], S.V[r * S.ldV + c], acc);
-      S.t[c2 * S.ldV + c] = acc;
+    if (i > 0) {
+      int p0, p1;
+      stage_rows(g, i - 1, n, m, p0, p1);
+      prefetch_stage_factor(S, q ^ 1, d, j - 1, p0, p1, true);
+    }
+    const TS* Z = S.Z[q];
+    // t = y_j - Z^T v over the active panel rows: four lanes per output (each
+    // a quarter of the rows, two partial sums), shuffle-reduced
+    {
+      const int outs = n * nr, span = (outs * 4 + 31) & ~31, rows = r1 - r0;
+      for (int e = threadIdx.x; e < span; e += blockDim.x) {
+        const int o = e >> 2, qq = e & 3;
+        const bool act = o < outs;
+        const int oo = act ? o : 0;
+        const int c2 = oo / nr, c = oo - c2 * nr;
+        const int ra = r0 + ((qq * rows) >> 2), rb = r0 + (((qq + 1) * rows) >> 2);
+        TS a0 = 0, a1 = 0;
+        int r = ra;
+        if (act) {
+          for (; r + 1 < rb; r += 2) {
+            a0 = fma(Z[r * S.ldZ + c2], S.V[r * S.ldV + c], a0);
+            a1 = fma(Z[(r + 1) * S.ldZ + c2], S.V[(r + 1) * S.ldV + c], a1);
+          }
+          if (r < rb) a0 = fma(Z[r * S.ldZ + c2], S.V[r * S.ldV + c], a0);
+        }
+        TS a = a0 + a1;
+        a += __shfl_xor_sync(0xffffffffu, a, 1);
+        a += __shfl_xor_sync(0xffffffffu, a, 2);
+        if (act && qq == 0) S.t[c2 * S.ldV + c] = (TS)y.p[(size_t)c2 * y.ld + c] - a;
+      }
     }
     __syncthreads();
-    trsv_upper(S.t, S.ldV, S.L, S.ldL, S.rinv, n, nr);
+    trsv_warp(S.t, S.ldV, S.L[q], S.ldL, S.rinv[q], n, nr, true);
     store_vec(y.p, y.ld, S.t, S.ldV, n, nr);
     for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
       const int r = e / nr, c = e - r * nr;
       S.V[r * S.ldV + c] = S.t[r * S.ldV + c];
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
 // Forward substitution (Algorithm 2) for one segment; the top level (P = 1)
@@ -626,28 +771,53 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
                d.RB + (size_t)j * n * kRhsChunk, n, nr);
     }
   };
+  int r0, r1;
+  stage_rows(g, 0, n, m, r0, r1);
+  prefetch_stage_factor(S, 0, d, g.f, r0, r1, false);
   // V_G <- 0, V_W <- rhs of the separator, t <- rhs of the first stage
   for (int e = threadIdx.x; e < (2 * n + m) * S.ldV; e += blockDim.x) S.V[e] = TS(0);
   __syncthreads();
   if (g.hasW) rhs(g.f - 1, S.V + oW * S.ldV);
   rhs(g.f, S.t);
-  __syncthreads();
   for (int i = 0; i < g.len; ++i) {
-    const int j = g.f + i;
-    const bool eRows = (i < g.len - 1) || g.hasF;
-    const int r0 = eRows ? 0 : n, r1 = n + m + (g.hasW ? n : 0);
-    load_stage_factor(S, d, j, r0, r1, false);
+    const int j = g.f + i, q = i & 1;
+    stage_rows(g, i, n, m, r0, r1);
     if (i + 1 < g.len) rhs(j + 1, S.V);  // V_E <- next stage's rhs (else 0: F-hat term)
+    cp_async_wait_all();
     __syncthreads();
-    trsv_lower(S.t, S.ldV, S.L, S.ldL, S.rinv, n, nr);
+    if (i + 1 < g.len) {
+      int p0, p1;
+      stage_rows(g, i + 1, n, m, p0, p1);
+      prefetch_stage_factor(S, q ^ 1, d, j + 1, p0, p1, false);
+    }
+    trsv_warp(S.t, S.ldV, S.L[q], S.ldL, S.rinv[q], n, nr, false);
     const VecView y = level_vec(d, b, ldb, j);
     store_vec(y.p, y.ld, S.t, S.ldV, n, nr);
-    // [V_E; V_G; V_W] -= Z y over the active panel rows
-    for (int e = threadIdx.x; e < (r1 - r0) * nr; e += blockDim.x) {
-      const int r = r0 + e / nr, c = e - (e / nr) * nr;
-      TS acc = 0;
-      for (int t2 = 0; t2 < n; ++t2) acc = fma(S.Z[r * S.ldZ + t2], S.t[t2 * S.ldV + c], acc);
-      S.V[r * S.ldV + c] -= acc;
+    // [V_E; V_G; V_W] -= Z y over the active panel rows: four lanes per output
+    // (each a quarter of the dot product, two partial sums), shuffle-reduced
+    const TS* Z = S.Z[q];
+    {
+      const int outs = (r1 - r0) * nr, span = (outs * 4 + 31) & ~31;
+      for (int e = threadIdx.x; e < span; e += blockDim.x) {
+        const int o = e >> 2, qq = e & 3;
+        const bool act = o < outs;
+        const int oo = act ? o : 0;
+        const int r = r0 + oo / nr, c = oo - (oo / nr) * nr;
+        const int k0 = (qq * n) >> 2, k1 = ((qq + 1) * n) >> 2;
+        TS a0 = 0, a1 = 0;
+        int t2 = k0;
+        if (act) {
+          for (; t2 + 1 < k1; t2 += 2) {
+            a0 = fma(Z[r * S.ldZ + t2], S.t[t2 * S.ldV + c], a0);
+            a1 = fma(Z[r * S.ldZ + t2 + 1], S.t[(t2 + 1) * S.ldV + c], a1);
+          }
+          if (t2 < k1) a0 = fma(Z[r * S.ldZ + t2], S.t[t2 * S.ldV + c], a0);
+        }
+        TS a = a0 + a1;
+        a += __shfl_xor_sync(0xffffffffu, a, 1);
+        a += __shfl_xor_sync(0xffffffffu, a, 2);
+        if (act && qq == 0) S.V[r * S.ldV + c] -= a;
+      }
     }
     __syncthreads();
     if (i + 1 < g.len) {
@@ -656,9 +826,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
         S.t[r * S.ldV + c] = S.V[r * S.ldV + c];
         S.V[r * S.ldV + c] = TS(0);
       }
-      __syncthreads();
+      __syncthreads();  // V_E is reloaded at the top of the next stage
     }
   }
+  __syncthreads();
   if (!d.is_top) {
     if (g.hasF) store_vec(d.YB + (size_t)k * n * kRhsChunk, kRhsChunk, S.V, S.ldV, n, nr);
     if (g.hasW) store_vec(d.YA + (size_t)(k - 1) * n * kRhsChunk, kRhsChunk, S.V + oW * S.ldV, S.ldV, n, nr);
@@ -678,19 +849,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
       v += (double)S.V[(oG + r) * S.ldV + c];
       gv[r * S.ldV + c] = (TS)v;
     }
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {  // R-hat, columns scaled
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {  // R-hat: columns scaled, rows scaled
       const int r = e / m, c = e - r * m;
-      S.L[r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[c]);
+      S.L[0][r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[c]);
+      S.L[1][r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[r]);
     }
-    for (int e = threadIdx.x; e < m; e += blockDim.x) S.rinv[e] = (TS)d.Rri[e];
+    for (int e = threadIdx.x; e < m; e += blockDim.x) S.rinv[0][e] = (TS)d.Rri[e];
     __syncthreads();
-    trsv_lower(gv, S.ldV, S.L, ldR, S.rinv, m, nr);
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {  // R-hat, rows scaled
-      const int r = e / m, c = e - r * m;
-      S.L[r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[r]);
-    }
-    __syncthreads();
-    trsv_upper(gv, S.ldV, S.L, ldR, S.rinv, m, nr);
+    trsv_warp(gv, S.ldV, S.L[0], ldR, S.rinv[0], m, nr, false);
+    trsv_warp(gv, S.ldV, S.L[1], ldR, S.rinv[0], m, nr, true);
     store_vec(bg, ldb, gv, S.ldV, m, nr);
   }
   // V <- [0; x_g; -] for the backward sweep of the top level
