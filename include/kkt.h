@@ -224,7 +224,9 @@ kkt_status kkt_get_factor(kkt_handle* h, int system, double* Ld, double* Le, dou
  * launches, in launch order (event i after launch i of the call; launches
  * beyond `count` record nothing). Lets a caller time each launch with no
  * extra work on the device. count = 0 or events = NULL detaches. The events
- * stay owned by the caller and must outlive their use. */
+ * stay owned by the caller and must outlive their use. When the stream is
+ * being captured into a CUDA graph, the records are captured as external
+ * event-record nodes and happen on every replay of the graph. */
 kkt_status kkt_set_launch_events(kkt_handle* h, void* const* events, int count);
 
 /* Number of kernel launches one kkt_factor / one kkt_solve (per chunk of up

@@ -163,10 +163,16 @@ struct kkt_handle {
 constexpr int kMaxSweeps = 16;
 
 namespace {
-// Record the caller's event `i` (if attached) after a launch.
+// Record the caller's event `i` (if attached) after a launch. Inside a
+// stream capture the record becomes an external event-record node of the
+// graph, so that every replay records the event.
 inline bool mark(const kkt_handle* h, int i, void* stream) {
-  if (i < (int)h->events.size() && h->events[i])
-    return cudaEventRecord(h->events[i], (cudaStream_t)stream) == cudaSuccess;
+  if (i < (int)h->events.size() && h->events[i]) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) return false;
+    const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    return cudaEventRecordWithFlags(h->events[i], (cudaStream_t)stream, flags) == cudaSuccess;
+  }
   return true;
 }
 }  // namespace
