@@ -240,6 +240,11 @@ def run_reference(args):
     }), flush=True)
 
 
+def device_sms() -> int:
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
 def per_launch_flops(kkt, plan):
     """Names and algorithmic FP64 flops (standard convention, as executed) of
     the launches of one factor + one solve, in launch order: factor levels
@@ -249,7 +254,8 @@ def per_launch_flops(kkt, plan):
     Ns = [N_STAGES]
     for p in plan[:-1]:
         Ns.append(p - 1)
-    suf = [kkt.kkt_plan_flops(Ns[l], N_BLOCK, M_ARROW, plan[l:], kkt.KKT_PARTITION_BALANCED)
+    sms = device_sms()
+    suf = [kkt.kkt_plan_flops(Ns[l], N_BLOCK, M_ARROW, plan[l:], kkt.KKT_PARTITION_BALANCED, sms)
            for l in range(L)]
     fac = [suf[l]["factor"] - (suf[l + 1]["factor"] if l + 1 < L else 0.0) for l in range(L)]
     sol = [suf[l]["solve"] - (suf[l + 1]["solve"] if l + 1 < L else 0.0) for l in range(L)]

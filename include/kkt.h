@@ -82,7 +82,14 @@ typedef enum { KKT_FP64 = 0, KKT_MIXED_FP32 = 1, KKT_MIXED_FP32_ALL = 2 } kkt_pr
  *                          for a few threads and costly for hundreds of CTAs.
  *  KKT_PARTITION_BALANCED  the same cost model with the kernel's per-stage
  *                          flop counts, stage by stage to the cheapest
- *                          segment: lengths N_1 and N_k or N_k + 1. */
+ *                          segment: lengths N_1 and N_k or N_k + 1. On a
+ *                          level whose factor tasks run as CTA pairs (see
+ *                          kkt_set_pairing) the fill-in rows are off the
+ *                          critical path and every segment's stages cost
+ *                          about the same, so the lengths come out nearly
+ *                          equal. A handle pairs a level when some segment
+ *                          has fill-in and two CTAs per segment task fit
+ *                          on the device's SMs (2 x tasks <= SMs). */
 typedef enum { KKT_PARTITION_PAPER = 0, KKT_PARTITION_BALANCED = 1 } kkt_partition_mode;
 
 typedef struct kkt_handle kkt_handle;
@@ -139,8 +146,9 @@ kkt_status kkt_partition(const kkt_handle* h, int system, int level, int* P_out,
 kkt_status kkt_partition_rule(int N, int P, int* seg_len);
 
 /* Segment lengths of the balanced partition (KKT_PARTITION_BALANCED) of N
- * stages of size n with arrow m into P segments. */
-kkt_status kkt_partition_balanced(int N, int n, int m, int P, int* seg_len);
+ * stages of size n with arrow m into P segments, for an unpaired (paired =
+ * 0) or a paired (paired = 1) level. */
+kkt_status kkt_partition_balanced(int N, int n, int m, int P, int paired, int* seg_len);
 
 /* Element offsets of every system's inputs in the packed batch layout
  * (arrays of length count+1; any pointer may be NULL). off_b counts rows. */
@@ -229,6 +237,21 @@ kkt_status kkt_get_factor(kkt_handle* h, int system, double* Ld, double* Le, dou
  * event-record nodes and happen on every replay of the graph. */
 kkt_status kkt_set_launch_events(kkt_handle* h, void* const* events, int count);
 
+/* Layout of the factor kernel's segment tasks. With pairing, a segment runs
+ * on a cluster of two CTAs on separate SMs: one carries the chain of
+ * Algorithm 1 (pivot factorization, E- and G-rows, their Schur updates), the
+ * other the fill-in rows W of segments k >= 2 and their updates of A~, Q~
+ * and the next W, fed through distributed shared memory. This gives a
+ * segment two SMs' FP64 units and pays off on levels with fewer segments
+ * than SM pairs. KKT_PAIR_AUTO (the default) pairs exactly those levels;
+ * KKT_PAIR_OFF and KKT_PAIR_ON force one layout on every level (the
+ * partition chosen at creation is kept). The layouts give bitwise identical
+ * results: each element is computed by the same operations in the same
+ * order; only the assignment to threads differs. Returns KKT_ERR_ARG for a
+ * NULL handle or an unknown policy. Takes effect at the next kkt_factor. */
+typedef enum { KKT_PAIR_AUTO = 0, KKT_PAIR_OFF = 1, KKT_PAIR_ON = 2 } kkt_pair_policy;
+kkt_status kkt_set_pairing(kkt_handle* h, int policy);
+
 /* Number of kernel launches one kkt_factor / one kkt_solve (per chunk of up
  * to 16 right-hand sides) enqueues for this handle. */
 kkt_status kkt_launch_counts(const kkt_handle* h, int* factor_launches, int* solve_launches);
@@ -241,9 +264,11 @@ kkt_status kkt_launch_counts(const kkt_handle* h, int* factor_launches, int* sol
 kkt_status kkt_flops(const kkt_handle* h, double* factor_flops, double* solve_flops,
                      double* sequential_factor_flops);
 
-/* Same counts as kkt_flops for one system planned like kkt_create_plan,
- * computed on the host without a handle or a GPU. */
-kkt_status kkt_plan_flops(int N, int n, int m, int nlevels, const int* P_levels, int partition,
+/* Same counts as kkt_flops for one system planned like kkt_create_plan on a
+ * device with `sms` SMs (which decides the paired levels of a balanced
+ * partition; 0 = no level paired), computed on the host without a handle
+ * or a GPU. */
+kkt_status kkt_plan_flops(int N, int n, int m, int nlevels, const int* P_levels, int partition, int sms,
                           double* factor_flops, double* solve_flops,
                           double* sequential_factor_flops);
 

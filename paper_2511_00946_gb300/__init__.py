@@ -21,13 +21,14 @@ LIB_PATH = os.path.join(_HERE, "_build", "libkkt.so")
  KKT_ERR_CAPACITY) = range(8)
 KKT_FP64, KKT_MIXED_FP32, KKT_MIXED_FP32_ALL = 0, 1, 2
 KKT_PARTITION_PAPER, KKT_PARTITION_BALANCED = 0, 1
+KKT_PAIR_AUTO, KKT_PAIR_OFF, KKT_PAIR_ON = 0, 1, 2
 RHS_CHUNK = 16
 
 EXPORTED = [
     "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_destroy",
     "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta",
     "kkt_get_info",
-    "kkt_get_factor", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
+    "kkt_get_factor", "kkt_set_pairing", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
 ]
 
 
@@ -54,7 +55,7 @@ _sig = {
     "kkt_create_levels": [_i, _i, _i, _i, _ip, _i, ctypes.POINTER(_vp)],
     "kkt_create_plan": [_i, _i, _i, _i, _ip, _i, _i, ctypes.POINTER(_vp)],
     "kkt_batch_create": [_i, _ip, _ip, _ip, _ip, _i, ctypes.POINTER(_vp)],
-    "kkt_partition_balanced": [_i, _i, _i, _i, _ip],
+    "kkt_partition_balanced": [_i, _i, _i, _i, _i, _ip],
     "kkt_destroy": [_vp],
     "kkt_partition": [_vp, _i, _i, _ip, _ip],
     "kkt_partition_rule": [_i, _i, _ip],
@@ -66,10 +67,11 @@ _sig = {
     "kkt_solve_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _vp, _vp, _i, _vp],
     "kkt_get_info": [_vp, _ip, _i],
     "kkt_get_factor": [_vp, _i, _dp, _dp, _dp, _dp, _dp, _dp],
+    "kkt_set_pairing": [_vp, _i],
     "kkt_set_launch_events": [_vp, ctypes.POINTER(_vp), _i],
     "kkt_launch_counts": [_vp, _ip, _ip],
     "kkt_flops": [_vp, _dp, _dp, _dp],
-    "kkt_plan_flops": [_i, _i, _i, _i, _ip, _i, _dp, _dp, _dp],
+    "kkt_plan_flops": [_i, _i, _i, _i, _ip, _i, _i, _dp, _dp, _dp],
     "kkt_solve_noalloc": [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp, _vp],
     "kkt_status_string": [_i],
 }
@@ -169,9 +171,9 @@ def kkt_partition_rule(N: int, P: int) -> list[int]:
     return list(seg[:P])
 
 
-def kkt_partition_balanced(N: int, n: int, m: int, P: int) -> list[int]:
+def kkt_partition_balanced(N: int, n: int, m: int, P: int, paired: bool = False) -> list[int]:
     seg = (ctypes.c_int * max(P, 1))()
-    _check(_lib.kkt_partition_balanced(N, n, m, P, seg), "kkt_partition_balanced")
+    _check(_lib.kkt_partition_balanced(N, n, m, P, int(bool(paired)), seg), "kkt_partition_balanced")
     return list(seg[:P])
 
 
@@ -240,6 +242,12 @@ def kkt_get_factor(h: int, N: int, n: int, m: int, system: int = 0) -> dict:
     return out
 
 
+def kkt_set_pairing(h: int, policy: int) -> None:
+    """KKT_PAIR_AUTO (default), KKT_PAIR_OFF or KKT_PAIR_ON: whether factor
+    tasks run on clusters of two CTAs (see the C header)."""
+    _check(_lib.kkt_set_pairing(h, int(policy)), "kkt_set_pairing")
+
+
 def kkt_set_launch_events(h: int, events) -> None:
     """events: list of torch.cuda.Event (created with enable_timing=True and
     already recorded once so that they own a CUDA event) or raw handles."""
@@ -262,9 +270,9 @@ def kkt_flops(h: int) -> dict:
     return dict(factor=a.value, solve=b.value, sequential_factor=c.value)
 
 
-def kkt_plan_flops(N: int, n: int, m: int, P_levels, partition: int = KKT_PARTITION_PAPER) -> dict:
+def kkt_plan_flops(N: int, n: int, m: int, P_levels, partition: int = KKT_PARTITION_PAPER, sms: int = 0) -> dict:
     a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-    _check(_lib.kkt_plan_flops(N, n, m, len(P_levels), _ints(P_levels), partition, ctypes.byref(a),
+    _check(_lib.kkt_plan_flops(N, n, m, len(P_levels), _ints(P_levels), partition, int(sms), ctypes.byref(a),
                                ctypes.byref(b), ctypes.byref(c)), "kkt_plan_flops")
     return dict(factor=a.value, solve=b.value, sequential_factor=c.value)
 

@@ -80,6 +80,10 @@ std::vector<int> starts_from(const std::vector<int>& len) {
 // least (first-segment stage weight w1, others w2), lowest index on ties.
 // Unlike Eq. (13) the other segments may differ in length by one stage, so
 // the rounding slack of large P is spread instead of piled onto segment 1.
+// Cost of a stage of a paired segment with fill-in relative to a first-
+// segment stage (the producer CTA also hands its blocks to the consumer).
+constexpr double kPairedStageCost = 1.05;
+
 std::vector<int> balanced_lengths(int N, int P, double w1, double w2) {
   std::vector<int> len(P, 1);
   // bulk fill: every segment up to the common cost level, then one by one
@@ -107,7 +111,10 @@ std::vector<int> balanced_lengths(int N, int P, double w1, double w2) {
   return len;
 }
 
-bool make_level(int N, int P, int mode, int n, int m, LevelPlan* L) {
+// `paired`: the level's factor tasks run as CTA pairs, whose fill-in rows
+// are off the segment's critical path (every segment then costs about what
+// the first one does per stage).
+bool make_level(int N, int P, int mode, int n, int m, bool paired, LevelPlan* L) {
   L->N = N;
   L->P = P;
   if (N < 1 || P < 1) return false;
@@ -118,7 +125,8 @@ bool make_level(int N, int P, int mode, int n, int m, LevelPlan* L) {
     // a stage also pays a fixed latency (pivot chain, barriers) that does not
     // grow with the panel height; measured on GB300 it is about 5 n^3 flops
     const double fixed = 5.0 * double(n) * n * n;
-    len = balanced_lengths(N, P, stage_flops(n, n + m) + fixed, stage_flops(n, 2 * n + m) + fixed);
+    const double w1 = stage_flops(n, n + m) + fixed;
+    len = balanced_lengths(N, P, w1, paired ? kPairedStageCost * w1 : stage_flops(n, 2 * n + m) + fixed);
   } else {
     int N1 = 0, Nk = 0;
     if (!partition_rule(N, P, &N1, &Nk)) return false;
@@ -158,6 +166,8 @@ struct kkt_handle {
   int* dconv = nullptr;                      // per-system convergence flags
   double* deta = nullptr;                    // eta history [kMaxSweeps][count]
   std::vector<int> level_mixed;              // per level index (all systems alike)
+  std::vector<int> level_pair;               // factor tasks of this level run as CTA pairs
+  int pair_policy = KKT_PAIR_AUTO;
 };
 
 constexpr int kMaxSweeps = 16;
@@ -188,12 +198,38 @@ struct Carver {
   }
 };
 
+// Levels whose factor tasks run as CTA pairs by default: some segment has
+// fill-in rows and the pairs fit on the device (two CTAs per task, at most
+// one CTA per SM).
+std::vector<int> paired_levels(const std::vector<std::vector<int>>& Plev, int sms) {
+  size_t L = 0;
+  for (const auto& ps : Plev) L = std::max(L, ps.size());
+  std::vector<int> pr(L, 0);
+  for (size_t l = 0; l < L; ++l) {
+    long long tasks = 0;
+    bool fill = false;
+    for (const auto& ps : Plev)
+      if (l < ps.size()) {
+        tasks += ps[l];
+        fill = fill || ps[l] > 1;
+      }
+    pr[l] = fill && 2 * tasks <= sms;
+  }
+  return pr;
+}
+
 kkt_status build_handle(int count, const int* N, const int* n, const int* m,
                         const std::vector<std::vector<int>>& Plev, int mode, int precision,
                         kkt_handle** out) {
   if (!out) return KKT_ERR_ARG;
   *out = nullptr;
   if (count < 1 || !N || !n || !m) return KKT_ERR_ARG;
+  int dev = 0, optin = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return KKT_ERR_CUDA;
+  const std::vector<int> pair_lv = paired_levels(Plev, sms);
   if (precision != KKT_FP64 && precision != KKT_MIXED_FP32 && precision != KKT_MIXED_FP32_ALL)
     return KKT_ERR_ARG;
   auto* h = new kkt_handle();
@@ -214,7 +250,7 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
     for (int j = 0; j < sp.N; ++j) nat[j] = j;
     for (size_t l = 0; l < Ps.size(); ++l) {
       LevelPlan L;
-      if (!make_level(Nl, Ps[l], mode, sp.n, sp.m, &L)) { delete h; return KKT_ERR_PARTITION; }
+      if (!make_level(Nl, Ps[l], mode, sp.n, sp.m, pair_lv[l] != 0, &L)) { delete h; return KKT_ERR_PARTITION; }
       L.nat = nat;
       L.mixed = (precision == KKT_MIXED_FP32_ALL) || (precision == KKT_MIXED_FP32 && l == 0);
       sp.lv.push_back(L);
@@ -238,12 +274,8 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
     h->maxL = std::max(h->maxL, (int)sp.lv.size());
   }
   // shared memory must fit: (n | 1)-padded blocks for the largest shapes
-  int dev = 0, optin = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
-    delete h;
-    return KKT_ERR_CUDA;
-  }
+  h->level_pair.assign(h->maxL, 0);
+  for (int l = 0; l < h->maxL && l < (int)pair_lv.size(); ++l) h->level_pair[l] = pair_lv[l];
   if (kkt::factor_smem_bytes(h->maxn, h->maxm, 0) > size_t(optin)) { delete h; return KKT_ERR_ARG; }
   h->level_mixed.assign(h->maxL, 0);
   for (const SysPlan& sp : h->sys)
@@ -519,10 +551,10 @@ kkt_status kkt_partition_rule(int N, int P, int* seg) {
   return KKT_OK;
 }
 
-kkt_status kkt_partition_balanced(int N, int n, int m, int P, int* seg) {
+kkt_status kkt_partition_balanced(int N, int n, int m, int P, int paired, int* seg) {
   if (!seg || n < 1 || m < 0) return KKT_ERR_ARG;
   LevelPlan L;
-  if (!make_level(N, P, KKT_PARTITION_BALANCED, n, m, &L)) return KKT_ERR_PARTITION;
+  if (!make_level(N, P, KKT_PARTITION_BALANCED, n, m, paired != 0, &L)) return KKT_ERR_PARTITION;
   for (int k = 0; k < P; ++k) seg[k] = seg_len(L, k);
   return KKT_OK;
 }
@@ -541,6 +573,22 @@ kkt_status kkt_batch_offsets(const kkt_handle* h, size_t* oD, size_t* oE, size_t
   return KKT_OK;
 }
 
+namespace {
+// Layout of a level's factor launch: the plan's choice (paired_levels)
+// unless the caller forced one.
+int level_paired(const kkt_handle* h, int l) {
+  if (h->pair_policy == KKT_PAIR_OFF) return 0;
+  if (h->pair_policy == KKT_PAIR_ON) return 1;
+  return h->level_pair[l];
+}
+}  // namespace
+
+kkt_status kkt_set_pairing(kkt_handle* h, int policy) {
+  if (!h || policy < KKT_PAIR_AUTO || policy > KKT_PAIR_ON) return KKT_ERR_ARG;
+  h->pair_policy = policy;
+  return KKT_OK;
+}
+
 kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const double* G,
                       const double* R, void* stream) {
   if (!h || !D) return KKT_ERR_ARG;
@@ -550,7 +598,8 @@ kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const dou
   for (int l = 0; l < h->maxL; ++l) {
     if (!h->fac_cnt[l]) continue;
     const int e = kkt::launch_factor(h->ddesc, h->dtasks + h->fac_off[l], h->fac_cnt[l], h->maxn,
-                                     h->maxm, h->level_mixed[l], D, E, G, R, h->dinfo, stream);
+                                     h->maxm, h->level_mixed[l], level_paired(h, l), D, E, G, R,
+                                     h->dinfo, stream);
     if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
   }
   h->factored = true;
@@ -777,16 +826,17 @@ kkt_status kkt_flops(const kkt_handle* h, double* ff, double* sf, double* seqf) 
   return KKT_OK;
 }
 
-kkt_status kkt_plan_flops(int N, int n, int m, int nlevels, const int* P_levels, int partition,
+kkt_status kkt_plan_flops(int N, int n, int m, int nlevels, const int* P_levels, int partition, int sms,
                           double* ff, double* sf, double* seqf) {
-  if (N < 1 || n < 1 || m < 0 || nlevels < 1 || !P_levels || P_levels[nlevels - 1] != 1)
+  if (N < 1 || n < 1 || m < 0 || nlevels < 1 || !P_levels || P_levels[nlevels - 1] != 1 || sms < 0)
     return KKT_ERR_ARG;
   SysPlan sp;
   sp.N = N; sp.n = n; sp.m = m;
+  const std::vector<int> pair_lv = paired_levels({std::vector<int>(P_levels, P_levels + nlevels)}, sms);
   int Nl = N;
   for (int l = 0; l < nlevels; ++l) {
     LevelPlan L;
-    if (!make_level(Nl, P_levels[l], partition, n, m, &L)) return KKT_ERR_PARTITION;
+    if (!make_level(Nl, P_levels[l], partition, n, m, pair_lv[l] != 0, &L)) return KKT_ERR_PARTITION;
     sp.lv.push_back(L);
     if (L.P == 1) {
       if (l + 1 != nlevels) return KKT_ERR_ARG;

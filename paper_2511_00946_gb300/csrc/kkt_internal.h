@@ -114,7 +114,7 @@ struct Info {
 // them. zb = bytes per panel element (8: FP64 path, 4: mixed). Odd leading
 // dimensions keep row- and column-wise accesses free of bank conflicts.
 struct FacLayout {
-  int q, R, ldD, ldZ, ldT, oDfac, oM, oRinv, oRinvZ, oZ, oT, oTab, total;
+  int q, R, ldD, ldZ, ldT, oDfac, oM, oRinv, oRinvZ, oZ, oT, oTab, oDfac2, oRinv2, total;
 };
 __host__ __device__ inline int kkt_align16(int b) { return (b + 15) & ~15; }
 __host__ __device__ inline FacLayout fac_layout(int n, int m, int zb) {
@@ -131,7 +131,11 @@ __host__ __device__ inline FacLayout fac_layout(int n, int m, int zb) {
   L.oZ = L.oRinvZ + kkt_align16(zb * L.q);
   L.oT = L.oZ + kkt_align16(zb * L.R * L.ldZ);
   L.oTab = L.oT + kkt_align16(8 * L.R * L.ldT);  // potrf element table, q(q-1)/2 ints
-  L.total = L.oTab + kkt_align16(4 * (L.q * (L.q - 1) / 2 + 1));
+  // second pivot block and rinv: the next stage's pivot factorization runs
+  // while the current stage's factor blocks are still being written
+  L.oDfac2 = L.oTab + kkt_align16(4 * (L.q * (L.q - 1) / 2 + 1));
+  L.oRinv2 = L.oDfac2 + kkt_align16(8 * L.q * L.ldD);
+  L.total = L.oRinv2 + kkt_align16(8 * L.q);
   return L;
 }
 // The substitution kernels double-buffer the factor blocks (L, rinv, Z) so
@@ -175,10 +179,12 @@ struct ResTask {
 constexpr int kResPartDoubles = kMaxM * kRhsChunk + 4 * kRhsChunk;
 
 // Kernel launchers (kkt_kernels.cu). Each returns the cudaError_t of the launch.
-// `mixed`: FP32 panel arithmetic in the factor; `single`: FP32 substitution
+// `mixed`: FP32 panel arithmetic in the factor; `pair`: every factor task runs
+// on a cluster of two CTAs (chain and fill-in rows on separate SMs);
+// `single`: FP32 substitution
 // with the FP32 factor copy (mixed levels only); `skip`: per-system flags
 // (null = never skip), a set flag makes the system's CTAs return at once.
-int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
+int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
                   void* stream);
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,

@@ -45,6 +45,26 @@ __device__ void record_breakdown(Info* info, int sys, int stage, int level) {
   }
 }
 
+// A group of threads working on one role of a CTA: thread index within the
+// group, group size and the named barrier that synchronizes it (0 = the whole
+// CTA, __syncthreads; -1 = a single warp, __syncwarp).
+struct Grp {
+  int tid, nt, bar;
+};
+__device__ __forceinline__ Grp cta_grp() { return Grp{(int)threadIdx.x, (int)blockDim.x, 0}; }
+
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void group_arrive(int id, int nthreads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void gsync(const Grp& g) {
+  if (g.bar == 0) __syncthreads();
+  else if (g.bar < 0) __syncwarp();
+  else group_bar(g.bar, g.nt);
+}
+
 // dst (rows x cols, smem, ld) <- A (+ B) from global row-major [rows][cols],
 // or the transpose of A (+ B) given as [cols][rows] when `trans`. A null A
 // loads zeros. Coalesced over the global array.
@@ -52,7 +72,7 @@ __device__ void record_breakdown(Info* info, int sys, int stage, int level) {
 // holds the FP64 pipe on this part.
 template <typename T>
 __device__ void load_blk(T* dst, int ld, const double* A, const double* B, int rows, int cols,
-                         bool trans) {
+                         bool trans, Grp g = cta_grp()) {
   const int tot = rows * cols;
   auto at = [&](int e) {
     int r, c;
@@ -61,11 +81,11 @@ __device__ void load_blk(T* dst, int ld, const double* A, const double* B, int r
     return r * ld + c;
   };
   if (A && B) {
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) dst[at(e)] = (T)(A[e] + B[e]);
+    for (int e = g.tid; e < tot; e += g.nt) dst[at(e)] = (T)(A[e] + B[e]);
   } else if (A) {
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) dst[at(e)] = (T)A[e];
+    for (int e = g.tid; e < tot; e += g.nt) dst[at(e)] = (T)A[e];
   } else {
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) dst[at(e)] = T(0);
+    for (int e = g.tid; e < tot; e += g.nt) dst[at(e)] = T(0);
   }
 }
 
@@ -73,9 +93,9 @@ __device__ void load_blk(T* dst, int ld, const double* A, const double* B, int r
 // (dst is then [cols][rows]). `lower` writes zeros above the diagonal.
 template <typename TD, typename TS>
 __device__ void store_blk(TD* dst, const TS* src, int ld, int rows, int cols, bool trans,
-                          bool lower) {
+                          bool lower, Grp g = cta_grp()) {
   const int tot = rows * cols;
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+  for (int e = g.tid; e < tot; e += g.nt) {
     int r, c;
     if (trans) { c = e / rows; r = e - c * rows; }
     else { r = e / cols; c = e - r * cols; }
@@ -87,8 +107,9 @@ __device__ void store_blk(TD* dst, const TS* src, int ld, int rows, int cols, bo
 
 // smem -> smem copy of a rows x cols block (with conversion)
 template <typename TD, typename TS>
-__device__ void copy_blk(TD* dst, int ldd, const TS* src, int lds, int rows, int cols) {
-  for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+__device__ void copy_blk(TD* dst, int ldd, const TS* src, int lds, int rows, int cols,
+                         Grp g = cta_grp()) {
+  for (int e = g.tid; e < rows * cols; e += g.nt) {
     const int r = e / cols, c = e - r * cols;
     dst[r * ldd + c] = (TD)src[r * lds + c];
   }
@@ -147,10 +168,6 @@ __device__ __forceinline__ double pivot_rsqrt(double d) {
   return __longlong_as_double(__double_as_longlong(r) - ((long long)k << 52));
 }
 
-__device__ __forceinline__ void group_bar(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 // Element table of the trailing updates of an n x n Cholesky: the pairs
 // (i, k) with 2 <= k <= i < n ordered by k descending (packed i << 16 | k),
 // so that the updates applied by column j form the prefix of length
@@ -165,77 +182,139 @@ __device__ void potrf_table(int* tab, int n) {
   }
 }
 
-// In-place lower Cholesky of A (n x n, FP64, n <= 64) by the first four warps
-// (one per FP64 sub-pipe); the CTA's other threads wait at the closing
-// __syncthreads. Writes rinv[j] = 1 / L_jj. On a pivot that is not positive
-// it sets *bad (first column + 1) and carries on (NaNs propagate; no trap).
-// Right-looking with a one-column look-ahead and one barrier per column: in
-// the phase of column j (final and scaled), warp 0 alone updates column j+1,
-// computes its pivot from the register holding the diagonal and scales it,
-// so the serial pivot chain runs on a sub-pipe of its own, while warps 1-3
-// walk the prefix of the element table `tab` for the trailing columns. Every
-// loop has a runtime trip count: on this part a predicated-off FP64
-// instruction still holds the FP64 pipe, so no FP64 work is issued for
-// inactive elements.
+// Column steps of the in-place lower Cholesky of A (n x n, FP64, n <= 64),
+// right-looking with a one-column look-ahead: in the phase of column j
+// (final and scaled), warp 0 alone updates column j+1, computes its pivot
+// from the register holding the diagonal and scales it, so the serial pivot
+// chain runs on a sub-pipe of its own, while warps 1-3 walk the prefix of the
+// element table `tab` for the trailing columns. Every loop has a runtime trip
+// count: on this part a predicated-off FP64 instruction still holds the FP64
+// pipe, so no FP64 work is issued for inactive elements. On a pivot that is
+// not positive *bad is set (first column + 1) and the factorization carries
+// on (NaNs propagate; no trap). rinv[j] = 1 / L_jj.
+__device__ __forceinline__ void potrf_col0(double* A, int ld, int n, double* rinv, int* bad, int lane) {
+  const double d = A[0];
+  const double r = pivot_rsqrt(d);
+  if (lane == 0) {
+    if (not_positive(d) && *bad == 0) *bad = 1;
+    A[0] = d * r;
+    rinv[0] = r;
+  }
+  for (int i = 1 + lane; i < n; i += 32) A[i * ld] *= r;
+}
+
+// warp 0 in the phase of column j: column j+1 updated, pivoted and scaled
+__device__ __forceinline__ void potrf_lookahead(double* A, int ld, int n, double* rinv, int* bad, int j,
+                                                int lane) {
+  const double lj = A[(j + 1) * ld + j];
+  const int i0 = j + 1 + lane, i1 = i0 + 32;
+  const bool two = j + 33 < n;  // warp-uniform: a second row per lane
+  double v0 = 0.0, v1 = 0.0;
+  if (i0 < n) v0 = fma(-A[i0 * ld + j], lj, A[i0 * ld + j + 1]);
+  if (two) {
+    if (i1 < n) v1 = fma(-A[i1 * ld + j], lj, A[i1 * ld + j + 1]);
+  }
+  double r = 0.0;
+  if (lane == 0) {  // v0 is the diagonal element (j+1, j+1)
+    if (not_positive(v0) && *bad == 0) *bad = j + 2;
+    r = pivot_rsqrt(v0);
+    A[(j + 1) * ld + j + 1] = v0 * r;
+    rinv[j + 1] = r;
+  }
+  r = __shfl_sync(0xffffffffu, r, 0);
+  if (lane > 0 && i0 < n) A[i0 * ld + j + 1] = v0 * r;
+  if (two) {
+    if (i1 < n) A[i1 * ld + j + 1] = v1 * r;
+  }
+}
+
+// warps 1-3 in the phase of column j: the updates of columns j+2.. by column j
+__device__ __forceinline__ void potrf_trailing(double* A, int ld, int n, const int* tab, int j, int t,
+                                               int nt) {
+  const int cnt = (n - 2 - j) * (n - 1 - j) / 2;
+  for (int e = t; e < cnt; e += nt) {
+    const int p = tab[e], i = p >> 16, k = p & 0xffff;
+    A[i * ld + k] = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
+  }
+}
+
+// In-place lower Cholesky by the first four warps (one per FP64 sub-pipe).
+// With `whole`, the CTA's other threads wait at the closing __syncthreads;
+// otherwise only warps 0-3 call it and it closes with their own barrier.
 constexpr int kPotrfThreads = 128;
 constexpr int kPotrfUpd = kPotrfThreads - 32;  // threads of warps 1-3
 
-__device__ void potrf_sm(double* A, int ld, int n, double* rinv, const int* tab, int* bad) {
+__device__ void potrf_sm(double* A, int ld, int n, double* rinv, const int* tab, int* bad,
+                         bool whole = true) {
   const int tid = threadIdx.x, lane = tid & 31;
-  if (tid < 32) {
-    // column 0: pivot and scaling by warp 0
-    const double d = A[0];
-    const double r = pivot_rsqrt(d);
-    if (lane == 0) {
-      if (not_positive(d) && *bad == 0) *bad = 1;
-      A[0] = d * r;
-      rinv[0] = r;
-    }
-    for (int i = 1 + lane; i < n; i += 32) A[i * ld] *= r;
-  }
+  if (tid < 32) potrf_col0(A, ld, n, rinv, bad, lane);
   if (tid < kPotrfThreads) {
     group_bar(1, kPotrfThreads);
     for (int j = 0; j + 1 < n; ++j) {
-      if (tid < 32) {
-        // look-ahead: column j+1 updated, pivoted and scaled by warp 0
-        const double lj = A[(j + 1) * ld + j];
-        const int i0 = j + 1 + lane, i1 = i0 + 32;
-        const bool two = j + 33 < n;  // warp-uniform: a second row per lane
-        double v0 = 0.0, v1 = 0.0;
-        if (i0 < n) v0 = fma(-A[i0 * ld + j], lj, A[i0 * ld + j + 1]);
-        if (two) {
-          if (i1 < n) v1 = fma(-A[i1 * ld + j], lj, A[i1 * ld + j + 1]);
-        }
-        double r = 0.0;
-        if (lane == 0) {  // v0 is the diagonal element (j+1, j+1)
-          if (not_positive(v0) && *bad == 0) *bad = j + 2;
-          r = pivot_rsqrt(v0);
-          A[(j + 1) * ld + j + 1] = v0 * r;
-          rinv[j + 1] = r;
-        }
-        r = __shfl_sync(0xffffffffu, r, 0);
-        if (lane > 0 && i0 < n) A[i0 * ld + j + 1] = v0 * r;
-        if (two) {
-          if (i1 < n) A[i1 * ld + j + 1] = v1 * r;
-        }
-      } else {
-        const int cnt = (n - 2 - j) * (n - 1 - j) / 2;
-        for (int e = tid - 32; e < cnt; e += kPotrfUpd) {
-          const int p = tab[e], i = p >> 16, k = p & 0xffff;
-          A[i * ld + k] = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
-        }
-      }
+      if (tid < 32) potrf_lookahead(A, ld, n, rinv, bad, j, lane);
+      else potrf_trailing(A, ld, n, tab, j, tid - 32, kPotrfUpd);
       group_bar(1, kPotrfThreads);
     }
   }
-  __syncthreads();
+  if (whole) __syncthreads();
 }
 
-// M[c][j] = L[c][j] / L[j][j] for c > j (strict lower triangle), rounded to TM.
+// Fused pivot factorization and panel solve (FP64): the Cholesky above and
+// Z[r0, r1) <- Z[r0, r1) L^{-T} in the division-free form of trsm_panel (the
+// same operations in the same order, so the results are bitwise those of
+// potrf_sm + panel_operand + trsm_panel). Warp 0 runs the pivot chain; in the
+// phase of column j the workers (warps 1-3 and 5-7) run, each as a tight
+// strided loop,
+//   - the trailing updates of columns j+2.. by column j,
+//   - the panel operand column M[c][j] = L[c][j] / L[j][j] (c > j),
+//   - the panel updates z_c -= z_{j-1} M[c][j-1] (c >= j) of every row,
+// so the panel lags the factorization by two columns and runs beside the
+// pivot chain instead of after it. x_c = z_c / L_cc closes the sweep. Warp 4 does not take part: it
+// returns at once and may run other work, touching neither A, rinv, M nor
+// panel rows [r0, r1). One named barrier (id 1, 224 threads) per phase; the
+// caller synchronizes the CTA before the results are read.
+constexpr int kFusedThreads = 224;
+constexpr int kFusedWorkers = 192;  // warps 1-3 and 5-7
+
+__device__ void potrf_trsm_sm(double* A, int ld, int n, double* rinv, double* M, const int* tab, int* bad,
+                              double* Z, int ldz, int r0, int r1) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid >= kPotrfThreads && tid < kPotrfThreads + 32) return;  // warp 4
+  const int w = tid < kPotrfThreads ? tid - 32 : tid - 64;       // worker index
+  const int rows = r1 - r0;
+  // panel mapping: `per` workers on a row, each on every per-th column
+  const int per = rows > 0 ? max(1, kFusedWorkers / rows) : 0;
+  const bool pact = tid >= 32 && w < rows * per;
+  const int pr = pact ? w % rows : 0, pc = pact ? w / rows : 0;
+  double* zr = Z + (r0 + pr) * ldz;
+  if (tid < 32) potrf_col0(A, ld, n, rinv, bad, lane);
+  group_bar(1, kFusedThreads);
+  for (int j = 0; j < n; ++j) {
+    if (tid < 32) {
+      if (j + 1 < n) potrf_lookahead(A, ld, n, rinv, bad, j, lane);
+    } else {
+      potrf_trailing(A, ld, n, tab, j, w, kFusedWorkers);
+      for (int c = j + 1 + w; c < n; c += kFusedWorkers) M[c * ld + j] = A[c * ld + j] * rinv[j];
+      if (pact && j >= 1) {
+        const double zj = zr[j - 1];
+        for (int c = j + pc; c < n; c += per) zr[c] = fma(-zj, M[c * ld + j - 1], zr[c]);
+      }
+    }
+    group_bar(1, kFusedThreads);
+  }
+  if (tid >= 32)
+    for (int e = w; e < rows * n; e += kFusedWorkers) {
+      const int r = e / n, c = e - r * n;
+      Z[(r0 + r) * ldz + c] *= rinv[c];
+    }
+}
+
+// Panel operand of the division-free trsm: M[c][j] = L[c][j] / L[j][j]
+// (strict lower triangle, computed as L[c][j] * rinv[j]), rounded to TM.
 template <typename TM>
-__device__ void scaled_cols(TM* M, const double* L, int ld, int n, const double* rinv) {
+__device__ void panel_operand(TM* M, const double* L, int ld, int n, const double* rinv, Grp g) {
   const int ntri = (n - 1) * n / 2;
-  for (int e = threadIdx.x; e < ntri; e += blockDim.x) {
+  for (int e = g.tid; e < ntri; e += g.nt) {
     int a, b;
     tri_rc(e, a, b);
     const int c = a + 1, j = b;
@@ -246,12 +325,15 @@ __device__ void scaled_cols(TM* M, const double* L, int ld, int n, const double*
 // Z[r0:r1) <- Z[r0:r1) L^{-T} with the pre-scaled columns M (M_cj = L_cj /
 // L_jj): for each row, u_c = z_c - sum_{k<c} u_k M_ck and x_c = u_c / L_cc.
 // FP64: column sweep (every thread on every column, FP64 from full warps),
-// thread t owning row r0 + t % rows and every (blockDim/rows)-th column.
+// thread t owning row r0 + t % rows and every (nt/rows)-th column. The
+// group needs at least as many threads as rows (true for every panel: rows
+// <= kMaxN + kMaxM per role of a split CTA, 2 kMaxN + kMaxM otherwise).
 __device__ void trsm_panel(double* Z, int ldz, int r0, int r1, const double* M, int ldm, int n,
-                           const double* rinv) {
+                           const double* rinv, Grp g) {
   const int rows = r1 - r0;
-  const int per = blockDim.x / rows;  // threads per row (>= 1: rows <= 2 kMaxN + kMaxM)
-  const int rr = threadIdx.x % rows, cc = threadIdx.x / rows;
+  if (rows <= 0) return;
+  const int per = g.nt / rows;  // threads per row (>= 1)
+  const int rr = g.tid % rows, cc = g.tid / rows;
   const bool act = cc < per;
   double* zr = Z + (r0 + rr) * ldz;
   for (int j = 0; j < n - 1; ++j) {
@@ -259,19 +341,21 @@ __device__ void trsm_panel(double* Z, int ldz, int r0, int r1, const double* M, 
       const double zj = zr[j];
       for (int c = j + 1 + cc; c < n; c += per) zr[c] = fma(-zj, M[c * ldm + j], zr[c]);
     }
-    __syncthreads();
+    gsync(g);
   }
   if (act)
     for (int c = cc; c < n; c += per) zr[c] *= rinv[c];
-  __syncthreads();
+  gsync(g);
 }
 
-// FP32: one thread per panel row runs the whole substitution in order (no
-// barriers; FP32 issue is cheap), four partial sums per dot product.
+// FP32 (M = L / diag by columns, rinv = 1/diag): one thread per panel row runs
+// the whole division-free substitution u_c = z_c - sum_{k<c} u_k M_ck, x_c =
+// u_c / L_cc in order (no barriers; FP32 issue is cheap), four partial sums
+// per dot product.
 __device__ void trsm_panel(float* Z, int ldz, int r0, int r1, const float* M, int ldm, int n,
-                           const float* rinv) {
+                           const float* rinv, Grp g) {
   const int rows = r1 - r0;
-  for (int rr = threadIdx.x; rr < rows; rr += blockDim.x) {
+  for (int rr = g.tid; rr < rows; rr += g.nt) {
     float* z = Z + (r0 + rr) * ldz;
     for (int c = 1; c < n; ++c) {
       const float* mc = M + c * ldm;
@@ -288,24 +372,30 @@ __device__ void trsm_panel(float* Z, int ldz, int r0, int r1, const float* M, in
     }
     for (int c = 0; c < n; ++c) z[c] *= rinv[c];
   }
-  __syncthreads();
+  gsync(g);
 }
 
-// T[i][j] -= sum_t Z[i][t] Z[j][t] for r0 <= j <= i < r1. The dot product is
+// T[a][b] -= sum_t Z[a][t] Z[b][t] for ra0 <= a < ra1, cb0 <= b <= a (cb0 <=
+// ra0: a rectangle of full rows beside a lower triangle; ra0 = cb0 is a plain
+// lower triangle). Panel rows below `zsplit` are read from Zlo, the others
+// from Z (same leading dimension and row numbering). The dot product is
 // formed in TZ (FP64, or FP32 in the mixed variant) and subtracted from the
 // FP64 accumulator once.
 template <typename TZ>
-__device__ void syrk_panel(double* T, int ldt, const TZ* Z, int ldz, int r0, int r1, int n) {
-  const int w = r1 - r0, ntri = w * (w + 1) / 2;
-  int a = 0, b = 0;
-  if ((int)threadIdx.x < ntri) tri_rc(threadIdx.x, a, b);
-  for (int e = threadIdx.x; e < ntri; e += blockDim.x) {
-    if (e != (int)threadIdx.x) {  // advance (a, b) by blockDim along the rows
-      b += blockDim.x;
-      while (b > a) { b -= a + 1; ++a; }
+__device__ void syrk_trap(double* T, int ldt, const TZ* Zlo, const TZ* Z, int zsplit, int ldz, int ra0,
+                          int ra1, int cb0, int n, Grp g) {
+  const int w0 = ra0 - cb0, h = ra1 - ra0;
+  const int tot = h * w0 + h * (h + 1) / 2;  // row a holds a - cb0 + 1 elements
+  // (a, b) of element g.tid, then advanced by g.nt along the rows
+  int a = ra0, b = cb0 + g.tid;
+  while (a < ra1 && b > a) { b -= a - cb0 + 1; ++a; }
+  for (int e = g.tid; e < tot; e += g.nt) {
+    if (e != g.tid) {
+      b += g.nt;
+      while (b > a) { b -= a - cb0 + 1; ++a; }
     }
-    const TZ* zi = Z + (r0 + a) * ldz;
-    const TZ* zj = Z + (r0 + b) * ldz;
+    const TZ* zi = (a < zsplit ? Zlo : Z) + a * ldz;
+    const TZ* zj = (b < zsplit ? Zlo : Z) + b * ldz;
     TZ s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     int t = 0;
     for (; t + 3 < n; t += 4) {
@@ -315,9 +405,38 @@ __device__ void syrk_panel(double* T, int ldt, const TZ* Z, int ldz, int r0, int
       s3 = fma(zi[t + 3], zj[t + 3], s3);
     }
     for (; t < n; ++t) s0 = fma(zi[t], zj[t], s0);
-    T[(r0 + a) * ldt + (r0 + b)] -= (double)((s0 + s1) + (s2 + s3));
+    T[a * ldt + b] -= (double)((s0 + s1) + (s2 + s3));
   }
-  __syncthreads();
+  gsync(g);
+}
+
+// Thread-block-cluster primitives (a factor task may run as a pair of CTAs).
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// split-phase hardware barrier over every thread of the cluster; arrive
+// releases this thread's earlier writes (local and remote shared memory),
+// wait acquires the other CTAs'
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of this CTA's shared-memory location p in CTA `rank`
+__device__ __forceinline__ unsigned cluster_addr(const void* p, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_cluster(unsigned addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster(unsigned addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
 struct SegGeom {
@@ -340,7 +459,37 @@ __device__ __forceinline__ SegGeom seg_geom(const LevelDesc& d, int k) {
 // TZ = double: every operation in FP64. TZ = float: FP64 pivots and Schur
 // accumulator, FP32 panel (trsm and dot products), FP32 factor copy written
 // for the correction solves.
+//
+// Roles. The panel rows of a segment with fill-in (k >= 1) fall into two
+// groups. The producer runs the chain of Algorithm 1 proper: potrf(D_i), the
+// E- and G-rows, and their Schur updates D_{i+1}, G_{i+1}, R~_k. The consumer
+// runs the fill-in rows: W_i D-hat_i^{-T} and the updates A~_k, Q~_k^T and
+// W_{i+1}, which read the producer's D-hat_i, E-hat_i and G-hat_i but feed
+// nothing back into the chain, so the consumer may lag a stage behind. Three
+// layouts (`mode`):
+//   kWhole  one CTA runs both (segment 1, the top level, and mixed levels
+//           that are not paired);
+//   kSplit  one CTA, warps 0-3 producer and warps 4-7 consumer (FP64 levels
+//           with more segments than SM pairs): the producer factors D_{i+1}
+//           while the consumer is still on stage i. Hand-offs are named
+//           barriers, each used once per stage by both roles:
+//             kBarFullM  M_i, rinv_i ready       kBarFreeM  M_i read
+//             kBarFullZ  E-hat_i, G-hat_i ready  kBarFreeZ  E-hat_i, G-hat_i read
+//   kPair   a cluster of two CTAs (levels with few segments): CTA 0 is the
+//           producer, CTA 1 the consumer, each on an SM of its own, so a
+//           segment gets two SMs' FP64 pipes. After its trsm of stage i the
+//           producer stores M_i, rinv_i, E-hat_i, G-hat_i into buffer i % 2
+//           of the consumer's shared memory and arrives at cluster barrier
+//           phase i; the consumer arrives at phase i when it is done with
+//           stage i-1 and waits for it before stage i; the producer waits for
+//           phase i-1 before it overwrites buffer i % 2 (double buffering).
+//           A last phase, after every remote store, ends the task.
 // ---------------------------------------------------------------------------
+static_assert(kFactorThreads == 256, "the factor roles assume 8 warps per CTA");
+constexpr int kWhole = 0, kSplit = 1, kPair = 2;
+constexpr int kBarProd = 2, kBarCons = 3, kBarFullM = 4, kBarFreeM = 5, kBarFullZ = 6, kBarFreeZ = 7;
+constexpr int kRoleThreads = 128;
+
 template <typename TZ>
 __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __restrict__ descs,
                                                            const Task* __restrict__ tasks,
@@ -348,10 +497,11 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
                                                            const double* __restrict__ uE,
                                                            const double* __restrict__ uG,
                                                            const double* __restrict__ uR,
-                                                           Info* info) {
+                                                           Info* info, int pair) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
-  const Task tk = tasks[blockIdx.x];
+  const unsigned rank = pair ? cluster_rank() : 0u;
+  const Task tk = tasks[pair ? blockIdx.x >> 1 : blockIdx.x];
   const LevelDesc& d = descs[tk.desc];
   constexpr bool mixed = sizeof(TZ) == 4;
   const int n = d.n, m = d.m, R = 2 * n + m;
@@ -368,6 +518,15 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
   const SegGeom g = seg_geom(d, tk.seg);
   const int s = g.f - 1;  // separator of this segment (k >= 1)
   const size_t nn = (size_t)n * n, mn = (size_t)m * n;
+  const int mode = pair ? kPair : (g.hasW && !mixed) ? kSplit : kWhole;
+  // consumer buffers of the pair layout: buffer 0 is (M, rinvZ, Z rows [0, n+m)),
+  // buffer 1 reuses the pivot block, rinv and the first rows of T, which a
+  // consumer CTA has no other use for
+  auto Mbuf = [&](int b) { return b ? (TZ*)Dfac : M; };
+  auto rinvbuf = [&](int b) { return b ? (TZ*)rinv : rinvZ; };
+  auto Zbuf = [&](int b) { return b ? (TZ*)T : Z; };
+  const bool eg = mode != kPair || rank == 0;       // this CTA holds the E/G rows
+  const bool wr = g.hasW && (mode != kPair || rank == 1);  // this CTA holds the W rows
 
   // level inputs: the caller's arrays at level 1, the slots of the level above otherwise
   const double* Din = d.level == 1 ? uD + d.offD : d.Dw;
@@ -381,95 +540,285 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
 
   if (threadIdx.x == 0) bad = 0;
   for (int e = threadIdx.x; e < R * ldT; e += blockDim.x) T[e] = 0.0;
-  potrf_table(tab, n);
+  if (eg) potrf_table(tab, n);
   __syncthreads();
-  load_blk(Dfac, ldD, Dp(Din, g.f), Dp(D2, g.f), n, n, false);
-  if (g.len > 1 || g.hasF) load_blk(Z, ldZ, Dp(Ein, g.f), none, n, n, false);
-  if (m) load_blk(Z + oG * ldZ, ldZ, Gp(Gin, g.f), Gp(G2, g.f), m, n, false);
-  if (g.hasW) {
+  if (eg) {
+    load_blk(Dfac, ldD, Dp(Din, g.f), Dp(D2, g.f), n, n, false);
+    if (g.len > 1 || g.hasF) load_blk(Z, ldZ, Dp(Ein, g.f), none, n, n, false);
+    if (m) load_blk(Z + oG * ldZ, ldZ, Gp(Gin, g.f), Gp(G2, g.f), m, n, false);
+    if (g.len > 1) {
+      load_blk(T, ldT, Dp(Din, g.f + 1), Dp(D2, g.f + 1), n, n, false);          // D_{2}
+      if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, g.f + 1), Gp(G2, g.f + 1), m, n, false);
+    }
+  }
+  if (wr) {
     load_blk(Z + oW * ldZ, ldZ, Dp(Ein, s), none, n, n, true);                 // W_1 = B_k = E[s]^T
     load_blk(T + oW * ldT + oW, ldT, Dp(Din, s), Dp(D2, s), n, n, false);       // A_k
     if (m) load_blk(T + oW * ldT + oG, ldT, Gp(Gin, s), Gp(G2, s), n, m, true);  // Q_k^T
   }
-  if (g.len > 1) {
-    load_blk(T, ldT, Dp(Din, g.f + 1), Dp(D2, g.f + 1), n, n, false);          // D_{2}
-    if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, g.f + 1), Gp(G2, g.f + 1), m, n, false);
-  }
   __syncthreads();
+  if (mode == kPair) {
+    // both CTAs have started before any remote store
+    cluster_arrive();
+    cluster_wait();
+  }
 
-  for (int i = 0; i < g.len; ++i) {
-    const int j = g.f + i;
-    const bool eRows = (i < g.len - 1) || g.hasF;
-    const int r0 = eRows ? 0 : n;
-    const int r1 = n + m + (g.hasW ? n : 0);
-    potrf_sm(Dfac, ldD, n, rinv, tab, &bad);
-    if (bad && threadIdx.x == 0) { record_breakdown(info, d.sys, d.nat[j], d.level); bad = 0; }
-    scaled_cols(M, Dfac, ldD, n, rinv);
-    for (int e = threadIdx.x; e < n; e += blockDim.x) rinvZ[e] = (TZ)rinv[e];
-    __syncthreads();
-    trsm_panel(Z, ldZ, r0, r1, M, ldD, n, rinvZ);
-    // factor blocks of this stage
-    store_blk(d.Ld + (size_t)j * nn, Dfac, ldD, n, n, false, true);
-    {
-      double* P = d.Lp + (size_t)j * R * n;
-      float* Pf = mixed ? d.Lpf + (size_t)j * R * n : nullptr;
-      for (int e = threadIdx.x; e < R * n; e += blockDim.x) {
-        const int r = e / n, c = e - r * n;
-        const TZ v = (r >= r0 && r < r1) ? Z[r * ldZ + c] : TZ(0);
-        P[e] = (double)v;
-        if (mixed) Pf[e] = (float)v;
-      }
-    }
-    // D-hat with its rows divided by their diagonal (backward substitution):
-    // the strict lower triangle is computed, the rest zero-filled, so that no
-    // FP64 multiply is issued for the upper half
+  const bool producer = mode == kWhole || (mode == kSplit && (int)threadIdx.x < kRoleThreads) ||
+                        (mode == kPair && rank == 0);
+  // factor blocks of stage j from the pivot factor L (Dp_, ld ldD) and
+  // rv = 1/diag: Ld = L, LdR = L with its rows divided by their diagonal
+  // (backward substitution), LdM = L with its columns divided by their
+  // diagonal (forward substitution: the panel operand Ms when given, else
+  // formed here with the same rounding), Lri = rv. Strict lower triangles are
+  // computed and the rest zero-filled, so that no FP64 multiply is issued for
+  // an upper half.
+  auto store_pivot = [&](int j, const double* Dp_, const double* rv, const TZ* Ms, Grp G) {
+    store_blk(d.Ld + (size_t)j * nn, Dp_, ldD, n, n, false, true, G);
     TZ* LdRj = mixed ? (TZ*)(d.LdRf + (size_t)j * nn) : (TZ*)(d.LdR + (size_t)j * nn);
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) LdRj[e] = TZ(0);
-    store_blk(mixed ? (TZ*)(d.LdMf + (size_t)j * nn) : (TZ*)(d.LdM + (size_t)j * nn), M, ldD, n, n,
-              false, true);
-    __syncthreads();
-    for (int e = threadIdx.x; e < (n - 1) * n / 2; e += blockDim.x) {
+    TZ* LdMj = mixed ? (TZ*)(d.LdMf + (size_t)j * nn) : (TZ*)(d.LdM + (size_t)j * nn);
+    for (int e = G.tid; e < n * n; e += G.nt) LdRj[e] = TZ(0);
+    if (Ms) store_blk(LdMj, Ms, ldD, n, n, false, true, G);
+    else
+      for (int e = G.tid; e < n * n; e += G.nt) LdMj[e] = TZ(0);
+    gsync(G);
+    for (int e = G.tid; e < (n - 1) * n / 2; e += G.nt) {
       int a, b;
       tri_rc(e, a, b);
       const int r = a + 1, c = b;
-      LdRj[r * n + c] = (TZ)(Dfac[r * ldD + c] * rinv[r]);
+      LdRj[r * n + c] = (TZ)(Dp_[r * ldD + c] * rv[r]);
+      if (!Ms) LdMj[r * n + c] = (TZ)(Dp_[r * ldD + c] * rv[c]);
     }
     if (mixed)
-      for (int e = threadIdx.x; e < n; e += blockDim.x) d.Lrif[(size_t)j * n + e] = (float)rinv[e];
-    for (int e = threadIdx.x; e < n; e += blockDim.x) d.Lri[(size_t)j * n + e] = rinv[e];
-    syrk_panel(T, ldT, Z, ldZ, r0, r1, n);
-    if (i + 1 < g.len) {
-      // rotate: the updated blocks become the next stage's inputs
-      copy_blk(Dfac, ldD, T, ldT, n, n);                                       // D_{i+1}
-      if (m) copy_blk(Z + oG * ldZ, ldZ, T + oG * ldT, ldT, m, n);             // G_{i+1}
-      if (g.hasW) copy_blk(Z + oW * ldZ, ldZ, T + oW * ldT, ldT, n, n);        // W_{i+1}
-      __syncthreads();
-      if ((i + 1 < g.len - 1) || g.hasF) load_blk(Z, ldZ, Dp(Ein, j + 1), none, n, n, false);
-      if (i + 2 < g.len) {
-        load_blk(T, ldT, Dp(Din, j + 2), Dp(D2, j + 2), n, n, false);
-        if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, j + 2), Gp(G2, j + 2), m, n, false);
-      } else {
-        load_blk(T, ldT, none, none, n, n, false);
-        if (m) load_blk(T + oG * ldT, ldT, none, none, m, n, false);
+      for (int e = G.tid; e < n; e += G.nt) d.Lrif[(size_t)j * n + e] = (float)rv[e];
+    for (int e = G.tid; e < n; e += G.nt) d.Lri[(size_t)j * n + e] = rv[e];
+  };
+  // panel rows [0, rows) of Lp for stage j: rows outside [r0, r1) are zero
+  // (a consumer writes the W-rows of a split or paired segment)
+  auto store_panel = [&](int j, int r0, int r1, int rows, Grp G) {
+    double* Pd = d.Lp + (size_t)j * R * n;
+    float* Pf = mixed ? d.Lpf + (size_t)j * R * n : nullptr;
+    for (int e = G.tid; e < rows * n; e += G.nt) {
+      const int r = e / n, c = e - r * n;
+      const TZ v = (r >= r0 && r < r1) ? Z[r * ldZ + c] : TZ(0);
+      Pd[e] = (double)v;
+      if (mixed) Pf[e] = (float)v;
+    }
+  };
+  // hand the trsm operand (strict lower triangle of Msrc, ld ldD), its
+  // 1/diag and panel rows [r0, r1) of stage i to the consumer CTA of a pair
+  auto push_stage = [&](int i, const TZ* Msrc, const TZ* rsrc, int r0, int r1, Grp G) {
+    const int b = i & 1;
+    const unsigned aM = cluster_addr(Mbuf(b), 1), aR = cluster_addr(rinvbuf(b), 1),
+                   aZ = cluster_addr(Zbuf(b), 1);
+    const int ntri = (n - 1) * n / 2;
+    for (int e = G.tid; e < ntri; e += G.nt) {
+      int a, c;
+      tri_rc(e, a, c);
+      const int off = (a + 1) * ldD + c;
+      st_cluster(aM + off * (unsigned)sizeof(TZ), Msrc[off]);
+    }
+    for (int e = G.tid; e < n; e += G.nt) st_cluster(aR + e * (unsigned)sizeof(TZ), rsrc[e]);
+    for (int e = G.tid; e < (r1 - r0) * n; e += G.nt) {
+      const int r = r0 + e / n, c = e - (r - r0) * n;
+      const int off = r * ldZ + c;
+      st_cluster(aZ + off * (unsigned)sizeof(TZ), Z[off]);
+    }
+  };
+  // rotate the panel after the Schur update of stage i (group G): the
+  // updated blocks become stage i+1's inputs, the next ones are loaded
+  auto rotate = [&](int i, int j, bool withW, Grp G) {
+    if (m) copy_blk(Z + oG * ldZ, ldZ, T + oG * ldT, ldT, m, n, G);          // G_{i+1}
+    if (withW) copy_blk(Z + oW * ldZ, ldZ, T + oW * ldT, ldT, n, n, G);      // W_{i+1}
+    if ((i + 1 < g.len - 1) || g.hasF) load_blk(Z, ldZ, Dp(Ein, j + 1), none, n, n, false, G);
+    gsync(G);
+    if (withW) load_blk(T + oW * ldT, ldT, none, none, n, n, false, G);     // W_{i+2} <- 0
+    if (i + 2 < g.len) {
+      load_blk(T, ldT, Dp(Din, j + 2), Dp(D2, j + 2), n, n, false, G);
+      if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, j + 2), Gp(G2, j + 2), m, n, false, G);
+    } else {
+      load_blk(T, ldT, none, none, n, n, false, G);
+      if (m) load_blk(T + oG * ldT, ldT, none, none, m, n, false, G);
+    }
+    gsync(G);
+  };
+
+  if (producer && mode == kSplit) {
+    // FP64, E- and G-rows on warps 0-3 (the consumer warps run the W-rows)
+    const Grp P{(int)threadIdx.x, kRoleThreads, kBarProd};
+    const int pr1 = n + m;
+    potrf_sm(Dfac, ldD, n, rinv, tab, &bad, false);
+    for (int i = 0; i < g.len; ++i) {
+      const int j = g.f + i;
+      const bool eRows = (i < g.len - 1) || g.hasF;
+      const int r0 = eRows ? 0 : n;
+      if (threadIdx.x == 0 && bad) { record_breakdown(info, d.sys, d.nat[j], d.level); bad = 0; }
+      if (i > 0) group_bar(kBarFreeM, kFactorThreads);
+      panel_operand(M, Dfac, ldD, n, rinv, P);
+      for (int e = P.tid; e < n; e += P.nt) rinvZ[e] = (TZ)rinv[e];
+      gsync(P);
+      group_arrive(kBarFullM, kFactorThreads);
+      trsm_panel(Z, ldZ, r0, pr1, M, ldD, n, rinvZ, P);
+      group_arrive(kBarFullZ, kFactorThreads);
+      store_pivot(j, Dfac, rinv, M, P);
+      store_panel(j, r0, pr1, pr1, P);
+      syrk_trap(T, ldT, Z, Z, 0, ldZ, r0, pr1, r0, n, P);
+      if (i + 1 < g.len) {
+        // D_{i+1} is final: factor it now, then rotate the panel once the
+        // consumer has read E-hat_i and G-hat_i
+        copy_blk(Dfac, ldD, T, ldT, n, n, P);
+        gsync(P);
+        potrf_sm(Dfac, ldD, n, rinv, tab, &bad, false);
+        group_bar(kBarFreeZ, kFactorThreads);
+        rotate(i, j, false, P);
       }
-      if (g.hasW) load_blk(T + oW * ldT, ldT, none, none, n, n, false);        // W_{i+2} <- 0
+    }
+  } else if (producer && !mixed) {
+    // FP64, whole CTA on the E- and G-rows (no fill-in rows here: segment 1,
+    // the top level, or the producer of a pair). Per stage: the fused pivot
+    // factorization and panel solve (warps 0-3 and 5-7) while warp 4 writes
+    // the previous stage's pivot blocks from the other pivot buffer; then the
+    // hand-off to the consumer, the Schur update and the rotation.
+    const Grp P = cta_grp();
+    const Grp W4{(int)(threadIdx.x & 31), 32, -1};
+    const bool w4 = (threadIdx.x >> 5) == 4;
+    const int pr1 = n + m;
+    const bool push = mode == kPair && g.hasW;
+    double* const Dfac2 = (double*)(smraw + lay.oDfac2);
+    double* const rinv2 = (double*)(smraw + lay.oRinv2);
+    auto Dbuf = [&](int b) { return b ? Dfac2 : Dfac; };
+    auto rvbuf = [&](int b) { return b ? rinv2 : rinv; };
+    for (int i = 0; i < g.len; ++i) {
+      const int j = g.f + i;
+      const int cur = i & 1;
+      const bool eRows = (i < g.len - 1) || g.hasF;
+      const int r0 = eRows ? 0 : n;
+      if (w4) {
+        if (i > 0) store_pivot(j - 1, Dbuf(cur ^ 1), rvbuf(cur ^ 1), nullptr, W4);
+      } else {
+        potrf_trsm_sm(Dbuf(cur), ldD, n, rvbuf(cur), (double*)M, tab, &bad, (double*)Z, ldZ, r0, pr1);  // TZ = double here
+      }
       __syncthreads();
+      if (threadIdx.x == 0 && bad) { record_breakdown(info, d.sys, d.nat[j], d.level); bad = 0; }
+      if (push) {
+        if (i > 0) cluster_wait();  // the consumer is done with stage i-2 (buffer i % 2)
+        push_stage(i, M, (const TZ*)rvbuf(cur), r0, pr1, P);
+        cluster_arrive();
+      }
+      store_panel(j, r0, pr1, mode == kWhole ? R : pr1, P);
+      syrk_trap(T, ldT, Z, Z, 0, ldZ, r0, pr1, r0, n, P);
+      if (i + 1 < g.len) {
+        copy_blk(Dbuf(cur ^ 1), ldD, T, ldT, n, n, P);                      // D_{i+1}
+        rotate(i, j, false, P);
+      } else {
+        store_pivot(j, Dbuf(cur), rvbuf(cur), nullptr, P);
+      }
+    }
+    if (push) cluster_wait();  // phase of the last stage
+  } else if (producer) {
+    // FP32 panel (mixed), whole CTA on the E- and G-rows (and the W-rows in
+    // the whole layout), with a one-stage look-ahead: once the E-rows of
+    // stage i are solved and D_{i+1} = D_{i+1} - E-hat_i E-hat_i^T is formed,
+    // warps 0-3 factor D_{i+1} into the second pivot buffer while warps 4-7
+    // write stage i's factor blocks, apply the remaining Schur updates of
+    // stage i (G- and W-rows) and rotate the panel.
+    const Grp P = cta_grp();
+    const Grp U{(int)threadIdx.x - kRoleThreads, kRoleThreads, kBarCons};  // warps 4-7
+    const bool upd = (int)threadIdx.x >= kRoleThreads;
+    const int pr1 = n + m + (mode == kWhole && g.hasW ? n : 0);  // end of the CTA's panel rows
+    const bool push = mode == kPair && g.hasW;
+    double* const Dfac2 = (double*)(smraw + lay.oDfac2);
+    double* const rinv2 = (double*)(smraw + lay.oRinv2);
+    auto Dbuf = [&](int b) { return b ? Dfac2 : Dfac; };
+    auto rvbuf = [&](int b) { return b ? rinv2 : rinv; };
+    potrf_sm(Dfac, ldD, n, rinv, tab, &bad, true);
+    for (int i = 0; i < g.len; ++i) {
+      const int j = g.f + i;
+      const int cur = i & 1;
+      const bool eRows = (i < g.len - 1) || g.hasF;
+      const int r0 = eRows ? 0 : n;
+      if (threadIdx.x == 0 && bad) { record_breakdown(info, d.sys, d.nat[j], d.level); bad = 0; }
+      panel_operand(M, Dbuf(cur), ldD, n, rvbuf(cur), P);
+      for (int e = P.tid; e < n; e += P.nt) rinvZ[e] = (TZ)rvbuf(cur)[e];
+      gsync(P);
+      trsm_panel(Z, ldZ, r0, pr1, M, ldD, n, rinvZ, P);
+      if (push) {
+        if (i > 0) cluster_wait();  // the consumer is done with stage i-2 (buffer i % 2)
+        push_stage(i, M, rinvZ, r0, n + m, P);
+        cluster_arrive();
+      }
+      if (i + 1 < g.len) {
+        // E-rows present (eRows): D_{i+1} -= E-hat E-hat^T, then the fork
+        syrk_trap(T, ldT, Z, Z, 0, ldZ, 0, n, 0, n, P);
+        copy_blk(Dbuf(cur ^ 1), ldD, T, ldT, n, n, P);
+        __syncthreads();
+        if (!upd) {
+          potrf_sm(Dbuf(cur ^ 1), ldD, n, rvbuf(cur ^ 1), tab, &bad, false);
+        } else {
+          store_pivot(j, Dbuf(cur), rvbuf(cur), M, U);
+          store_panel(j, r0, pr1, mode == kWhole ? R : n + m, U);
+          syrk_trap(T, ldT, Z, Z, 0, ldZ, n, pr1, 0, n, U);                 // G- (and W-) rows
+          rotate(i, j, mode == kWhole && g.hasW, U);
+        }
+        __syncthreads();
+      } else {
+        store_pivot(j, Dbuf(cur), rvbuf(cur), M, P);
+        store_panel(j, r0, pr1, mode == kWhole ? R : n + m, P);
+        syrk_trap(T, ldT, Z, Z, 0, ldZ, r0, pr1, r0, n, P);
+      }
+    }
+    if (push) cluster_wait();  // phase of the last stage
+  } else if (wr) {
+    // fill-in rows W
+    const Grp C = mode == kSplit ? Grp{(int)threadIdx.x - kRoleThreads, kRoleThreads, kBarCons} : cta_grp();
+    for (int i = 0; i < g.len; ++i) {
+      const int j = g.f + i;
+      const bool eRows = (i < g.len - 1) || g.hasF;
+      const int r0 = eRows ? 0 : n;
+      const int b = mode == kPair ? (i & 1) : 0;
+      if (mode == kSplit) {
+        group_bar(kBarFullM, kFactorThreads);
+      } else {
+        cluster_arrive();  // done with stage i-1
+        cluster_wait();    // stage i's blocks are in buffer b
+      }
+      trsm_panel(Z, ldZ, oW, R, Mbuf(b), ldD, n, rinvbuf(b), C);
+      if (mode == kSplit && i + 1 < g.len) group_arrive(kBarFreeM, kFactorThreads);
+      {
+        double* Pd = d.Lp + (size_t)j * R * n + (size_t)oW * n;
+        float* Pf = mixed ? d.Lpf + (size_t)j * R * n + (size_t)oW * n : nullptr;
+        for (int e = C.tid; e < n * n; e += C.nt) {
+          const int r = e / n, c = e - r * n;
+          const TZ v = Z[(oW + r) * ldZ + c];
+          Pd[e] = (double)v;
+          if (mixed) Pf[e] = (float)v;
+        }
+      }
+      if (mode == kSplit) group_bar(kBarFullZ, kFactorThreads);
+      syrk_trap(T, ldT, Zbuf(b), Z, oW, ldZ, oW, R, r0, n, C);
+      if (i + 1 < g.len) {
+        if (mode == kSplit) group_arrive(kBarFreeZ, kFactorThreads);
+        copy_blk(Z + oW * ldZ, ldZ, T + oW * ldT, ldT, n, n, C);               // W_{i+1}
+        gsync(C);
+        load_blk(T + oW * ldT, ldT, none, none, n, n, false, C);               // W_{i+2} <- 0
+        gsync(C);
+      }
     }
   }
+  __syncthreads();
 
   if (!d.is_top) {
     const int k = tk.seg;
-    if (g.hasF) {
+    if (eg && g.hasF) {
       store_blk(d.DB + (size_t)k * nn, T, ldT, n, n, false, true);             // -F^ F^T
       if (m) store_blk(d.GB + (size_t)k * mn, T + oG * ldT, ldT, m, n, false, false);  // -G^ F^T
     }
-    if (g.hasW) {
+    if (wr) {
       store_blk(d.DA + (size_t)(k - 1) * nn, T + oW * ldT + oW, ldT, n, n, false, true);  // A~_k
       if (m) store_blk(d.GA + (size_t)(k - 1) * mn, T + oW * ldT + oG, ldT, n, m, true, false);  // Q~_k
       if (g.hasF) store_blk(d.EN + (size_t)(k - 1) * nn, T + oW * ldT, ldT, n, n, true, false);  // H~_k
     }
-    if (m) store_blk(d.Rpart + (size_t)k * m * m, T + oG * ldT + oG, ldT, m, m, false, true);
-  } else if (m) {
+    if (eg && m) store_blk(d.Rpart + (size_t)k * m * m, T + oG * ldT + oG, ldT, m, m, false, true);
+  } else if (eg && m) {
     // corner: R-hat = chol(R + sum_k R~_k over every level), in a fixed order
     double* Rs = Dfac;  // reuse
     const int ldR = odd(m);
@@ -487,6 +836,12 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
     if (bad && threadIdx.x == 0) record_breakdown(info, d.sys, d.Nnat, d.level);
     store_blk(d.Rhat, Rs, ldR, m, m, false, true);
     for (int e = threadIdx.x; e < m; e += blockDim.x) d.Rri[e] = rinv[e];
+  }
+  if (mode == kPair) {
+    // a segment without fill-in leaves its consumer idle; every CTA of the
+    // pair then meets once more, after which no remote store is in flight
+    cluster_arrive();
+    cluster_wait();
   }
 }
 
@@ -1173,7 +1528,7 @@ size_t residual_smem_bytes(int n) {
                            (size_t)kMaxM * kRhsChunk + 4 * 256);
 }
 
-int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
+int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
                   void* stream) {
   if (ntasks <= 0) return 0;
@@ -1181,11 +1536,23 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
   const void* fn = mixed ? (const void*)k_factor<float> : (const void*)k_factor<double>;
   int e = set_smem(fn, sm);
   if (e) return e;
-  if (mixed)
-    k_factor<float><<<ntasks, kFactorThreads, sm, (cudaStream_t)stream>>>(d, t, D, E, G, R, info);
-  else
-    k_factor<double><<<ntasks, kFactorThreads, sm, (cudaStream_t)stream>>>(d, t, D, E, G, R, info);
-  return (int)cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = dim3((unsigned)(pair ? 2 * ntasks : ntasks));
+  cfg.blockDim = dim3(kFactorThreads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = (cudaStream_t)stream;
+  if (pair) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  const int p = pair ? 1 : 0;
+  if (mixed) return (int)cudaLaunchKernelEx(&cfg, k_factor<float>, d, t, D, E, G, R, info, p);
+  return (int)cudaLaunchKernelEx(&cfg, k_factor<double>, d, t, D, E, G, R, info, p);
 }
 
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,

@@ -174,8 +174,8 @@ extern "C" kkt_status kkt_solve_noalloc(int N, int n, int m, int P, const double
 
   const kkt::LevelDesc* ddesc = (const kkt::LevelDesc*)(base + oDesc);
   const kkt::Task* dtask = (const kkt::Task*)(base + oTask);
-  if (kkt::launch_factor(ddesc, dtask, P, n, m, 0, D, E, G, R, dinfo, stream)) return KKT_ERR_CUDA;
-  if (two && kkt::launch_factor(ddesc, dtask + P, 1, n, m, 0, D, E, G, R, dinfo, stream)) return KKT_ERR_CUDA;
+  if (kkt::launch_factor(ddesc, dtask, P, n, m, 0, 0, D, E, G, R, dinfo, stream)) return KKT_ERR_CUDA;
+  if (two && kkt::launch_factor(ddesc, dtask + P, 1, n, m, 0, 0, D, E, G, R, dinfo, stream)) return KKT_ERR_CUDA;
   for (int c0 = 0; c0 < nrhs; c0 += kkt::kRhsChunk) {
     const int nr = nrhs - c0 < kkt::kRhsChunk ? nrhs - c0 : kkt::kRhsChunk;
     if (kkt::launch_forward(ddesc, dtask, P, n, m, 0, b + c0, ldb, nr, nullptr, stream)) return KKT_ERR_CUDA;

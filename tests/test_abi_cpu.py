@@ -65,21 +65,42 @@ def test_flop_model_matches_oracle_counters(kkt, orc, N, n, m, P):
     assert got["sequential_factor"] == pytest.approx(seq_std, rel=1e-12)
 
 
+@pytest.mark.parametrize("paired", [False, True])
 @pytest.mark.parametrize("N,n,m,P", [(1024, 32, 8, 152), (1024, 32, 8, 304), (151, 32, 8, 38), (8192, 6, 2, 2048),
                                      (50, 4, 0, 25), (16, 8, 4, 4), (37, 32, 8, 10), (5, 3, 0, 3)])
-def test_balanced_partition(kkt, N, n, m, P):
+def test_balanced_partition(kkt, N, n, m, P, paired):
     """Balanced mode: same constraint as Eq. (13), every segment >= 1 stage,
     the other segments within one stage of each other, and a maximum segment
-    cost never above the paper rule's."""
-    seg = kkt.kkt_partition_balanced(N, n, m, P)
+    cost (under the stage costs of the layout) never above the paper rule's.
+    A paired segment's stage costs 1.05 first-segment stages (the fill-in
+    rows run on the other CTA of the pair)."""
+    seg = kkt.kkt_partition_balanced(N, n, m, P, paired)
     assert len(seg) == P and min(seg) >= 1
     assert sum(seg) + P - 1 == N
     if P > 2:
         assert max(seg[1:]) - min(seg[1:]) <= 1
     w = lambda R: n ** 3 / 3 + n * n / 2 + n / 6 + R * n * n + R * (R + 1) * n + 5 * n ** 3
-    cost = lambda s: max([s[0] * w(n + m)] + [x * w(2 * n + m) for x in s[1:]])
+    w2 = 1.05 * w(n + m) if paired else w(2 * n + m)
+    cost = lambda s: max([s[0] * w(n + m)] + [x * w2 for x in s[1:]])
     paper = kkt.kkt_partition_rule(N, P)
     assert cost(seg) <= cost(paper) + 1e-9
+    if paired and P > 2:
+        assert abs(seg[0] - seg[1]) <= 1 + seg[1] // 10   # nearly equal lengths
+
+
+def test_plan_flops_follow_pairing(kkt):
+    """The paired levels of a plan depend on the SM count only through
+    2 x tasks <= SMs; with no SMs nothing is paired."""
+    plan = [152, 38, 10, 1]
+    a = kkt.kkt_plan_flops(1024, 32, 8, plan, kkt.KKT_PARTITION_BALANCED, sms=0)
+    b = kkt.kkt_plan_flops(1024, 32, 8, plan, kkt.KKT_PARTITION_BALANCED, sms=152)
+    c = kkt.kkt_plan_flops(1024, 32, 8, plan, kkt.KKT_PARTITION_BALANCED, sms=75)
+    assert a["sequential_factor"] == b["sequential_factor"]
+    assert a["factor"] != b["factor"]        # level 2 (38 tasks) is paired on 152 SMs
+    assert c["factor"] != b["factor"]        # on 75 SMs level 2 is not paired
+    d = kkt.kkt_plan_flops(1024, 32, 8, plan, kkt.KKT_PARTITION_PAPER, sms=152)
+    e = kkt.kkt_plan_flops(1024, 32, 8, plan, kkt.KKT_PARTITION_PAPER, sms=0)
+    assert d == e                            # the paper rule ignores the layout
 
 
 def test_invalid_arguments(kkt):

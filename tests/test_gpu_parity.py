@@ -33,7 +33,10 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
 
 
-def gpu_solve(kkt, D, E, G, R, b, P=1, levels=None, want_factor=False, balanced=False):
+PAIRINGS = ["off", "on"]
+
+
+def gpu_solve(kkt, D, E, G, R, b, P=1, levels=None, want_factor=False, balanced=False, pairing=None):
     import torch
     N, n = D.shape[0], D.shape[1]
     m = 0 if R is None or np.size(R) == 0 else R.shape[0]
@@ -44,6 +47,9 @@ def gpu_solve(kkt, D, E, G, R, b, P=1, levels=None, want_factor=False, balanced=
     else:
         h = kkt.kkt_create(N, n, m, P)
     try:
+        if pairing is not None:
+            kkt.kkt_set_pairing(h, {"off": kkt.KKT_PAIR_OFF, "on": kkt.KKT_PAIR_ON,
+                                    "auto": kkt.KKT_PAIR_AUTO}[pairing])
         Ed = dev(E) if N > 1 else None
         Gd = dev(G) if m else None
         Rd = dev(R) if m else None
@@ -91,13 +97,15 @@ def check_solution(orc, D, E, G, R, x, b, xo=None, fwd_tol=None):
 
 # ------------------------------------------------------------- config 1
 
+@pytest.mark.parametrize("pairing", PAIRINGS)
 @pytest.mark.parametrize("P", [1, 2, 3, 4, 5, 8])
-def test_known_factor_blocks_and_solution(kkt, orc, P):
+def test_known_factor_blocks_and_solution(kkt, orc, P, pairing):
     """N = 16 stages of n = 8, arrow m = 4, Psi = L L^T: factor blocks equal
-    the oracle's Algorithm 1 blocks; at P = 1 they equal the generating L."""
+    the oracle's Algorithm 1 blocks; at P = 1 they equal the generating L.
+    Both factor layouts (one CTA per segment, or a pair of CTAs)."""
     D, E, G, R, Lf = gen.known_factor(16, 8, 4, seed=0)
     b = gen.rhs(16 * 8 + 4, 1, seed=1)
-    x, F = gpu_solve(kkt, D, E, G, R, b, P=P, want_factor=True)
+    x, F = gpu_solve(kkt, D, E, G, R, b, P=P, want_factor=True, pairing=pairing)
     Fo = orc.par_factor(D, E, G, R, P=P)
     xo = orc.par_solve(Fo, b)
     for key in ("Ld", "Le", "Lw", "Lh", "Lg", "Lr"):
@@ -114,8 +122,10 @@ def test_known_factor_blocks_and_solution(kkt, orc, P):
 
 @pytest.mark.parametrize("N,n,m,P", [
     (1, 8, 4, 1), (2, 8, 0, 1), (3, 1, 0, 2), (3, 1, 1, 2), (5, 3, 2, 3), (9, 5, 0, 5),
-    (17, 7, 3, 9), (11, 2, 16, 4), (24, 48, 4, 3), (30, 12, 0, 7), (7, 6, 2, 4), (64, 13, 5, 31)])
-def test_edge_shapes(kkt, orc, N, n, m, P):
+    (17, 7, 3, 9), (11, 2, 16, 4), (24, 48, 4, 3), (30, 12, 0, 7), (7, 6, 2, 4), (64, 13, 5, 31),
+    (20, 48, 16, 4)])
+@pytest.mark.parametrize("pairing", PAIRINGS)
+def test_edge_shapes(kkt, orc, N, n, m, P, pairing):
     """Single stage, no arrow, odd and tiny blocks, an arrow wider than the
     block, the largest block, P at its feasibility limit (all segments of
     one stage). Blocks larger than 16 use the IPM generator with a mild
@@ -126,7 +136,7 @@ def test_edge_shapes(kkt, orc, N, n, m, P):
     else:
         D, E, G, R = gen.ipm(N, n, m, seed=N + n + m, sigma_decades=1.0)
     b = gen.rhs(N * n + m, 1, seed=3)
-    x, F = gpu_solve(kkt, D, E, G, R, b, P=P, want_factor=True)
+    x, F = gpu_solve(kkt, D, E, G, R, b, P=P, want_factor=True, pairing=pairing)
     Fo = orc.par_factor(D, E, G, R, P=P)
     xo = orc.par_solve(Fo, b)
     for key in ("Ld", "Le", "Lw", "Lh", "Lg", "Lr"):
@@ -159,13 +169,14 @@ def test_multiple_rhs(kkt, orc, nrhs, ldb):
 
 # ------------------------------------------------------------- IPM-shaped
 
+@pytest.mark.parametrize("pairing", PAIRINGS)
 @pytest.mark.parametrize("N,n,m,P", [(128, 32, 8, 1), (128, 32, 8, 16), (200, 24, 4, 13), (96, 12, 0, 20)])
-def test_ipm_shaped(kkt, orc, N, n, m, P):
+def test_ipm_shaped(kkt, orc, N, n, m, P, pairing):
     """Barrier-scaled blocks (Sigma over 16 decades): backward error at the
     FP64 floor, residual and forward difference as the oracle's."""
     D, E, G, R = gen.ipm(N, n, m, seed=11)
     b = gen.rhs(N * n + m, 1, seed=12)
-    x, _ = gpu_solve(kkt, D, E, G, R, b, P=P)
+    x, _ = gpu_solve(kkt, D, E, G, R, b, P=P, pairing=pairing)
     xo = orc.par_solve(orc.par_factor(D, E, G, R, P=P), b)
     check_solution(orc, D, E, G, R, x, b, xo, fwd_tol=1e-5)
 
@@ -183,15 +194,16 @@ def test_ipm_full_size_two_levels(kkt, orc):
 
 # ------------------------------------------------------------- recursion
 
+@pytest.mark.parametrize("pairing", PAIRINGS)
 @pytest.mark.parametrize("N,levels", [(16, [4, 2, 1]), (64, [16, 4, 1]), (200, [40, 10, 3, 1]),
                                       (100, [50, 25, 12, 6, 3, 1])])
-def test_recursive_levels(kkt, orc, N, levels):
+def test_recursive_levels(kkt, orc, N, levels, pairing):
     """The reduced system partitioned again (same block-tridiagonal-arrow
     form): the solution is unchanged up to rounding."""
     n, m = 6, 2
     D, E, G, R, _ = gen.known_factor(N, n, m, seed=5)
     b = gen.rhs(N * n + m, 2, seed=6)
-    x, _ = gpu_solve(kkt, D, E, G, R, b, levels=levels)
+    x, _ = gpu_solve(kkt, D, E, G, R, b, levels=levels, pairing=pairing)
     xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b)
     np.testing.assert_allclose(x, xo, rtol=0, atol=1e-11 * np.abs(xo).max())
 
@@ -210,9 +222,11 @@ def test_balanced_partition_solution(kkt, orc, N, n, m, levels):
 def test_balanced_two_level_blocks(kkt, orc):
     """Two balanced levels: the factor blocks are Algorithm 1's on the
     oracle's run with the same segment lengths."""
+    import torch
     N, n, m, P = 40, 5, 2, 9
     D, E, G, R, _ = gen.known_factor(N, n, m, seed=3)
-    seg = kkt.kkt_partition_balanced(N, n, m, P)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    seg = kkt.kkt_partition_balanced(N, n, m, P, paired=2 * P <= sms)
     b = gen.rhs(N * n + m, 1, seed=4)
     x, F = gpu_solve(kkt, D, E, G, R, b, P=P, want_factor=True, balanced=True)
     Fo = orc.par_factor(D, E, G, R, seg_len=seg)
@@ -300,8 +314,9 @@ def test_uneven_batch(kkt, orc):
 
 # ------------------------------------------------------------- failure, determinism, graphs
 
-@pytest.mark.parametrize("P,bad_stage", [(1, 5), (4, 9), (4, 7)])
-def test_not_spd_reported(kkt, P, bad_stage):
+@pytest.mark.parametrize("pairing", PAIRINGS)
+@pytest.mark.parametrize("P,bad_stage", [(1, 5), (4, 9), (4, 7), (4, 8)])
+def test_not_spd_reported(kkt, P, bad_stage, pairing):
     """A negated diagonal block (made on the host) is reported as
     KKT_ERR_NOT_SPD with its natural stage; nothing traps."""
     import torch
@@ -311,6 +326,7 @@ def test_not_spd_reported(kkt, P, bad_stage):
     D[bad_stage] = -D[bad_stage]
     h = kkt.kkt_create(N, n, m, P)
     try:
+        kkt.kkt_set_pairing(h, kkt.KKT_PAIR_OFF if pairing == "off" else kkt.KKT_PAIR_ON)
         kkt.kkt_factor(h, dev(D), dev(E), dev(G), dev(R))
         torch.cuda.synchronize()
         info = kkt.kkt_get_info(h)
@@ -384,3 +400,37 @@ def test_deterministic_and_graph_capturable(kkt):
         np.testing.assert_array_equal(bd.cpu().numpy(), outs[0])
     finally:
         kkt.kkt_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_factor_layouts_bitwise_identical(kkt, precision):
+    """The three factor layouts (whole CTA, warp-split CTA, CTA pair) assign
+    the same per-element arithmetic to different threads: the factor and
+    the (refined, for mixed precision) solution agree bit for bit."""
+    import torch
+    N, n, m = 600, 24, 6
+    levels = [60, 12, 3, 1]
+    D, E, G, R = gen.ipm(N, n, m, seed=31)
+    b = gen.rhs(N * n + m, 3, seed=32).reshape(N * n + m, 3)
+    Dd, Ed, Gd, Rd = dev(D), dev(E), dev(G), dev(R)
+    outs = []
+    for policy in (kkt.KKT_PAIR_OFF, kkt.KKT_PAIR_ON, kkt.KKT_PAIR_AUTO):
+        h = kkt.kkt_create_plan(N, n, m, levels, kkt.KKT_PARTITION_BALANCED, precision)
+        try:
+            kkt.kkt_set_pairing(h, policy)
+            bd = dev(b)
+            if precision == 0:
+                kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+                kkt.kkt_solve(h, bd, nrhs=3, ldb=3)
+                x = bd
+            else:
+                x = torch.zeros_like(bd)
+                kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+                kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, bd, x, nrhs=3, sweeps=4, tol=0.0)
+            torch.cuda.synchronize()
+            assert kkt.kkt_get_info(h)["status"] == 0
+            outs.append(x.cpu().numpy())
+        finally:
+            kkt.kkt_destroy(h)
+    np.testing.assert_array_equal(outs[0], outs[1])
+    np.testing.assert_array_equal(outs[0], outs[2])
