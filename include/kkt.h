@@ -87,9 +87,11 @@ typedef enum { KKT_FP64 = 0, KKT_MIXED_FP32 = 1, KKT_MIXED_FP32_ALL = 2 } kkt_pr
  *                          kkt_set_pairing) the fill-in rows are off the
  *                          critical path and every segment's stages cost
  *                          about the same, so the lengths come out nearly
- *                          equal. A handle pairs a level when some segment
- *                          has fill-in and two CTAs per segment task fit
- *                          on the device's SMs (2 x tasks <= SMs). */
+ *                          equal. A handle pairs a level when the second
+ *                          CTA has work (some segment has fill-in, or it is
+ *                          the top level of a plan with lower levels, whose
+ *                          corner partials it sums) and two CTAs per task
+ *                          fit on the device's SMs (2 x tasks <= SMs). */
 typedef enum { KKT_PARTITION_PAPER = 0, KKT_PARTITION_BALANCED = 1 } kkt_partition_mode;
 
 typedef struct kkt_handle kkt_handle;
@@ -241,9 +243,10 @@ kkt_status kkt_set_launch_events(kkt_handle* h, void* const* events, int count);
  * on a cluster of two CTAs on separate SMs: one carries the chain of
  * Algorithm 1 (pivot factorization, E- and G-rows, their Schur updates), the
  * other the fill-in rows W of segments k >= 2 and their updates of A~, Q~
- * and the next W, fed through distributed shared memory. This gives a
- * segment two SMs' FP64 units and pays off on levels with fewer segments
- * than SM pairs. KKT_PAIR_AUTO (the default) pairs exactly those levels;
+ * and the next W, fed through distributed shared memory; on the top level
+ * the second CTA sums the lower levels' corner partials while the first
+ * runs the stages. This gives a task two SMs' FP64 units and pays off on
+ * levels with fewer tasks than SM pairs. KKT_PAIR_AUTO (the default) pairs exactly those levels;
  * KKT_PAIR_OFF and KKT_PAIR_ON force one layout on every level (the
  * partition chosen at creation is kept). The layouts give bitwise identical
  * results: each element is computed by the same operations in the same

@@ -201,19 +201,22 @@ struct Carver {
 // Levels whose factor tasks run as CTA pairs by default: some segment has
 // fill-in rows and the pairs fit on the device (two CTAs per task, at most
 // one CTA per SM).
+// The second CTA of a pair has work when a segment of the level has fill-in
+// rows, or on a top level below which other levels left corner partials to
+// sum (the sum then runs beside the top level's stages).
 std::vector<int> paired_levels(const std::vector<std::vector<int>>& Plev, int sms) {
   size_t L = 0;
   for (const auto& ps : Plev) L = std::max(L, ps.size());
   std::vector<int> pr(L, 0);
   for (size_t l = 0; l < L; ++l) {
     long long tasks = 0;
-    bool fill = false;
+    bool work = false;
     for (const auto& ps : Plev)
       if (l < ps.size()) {
         tasks += ps[l];
-        fill = fill || ps[l] > 1;
+        work = work || ps[l] > 1 || (l + 1 == ps.size() && l > 0);
       }
-    pr[l] = fill && 2 * tasks <= sms;
+    pr[l] = work && 2 * tasks <= sms;
   }
   return pr;
 }

@@ -114,7 +114,7 @@ struct Info {
 // them. zb = bytes per panel element (8: FP64 path, 4: mixed). Odd leading
 // dimensions keep row- and column-wise accesses free of bank conflicts.
 struct FacLayout {
-  int q, R, ldD, ldZ, ldT, oDfac, oM, oRinv, oRinvZ, oZ, oT, oTab, oDfac2, oRinv2, total;
+  int q, R, ldD, ldZ, ldT, oDfac, oM, oRinv, oRinvZ, oZ, oT, oTab, oDfac2, oRinv2, oCorner, total;
 };
 __host__ __device__ inline int kkt_align16(int b) { return (b + 15) & ~15; }
 __host__ __device__ inline FacLayout fac_layout(int n, int m, int zb) {
@@ -135,7 +135,9 @@ __host__ __device__ inline FacLayout fac_layout(int n, int m, int zb) {
   // while the current stage's factor blocks are still being written
   L.oDfac2 = L.oTab + kkt_align16(4 * (L.q * (L.q - 1) / 2 + 1));
   L.oRinv2 = L.oDfac2 + kkt_align16(8 * L.q * L.ldD);
-  L.total = L.oRinv2 + kkt_align16(8 * L.q);
+  // sum of the lower levels' corner partials (m x m), formed before the corner
+  L.oCorner = L.oRinv2 + kkt_align16(8 * L.q);
+  L.total = L.oCorner + kkt_align16(8 * kMaxM * kMaxM);
   return L;
 }
 // The substitution kernels double-buffer the factor blocks (L, rinv, Z) so

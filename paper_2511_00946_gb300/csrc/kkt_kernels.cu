@@ -439,6 +439,35 @@ __device__ __forceinline__ void st_cluster(unsigned addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
+// sum_{p < np} part(p, o) for every output o < nout, by the whole CTA, in a
+// fixed order that depends only on (nout, np, blockDim): `sp` adjacent lanes
+// (a power of two, at most 32) per output each add every sp-th partial into
+// two accumulators, then a shuffle tree combines the lanes; out(o, sum) is
+// called once per output. Many partials (one per segment of every lower
+// level) are summed with all FP64 sub-pipes instead of one dependent chain
+// per output.
+template <typename Fpart, typename Fout>
+__device__ void sum_partials(int nout, int np, Fpart part, Fout out) {
+  int sp = 1;
+  while (sp < 32 && sp * 2 * nout <= (int)blockDim.x) sp *= 2;
+  const int groups = (int)blockDim.x / sp, sub = (int)threadIdx.x & (sp - 1);
+  for (int o0 = 0; o0 < nout; o0 += groups) {
+    const int o = o0 + (int)threadIdx.x / sp;
+    double a0 = 0.0, a1 = 0.0;
+    if (o < nout) {
+      int p = sub;
+      for (; p + sp < np; p += 2 * sp) {
+        a0 += part(p, o);
+        a1 += part(p + sp, o);
+      }
+      if (p < np) a0 += part(p, o);
+    }
+    double a = a0 + a1;
+    for (int s = sp >> 1; s > 0; s >>= 1) a += __shfl_xor_sync(0xffffffffu, a, s);
+    if (o < nout && sub == 0) out(o, a);
+  }
+}
+
 struct SegGeom {
   int f, len, hasW, hasF;
 };
@@ -818,17 +847,35 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
       if (g.hasF) store_blk(d.EN + (size_t)(k - 1) * nn, T + oW * ldT, ldT, n, n, true, false);  // H~_k
     }
     if (eg && m) store_blk(d.Rpart + (size_t)k * m * m, T + oG * ldT + oG, ldT, m, m, false, true);
-  } else if (eg && m) {
-    // corner: R-hat = chol(R + sum_k R~_k over every level), in a fixed order
+  } else if (m) {
+    // corner: R-hat = chol(R + sum_k R~_k over every level), in a fixed order:
+    // the lower levels' partials are summed by the pair's idle CTA while this
+    // one runs the stages (or here, without a pair), then R and this level's
+    // own partial are added
+    double* Psum = (double*)(smraw + lay.oCorner);
+    auto part = [&](int p, int o) { return d.Rpart_all[(size_t)p * m * m + o]; };
+    if (mode == kPair && rank == 1) {
+      const unsigned aP = cluster_addr(Psum, 0);
+      sum_partials(m * m, d.nRpart_all, part,
+                   [&](int o, double v) { st_cluster(aP + o * (unsigned)sizeof(double), v); });
+    } else if (mode != kPair) {
+      sum_partials(m * m, d.nRpart_all, part, [&](int o, double v) { Psum[o] = v; });
+    }
+    if (mode == kPair) {
+      cluster_arrive();
+      cluster_wait();
+    } else {
+      __syncthreads();
+    }
+  }
+  if (d.is_top && eg && m) {
+    double* Psum = (double*)(smraw + lay.oCorner);
     double* Rs = Dfac;  // reuse
     const int ldR = odd(m);
     const double* Ru = uR + d.offR;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       const int r = e / m, c = e - r * m;
-      double v = Ru[e];
-      for (int p = 0; p < d.nRpart_all; ++p) v += d.Rpart_all[(size_t)p * m * m + e];
-      v += T[(oG + r) * ldT + oG + c];
-      Rs[r * ldR + c] = v;
+      Rs[r * ldR + c] = (Ru[e] + Psum[e]) + T[(oG + r) * ldT + oG + c];
     }
     potrf_table(tab, m);
     __syncthreads();
@@ -1197,13 +1244,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
     double* bg = b + (size_t)d.rowG * ldb;
     TS* gv = S.t;
     const int ldR = odd(m);
-    for (int e = threadIdx.x; e < m * nr; e += blockDim.x) {
-      const int r = e / nr, c = e - r * nr;
-      double v = bg[(size_t)r * ldb + c];
-      for (int p = 0; p < d.nyg_all; ++p) v += d.yg_all[((size_t)p * m + r) * kRhsChunk + c];
-      v += (double)S.V[(oG + r) * S.ldV + c];
-      gv[r * S.ldV + c] = (TS)v;
-    }
+    sum_partials(
+        m * nr, d.nyg_all,
+        [&](int p, int o) { return d.yg_all[((size_t)p * m + o / nr) * kRhsChunk + o % nr]; },
+        [&](int o, double v) {
+          const int r = o / nr, c = o - r * nr;
+          gv[r * S.ldV + c] = (TS)((bg[(size_t)r * ldb + c] + v) + (double)S.V[(oG + r) * S.ldV + c]);
+        });
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {  // R-hat: columns scaled, rows scaled
       const int r = e / m, c = e - r * m;
       S.L[0][r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[c]);
