@@ -64,12 +64,15 @@ def known_factor(N=16, n=8, m=4, seed=0):
     return D, E, G, R, dict(Ld=Ld, Le=Le, Lg=Lg, Lr=Lr)
 
 
-def ipm(N=1024, n=32, m=8, seed=0, sigma_decades=8.0, g_rows=None, reg=1e-8):
+def ipm(N=1024, n=32, m=8, seed=0, sigma_decades=8.0, g_rows=None, reg=1e-8, psd_couplings=False):
     """Interior-point-shaped KKT matrix: D_j = Q_j + G_j^T Sigma_j G_j + reg I
     with Q_j = R_j R_j^T (R_j ~ N(0,1), n x n), constraint rows G_j ~ N(0,1)
     (g_rows x n, default 2n), Sigma_j diagonal log-uniform in
     [10^-d, 10^d]; couplings E_j ~ N(0, 1/n) (random dynamics); arrow as in
-    ``_arrow``."""
+    ``_arrow``. With ``psd_couplings`` every coupling is embedded as the PSD
+    pair [[C^T C, C^T], [C, I]] on stages (j, j+1) (E_j = C_j, D_j += C_j^T C_j,
+    D_{j+1} += I), which keeps Psi SPD for any draw: without it small blocks
+    (n = 12, no arrow) can give an indefinite matrix."""
     rng = np.random.default_rng(seed)
     g_rows = 2 * n if g_rows is None else g_rows
     Rq = rng.normal(size=(N, n, n))
@@ -78,6 +81,9 @@ def ipm(N=1024, n=32, m=8, seed=0, sigma_decades=8.0, g_rows=None, reg=1e-8):
     D = np.einsum("jab,jcb->jac", Rq, Rq) + np.einsum("jra,jr,jrb->jab", Gc, sig, Gc)
     D += reg * np.eye(n)[None]
     E = rng.normal(0.0, 1.0 / np.sqrt(n), size=(max(N - 1, 0), n, n))
+    if psd_couplings and N > 1:
+        D[:-1] += np.einsum("jab,jac->jbc", E, E)
+        D[1:] += np.eye(n)[None]
     G, R = _arrow(rng, N, n, m, D)
     return D, E, G, R
 
@@ -103,16 +109,16 @@ def raceline(N=8192, n=6, m=2, seed=0, sigma_decades=8.0, g_rows=4, reg=1e-2, co
 
 def uneven_batch(count=4096, seed=0, N_range=(20, 200), n_choices=(12, 24, 48), m_choices=(0, 4),
                  sigma_decades=6.0):
-    """A batch of independent ``ipm`` systems: N uniform in N_range, n and m
-    drawn from the given choices, Sigma log-uniform over +-sigma_decades.
-    Returns a list of (D, E, G, R)."""
+    """A batch of independent ``ipm`` systems with PSD-embedded couplings:
+    N uniform in N_range, n and m drawn from the given choices, Sigma
+    log-uniform over +-sigma_decades. Returns a list of (D, E, G, R)."""
     rng = np.random.default_rng(seed)
     out = []
     for s in range(count):
         N = int(rng.integers(N_range[0], N_range[1] + 1))
         n = int(rng.choice(n_choices))
         m = int(rng.choice(m_choices))
-        out.append(ipm(N, n, m, seed=int(rng.integers(2**31)), sigma_decades=sigma_decades))
+        out.append(ipm(N, n, m, seed=int(rng.integers(2**31)), sigma_decades=sigma_decades, psd_couplings=True))
     return out
 
 

@@ -135,6 +135,23 @@ kkt_status kkt_create_plan(int N, int n, int m, int nlevels, const int* P_levels
 kkt_status kkt_batch_create(int count, const int* N, const int* n, const int* m, const int* P,
                             int precision, kkt_handle** out);
 
+/* Batch of `count` independent systems whose level plans (segments per
+ * level, KKT_PARTITION_BALANCED partitions) are picked by an autotuner: it
+ * times one factor + one single-RHS solve of every candidate on the current
+ * device, with synthetic inputs of the batch's shapes (identity pivot blocks;
+ * the kernels' run time does not depend on the values), and keeps the
+ * fastest. Candidates: every system sequential (P = 1, no fill-in; best when
+ * the systems alone fill the GPU), and level-1 segment totals of 1/2, 1, 2,
+ * 4 and 8 per SM spread over the systems in proportion to their stage
+ * counts, with 4x or 8x fewer segments on each level above, down to a
+ * sequential top level. levels_out (optional, length count) receives the
+ * number of levels chosen per system; kkt_partition reads the plan. Blocks
+ * until the tuning runs finish and allocates scratch memory for them
+ * (freed before returning): call it outside any graph capture. Errors as
+ * for kkt_batch_create, KKT_ERR_CUDA when the tuning runs fail. */
+kkt_status kkt_batch_create_tuned(int count, const int* N, const int* n, const int* m, int precision,
+                                  int* levels_out, kkt_handle** out);
+
 /* Free the handle and its device memory (NULL is accepted). */
 kkt_status kkt_destroy(kkt_handle* h);
 

@@ -25,7 +25,7 @@ KKT_PAIR_AUTO, KKT_PAIR_OFF, KKT_PAIR_ON = 0, 1, 2
 RHS_CHUNK = 16
 
 EXPORTED = [
-    "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_destroy",
+    "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_batch_create_tuned", "kkt_destroy",
     "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta",
     "kkt_get_info",
     "kkt_get_factor", "kkt_set_pairing", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
@@ -55,6 +55,7 @@ _sig = {
     "kkt_create_levels": [_i, _i, _i, _i, _ip, _i, ctypes.POINTER(_vp)],
     "kkt_create_plan": [_i, _i, _i, _i, _ip, _i, _i, ctypes.POINTER(_vp)],
     "kkt_batch_create": [_i, _ip, _ip, _ip, _ip, _i, ctypes.POINTER(_vp)],
+    "kkt_batch_create_tuned": [_i, _ip, _ip, _ip, _i, _ip, ctypes.POINTER(_vp)],
     "kkt_partition_balanced": [_i, _i, _i, _i, _i, _ip],
     "kkt_destroy": [_vp],
     "kkt_partition": [_vp, _i, _i, _ip, _ip],
@@ -151,6 +152,17 @@ def kkt_batch_create(N, n, m, P=None, precision: int = KKT_FP64) -> int:
     _check(_lib.kkt_batch_create(count, _ints(N), _ints(n), _ints(m), _ints(P) if P is not None else None,
                                  precision, ctypes.byref(h)), "kkt_batch_create")
     return h.value
+
+
+def kkt_batch_create_tuned(N, n, m, precision: int = KKT_FP64):
+    """Batch handle whose level plans are picked by timing candidates on the
+    device (see the C header); returns (handle, levels per system)."""
+    c = len(N)
+    h = _vp()
+    lv = (ctypes.c_int * c)()
+    _check(_lib.kkt_batch_create_tuned(c, _ints(N), _ints(n), _ints(m), precision, lv, ctypes.byref(h)),
+           "kkt_batch_create_tuned")
+    return h.value, list(lv)
 
 
 def kkt_destroy(h: int):

@@ -527,6 +527,113 @@ kkt_status kkt_batch_create(int count, const int* N, const int* n, const int* m,
   return build_handle(count, N, n, m, Ps, KKT_PARTITION_PAPER, precision, out);
 }
 
+namespace {
+// Segments per level for one system: P1 on level 1, then every level has
+// 1/ratio as many segments as the one below, down to a sequential top level.
+std::vector<int> level_plan(int N, int P1, int ratio) {
+  std::vector<int> v;
+  int Nl = N, P = P1;
+  for (;;) {
+    P = std::min(P, (Nl + 1) / 2);
+    if (P <= 1) {
+      v.push_back(1);
+      return v;
+    }
+    v.push_back(P);
+    Nl = P - 1;
+    P /= ratio;
+  }
+}
+
+// Device time (ms) of one factor + one single-RHS solve of the handle, median
+// of `reps` runs on the legacy stream; < 0 on a CUDA error.
+float time_handle(kkt_handle* h, const double* D, const double* E, const double* G, const double* R,
+                  double* b, int reps) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.f; }
+  std::vector<float> t;
+  bool ok = true;
+  for (int r = 0; r <= reps && ok; ++r) {  // the first run warms up
+    ok = cudaEventRecord(e0, 0) == cudaSuccess && kkt_factor(h, D, E, G, R, nullptr) == KKT_OK &&
+         kkt_solve(h, b, 1, 1, nullptr) == KKT_OK && cudaEventRecord(e1, 0) == cudaSuccess &&
+         cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0.f;
+    if (ok && r > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t.push_back(ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok || t.empty()) return -1.f;
+  std::sort(t.begin(), t.end());
+  return t[t.size() / 2];
+}
+}  // namespace
+
+kkt_status kkt_batch_create_tuned(int count, const int* N, const int* n, const int* m, int precision,
+                                  int* levels_out, kkt_handle** out) {
+  if (!out) return KKT_ERR_ARG;
+  *out = nullptr;
+  if (count < 1 || !N || !n || !m) return KKT_ERR_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return KKT_ERR_CUDA;
+  double sumN = 0.0;
+  for (int s = 0; s < count; ++s) {
+    if (N[s] < 1) return KKT_ERR_ARG;
+    sumN += N[s];
+  }
+  // candidates: every system sequential, then level-1 segment totals of
+  // 1/2 .. 8 per SM spread over the systems by stage count, with 4x or 8x
+  // fewer segments per level above
+  std::vector<std::vector<std::vector<int>>> cands;
+  cands.push_back(std::vector<std::vector<int>>(count, std::vector<int>{1}));
+  for (int T1 : {sms / 2, sms, 2 * sms, 4 * sms, 8 * sms})
+    for (int ratio : {4, 8}) {
+      std::vector<std::vector<int>> pl(count);
+      for (int s = 0; s < count; ++s)
+        pl[s] = level_plan(N[s], std::max(1, (int)std::llround((double)T1 * N[s] / sumN)), ratio);
+      bool dup = false;
+      for (const auto& c : cands) dup = dup || c == pl;
+      if (!dup) cands.push_back(pl);
+    }
+  // synthetic inputs of the batch's shapes: identity pivot blocks and corners
+  kkt_handle* h = nullptr;
+  kkt_status st = build_handle(count, N, n, m, cands[0], KKT_PARTITION_BALANCED, precision, &h);
+  if (st != KKT_OK) return st;
+  const size_t nD = h->tot_D, nE = std::max<size_t>(h->tot_E, 1), nG = std::max<size_t>(h->tot_G, 1),
+               nR = std::max<size_t>(h->tot_R, 1), nB = h->tot_B;
+  double* buf = nullptr;
+  if (cudaMalloc(&buf, sizeof(double) * (nD + nE + nG + nR + nB)) != cudaSuccess) {
+    kkt_destroy(h);
+    return KKT_ERR_CUDA;
+  }
+  double *D = buf, *E = D + nD, *G = E + nE, *R = G + nG, *b = R + nR;
+  bool ok = cudaMemset(buf, 0, sizeof(double) * (nD + nE + nG + nR + nB)) == cudaSuccess &&
+            kkt::launch_fill_identity(h->ddesc, h->dsys_desc, count, D, R, nullptr) == 0 &&
+            cudaDeviceSynchronize() == cudaSuccess;
+  size_t best = 0;
+  float best_ms = -1.f;
+  for (size_t c = 0; c < cands.size() && ok; ++c) {
+    if (c > 0) {
+      kkt_destroy(h);
+      h = nullptr;
+      st = build_handle(count, N, n, m, cands[c], KKT_PARTITION_BALANCED, precision, &h);
+      if (st != KKT_OK) { h = nullptr; continue; }  // a candidate that does not fit is skipped
+    }
+    const float ms = time_handle(h, D, E, G, R, b, 3);
+    if (ms < 0.f) { ok = false; break; }
+    if (best_ms < 0.f || ms < best_ms) { best_ms = ms; best = c; }
+  }
+  if (h) kkt_destroy(h);
+  cudaFree(buf);
+  if (!ok || best_ms < 0.f) return KKT_ERR_CUDA;
+  st = build_handle(count, N, n, m, cands[best], KKT_PARTITION_BALANCED, precision, out);
+  if (st == KKT_OK && levels_out)
+    for (int s = 0; s < count; ++s) levels_out[s] = (int)cands[best][s].size();
+  return st;
+}
+
 kkt_status kkt_destroy(kkt_handle* h) {
   if (!h) return KKT_OK;
   if (h->dmem) cudaFree(h->dmem);
@@ -669,11 +776,13 @@ kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, co
       kkt_status s2 = solve_chunk(h, h->dcorr, CH, nr, h->dconv, stream, nullptr);
       if (s2 != KKT_OK) return s2;
       if (kkt::launch_axpy(h->ddesc, h->dres, nres, x + c0, ldx, h->dcorr, nr, h->dconv, stream) ||
-          kkt::launch_residual(h->ddesc, h->dres, nres, h->maxn, D, E, G, b + c0, ldb, x + c0, ldx,
-                               h->dcorr, nr, h->dparts, h->dconv, stream) ||
+          kkt::launch_residual(h->ddesc, h->dres, nres, D, E, G, b + c0, ldb, x + c0, ldx, h->dcorr, nr,
+                               h->dparts, h->dconv, c0 == 0 && sw == 0, stream) ||
           kkt::launch_residual_final(h->ddesc, h->dsys_desc, h->dpart0, h->count, G, R, b + c0, ldb,
                                      x + c0, ldx, h->dcorr, nr, h->dparts, tol,
-                                     h->deta + (size_t)sw * h->count, h->dconv, stream))
+                                     h->deta + (size_t)sw * h->count,
+                                     sw > 0 ? h->deta + (size_t)(sw - 1) * h->count : nullptr, h->dconv,
+                                     stream))
         return KKT_ERR_CUDA;
     }
   }

@@ -197,21 +197,25 @@ int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
 int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int ldx, const double* c,
                 int nr, const int* skip, void* stream);
 // c = b - Psi x over the stage rows of each task (+ partials for the g rows
-// and the norms); c has leading dimension kRhsChunk
-int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, int maxn, const double* D,
-                    const double* E, const double* G, const double* b, int ldb, const double* x,
-                    int ldx, double* c, int nr, double* parts, const int* skip, void* stream);
-// g rows of c, eta per system, converged[s] = (eta <= tol)
+// and the max norms; the row sums of |Psi| only when `norms`, otherwise the
+// values of an earlier call stay in `parts`); c has leading dimension kRhsChunk
+int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, const double* D, const double* E,
+                    const double* G, const double* b, int ldb, const double* x, int ldx, double* c, int nr,
+                    double* parts, const int* skip, int norms, void* stream);
+// g rows of c, eta per system, converged[s] = (eta <= tol); a system that had
+// converged before copies its eta from eta_prev (the previous sweep's; may be null)
 int launch_residual_final(const LevelDesc* d, const int* sys_desc, const int* part0, int count,
                           const double* G, const double* R, const double* b, int ldb, const double* x,
                           int ldx, double* c, int nr, const double* parts, double tol, double* eta_out,
-                          int* converged, void* stream);
+                          const double* eta_prev, int* converged, void* stream);
 // adjoint block gradients (symmetric-entry convention) per residual task
 int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const double* x, int ldx,
                         const double* xb, int ldxb, int nr, double* dD, double* dE, double* dG,
                         double* dR, void* stream);
+// D (every system's stage blocks) <- identity blocks, R <- identity corners
+int launch_fill_identity(const LevelDesc* d, const int* sys_desc, int count, double* D, double* R,
+                         void* stream);
 size_t factor_smem_bytes(int maxn, int maxm, int mixed);
 size_t solve_smem_bytes(int maxn, int maxm, int single);
-size_t residual_smem_bytes(int maxn);
 
 }  // namespace kkt

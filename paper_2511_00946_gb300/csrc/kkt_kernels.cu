@@ -259,7 +259,8 @@ __device__ void potrf_sm(double* A, int ld, int n, double* rinv, const int* tab,
   if (whole) __syncthreads();
 }
 
-// Fused pivot factorization and panel solve (FP64): the Cholesky above and
+// Fused pivot factorization (FP64) and panel solve (in the panel type TZ:
+// FP64, or FP32 in the mixed variant): the Cholesky above and
 // Z[r0, r1) <- Z[r0, r1) L^{-T} in the division-free form of trsm_panel (the
 // same operations in the same order, so the results are bitwise those of
 // potrf_sm + panel_operand + trsm_panel). Warp 0 runs the pivot chain; in the
@@ -276,8 +277,9 @@ __device__ void potrf_sm(double* A, int ld, int n, double* rinv, const int* tab,
 constexpr int kFusedThreads = 224;
 constexpr int kFusedWorkers = 192;  // warps 1-3 and 5-7
 
-__device__ void potrf_trsm_sm(double* A, int ld, int n, double* rinv, double* M, const int* tab, int* bad,
-                              double* Z, int ldz, int r0, int r1) {
+template <typename TZ>
+__device__ void potrf_trsm_sm(double* A, int ld, int n, double* rinv, TZ* M, const int* tab, int* bad,
+                              TZ* Z, int ldz, int r0, int r1) {
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid >= kPotrfThreads && tid < kPotrfThreads + 32) return;  // warp 4
   const int w = tid < kPotrfThreads ? tid - 32 : tid - 64;       // worker index
@@ -286,7 +288,7 @@ __device__ void potrf_trsm_sm(double* A, int ld, int n, double* rinv, double* M,
   const int per = rows > 0 ? max(1, kFusedWorkers / rows) : 0;
   const bool pact = tid >= 32 && w < rows * per;
   const int pr = pact ? w % rows : 0, pc = pact ? w / rows : 0;
-  double* zr = Z + (r0 + pr) * ldz;
+  TZ* zr = Z + (r0 + pr) * ldz;
   if (tid < 32) potrf_col0(A, ld, n, rinv, bad, lane);
   group_bar(1, kFusedThreads);
   for (int j = 0; j < n; ++j) {
@@ -294,9 +296,9 @@ __device__ void potrf_trsm_sm(double* A, int ld, int n, double* rinv, double* M,
       if (j + 1 < n) potrf_lookahead(A, ld, n, rinv, bad, j, lane);
     } else {
       potrf_trailing(A, ld, n, tab, j, w, kFusedWorkers);
-      for (int c = j + 1 + w; c < n; c += kFusedWorkers) M[c * ld + j] = A[c * ld + j] * rinv[j];
+      for (int c = j + 1 + w; c < n; c += kFusedWorkers) M[c * ld + j] = (TZ)(A[c * ld + j] * rinv[j]);
       if (pact && j >= 1) {
-        const double zj = zr[j - 1];
+        const TZ zj = zr[j - 1];
         for (int c = j + pc; c < n; c += per) zr[c] = fma(-zj, M[c * ld + j - 1], zr[c]);
       }
     }
@@ -305,7 +307,7 @@ __device__ void potrf_trsm_sm(double* A, int ld, int n, double* rinv, double* M,
   if (tid >= 32)
     for (int e = w; e < rows * n; e += kFusedWorkers) {
       const int r = e / n, c = e - r * n;
-      Z[(r0 + r) * ldz + c] *= rinv[c];
+      Z[(r0 + r) * ldz + c] *= (TZ)rinv[c];
     }
 }
 
@@ -323,55 +325,30 @@ __device__ void panel_operand(TM* M, const double* L, int ld, int n, const doubl
 }
 
 // Z[r0:r1) <- Z[r0:r1) L^{-T} with the pre-scaled columns M (M_cj = L_cj /
-// L_jj): for each row, u_c = z_c - sum_{k<c} u_k M_ck and x_c = u_c / L_cc.
-// FP64: column sweep (every thread on every column, FP64 from full warps),
-// thread t owning row r0 + t % rows and every (nt/rows)-th column. The
-// group needs at least as many threads as rows (true for every panel: rows
-// <= kMaxN + kMaxM per role of a split CTA, 2 kMaxN + kMaxM otherwise).
-__device__ void trsm_panel(double* Z, int ldz, int r0, int r1, const double* M, int ldm, int n,
-                           const double* rinv, Grp g) {
+// L_jj), in the panel type TZ: for each row, u_c = z_c - sum_{k<c} u_k M_ck
+// (in k order) and x_c = u_c / L_cc (times rinv). Column sweep: every thread
+// works on every column (FP64 from full warps), thread t owning row
+// r0 + t % rows and every (nt/rows)-th column. The group needs at least as
+// many threads as rows (true for every panel: rows <= kMaxN + kMaxM per
+// role of a split CTA, 2 kMaxN + kMaxM otherwise).
+template <typename TZ>
+__device__ void trsm_panel(TZ* Z, int ldz, int r0, int r1, const TZ* M, int ldm, int n, const TZ* rinv,
+                           Grp g) {
   const int rows = r1 - r0;
   if (rows <= 0) return;
   const int per = g.nt / rows;  // threads per row (>= 1)
   const int rr = g.tid % rows, cc = g.tid / rows;
   const bool act = cc < per;
-  double* zr = Z + (r0 + rr) * ldz;
+  TZ* zr = Z + (r0 + rr) * ldz;
   for (int j = 0; j < n - 1; ++j) {
     if (act) {
-      const double zj = zr[j];
+      const TZ zj = zr[j];
       for (int c = j + 1 + cc; c < n; c += per) zr[c] = fma(-zj, M[c * ldm + j], zr[c]);
     }
     gsync(g);
   }
   if (act)
     for (int c = cc; c < n; c += per) zr[c] *= rinv[c];
-  gsync(g);
-}
-
-// FP32 (M = L / diag by columns, rinv = 1/diag): one thread per panel row runs
-// the whole division-free substitution u_c = z_c - sum_{k<c} u_k M_ck, x_c =
-// u_c / L_cc in order (no barriers; FP32 issue is cheap), four partial sums
-// per dot product.
-__device__ void trsm_panel(float* Z, int ldz, int r0, int r1, const float* M, int ldm, int n,
-                           const float* rinv, Grp g) {
-  const int rows = r1 - r0;
-  for (int rr = g.tid; rr < rows; rr += g.nt) {
-    float* z = Z + (r0 + rr) * ldz;
-    for (int c = 1; c < n; ++c) {
-      const float* mc = M + c * ldm;
-      float s0 = z[c], s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      int k = 0;
-      for (; k + 3 < c; k += 4) {
-        s0 = fmaf(-mc[k], z[k], s0);
-        s1 = fmaf(-mc[k + 1], z[k + 1], s1);
-        s2 = fmaf(-mc[k + 2], z[k + 2], s2);
-        s3 = fmaf(-mc[k + 3], z[k + 3], s3);
-      }
-      for (; k < c; ++k) s0 = fmaf(-mc[k], z[k], s0);
-      z[c] = (s0 + s1) + (s2 + s3);
-    }
-    for (int c = 0; c < n; ++c) z[c] *= rinv[c];
-  }
   gsync(g);
 }
 
@@ -701,16 +678,17 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
         rotate(i, j, false, P);
       }
     }
-  } else if (producer && !mixed) {
-    // FP64, whole CTA on the E- and G-rows (no fill-in rows here: segment 1,
-    // the top level, or the producer of a pair). Per stage: the fused pivot
-    // factorization and panel solve (warps 0-3 and 5-7) while warp 4 writes
-    // the previous stage's pivot blocks from the other pivot buffer; then the
-    // hand-off to the consumer, the Schur update and the rotation.
+  } else if (producer) {
+    // Whole CTA on the E- and G-rows (and the W-rows in the whole layout of a
+    // mixed level; FP64 levels with fill-in rows split or pair). Per stage:
+    // the fused pivot factorization and panel solve (warps 0-3 and 5-7)
+    // while warp 4 writes the previous stage's pivot blocks from the other
+    // pivot buffer; then the hand-off to the consumer, the Schur update and
+    // the rotation.
     const Grp P = cta_grp();
     const Grp W4{(int)(threadIdx.x & 31), 32, -1};
     const bool w4 = (threadIdx.x >> 5) == 4;
-    const int pr1 = n + m;
+    const int pr1 = n + m + (mode == kWhole && g.hasW ? n : 0);  // end of the CTA's panel rows
     const bool push = mode == kPair && g.hasW;
     double* const Dfac2 = (double*)(smraw + lay.oDfac2);
     double* const rinv2 = (double*)(smraw + lay.oRinv2);
@@ -724,75 +702,24 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
       if (w4) {
         if (i > 0) store_pivot(j - 1, Dbuf(cur ^ 1), rvbuf(cur ^ 1), nullptr, W4);
       } else {
-        potrf_trsm_sm(Dbuf(cur), ldD, n, rvbuf(cur), (double*)M, tab, &bad, (double*)Z, ldZ, r0, pr1);  // TZ = double here
+        potrf_trsm_sm(Dbuf(cur), ldD, n, rvbuf(cur), M, tab, &bad, Z, ldZ, r0, pr1);
       }
       __syncthreads();
       if (threadIdx.x == 0 && bad) { record_breakdown(info, d.sys, d.nat[j], d.level); bad = 0; }
       if (push) {
-        if (i > 0) cluster_wait();  // the consumer is done with stage i-2 (buffer i % 2)
-        push_stage(i, M, (const TZ*)rvbuf(cur), r0, pr1, P);
-        cluster_arrive();
-      }
-      store_panel(j, r0, pr1, mode == kWhole ? R : pr1, P);
-      syrk_trap(T, ldT, Z, Z, 0, ldZ, r0, pr1, r0, n, P);
-      if (i + 1 < g.len) {
-        copy_blk(Dbuf(cur ^ 1), ldD, T, ldT, n, n, P);                      // D_{i+1}
-        rotate(i, j, false, P);
-      } else {
-        store_pivot(j, Dbuf(cur), rvbuf(cur), nullptr, P);
-      }
-    }
-    if (push) cluster_wait();  // phase of the last stage
-  } else if (producer) {
-    // FP32 panel (mixed), whole CTA on the E- and G-rows (and the W-rows in
-    // the whole layout), with a one-stage look-ahead: once the E-rows of
-    // stage i are solved and D_{i+1} = D_{i+1} - E-hat_i E-hat_i^T is formed,
-    // warps 0-3 factor D_{i+1} into the second pivot buffer while warps 4-7
-    // write stage i's factor blocks, apply the remaining Schur updates of
-    // stage i (G- and W-rows) and rotate the panel.
-    const Grp P = cta_grp();
-    const Grp U{(int)threadIdx.x - kRoleThreads, kRoleThreads, kBarCons};  // warps 4-7
-    const bool upd = (int)threadIdx.x >= kRoleThreads;
-    const int pr1 = n + m + (mode == kWhole && g.hasW ? n : 0);  // end of the CTA's panel rows
-    const bool push = mode == kPair && g.hasW;
-    double* const Dfac2 = (double*)(smraw + lay.oDfac2);
-    double* const rinv2 = (double*)(smraw + lay.oRinv2);
-    auto Dbuf = [&](int b) { return b ? Dfac2 : Dfac; };
-    auto rvbuf = [&](int b) { return b ? rinv2 : rinv; };
-    potrf_sm(Dfac, ldD, n, rinv, tab, &bad, true);
-    for (int i = 0; i < g.len; ++i) {
-      const int j = g.f + i;
-      const int cur = i & 1;
-      const bool eRows = (i < g.len - 1) || g.hasF;
-      const int r0 = eRows ? 0 : n;
-      if (threadIdx.x == 0 && bad) { record_breakdown(info, d.sys, d.nat[j], d.level); bad = 0; }
-      panel_operand(M, Dbuf(cur), ldD, n, rvbuf(cur), P);
-      for (int e = P.tid; e < n; e += P.nt) rinvZ[e] = (TZ)rvbuf(cur)[e];
-      gsync(P);
-      trsm_panel(Z, ldZ, r0, pr1, M, ldD, n, rinvZ, P);
-      if (push) {
+        for (int e = P.tid; e < n; e += P.nt) rinvZ[e] = (TZ)rvbuf(cur)[e];
+        __syncthreads();
         if (i > 0) cluster_wait();  // the consumer is done with stage i-2 (buffer i % 2)
         push_stage(i, M, rinvZ, r0, n + m, P);
         cluster_arrive();
       }
+      store_panel(j, r0, pr1, mode == kWhole ? R : n + m, P);
+      syrk_trap(T, ldT, Z, Z, 0, ldZ, r0, pr1, r0, n, P);
       if (i + 1 < g.len) {
-        // E-rows present (eRows): D_{i+1} -= E-hat E-hat^T, then the fork
-        syrk_trap(T, ldT, Z, Z, 0, ldZ, 0, n, 0, n, P);
-        copy_blk(Dbuf(cur ^ 1), ldD, T, ldT, n, n, P);
-        __syncthreads();
-        if (!upd) {
-          potrf_sm(Dbuf(cur ^ 1), ldD, n, rvbuf(cur ^ 1), tab, &bad, false);
-        } else {
-          store_pivot(j, Dbuf(cur), rvbuf(cur), M, U);
-          store_panel(j, r0, pr1, mode == kWhole ? R : n + m, U);
-          syrk_trap(T, ldT, Z, Z, 0, ldZ, n, pr1, 0, n, U);                 // G- (and W-) rows
-          rotate(i, j, mode == kWhole && g.hasW, U);
-        }
-        __syncthreads();
+        copy_blk(Dbuf(cur ^ 1), ldD, T, ldT, n, n, P);                      // D_{i+1}
+        rotate(i, j, mode == kWhole && g.hasW, P);
       } else {
-        store_pivot(j, Dbuf(cur), rvbuf(cur), M, P);
-        store_panel(j, r0, pr1, mode == kWhole ? R : n + m, P);
-        syrk_trap(T, ldT, Z, Z, 0, ldZ, r0, pr1, r0, n, P);
+        store_pivot(j, Dbuf(cur), rvbuf(cur), nullptr, P);
       }
     }
     if (push) cluster_wait();  // phase of the last stage
@@ -1332,115 +1259,156 @@ __global__ void k_axpy(const LevelDesc* __restrict__ descs, const ResTask* __res
     }
 }
 
-// c = b - Psi x for the stage rows of one chunk. The g rows are finished by
-// k_residual_final from the partials written here: sum_j G_j x_j over the
-// chunk, the largest |r|, |x|, |b| and |Psi| row sum, and the chunk's |G|
-// column sums for the g rows of ||Psi||_inf.
-__global__ void k_residual(const LevelDesc* __restrict__ descs, const ResTask* __restrict__ tasks,
-                           const double* __restrict__ uD, const double* __restrict__ uE,
-                           const double* __restrict__ uG, const double* __restrict__ b, int ldb,
-                           const double* __restrict__ x, int ldx, double* c, int nr, double* parts,
-                           const int* skip) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const ResTask tk = tasks[blockIdx.x];
+// FP64 residual c = b - Psi x (blocks of Eq. (3)) over the stage rows of one
+// residual task (kResChunk consecutive stages of one system) per warp: lane
+// i owns row i of the stage (and row i + 32 when n > 32) and forms
+//   (E_{j-1} x_{j-1} + D_j x_j + E_j^T x_{j+1} + G_j^T x_g)_i
+// from the blocks in global memory (lower triangle of D_j by symmetry), with
+// x_k broadcast by shuffles, so every FP64 instruction has a lane per row
+// and Psi is read once. A matrix-vector product does 2 flop per 8-byte
+// element, more than the FP64 units sustain at full HBM bandwidth on this
+// part, so the kernel keeps FP64 work to the products themselves: the row
+// sums of |Psi| (for eta) are only formed when `norms` is set (the first
+// sweep of a refinement; they depend on the matrix alone). Per task it
+// writes the g-row partials sum_j G_j x_j (m x nr), max|c|, max|x|, max|b|
+// and, with `norms`, the largest stage-row sum of |Psi| and the |G| sums of
+// the g rows; k_residual_final combines them per system.
+__global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ descs,
+                                                  const ResTask* __restrict__ tasks, int ntasks,
+                                                  const double* __restrict__ uD, const double* __restrict__ uE,
+                                                  const double* __restrict__ uG, const double* __restrict__ b,
+                                                  int ldb, const double* __restrict__ x, int ldx, double* c,
+                                                  int nr, double* parts, const int* skip, int norms) {
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= ntasks) return;  // whole warp
+  const ResTask tk = tasks[t];
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
   const int n = d.n, m = d.m, N = d.N;
-  const int j1 = min(tk.j0 + kResChunk, N);
-  const int ld = odd(n);
-  double* Ds = (double*)smraw;           // D_j      n x n
-  double* Ep = Ds + n * ld;              // E_{j-1}  n x n
-  double* En = Ep + n * ld;              // E_j      n x n
-  double* Gs = En + n * ld;              // G_j      m x n
-  double* xv = Gs + kMaxM * ld;          // x_{j-1}, x_j, x_{j+1}: 3 n x kRhsChunk
-  double* xg = xv + 3 * n * kRhsChunk;   // x_g      m x kRhsChunk
-  double* red = xg + kMaxM * kRhsChunk;  // reductions [4][blockDim]
+  const int j0 = tk.j0, j1 = min(tk.j0 + kResChunk, N);
   const size_t nn = (size_t)n * n, mn = (size_t)m * n;
   const double* D = uD + d.offD;
   const double* E = uE ? uE + d.offE : nullptr;
   const double* G = m ? uG + d.offG : nullptr;
-  const double* none = nullptr;
-  double* part = parts + (size_t)blockIdx.x * kResPartDoubles;
-  double* pg = part;  // g partials m x kRhsChunk
+  double* part = parts + (size_t)t * kResPartDoubles;
+  const int i0 = lane, i1 = lane + 32;
+  const bool r0ok = i0 < n, r1ok = i1 < n, two = n > 32;  // `two` is warp-uniform
+  const int a0 = r0ok ? i0 : 0, a1 = r1ok ? i1 : 0;     // clamped rows for the loads
   double mr = 0.0, mx = 0.0, mb = 0.0, mrow = 0.0;
-  double gabs[kMaxM];
-  for (int q = 0; q < kMaxM; ++q) gabs[q] = 0.0;
-  for (int e = threadIdx.x; e < m * kRhsChunk; e += blockDim.x) pg[e] = 0.0;
-  for (int e = threadIdx.x; e < m * nr; e += blockDim.x) {
-    const int r = e / nr, col = e - r * nr;
-    xg[r * kRhsChunk + col] = x[(size_t)(d.rowG + r) * ldx + col];
-  }
-  for (int j = tk.j0; j < j1; ++j) {
-    __syncthreads();
-    load_blk(Ds, ld, D + (size_t)j * nn, none, n, n, false);
-    load_blk(Ep, ld, (j > 0 && E) ? E + (size_t)(j - 1) * nn : none, none, n, n, false);
-    load_blk(En, ld, (j < N - 1 && E) ? E + (size_t)j * nn : none, none, n, n, false);
-    if (m) load_blk(Gs, ld, G + (size_t)j * mn, none, m, n, false);
-    for (int e = threadIdx.x; e < 3 * n * nr; e += blockDim.x) {
-      const int q = e / (n * nr), rem = e - q * n * nr, r = rem / nr, col = rem - r * nr;
-      const int jj = j - 1 + q;
-      xv[(q * n + r) * kRhsChunk + col] =
-          (jj >= 0 && jj < N) ? x[(size_t)(d.offB + (long long)jj * n + r) * ldx + col] : 0.0;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
-      const int i = e / nr, col = e - i * nr;
-      double acc = 0.0, rs = 0.0;
+  double gab = 0.0;  // |G| sum of g row `lane` (lane < m)
+  auto xat = [&](long long row, int col) { return x[(size_t)row * ldx + col]; };
+  for (int col = 0; col < nr; ++col) {
+    double xg_l = lane < m ? xat(d.rowG + lane, col) : 0.0;  // x_g, lane q holds row q
+    double gacc[kMaxM];  // this lane's terms of sum_j G_j x_j per g row
+#pragma unroll
+    for (int q = 0; q < kMaxM; ++q) gacc[q] = 0.0;
+    for (int j = j0; j < j1; ++j) {
+      const long long rb = d.offB + (long long)j * n;
+      const double* Dj = D + (size_t)j * nn;
+      const double* Ep = (j > 0 && E) ? E + (size_t)(j - 1) * nn : nullptr;
+      const double* En = (j < N - 1 && E) ? E + (size_t)j * nn : nullptr;
+      const double xc0 = r0ok ? xat(rb + i0, col) : 0.0, xc1 = r1ok ? xat(rb + i1, col) : 0.0;
+      const double xp0 = (Ep && r0ok) ? xat(rb - n + i0, col) : 0.0, xp1 = (Ep && r1ok) ? xat(rb - n + i1, col) : 0.0;
+      const double xn0 = (En && r0ok) ? xat(rb + n + i0, col) : 0.0, xn1 = (En && r1ok) ? xat(rb + n + i1, col) : 0.0;
+      double acc0 = 0.0, acc1 = 0.0, rs0 = 0.0, rs1 = 0.0;
       for (int k = 0; k < n; ++k) {
-        const double a = k <= i ? Ds[i * ld + k] : Ds[k * ld + i];  // lower triangle read
-        acc = fma(a, xv[(n + k) * kRhsChunk + col], acc);
-        acc = fma(Ep[i * ld + k], xv[k * kRhsChunk + col], acc);
-        acc = fma(En[k * ld + i], xv[(2 * n + k) * kRhsChunk + col], acc);
-        if (col == 0) rs += fabs(a) + fabs(Ep[i * ld + k]) + fabs(En[k * ld + i]);
+        const double xk = __shfl_sync(0xffffffffu, k < 32 ? xc0 : xc1, k & 31);
+        const double d0 = k <= a0 ? Dj[a0 * n + k] : Dj[k * n + a0];
+        acc0 = fma(d0, xk, acc0);
+        if (norms) rs0 += fabs(d0);
+        if (two) {
+          const double d1 = k <= a1 ? Dj[a1 * n + k] : Dj[k * n + a1];
+          acc1 = fma(d1, xk, acc1);
+          if (norms) rs1 += fabs(d1);
+        }
       }
-      for (int q = 0; q < m; ++q) {
-        acc = fma(Gs[q * ld + i], xg[q * kRhsChunk + col], acc);
-        if (col == 0) rs += fabs(Gs[q * ld + i]);
+      if (Ep) {
+        for (int k = 0; k < n; ++k) {
+          const double xk = __shfl_sync(0xffffffffu, k < 32 ? xp0 : xp1, k & 31);
+          const double e0 = Ep[a0 * n + k];
+          acc0 = fma(e0, xk, acc0);
+          if (norms) rs0 += fabs(e0);
+          if (two) {
+            const double e1 = Ep[a1 * n + k];
+            acc1 = fma(e1, xk, acc1);
+            if (norms) rs1 += fabs(e1);
+          }
+        }
       }
-      const size_t row = (size_t)(d.offB + (long long)j * n + i);
-      const double bv = b[row * ldb + col];
-      const double r = bv - acc;
-      c[row * kRhsChunk + col] = r;
-      mr = fmax(mr, fabs(r));
-      mb = fmax(mb, fabs(bv));
-      mx = fmax(mx, fabs(xv[(n + i) * kRhsChunk + col]));
-      mrow = fmax(mrow, rs);
+      if (En) {
+        for (int k = 0; k < n; ++k) {
+          const double xk = __shfl_sync(0xffffffffu, k < 32 ? xn0 : xn1, k & 31);
+          const double e0 = En[k * n + a0];
+          acc0 = fma(e0, xk, acc0);
+          if (norms) rs0 += fabs(e0);
+          if (two) {
+            const double e1 = En[k * n + a1];
+            acc1 = fma(e1, xk, acc1);
+            if (norms) rs1 += fabs(e1);
+          }
+        }
+      }
+      if (m) {
+        const double* Gj = G + (size_t)j * mn;
+#pragma unroll
+        for (int q = 0; q < kMaxM; ++q) {
+          if (q >= m) break;  // warp-uniform; full unrolling keeps gacc in registers
+          const double xq = __shfl_sync(0xffffffffu, xg_l, q);
+          const double g0 = Gj[q * n + a0];
+          acc0 = fma(g0, xq, acc0);
+          gacc[q] = fma(g0, xc0, gacc[q]);
+          if (norms) rs0 += fabs(g0);
+          if (two) {
+            const double g1 = Gj[q * n + a1];
+            acc1 = fma(g1, xq, acc1);
+            gacc[q] = fma(g1, xc1, gacc[q]);
+            if (norms) rs1 += fabs(g1);
+          }
+        }
+      }
+      if (r0ok) {
+        const double bv = b[(size_t)(rb + i0) * ldb + col], r = bv - acc0;
+        c[(size_t)(rb + i0) * kRhsChunk + col] = r;
+        mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xc0));
+        if (norms) mrow = fmax(mrow, rs0);
+      }
+      if (r1ok) {
+        const double bv = b[(size_t)(rb + i1) * ldb + col], r = bv - acc1;
+        c[(size_t)(rb + i1) * kRhsChunk + col] = r;
+        mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xc1));
+        if (norms) mrow = fmax(mrow, rs1);
+      }
     }
-    // g partial: pg[q][col] += sum_i G_j[q][i] x_j[i][col]; |G| sums per g row
-    for (int e = threadIdx.x; e < m * nr; e += blockDim.x) {
-      const int q = e / nr, col = e - q * nr;
-      double acc = 0.0, ga = 0.0;
-      for (int i = 0; i < n; ++i) {
-        acc = fma(Gs[q * ld + i], xv[(n + i) * kRhsChunk + col], acc);
-        if (col == 0) ga += fabs(Gs[q * ld + i]);
-      }
-      pg[q * kRhsChunk + col] += acc;
-      if (col == 0) gabs[q] += ga;
+    // g-row partials of this column: lane sums, then a shuffle tree
+#pragma unroll
+    for (int q = 0; q < kMaxM; ++q) {
+      if (q >= m) break;
+      double v = gacc[q];  // rows beyond n hold x = 0
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) part[q * kRhsChunk + col] = v;
     }
   }
-  double* rmr = red;
-  double* rmx = red + blockDim.x;
-  double* rmb = red + 2 * blockDim.x;
-  double* rrow = red + 3 * blockDim.x;
-  __syncthreads();
-  rmr[threadIdx.x] = mr; rmx[threadIdx.x] = mx; rmb[threadIdx.x] = mb; rrow[threadIdx.x] = mrow;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      rmr[threadIdx.x] = fmax(rmr[threadIdx.x], rmr[threadIdx.x + w]);
-      rmx[threadIdx.x] = fmax(rmx[threadIdx.x], rmx[threadIdx.x + w]);
-      rmb[threadIdx.x] = fmax(rmb[threadIdx.x], rmb[threadIdx.x + w]);
-      rrow[threadIdx.x] = fmax(rrow[threadIdx.x], rrow[threadIdx.x + w]);
+  if (norms && m) {
+    // |G| sums of the g rows over the task's stages: lane q sums row q
+    for (int j = j0; j < j1; ++j) {
+      const double* Gj = G + (size_t)j * mn;
+      if (lane < m)
+        for (int i = 0; i < n; ++i) gab += fabs(Gj[lane * n + i]);
     }
-    __syncthreads();
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    if (norms) mrow = fmax(mrow, __shfl_xor_sync(0xffffffffu, mrow, o));
   }
   double* pm = part + kMaxM * kRhsChunk;
-  if (threadIdx.x == 0) { pm[0] = rmr[0]; pm[1] = rmx[0]; pm[2] = rmb[0]; pm[3] = rrow[0]; }
-  // the thread that handled (q, col 0) holds the |G| sums of g row q
-  for (int e = threadIdx.x; e < m * nr; e += blockDim.x) {
-    const int q = e / nr, col = e - q * nr;
-    if (col == 0) pm[4 + q] = gabs[q];
+  if (lane == 0) {
+    pm[0] = mr; pm[1] = mx; pm[2] = mb;
+    if (norms) pm[3] = mrow;
   }
+  if (norms && lane < m) pm[4 + lane] = gab;
 }
 
 // Finish the g rows of one system from the chunk partials, then eta and the
@@ -1450,12 +1418,15 @@ __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int*
                                  const double* __restrict__ uR, const double* __restrict__ b, int ldb,
                                  const double* __restrict__ x, int ldx, double* c, int nr,
                                  const double* __restrict__ parts, double tol, double* eta_out,
-                                 int* converged) {
+                                 const double* __restrict__ eta_prev, int* converged) {
   __shared__ double red[4][256];
   __shared__ double gsum[kMaxM];
   const int s = blockIdx.x;
   const LevelDesc& d = descs[sys_desc[s]];
-  if (converged && converged[s]) return;
+  if (converged && converged[s]) {  // keeps the eta of its converging sweep
+    if (threadIdx.x == 0 && eta_prev) eta_out[s] = eta_prev[s];
+    return;
+  }
   const int m = d.m;
   const int p0 = part0[s], np = (d.N + kResChunk - 1) / kResChunk;
   const double* R = m ? uR + d.offR : nullptr;
@@ -1555,6 +1526,19 @@ __global__ void k_adjoint_grad(const LevelDesc* __restrict__ descs, const ResTas
     }
 }
 
+// Identity pivot blocks and corner for every system of a batch (synthetic
+// inputs of the autotuner: the kernels' run time does not depend on values).
+__global__ void k_fill_identity(const LevelDesc* __restrict__ descs, const int* __restrict__ sys_desc,
+                                double* D, double* R) {
+  const LevelDesc& d = descs[sys_desc[blockIdx.x]];
+  const long long nn = (long long)d.n * d.n, tot = (long long)d.N * nn;
+  for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
+    const long long r = e % nn;
+    D[d.offD + e] = (r % (d.n + 1) == 0) ? 1.0 : 0.0;
+  }
+  for (int e = threadIdx.x; e < d.m * d.m; e += blockDim.x) R[d.offR + e] = (e % (d.m + 1) == 0) ? 1.0 : 0.0;
+}
+
 int set_smem(const void* fn, size_t bytes) {
   return (int)cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
@@ -1567,12 +1551,6 @@ size_t factor_smem_bytes(int n, int m, int mixed) {
 
 size_t solve_smem_bytes(int n, int m, int single) {
   return (size_t)sol_layout(n, m, single ? 4 : 8).total;
-}
-
-size_t residual_smem_bytes(int n) {
-  const int ld = n | 1;
-  return sizeof(double) * ((size_t)3 * n * ld + (size_t)kMaxM * ld + 3 * (size_t)n * kRhsChunk +
-                           (size_t)kMaxM * kRhsChunk + 4 * 256);
 }
 
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
@@ -1637,6 +1615,13 @@ int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int
   return (int)cudaGetLastError();
 }
 
+int launch_fill_identity(const LevelDesc* d, const int* sys_desc, int count, double* D, double* R,
+                         void* stream) {
+  if (count <= 0) return 0;
+  k_fill_identity<<<count, 256, 0, (cudaStream_t)stream>>>(d, sys_desc, D, R);
+  return (int)cudaGetLastError();
+}
+
 int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const double* x, int ldx,
                         const double* xb, int ldxb, int nr, double* dD, double* dE, double* dG,
                         double* dR, void* stream) {
@@ -1645,25 +1630,22 @@ int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const 
   return (int)cudaGetLastError();
 }
 
-int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, int maxn, const double* D,
-                    const double* E, const double* G, const double* b, int ldb, const double* x,
-                    int ldx, double* c, int nr, double* parts, const int* skip, void* stream) {
+int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, const double* D, const double* E,
+                    const double* G, const double* b, int ldb, const double* x, int ldx, double* c, int nr,
+                    double* parts, const int* skip, int norms, void* stream) {
   if (ntasks <= 0) return 0;
-  const size_t sm = residual_smem_bytes(maxn);
-  int e = set_smem((const void*)k_residual, sm);
-  if (e) return e;
-  k_residual<<<ntasks, 256, sm, (cudaStream_t)stream>>>(d, t, D, E, G, b, ldb, x, ldx, c, nr, parts,
-                                                        skip);
+  k_residual<<<(ntasks + 7) / 8, 256, 0, (cudaStream_t)stream>>>(d, t, ntasks, D, E, G, b, ldb, x, ldx, c,
+                                                                 nr, parts, skip, norms);
   return (int)cudaGetLastError();
 }
 
 int launch_residual_final(const LevelDesc* d, const int* sys_desc, const int* part0, int count,
                           const double* G, const double* R, const double* b, int ldb, const double* x,
                           int ldx, double* c, int nr, const double* parts, double tol, double* eta_out,
-                          int* converged, void* stream) {
+                          const double* eta_prev, int* converged, void* stream) {
   if (count <= 0) return 0;
   k_residual_final<<<count, 256, 0, (cudaStream_t)stream>>>(d, sys_desc, part0, G, R, b, ldb, x, ldx, c,
-                                                            nr, parts, tol, eta_out, converged);
+                                                            nr, parts, tol, eta_out, eta_prev, converged);
   return (int)cudaGetLastError();
 }
 

@@ -110,6 +110,7 @@ def test_refinement_multiple_rhs_and_early_stop(kkt, orc):
         kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
         x8 = torch.zeros_like(bd)
         kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, bd, x8, sweeps=8, tol=1e-13)
+        etas8 = [kkt.kkt_refine_eta(h, s, 1)[0] for s in range(8)]
         x3 = torch.zeros_like(bd)
         kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, bd, x3, sweeps=3, tol=1e-13)
         torch.cuda.synchronize()
@@ -117,6 +118,11 @@ def test_refinement_multiple_rhs_and_early_stop(kkt, orc):
     finally:
         kkt.kkt_destroy(h)
     np.testing.assert_array_equal(x8, x3)          # converged within 3 sweeps, then stopped
+    # after convergence the recorded eta stays that of the converging sweep
+    conv = next(s for s in range(8) if etas8[s] <= 1e-13)
+    assert 0.0 < etas8[conv] <= 1e-13
+    assert all(etas8[s] == etas8[conv] for s in range(conv, 8))
+    assert all(etas8[s] > 1e-13 for s in range(conv))
     for c in range(17):
         assert eta(orc, D, E, G, R, x8[:, c], b[:, c]) <= 1e-13
 

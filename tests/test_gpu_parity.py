@@ -434,3 +434,53 @@ def test_factor_layouts_bitwise_identical(kkt, precision):
             kkt.kkt_destroy(h)
     np.testing.assert_array_equal(outs[0], outs[1])
     np.testing.assert_array_equal(outs[0], outs[2])
+
+
+# ------------------------------------------------------------- autotuned batches
+
+def test_tuned_uneven_batch(kkt, orc):
+    """The autotuner's plan (timed on the device) solves an uneven batch like
+    the oracle; every chosen level plan is a valid hierarchy."""
+    import torch
+    sy = gen.uneven_batch(10, seed=9, N_range=(8, 60))
+    Ns = [s[0].shape[0] for s in sy]
+    ns = [s[0].shape[1] for s in sy]
+    ms = [s[3].shape[0] for s in sy]
+    h, lv = kkt.kkt_batch_create_tuned(Ns, ns, ms)
+    try:
+        assert len(lv) == len(sy) and min(lv) >= 1
+        for i, N in enumerate(Ns):
+            Nl = N
+            for l in range(1, lv[i] + 1):
+                seg = kkt.kkt_partition(h, i, l)
+                assert sum(seg) + len(seg) - 1 == Nl and min(seg) >= 1
+                Nl = len(seg) - 1
+            assert len(kkt.kkt_partition(h, i, lv[i])) == 1     # sequential top level
+        off = kkt.kkt_batch_offsets(h, len(sy))
+        cat = lambda i: dev(np.concatenate([s[i].ravel() for s in sy] + [np.zeros(1)]))
+        bs = [gen.rhs(N * n + m, 1, seed=40 + i) for i, (N, n, m) in enumerate(zip(Ns, ns, ms))]
+        b = dev(np.concatenate(bs))
+        kkt.kkt_factor(h, cat(0), cat(1), cat(2), cat(3))
+        kkt.kkt_solve(h, b)
+        torch.cuda.synchronize()
+        assert kkt.kkt_get_info(h)["status"] == 0
+        x = b.cpu().numpy()
+    finally:
+        kkt.kkt_destroy(h)
+    for i, s in enumerate(sy):
+        xi = x[off["b"][i]:off["b"][i + 1]]
+        xo = orc.seq_solve(orc.seq_factor(*s), bs[i])
+        check_solution(orc, *s, xi, bs[i], xo, fwd_tol=1e-6)
+
+
+def test_tuned_plans_follow_the_batch(kkt):
+    """Many short systems fill the GPU on their own: the tuner keeps them
+    sequential (no fill-in). A single long system gets a partitioned plan."""
+    h, lv = kkt.kkt_batch_create_tuned([40] * 2048, [8] * 2048, [2] * 2048)
+    kkt.kkt_destroy(h)
+    assert max(lv) == 1
+    h, lv = kkt.kkt_batch_create_tuned([4096], [16], [4])
+    try:
+        assert lv[0] >= 2 and len(kkt.kkt_partition(h, 0, 1)) > 1
+    finally:
+        kkt.kkt_destroy(h)
