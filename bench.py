@@ -481,8 +481,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="ipm1024", choices=["ipm1024"] + sorted(BATCHES),
                     help="ipm1024: the single-system workload (default); the others are the batched ones")
-    ap.add_argument("--sweeps", type=int, default=4, help="refinement sweeps of the mixed path")
-    ap.add_argument("--tol", type=float, default=1e-16, help="refinement stop (eta) of the mixed path")
+    ap.add_argument("--sweeps", type=int, default=4, help="refinement sweeps of the mixed path (at most)")
+    ap.add_argument("--tol", type=float, default=1e-14,
+                    help="refinement stop of the mixed path: a system stops once its eta is below this")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

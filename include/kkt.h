@@ -142,8 +142,8 @@ kkt_status kkt_batch_create(int count, const int* N, const int* n, const int* m,
  * the kernels' run time does not depend on the values), and keeps the
  * fastest. Candidates: every system sequential (P = 1, no fill-in; best when
  * the systems alone fill the GPU), and level-1 segment totals of 1/2, 1, 2,
- * 4 and 8 per SM spread over the systems in proportion to their stage
- * counts, with 4x or 8x fewer segments on each level above, down to a
+ * 4, 8, 16, 32 and 64 per SM spread over the systems in proportion to their
+ * stage counts, with 4x or 8x fewer segments on each level above, down to a
  * sequential top level. levels_out (optional, length count) receives the
  * number of levels chosen per system; kkt_partition reads the plan. Blocks
  * until the tuning runs finish and allocates scratch memory for them
@@ -264,6 +264,9 @@ kkt_status kkt_set_launch_events(kkt_handle* h, void* const* events, int count);
  * the second CTA sums the lower levels' corner partials while the first
  * runs the stages. This gives a task two SMs' FP64 units and pays off on
  * levels with fewer tasks than SM pairs. KKT_PAIR_AUTO (the default) pairs exactly those levels;
+ * Systems with blocks n <= 16 run one warp per segment task (several tasks
+ * per CTA) in every case and never pair: at that size what counts is how
+ * many independent stage chains an SM interleaves.
  * KKT_PAIR_OFF and KKT_PAIR_ON force one layout on every level (the
  * partition chosen at creation is kept). The layouts give bitwise identical
  * results: each element is computed by the same operations in the same

@@ -147,6 +147,15 @@ struct kkt_handle {
   std::vector<LevelDesc> hdesc;              // host copy of the descriptors
   std::vector<std::vector<int>> desc_of;     // desc_of[s][level-1]
   std::vector<int> fac_off, fac_cnt;         // task ranges per level (factor + forward)
+  // launch groups of a level: tasks of one block-size class, contiguous in
+  // the task array (small blocks, one warp per task, first; then one group
+  // per larger block size, one CTA or CTA pair per task), each launched with
+  // shared memory for its own largest n and m
+  struct Group {
+    int off, cnt, n, m;
+    bool warp;
+  };
+  std::vector<std::vector<Group>> fac_groups, bwd_groups;
   std::vector<int> bwd_off, bwd_cnt;         // task ranges per level (backward)
   void* dmem = nullptr;                      // one allocation for everything
   size_t dbytes = 0;
@@ -204,18 +213,22 @@ struct Carver {
 // The second CTA of a pair has work when a segment of the level has fill-in
 // rows, or on a top level below which other levels left corner partials to
 // sum (the sum then runs beside the top level's stages).
-std::vector<int> paired_levels(const std::vector<std::vector<int>>& Plev, int sms) {
+// Only systems with blocks above kWarpMaxN run on the CTA kernel (the others
+// take one warp per task and never pair).
+std::vector<int> paired_levels(const std::vector<std::vector<int>>& Plev, const int* n, int sms) {
   size_t L = 0;
   for (const auto& ps : Plev) L = std::max(L, ps.size());
   std::vector<int> pr(L, 0);
   for (size_t l = 0; l < L; ++l) {
     long long tasks = 0;
     bool work = false;
-    for (const auto& ps : Plev)
-      if (l < ps.size()) {
+    for (size_t s = 0; s < Plev.size(); ++s) {
+      const auto& ps = Plev[s];
+      if (l < ps.size() && n[s] > kkt::kWarpMaxN) {
         tasks += ps[l];
         work = work || ps[l] > 1 || (l + 1 == ps.size() && l > 0);
       }
+    }
     pr[l] = work && 2 * tasks <= sms;
   }
   return pr;
@@ -232,7 +245,7 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return KKT_ERR_CUDA;
-  const std::vector<int> pair_lv = paired_levels(Plev, sms);
+  const std::vector<int> pair_lv = paired_levels(Plev, n, sms);
   if (precision != KKT_FP64 && precision != KKT_MIXED_FP32 && precision != KKT_MIXED_FP32_ALL)
     return KKT_ERR_ARG;
   auto* h = new kkt_handle();
@@ -253,7 +266,10 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
     for (int j = 0; j < sp.N; ++j) nat[j] = j;
     for (size_t l = 0; l < Ps.size(); ++l) {
       LevelPlan L;
-      if (!make_level(Nl, Ps[l], mode, sp.n, sp.m, pair_lv[l] != 0, &L)) { delete h; return KKT_ERR_PARTITION; }
+      if (!make_level(Nl, Ps[l], mode, sp.n, sp.m, pair_lv[l] != 0 && sp.n > kkt::kWarpMaxN, &L)) {
+        delete h;
+        return KKT_ERR_PARTITION;
+      }
       L.nat = nat;
       L.mixed = (precision == KKT_MIXED_FP32_ALL) || (precision == KKT_MIXED_FP32 && l == 0);
       sp.lv.push_back(L);
@@ -343,18 +359,34 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
   // task lists: factor/forward per level, then backward per level
   h->fac_off.assign(h->maxL, 0); h->fac_cnt.assign(h->maxL, 0);
   h->bwd_off.assign(h->maxL, 0); h->bwd_cnt.assign(h->maxL, 0);
+  // tasks of a level ordered by block size (small blocks first), one launch group per size class
+  auto build_groups = [&](int l, bool backward, std::vector<kkt_handle::Group>& groups) {
+    std::vector<int> sys_at;
+    for (int s = 0; s < count; ++s)
+      if ((backward ? l + 1 : l) < (int)h->sys[s].lv.size()) sys_at.push_back(s);
+    std::stable_sort(sys_at.begin(), sys_at.end(), [&](int a, int b) { return h->sys[a].n < h->sys[b].n; });
+    for (int s : sys_at) {
+      const SysPlan& sp = h->sys[s];
+      const bool warp = sp.n <= kkt::kWarpMaxN;
+      if (groups.empty() || groups.back().warp != warp || (!warp && groups.back().n != sp.n))
+        groups.push_back(kkt_handle::Group{(int)tasks.size(), 0, sp.n, sp.m, warp});
+      kkt_handle::Group& gr = groups.back();
+      for (int k = 0; k < sp.lv[l].P; ++k) tasks.push_back(Task{h->desc_of[s][l], k});
+      gr.cnt += sp.lv[l].P;
+      gr.n = std::max(gr.n, sp.n);
+      gr.m = std::max(gr.m, sp.m);
+    }
+  };
+  h->fac_groups.assign(h->maxL, {});
+  h->bwd_groups.assign(h->maxL, {});
   for (int l = 0; l < h->maxL; ++l) {
     h->fac_off[l] = (int)tasks.size();
-    for (int s = 0; s < count; ++s)
-      if (l < (int)h->sys[s].lv.size())
-        for (int k = 0; k < h->sys[s].lv[l].P; ++k) tasks.push_back(Task{h->desc_of[s][l], k});
+    build_groups(l, false, h->fac_groups[l]);
     h->fac_cnt[l] = (int)tasks.size() - h->fac_off[l];
   }
   for (int l = 0; l < h->maxL; ++l) {
     h->bwd_off[l] = (int)tasks.size();
-    for (int s = 0; s < count; ++s)
-      if (l + 1 < (int)h->sys[s].lv.size())
-        for (int k = 0; k < h->sys[s].lv[l].P; ++k) tasks.push_back(Task{h->desc_of[s][l], k});
+    build_groups(l, true, h->bwd_groups[l]);
     h->bwd_cnt[l] = (int)tasks.size() - h->bwd_off[l];
   }
   const size_t task_off = cv.take(sizeof(Task) * std::max<size_t>(tasks.size(), 1));
@@ -584,11 +616,12 @@ kkt_status kkt_batch_create_tuned(int count, const int* N, const int* n, const i
     sumN += N[s];
   }
   // candidates: every system sequential, then level-1 segment totals of
-  // 1/2 .. 8 per SM spread over the systems by stage count, with 4x or 8x
-  // fewer segments per level above
+  // 1/2 .. 64 per SM (small blocks run one warp per segment, many per SM)
+  // spread over the systems by stage count, with 4x or 8x fewer segments per
+  // level above
   std::vector<std::vector<std::vector<int>>> cands;
   cands.push_back(std::vector<std::vector<int>>(count, std::vector<int>{1}));
-  for (int T1 : {sms / 2, sms, 2 * sms, 4 * sms, 8 * sms})
+  for (int T1 : {sms / 2, sms, 2 * sms, 4 * sms, 8 * sms, 16 * sms, 32 * sms, 64 * sms})
     for (int ratio : {4, 8}) {
       std::vector<std::vector<int>> pl(count);
       for (int s = 0; s < count; ++s)
@@ -705,13 +738,15 @@ kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const dou
   if (h->tot_E > 0 && !E) return KKT_ERR_ARG;
   if (h->maxm > 0 && (!G || !R)) return KKT_ERR_ARG;
   int li = 0;
-  for (int l = 0; l < h->maxL; ++l) {
-    if (!h->fac_cnt[l]) continue;
-    const int e = kkt::launch_factor(h->ddesc, h->dtasks + h->fac_off[l], h->fac_cnt[l], h->maxn,
-                                     h->maxm, h->level_mixed[l], level_paired(h, l), D, E, G, R,
-                                     h->dinfo, stream);
-    if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
-  }
+  for (int l = 0; l < h->maxL; ++l)
+    for (const kkt_handle::Group& gr : h->fac_groups[l]) {
+      const int e = gr.warp ? kkt::launch_factor_w(h->ddesc, h->dtasks + gr.off, gr.cnt, gr.n, gr.m,
+                                                   h->level_mixed[l], D, E, G, R, h->dinfo, stream)
+                            : kkt::launch_factor(h->ddesc, h->dtasks + gr.off, gr.cnt, gr.n, gr.m,
+                                                 h->level_mixed[l], level_paired(h, l), D, E, G, R,
+                                                 h->dinfo, stream);
+      if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
+    }
   h->factored = true;
   return KKT_OK;
 }
@@ -720,18 +755,23 @@ namespace {
 // One forward/backward sweep over every level for up to kRhsChunk columns.
 kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* skip, void* stream,
                        int* li) {
-  for (int l = 0; l < h->maxL; ++l) {
-    if (!h->fac_cnt[l]) continue;
-    const int e = kkt::launch_forward(h->ddesc, h->dtasks + h->fac_off[l], h->fac_cnt[l], h->maxn,
-                                      h->maxm, h->level_mixed[l], b, ldb, nr, skip, stream);
-    if (e || (li && !mark(h, (*li)++, stream))) return KKT_ERR_CUDA;
-  }
-  for (int l = h->maxL - 2; l >= 0; --l) {
-    if (!h->bwd_cnt[l]) continue;
-    const int e = kkt::launch_backward(h->ddesc, h->dtasks + h->bwd_off[l], h->bwd_cnt[l], h->maxn,
-                                       h->maxm, h->level_mixed[l], b, ldb, nr, skip, stream);
-    if (e || (li && !mark(h, (*li)++, stream))) return KKT_ERR_CUDA;
-  }
+  // one launch per group: small blocks one warp per task, the others one CTA per task
+  auto run = [&](bool backward, int l, const std::vector<kkt_handle::Group>& groups) -> bool {
+    for (const kkt_handle::Group& gr : groups) {
+      const Task* t = h->dtasks + gr.off;
+      const int mx = h->level_mixed[l];
+      const int e = gr.warp ? kkt::launch_solve_w(backward, h->ddesc, t, gr.cnt, gr.n, gr.m, mx, b, ldb, nr, skip,
+                                                  stream)
+                    : backward ? kkt::launch_backward(h->ddesc, t, gr.cnt, gr.n, gr.m, mx, b, ldb, nr, skip, stream)
+                               : kkt::launch_forward(h->ddesc, t, gr.cnt, gr.n, gr.m, mx, b, ldb, nr, skip, stream);
+      if (e || (li && !mark(h, (*li)++, stream))) return false;
+    }
+    return true;
+  };
+  for (int l = 0; l < h->maxL; ++l)
+    if (!run(false, l, h->fac_groups[l])) return KKT_ERR_CUDA;
+  for (int l = h->maxL - 2; l >= 0; --l)
+    if (!run(true, l, h->bwd_groups[l])) return KKT_ERR_CUDA;
   return KKT_OK;
 }
 }  // namespace
@@ -742,7 +782,7 @@ kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream) 
   // attached events: the factor's launches take the first slots, then the
   // solve's launches in order
   int li = 0;
-  for (int l = 0; l < h->maxL; ++l) li += h->fac_cnt[l] > 0;
+  for (int l = 0; l < h->maxL; ++l) li += (int)h->fac_groups[l].size();
   for (int c0 = 0; c0 < nrhs; c0 += kkt::kRhsChunk) {
     const int nr = std::min(kkt::kRhsChunk, nrhs - c0);
     const kkt_status st = solve_chunk(h, b + c0, ldb, nr, nullptr, stream, &li);
@@ -905,9 +945,8 @@ kkt_status kkt_launch_counts(const kkt_handle* h, int* fl, int* sl) {
   if (!h) return KKT_ERR_ARG;
   int f = 0, sv = 0;
   for (int l = 0; l < h->maxL; ++l) {
-    f += h->fac_cnt[l] > 0;
-    sv += h->fac_cnt[l] > 0;
-    sv += h->bwd_cnt[l] > 0;
+    f += (int)h->fac_groups[l].size();
+    sv += (int)h->fac_groups[l].size() + (int)h->bwd_groups[l].size();
   }
   if (fl) *fl = f;
   if (sl) *sl = sv;
@@ -944,7 +983,7 @@ kkt_status kkt_plan_flops(int N, int n, int m, int nlevels, const int* P_levels,
     return KKT_ERR_ARG;
   SysPlan sp;
   sp.N = N; sp.n = n; sp.m = m;
-  const std::vector<int> pair_lv = paired_levels({std::vector<int>(P_levels, P_levels + nlevels)}, sms);
+  const std::vector<int> pair_lv = paired_levels({std::vector<int>(P_levels, P_levels + nlevels)}, &n, sms);
   int Nl = N;
   for (int l = 0; l < nlevels; ++l) {
     LevelPlan L;

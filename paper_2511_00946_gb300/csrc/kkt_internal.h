@@ -140,6 +140,16 @@ __host__ __device__ inline FacLayout fac_layout(int n, int m, int zb) {
   L.total = L.oCorner + kkt_align16(8 * kMaxM * kMaxM);
   return L;
 }
+// One warp's slice for a small-block segment task (k_factor_w): the same
+// blocks without the second pivot buffer, and an m x m corner sum.
+__host__ __device__ inline FacLayout fac_layout_w(int n, int m, int zb) {
+  FacLayout L = fac_layout(n, m, zb);
+  L.oDfac2 = L.oRinv2 = 0;
+  L.oCorner = L.oTab + kkt_align16(4 * (L.q * (L.q - 1) / 2 + 1));
+  L.total = L.oCorner + kkt_align16(8 * (m * m > 0 ? m * m : 1));
+  return L;
+}
+constexpr int kWarpMaxN = 16;  // largest stage block of the warp-per-task kernels
 // The substitution kernels double-buffer the factor blocks (L, rinv, Z) so
 // that the next stage's blocks stream in while the current stage is solved.
 struct SolLayout {
@@ -186,6 +196,10 @@ constexpr int kResPartDoubles = kMaxM * kRhsChunk + 4 * kRhsChunk;
 // `single`: FP32 substitution
 // with the FP32 factor copy (mixed levels only); `skip`: per-system flags
 // (null = never skip), a set flag makes the system's CTAs return at once.
+// one warp per task (blocks n <= kWarpMaxN), several tasks per CTA
+int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
+                    const double* D, const double* E, const double* G, const double* R, Info* info,
+                    void* stream);
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
                   void* stream);
@@ -193,6 +207,9 @@ int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int 
                    double* b, int ldb, int nrhs, const int* skip, void* stream);
 int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
                     double* b, int ldb, int nrhs, const int* skip, void* stream);
+// one warp per task (blocks n <= kWarpMaxN), forward or backward substitution
+int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
+                   double* b, int ldb, int nrhs, const int* skip, void* stream);
 // x += c (stage rows per residual task, g rows by each system's first task)
 int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int ldx, const double* c,
                 int nr, const int* skip, void* stream);

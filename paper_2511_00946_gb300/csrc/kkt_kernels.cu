@@ -18,6 +18,8 @@
 // accumulator once.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kkt_internal.h"
 
 namespace kkt {
@@ -417,19 +419,19 @@ __device__ __forceinline__ void st_cluster(unsigned addr, float v) {
 }
 
 // sum_{p < np} part(p, o) for every output o < nout, by the whole CTA, in a
-// fixed order that depends only on (nout, np, blockDim): `sp` adjacent lanes
+// fixed order that depends only on (nout, np, group size): `sp` adjacent lanes
 // (a power of two, at most 32) per output each add every sp-th partial into
 // two accumulators, then a shuffle tree combines the lanes; out(o, sum) is
 // called once per output. Many partials (one per segment of every lower
 // level) are summed with all FP64 sub-pipes instead of one dependent chain
 // per output.
 template <typename Fpart, typename Fout>
-__device__ void sum_partials(int nout, int np, Fpart part, Fout out) {
+__device__ void sum_partials(Grp G, int nout, int np, Fpart part, Fout out) {
   int sp = 1;
-  while (sp < 32 && sp * 2 * nout <= (int)blockDim.x) sp *= 2;
-  const int groups = (int)blockDim.x / sp, sub = (int)threadIdx.x & (sp - 1);
+  while (sp < 32 && sp * 2 * nout <= G.nt) sp *= 2;
+  const int groups = G.nt / sp, sub = G.tid & (sp - 1);
   for (int o0 = 0; o0 < nout; o0 += groups) {
-    const int o = o0 + (int)threadIdx.x / sp;
+    const int o = o0 + G.tid / sp;
     double a0 = 0.0, a1 = 0.0;
     if (o < nout) {
       int p = sub;
@@ -496,6 +498,143 @@ constexpr int kWhole = 0, kSplit = 1, kPair = 2;
 constexpr int kBarProd = 2, kBarCons = 3, kBarFullM = 4, kBarFreeM = 5, kBarFullZ = 6, kBarFreeZ = 7;
 constexpr int kRoleThreads = 128;
 
+// Shared-memory view and per-stage bookkeeping of one segment task of
+// Algorithm 1: where the stage's blocks live, the loads of its inputs (the
+// caller's arrays at level 1, the slots of the level below otherwise), the
+// stores of its factor blocks and the next level's slots. Used by the CTA
+// kernel (k_factor) and the warp kernel (k_factor_w) alike.
+template <typename TZ>
+struct FacCtx {
+  static constexpr bool mixed = sizeof(TZ) == 4;
+  const LevelDesc* d;
+  int n, m, R, ldD, ldZ, ldT, oG, oW, s;
+  size_t nn, mn;
+  SegGeom g;
+  double *Dfac, *rinv, *T;
+  TZ *M, *rinvZ, *Z;
+  int* tab;
+  const double *Din, *D2, *Ein, *Gin, *G2;
+
+  __device__ FacCtx(const LevelDesc& dd, int seg, unsigned char* sm, const FacLayout& lay, const double* uD,
+                    const double* uE, const double* uG) {
+    d = &dd;
+    n = dd.n; m = dd.m; R = 2 * n + m;
+    ldD = odd(n); ldZ = lay.ldZ; ldT = lay.ldT;
+    oG = n; oW = n + m;  // panel row offsets
+    g = seg_geom(dd, seg);
+    s = g.f - 1;         // separator of this segment (k >= 1)
+    nn = (size_t)n * n; mn = (size_t)m * n;
+    Dfac = (double*)(sm + lay.oDfac);
+    M = (TZ*)(sm + lay.oM);
+    rinv = (double*)(sm + lay.oRinv);
+    rinvZ = (TZ*)(sm + lay.oRinvZ);
+    Z = (TZ*)(sm + lay.oZ);
+    T = (double*)(sm + lay.oT);
+    tab = (int*)(sm + lay.oTab);
+    Din = dd.level == 1 ? uD + dd.offD : dd.Dw;
+    D2 = dd.level == 1 ? nullptr : dd.D2w;
+    Ein = dd.level == 1 ? uE + dd.offE : dd.Ew;
+    Gin = dd.level == 1 ? (m ? uG + dd.offG : nullptr) : dd.Gw;
+    G2 = dd.level == 1 ? nullptr : dd.G2w;
+  }
+  __device__ const double* Dp(const double* b, int j) const { return b ? b + (size_t)j * nn : nullptr; }
+  __device__ const double* Gp(const double* b, int j) const { return b ? b + (size_t)j * mn : nullptr; }
+
+  // the first stage's inputs: pivot block, E- and G-rows and the next D, G
+  // (eg); the fill-in rows W_1 = E[s]^T, A_k and Q_k^T (wr)
+  __device__ void load_first(bool eg, bool wr, Grp G) const {
+    const double* none = nullptr;
+    if (eg) {
+      load_blk(Dfac, ldD, Dp(Din, g.f), Dp(D2, g.f), n, n, false, G);
+      if (g.len > 1 || g.hasF) load_blk(Z, ldZ, Dp(Ein, g.f), none, n, n, false, G);
+      if (m) load_blk(Z + oG * ldZ, ldZ, Gp(Gin, g.f), Gp(G2, g.f), m, n, false, G);
+      if (g.len > 1) {
+        load_blk(T, ldT, Dp(Din, g.f + 1), Dp(D2, g.f + 1), n, n, false, G);          // D_{2}
+        if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, g.f + 1), Gp(G2, g.f + 1), m, n, false, G);
+      }
+    }
+    if (wr) {
+      load_blk(Z + oW * ldZ, ldZ, Dp(Ein, s), none, n, n, true, G);                 // W_1 = B_k = E[s]^T
+      load_blk(T + oW * ldT + oW, ldT, Dp(Din, s), Dp(D2, s), n, n, false, G);       // A_k
+      if (m) load_blk(T + oW * ldT + oG, ldT, Gp(Gin, s), Gp(G2, s), n, m, true, G);  // Q_k^T
+    }
+  }
+
+  // factor blocks of stage j from the pivot factor L (Dp_, ld ldD) and
+  // rv = 1/diag: Ld = L, LdR = L with its rows divided by their diagonal
+  // (backward substitution), LdM = L with its columns divided by their
+  // diagonal (forward substitution: the panel operand Ms when given, else
+  // formed here with the same rounding), Lri = rv. Strict lower triangles are
+  // computed and the rest zero-filled, so that no FP64 multiply is issued for
+  // an upper half.
+  __device__ void store_pivot(int j, const double* Dp_, const double* rv, const TZ* Ms, Grp G) const {
+    store_blk(d->Ld + (size_t)j * nn, Dp_, ldD, n, n, false, true, G);
+    TZ* LdRj = mixed ? (TZ*)(d->LdRf + (size_t)j * nn) : (TZ*)(d->LdR + (size_t)j * nn);
+    TZ* LdMj = mixed ? (TZ*)(d->LdMf + (size_t)j * nn) : (TZ*)(d->LdM + (size_t)j * nn);
+    for (int e = G.tid; e < n * n; e += G.nt) LdRj[e] = TZ(0);
+    if (Ms) store_blk(LdMj, Ms, ldD, n, n, false, true, G);
+    else
+      for (int e = G.tid; e < n * n; e += G.nt) LdMj[e] = TZ(0);
+    gsync(G);
+    for (int e = G.tid; e < (n - 1) * n / 2; e += G.nt) {
+      int a, b;
+      tri_rc(e, a, b);
+      const int r = a + 1, c = b;
+      LdRj[r * n + c] = (TZ)(Dp_[r * ldD + c] * rv[r]);
+      if (!Ms) LdMj[r * n + c] = (TZ)(Dp_[r * ldD + c] * rv[c]);
+    }
+    if (mixed)
+      for (int e = G.tid; e < n; e += G.nt) d->Lrif[(size_t)j * n + e] = (float)rv[e];
+    for (int e = G.tid; e < n; e += G.nt) d->Lri[(size_t)j * n + e] = rv[e];
+  }
+
+  // panel rows [0, rows) of Lp for stage j: rows outside [r0, r1) are zero
+  // (a consumer writes the W-rows of a split or paired segment)
+  __device__ void store_panel(int j, int r0, int r1, int rows, Grp G) const {
+    double* Pd = d->Lp + (size_t)j * R * n;
+    float* Pf = mixed ? d->Lpf + (size_t)j * R * n : nullptr;
+    for (int e = G.tid; e < rows * n; e += G.nt) {
+      const int r = e / n, c = e - r * n;
+      const TZ v = (r >= r0 && r < r1) ? Z[r * ldZ + c] : TZ(0);
+      Pd[e] = (double)v;
+      if (mixed) Pf[e] = (float)v;
+    }
+  }
+
+  // rotate the panel after the Schur update of stage i: the updated blocks
+  // become stage i+1's inputs, the next ones are loaded
+  __device__ void rotate(int i, int j, bool withW, Grp G) const {
+    const double* none = nullptr;
+    if (m) copy_blk(Z + oG * ldZ, ldZ, T + oG * ldT, ldT, m, n, G);          // G_{i+1}
+    if (withW) copy_blk(Z + oW * ldZ, ldZ, T + oW * ldT, ldT, n, n, G);      // W_{i+1}
+    if ((i + 1 < g.len - 1) || g.hasF) load_blk(Z, ldZ, Dp(Ein, j + 1), none, n, n, false, G);
+    gsync(G);
+    if (withW) load_blk(T + oW * ldT, ldT, none, none, n, n, false, G);     // W_{i+2} <- 0
+    if (i + 2 < g.len) {
+      load_blk(T, ldT, Dp(Din, j + 2), Dp(D2, j + 2), n, n, false, G);
+      if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, j + 2), Gp(G2, j + 2), m, n, false, G);
+    } else {
+      load_blk(T, ldT, none, none, n, n, false, G);
+      if (m) load_blk(T + oG * ldT, ldT, none, none, m, n, false, G);
+    }
+    gsync(G);
+  }
+
+  // the next level's slots of segment k (not on the top level)
+  __device__ void store_slots(int k, bool eg, bool wr, Grp G) const {
+    if (eg && g.hasF) {
+      store_blk(d->DB + (size_t)k * nn, T, ldT, n, n, false, true, G);             // -F^ F^T
+      if (m) store_blk(d->GB + (size_t)k * mn, T + oG * ldT, ldT, m, n, false, false, G);  // -G^ F^T
+    }
+    if (wr) {
+      store_blk(d->DA + (size_t)(k - 1) * nn, T + oW * ldT + oW, ldT, n, n, false, true, G);  // A~_k
+      if (m) store_blk(d->GA + (size_t)(k - 1) * mn, T + oW * ldT + oG, ldT, n, m, true, false, G);  // Q~_k
+      if (g.hasF) store_blk(d->EN + (size_t)(k - 1) * nn, T + oW * ldT, ldT, n, n, true, false, G);  // H~_k
+    }
+    if (eg && m) store_blk(d->Rpart + (size_t)k * m * m, T + oG * ldT + oG, ldT, m, m, false, true, G);
+  }
+};
+
 template <typename TZ>
 __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __restrict__ descs,
                                                            const Task* __restrict__ tasks,
@@ -510,20 +649,17 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
   const Task tk = tasks[pair ? blockIdx.x >> 1 : blockIdx.x];
   const LevelDesc& d = descs[tk.desc];
   constexpr bool mixed = sizeof(TZ) == 4;
-  const int n = d.n, m = d.m, R = 2 * n + m;
-  const FacLayout lay = fac_layout(n, m, (int)sizeof(TZ));
-  const int ldD = odd(n), ldZ = lay.ldZ, ldT = lay.ldT;
-  double* Dfac = (double*)(smraw + lay.oDfac);
-  TZ* M = (TZ*)(smraw + lay.oM);
-  double* rinv = (double*)(smraw + lay.oRinv);
-  TZ* rinvZ = (TZ*)(smraw + lay.oRinvZ);
-  TZ* Z = (TZ*)(smraw + lay.oZ);
-  double* T = (double*)(smraw + lay.oT);
-  int* tab = (int*)(smraw + lay.oTab);
-  const int oG = n, oW = n + m;  // panel row offsets
-  const SegGeom g = seg_geom(d, tk.seg);
-  const int s = g.f - 1;  // separator of this segment (k >= 1)
-  const size_t nn = (size_t)n * n, mn = (size_t)m * n;
+  const FacLayout lay = fac_layout(d.n, d.m, (int)sizeof(TZ));
+  const FacCtx<TZ> cx(d, tk.seg, smraw, lay, uD, uE, uG);
+  const int n = cx.n, m = cx.m, R = cx.R, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG, oW = cx.oW;
+  double* const Dfac = cx.Dfac;
+  double* const rinv = cx.rinv;
+  double* const T = cx.T;
+  TZ* const M = cx.M;
+  TZ* const rinvZ = cx.rinvZ;
+  TZ* const Z = cx.Z;
+  int* const tab = cx.tab;
+  const SegGeom g = cx.g;
   const int mode = pair ? kPair : (g.hasW && !mixed) ? kSplit : kWhole;
   // consumer buffers of the pair layout: buffer 0 is (M, rinvZ, Z rows [0, n+m)),
   // buffer 1 reuses the pivot block, rinv and the first rows of T, which a
@@ -534,34 +670,11 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
   const bool eg = mode != kPair || rank == 0;       // this CTA holds the E/G rows
   const bool wr = g.hasW && (mode != kPair || rank == 1);  // this CTA holds the W rows
 
-  // level inputs: the caller's arrays at level 1, the slots of the level above otherwise
-  const double* Din = d.level == 1 ? uD + d.offD : d.Dw;
-  const double* D2 = d.level == 1 ? nullptr : d.D2w;
-  const double* Ein = d.level == 1 ? uE + d.offE : d.Ew;
-  const double* Gin = d.level == 1 ? (m ? uG + d.offG : nullptr) : d.Gw;
-  const double* G2 = d.level == 1 ? nullptr : d.G2w;
-  auto Dp = [&](const double* b, int j) { return b ? b + (size_t)j * nn : nullptr; };
-  auto Gp = [&](const double* b, int j) { return b ? b + (size_t)j * mn : nullptr; };
-  const double* none = nullptr;
-
   if (threadIdx.x == 0) bad = 0;
   for (int e = threadIdx.x; e < R * ldT; e += blockDim.x) T[e] = 0.0;
   if (eg) potrf_table(tab, n);
   __syncthreads();
-  if (eg) {
-    load_blk(Dfac, ldD, Dp(Din, g.f), Dp(D2, g.f), n, n, false);
-    if (g.len > 1 || g.hasF) load_blk(Z, ldZ, Dp(Ein, g.f), none, n, n, false);
-    if (m) load_blk(Z + oG * ldZ, ldZ, Gp(Gin, g.f), Gp(G2, g.f), m, n, false);
-    if (g.len > 1) {
-      load_blk(T, ldT, Dp(Din, g.f + 1), Dp(D2, g.f + 1), n, n, false);          // D_{2}
-      if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, g.f + 1), Gp(G2, g.f + 1), m, n, false);
-    }
-  }
-  if (wr) {
-    load_blk(Z + oW * ldZ, ldZ, Dp(Ein, s), none, n, n, true);                 // W_1 = B_k = E[s]^T
-    load_blk(T + oW * ldT + oW, ldT, Dp(Din, s), Dp(D2, s), n, n, false);       // A_k
-    if (m) load_blk(T + oW * ldT + oG, ldT, Gp(Gin, s), Gp(G2, s), n, m, true);  // Q_k^T
-  }
+  cx.load_first(eg, wr, cta_grp());
   __syncthreads();
   if (mode == kPair) {
     // both CTAs have started before any remote store
@@ -571,45 +684,10 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
 
   const bool producer = mode == kWhole || (mode == kSplit && (int)threadIdx.x < kRoleThreads) ||
                         (mode == kPair && rank == 0);
-  // factor blocks of stage j from the pivot factor L (Dp_, ld ldD) and
-  // rv = 1/diag: Ld = L, LdR = L with its rows divided by their diagonal
-  // (backward substitution), LdM = L with its columns divided by their
-  // diagonal (forward substitution: the panel operand Ms when given, else
-  // formed here with the same rounding), Lri = rv. Strict lower triangles are
-  // computed and the rest zero-filled, so that no FP64 multiply is issued for
-  // an upper half.
   auto store_pivot = [&](int j, const double* Dp_, const double* rv, const TZ* Ms, Grp G) {
-    store_blk(d.Ld + (size_t)j * nn, Dp_, ldD, n, n, false, true, G);
-    TZ* LdRj = mixed ? (TZ*)(d.LdRf + (size_t)j * nn) : (TZ*)(d.LdR + (size_t)j * nn);
-    TZ* LdMj = mixed ? (TZ*)(d.LdMf + (size_t)j * nn) : (TZ*)(d.LdM + (size_t)j * nn);
-    for (int e = G.tid; e < n * n; e += G.nt) LdRj[e] = TZ(0);
-    if (Ms) store_blk(LdMj, Ms, ldD, n, n, false, true, G);
-    else
-      for (int e = G.tid; e < n * n; e += G.nt) LdMj[e] = TZ(0);
-    gsync(G);
-    for (int e = G.tid; e < (n - 1) * n / 2; e += G.nt) {
-      int a, b;
-      tri_rc(e, a, b);
-      const int r = a + 1, c = b;
-      LdRj[r * n + c] = (TZ)(Dp_[r * ldD + c] * rv[r]);
-      if (!Ms) LdMj[r * n + c] = (TZ)(Dp_[r * ldD + c] * rv[c]);
-    }
-    if (mixed)
-      for (int e = G.tid; e < n; e += G.nt) d.Lrif[(size_t)j * n + e] = (float)rv[e];
-    for (int e = G.tid; e < n; e += G.nt) d.Lri[(size_t)j * n + e] = rv[e];
+    cx.store_pivot(j, Dp_, rv, Ms, G);
   };
-  // panel rows [0, rows) of Lp for stage j: rows outside [r0, r1) are zero
-  // (a consumer writes the W-rows of a split or paired segment)
-  auto store_panel = [&](int j, int r0, int r1, int rows, Grp G) {
-    double* Pd = d.Lp + (size_t)j * R * n;
-    float* Pf = mixed ? d.Lpf + (size_t)j * R * n : nullptr;
-    for (int e = G.tid; e < rows * n; e += G.nt) {
-      const int r = e / n, c = e - r * n;
-      const TZ v = (r >= r0 && r < r1) ? Z[r * ldZ + c] : TZ(0);
-      Pd[e] = (double)v;
-      if (mixed) Pf[e] = (float)v;
-    }
-  };
+  auto store_panel = [&](int j, int r0, int r1, int rows, Grp G) { cx.store_panel(j, r0, r1, rows, G); };
   // hand the trsm operand (strict lower triangle of Msrc, ld ldD), its
   // 1/diag and panel rows [r0, r1) of stage i to the consumer CTA of a pair
   auto push_stage = [&](int i, const TZ* Msrc, const TZ* rsrc, int r0, int r1, Grp G) {
@@ -630,23 +708,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
       st_cluster(aZ + off * (unsigned)sizeof(TZ), Z[off]);
     }
   };
-  // rotate the panel after the Schur update of stage i (group G): the
-  // updated blocks become stage i+1's inputs, the next ones are loaded
-  auto rotate = [&](int i, int j, bool withW, Grp G) {
-    if (m) copy_blk(Z + oG * ldZ, ldZ, T + oG * ldT, ldT, m, n, G);          // G_{i+1}
-    if (withW) copy_blk(Z + oW * ldZ, ldZ, T + oW * ldT, ldT, n, n, G);      // W_{i+1}
-    if ((i + 1 < g.len - 1) || g.hasF) load_blk(Z, ldZ, Dp(Ein, j + 1), none, n, n, false, G);
-    gsync(G);
-    if (withW) load_blk(T + oW * ldT, ldT, none, none, n, n, false, G);     // W_{i+2} <- 0
-    if (i + 2 < g.len) {
-      load_blk(T, ldT, Dp(Din, j + 2), Dp(D2, j + 2), n, n, false, G);
-      if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, j + 2), Gp(G2, j + 2), m, n, false, G);
-    } else {
-      load_blk(T, ldT, none, none, n, n, false, G);
-      if (m) load_blk(T + oG * ldT, ldT, none, none, m, n, false, G);
-    }
-    gsync(G);
-  };
+  auto rotate = [&](int i, int j, bool withW, Grp G) { cx.rotate(i, j, withW, G); };
 
   if (producer && mode == kSplit) {
     // FP64, E- and G-rows on warps 0-3 (the consumer warps run the W-rows)
@@ -755,7 +817,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
         if (mode == kSplit) group_arrive(kBarFreeZ, kFactorThreads);
         copy_blk(Z + oW * ldZ, ldZ, T + oW * ldT, ldT, n, n, C);               // W_{i+1}
         gsync(C);
-        load_blk(T + oW * ldT, ldT, none, none, n, n, false, C);               // W_{i+2} <- 0
+        load_blk(T + oW * ldT, ldT, (const double*)nullptr, (const double*)nullptr, n, n, false, C);  // W_{i+2} <- 0
         gsync(C);
       }
     }
@@ -763,17 +825,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
   __syncthreads();
 
   if (!d.is_top) {
-    const int k = tk.seg;
-    if (eg && g.hasF) {
-      store_blk(d.DB + (size_t)k * nn, T, ldT, n, n, false, true);             // -F^ F^T
-      if (m) store_blk(d.GB + (size_t)k * mn, T + oG * ldT, ldT, m, n, false, false);  // -G^ F^T
-    }
-    if (wr) {
-      store_blk(d.DA + (size_t)(k - 1) * nn, T + oW * ldT + oW, ldT, n, n, false, true);  // A~_k
-      if (m) store_blk(d.GA + (size_t)(k - 1) * mn, T + oW * ldT + oG, ldT, n, m, true, false);  // Q~_k
-      if (g.hasF) store_blk(d.EN + (size_t)(k - 1) * nn, T + oW * ldT, ldT, n, n, true, false);  // H~_k
-    }
-    if (eg && m) store_blk(d.Rpart + (size_t)k * m * m, T + oG * ldT + oG, ldT, m, m, false, true);
+    cx.store_slots(tk.seg, eg, wr, cta_grp());
   } else if (m) {
     // corner: R-hat = chol(R + sum_k R~_k over every level), in a fixed order:
     // the lower levels' partials are summed by the pair's idle CTA while this
@@ -783,10 +835,10 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
     auto part = [&](int p, int o) { return d.Rpart_all[(size_t)p * m * m + o]; };
     if (mode == kPair && rank == 1) {
       const unsigned aP = cluster_addr(Psum, 0);
-      sum_partials(m * m, d.nRpart_all, part,
+      sum_partials(cta_grp(), m * m, d.nRpart_all, part,
                    [&](int o, double v) { st_cluster(aP + o * (unsigned)sizeof(double), v); });
     } else if (mode != kPair) {
-      sum_partials(m * m, d.nRpart_all, part, [&](int o, double v) { Psum[o] = v; });
+      sum_partials(cta_grp(), m * m, d.nRpart_all, part, [&](int o, double v) { Psum[o] = v; });
     }
     if (mode == kPair) {
       cluster_arrive();
@@ -819,6 +871,147 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Small blocks (n <= kWarpMaxN): one warp per segment task, every step of a
+// stage warp-synchronous, several tasks per CTA with a shared-memory slice
+// each. The CTA kernel's role split needs blocks large enough to keep eight
+// warps busy; at n = 6 a stage is a few hundred FMAs, and what counts is how
+// many independent stage chains an SM interleaves. The operations per
+// element are those of the CTA kernel, in the same order.
+// ---------------------------------------------------------------------------
+
+// Pairs (i, k) with 1 <= k <= i < n ordered by k descending (packed
+// i << 16 | k): the updates by column j are the prefix of length
+// (n-1-j)(n-j)/2.
+__device__ void pair_table_w(int* tab, int n, int lane) {
+  const int np = (n - 1) * n / 2;
+  for (int e = lane; e < np; e += 32) {
+    int a, b;
+    tri_rc(e, a, b);
+    const int k = n - 1 - a;
+    tab[e] = (k + b) << 16 | k;
+  }
+  __syncwarp();
+}
+
+// In-place lower Cholesky of A (n x n, FP64, n <= kWarpMaxN) by one warp,
+// right-looking: pivot by lane 0, column scaled by the lanes, then the
+// trailing update by column j over the pair table. Returns the first bad
+// column + 1 (0 if every pivot was positive) in lane 0.
+__device__ int potrf_w(double* A, int ld, int n, double* rinv, const int* tab, int lane) {
+  int bad = 0;
+  for (int j = 0; j < n; ++j) {
+    double r = 0.0;
+    if (lane == 0) {
+      const double dj = A[j * ld + j];
+      if (not_positive(dj) && bad == 0) bad = j + 1;
+      r = pivot_rsqrt(dj);
+      A[j * ld + j] = dj * r;
+      rinv[j] = r;
+    }
+    r = __shfl_sync(0xffffffffu, r, 0);
+    for (int i = j + 1 + lane; i < n; i += 32) A[i * ld + j] *= r;
+    __syncwarp();
+    const int cnt = (n - 1 - j) * (n - j) / 2;
+    for (int e = lane; e < cnt; e += 32) {
+      const int p = tab[e], i = p >> 16, k = p & 0xffff;
+      A[i * ld + k] = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
+    }
+    __syncwarp();
+  }
+  return bad;
+}
+
+// Z[r0:r1) <- Z[r0:r1) L^{-T} by one warp, one panel row per lane: the
+// division-free substitution of trsm_panel, in the same order per element.
+template <typename TZ>
+__device__ void trsm_w(TZ* Z, int ldz, int r0, int r1, const TZ* M, int ldm, int n, const TZ* rinv, int lane) {
+  for (int r = r0 + lane; r < r1; r += 32) {
+    TZ* z = Z + r * ldz;
+    for (int j = 0; j < n - 1; ++j) {
+      const TZ zj = z[j];
+      for (int c = j + 1; c < n; ++c) z[c] = fma(-zj, M[c * ldm + j], z[c]);
+    }
+    for (int c = 0; c < n; ++c) z[c] *= rinv[c];
+  }
+  __syncwarp();
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(256) k_factor_w(const LevelDesc* __restrict__ descs,
+                                                  const Task* __restrict__ tasks, int ntasks,
+                                                  const double* __restrict__ uD, const double* __restrict__ uE,
+                                                  const double* __restrict__ uG, const double* __restrict__ uR,
+                                                  Info* info, int slice) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int t = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (t >= ntasks) return;  // whole warp
+  const Task tk = tasks[t];
+  const LevelDesc& d = descs[tk.desc];
+  unsigned char* sm = smraw + (size_t)wid * slice;
+  const FacLayout lay = fac_layout_w(d.n, d.m, (int)sizeof(TZ));
+  const FacCtx<TZ> cx(d, tk.seg, sm, lay, uD, uE, uG);
+  const int n = cx.n, m = cx.m, R = cx.R, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG;
+  const SegGeom g = cx.g;
+  const Grp W{lane, 32, -1};
+  for (int e = lane; e < R * ldT; e += 32) cx.T[e] = 0.0;
+  pair_table_w(cx.tab, n, lane);
+  cx.load_first(true, g.hasW, W);
+  __syncwarp();
+  const int pr1 = n + m + (g.hasW ? n : 0);
+  for (int i = 0; i < g.len; ++i) {
+    const int j = g.f + i;
+    const bool eRows = (i < g.len - 1) || g.hasF;
+    const int r0 = eRows ? 0 : n;
+    const int bad = potrf_w(cx.Dfac, ldD, n, cx.rinv, cx.tab, lane);
+    if (lane == 0 && bad) record_breakdown(info, d.sys, d.nat[j], d.level);
+    panel_operand(cx.M, cx.Dfac, ldD, n, cx.rinv, W);
+    for (int e = lane; e < n; e += 32) cx.rinvZ[e] = (TZ)cx.rinv[e];
+    __syncwarp();
+    trsm_w(cx.Z, ldZ, r0, pr1, cx.M, ldD, n, cx.rinvZ, lane);
+    cx.store_pivot(j, cx.Dfac, cx.rinv, cx.M, W);
+    cx.store_panel(j, r0, pr1, R, W);
+    syrk_trap(cx.T, ldT, cx.Z, cx.Z, 0, ldZ, r0, pr1, r0, n, W);
+    if (i + 1 < g.len) {
+      copy_blk(cx.Dfac, ldD, cx.T, ldT, n, n, W);                                  // D_{i+1}
+      __syncwarp();
+      cx.rotate(i, j, g.hasW, W);
+    }
+  }
+  __syncwarp();
+  if (!d.is_top) {
+    cx.store_slots(tk.seg, true, g.hasW, W);
+  } else if (m) {
+    // corner: R-hat = chol((R + sum of the lower levels' partials) + this level's)
+    double* Rs = cx.Dfac;  // reuse (n >= m is not needed: the slice has room for q x q)
+    double* Psum = (double*)(sm + lay.oCorner);
+    const int ldR = odd(m);
+    for (int o = lane; o < m * m; o += 32) {
+      double a0 = 0.0, a1 = 0.0;
+      int p = 0;
+      for (; p + 1 < d.nRpart_all; p += 2) {
+        a0 += d.Rpart_all[(size_t)p * m * m + o];
+        a1 += d.Rpart_all[(size_t)(p + 1) * m * m + o];
+      }
+      if (p < d.nRpart_all) a0 += d.Rpart_all[(size_t)p * m * m + o];
+      Psum[o] = a0 + a1;
+    }
+    __syncwarp();
+    const double* Ru = uR + d.offR;
+    for (int e = lane; e < m * m; e += 32) {
+      const int r = e / m, c = e - r * m;
+      Rs[r * ldR + c] = (Ru[e] + Psum[e]) + cx.T[(oG + r) * ldT + oG + c];
+    }
+    pair_table_w(cx.tab, m, lane);
+    const int bad = potrf_w(Rs, ldR, m, cx.rinv, cx.tab, lane);
+    if (lane == 0 && bad) record_breakdown(info, d.sys, d.Nnat, d.level);
+    store_blk(d.Rhat, Rs, ldR, m, m, false, true, W);
+    for (int e = lane; e < m; e += 32) d.Rri[e] = cx.rinv[e];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Solve. TS = double: FP64 factor and vectors. TS = float: the FP32 factor
 // copy of a mixed level and FP32 vectors (the correction solves of iterative
@@ -842,14 +1035,14 @@ __device__ __forceinline__ VecView level_vec(const LevelDesc& d, double* b, int 
 // dst (rows x nr, smem ld) <- src rows (global, stride lds) (+ src2, stride kRhsChunk)
 template <typename TS>
 __device__ void load_vec(TS* dst, int ldd, const double* src, int lds, const double* src2, int rows,
-                         int nr) {
+                         int nr, Grp G) {
   if (src2) {
-    for (int e = threadIdx.x; e < rows * nr; e += blockDim.x) {
+    for (int e = G.tid; e < rows * nr; e += G.nt) {
       const int r = e / nr, c = e - r * nr;
       dst[r * ldd + c] = (TS)(src[(size_t)r * lds + c] + src2[(size_t)r * kRhsChunk + c]);
     }
   } else {
-    for (int e = threadIdx.x; e < rows * nr; e += blockDim.x) {
+    for (int e = G.tid; e < rows * nr; e += G.nt) {
       const int r = e / nr, c = e - r * nr;
       dst[r * ldd + c] = (TS)src[(size_t)r * lds + c];
     }
@@ -857,8 +1050,8 @@ __device__ void load_vec(TS* dst, int ldd, const double* src, int lds, const dou
 }
 
 template <typename TS>
-__device__ void store_vec(double* dst, int ldd, const TS* src, int lds, int rows, int nr) {
-  for (int e = threadIdx.x; e < rows * nr; e += blockDim.x) {
+__device__ void store_vec(double* dst, int ldd, const TS* src, int lds, int rows, int nr, Grp G) {
+  for (int e = G.tid; e < rows * nr; e += G.nt) {
     const int r = e / nr, c = e - r * nr;
     dst[(size_t)r * ldd + c] = (double)src[r * lds + c];
   }
@@ -885,11 +1078,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // and i + 32 of a column live in lane i. Forward uses M (columns of L divided
 // by their diagonal): u_i -= M_ij u_j, x = u * rinv. Backward uses MR (rows
 // of L divided by their diagonal): u_i -= MR_ji u_j for i < j, x = u * rinv.
-// Ends with a block barrier.
+// The group's warps take the columns in turn; ends with the group's barrier.
 template <typename TS>
 __device__ void trsv_warp(TS* t, int ldt, const TS* M, int ldl, const TS* rinv, int n, int nr,
-                          bool backward) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                          bool backward, Grp G) {
+  const int lane = G.tid & 31, warp = G.tid >> 5, nw = G.nt >> 5;
   const int i0 = lane, i1 = lane + 32;
   for (int c = warp; c < nr; c += nw) {
     TS u0 = i0 < n ? t[i0 * ldt + c] : TS(0);
@@ -951,13 +1144,19 @@ __device__ void trsv_warp(TS* t, int ldt, const TS* M, int ldl, const TS* rinv, 
     }
     if (i0 < n) t[i0 * ldt + c] = u0 * rinv[i0];
   }
-  __syncthreads();
+  gsync(G);
 }
 
+// Shared-memory view of a substitution task: double-buffered factor blocks
+// (selected by value, not by a run-time array index, which would put the
+// pointers in local memory), the panel vector V and the stage vector t.
 template <typename TS>
 struct SolveSmem {
-  TS *L[2], *rinv[2], *Z[2], *V, *t;
+  TS *L0, *L1, *ri0, *ri1, *Z0, *Z1, *V, *t;
   int ldL, ldZ, ldV;
+  __device__ TS* L(int q) const { return q ? L1 : L0; }
+  __device__ TS* rinv(int q) const { return q ? ri1 : ri0; }
+  __device__ TS* Z(int q) const { return q ? Z1 : Z0; }
 };
 
 template <typename TS>
@@ -967,11 +1166,12 @@ __device__ __forceinline__ SolveSmem<TS> solve_smem(unsigned char* sm, int n, in
   S.ldL = odd(n);
   S.ldZ = L.ldZ;
   S.ldV = L.ldV;
-  for (int q = 0; q < 2; ++q) {
-    S.L[q] = (TS*)(sm + L.oL[q]);
-    S.rinv[q] = (TS*)(sm + L.oRinv[q]);
-    S.Z[q] = (TS*)(sm + L.oZ[q]);
-  }
+  S.L0 = (TS*)(sm + L.oL[0]);
+  S.L1 = (TS*)(sm + L.oL[1]);
+  S.ri0 = (TS*)(sm + L.oRinv[0]);
+  S.ri1 = (TS*)(sm + L.oRinv[1]);
+  S.Z0 = (TS*)(sm + L.oZ[0]);
+  S.Z1 = (TS*)(sm + L.oZ[1]);
   S.V = (TS*)(sm + L.oV);
   S.t = (TS*)(sm + L.oT);
   return S;
@@ -993,19 +1193,19 @@ __device__ __forceinline__ FactorView<float> factor_view(const LevelDesc& d, flo
 // diagonal, 1/diag, panel rows [r0, r1)).
 template <typename TS>
 __device__ void prefetch_stage_factor(const SolveSmem<TS>& S, int q, const LevelDesc& d, int j, int r0,
-                                      int r1, bool backward) {
+                                      int r1, bool backward, Grp G) {
   const int n = d.n, R = 2 * n + d.m;
   const FactorView<TS> F = factor_view(d, TS(0));
   const TS* Lg = (backward ? F.MR : F.M) + (size_t)j * n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+  for (int e = G.tid; e < n * n; e += G.nt) {
     const int r = e / n, c = e - r * n;
-    cp_async_elem(S.L[q] + r * S.ldL + c, Lg + e);
+    cp_async_elem(S.L(q) + r * S.ldL + c, Lg + e);
   }
-  for (int e = threadIdx.x; e < n; e += blockDim.x) cp_async_elem(S.rinv[q] + e, F.ri + (size_t)j * n + e);
+  for (int e = G.tid; e < n; e += G.nt) cp_async_elem(S.rinv(q) + e, F.ri + (size_t)j * n + e);
   const TS* P = F.P + (size_t)j * R * n;
-  for (int e = threadIdx.x + r0 * n; e < r1 * n; e += blockDim.x) {
+  for (int e = G.tid + r0 * n; e < r1 * n; e += G.nt) {
     const int r = e / n, c = e - r * n;
-    cp_async_elem(S.Z[q] + r * S.ldZ + c, P + e);
+    cp_async_elem(S.Z(q) + r * S.ldZ + c, P + e);
   }
   cp_async_commit();
 }
@@ -1022,28 +1222,28 @@ __device__ __forceinline__ void stage_rows(const SegGeom& g, int i, int n, int m
 // blocks of the next stage stream in while the current one is solved.
 template <typename TS>
 __device__ void backward_segment(const SolveSmem<TS>& S, const LevelDesc& d, const SegGeom& g,
-                                 double* b, int ldb, int nr) {
+                                 double* b, int ldb, int nr, Grp G) {
   const int n = d.n, m = d.m;
   int r0, r1;
   stage_rows(g, g.len - 1, n, m, r0, r1);
-  prefetch_stage_factor(S, 0, d, g.f + g.len - 1, r0, r1, true);
+  prefetch_stage_factor(S, 0, d, g.f + g.len - 1, r0, r1, true, G);
   for (int i = g.len - 1; i >= 0; --i) {
     const int j = g.f + i, q = (g.len - 1 - i) & 1;
     stage_rows(g, i, n, m, r0, r1);
     const VecView y = level_vec(d, b, ldb, j);
     cp_async_wait_all();
-    __syncthreads();
+    gsync(G);
     if (i > 0) {
       int p0, p1;
       stage_rows(g, i - 1, n, m, p0, p1);
-      prefetch_stage_factor(S, q ^ 1, d, j - 1, p0, p1, true);
+      prefetch_stage_factor(S, q ^ 1, d, j - 1, p0, p1, true, G);
     }
-    const TS* Z = S.Z[q];
+    const TS* Z = S.Z(q);
     // t = y_j - Z^T v over the active panel rows: four lanes per output (each
     // a quarter of the rows, two partial sums), shuffle-reduced
     {
       const int outs = n * nr, span = (outs * 4 + 31) & ~31, rows = r1 - r0;
-      for (int e = threadIdx.x; e < span; e += blockDim.x) {
+      for (int e = G.tid; e < span; e += G.nt) {
         const int o = e >> 2, qq = e & 3;
         const bool act = o < outs;
         const int oo = act ? o : 0;
@@ -1064,26 +1264,23 @@ __device__ void backward_segment(const SolveSmem<TS>& S, const LevelDesc& d, con
         if (act && qq == 0) S.t[c2 * S.ldV + c] = (TS)y.p[(size_t)c2 * y.ld + c] - a;
       }
     }
-    __syncthreads();
-    trsv_warp(S.t, S.ldV, S.L[q], S.ldL, S.rinv[q], n, nr, true);
-    store_vec(y.p, y.ld, S.t, S.ldV, n, nr);
-    for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
+    gsync(G);
+    trsv_warp(S.t, S.ldV, S.L(q), S.ldL, S.rinv(q), n, nr, true, G);
+    store_vec(y.p, y.ld, S.t, S.ldV, n, nr, G);
+    for (int e = G.tid; e < n * nr; e += G.nt) {
       const int r = e / nr, c = e - r * nr;
       S.V[r * S.ldV + c] = S.t[r * S.ldV + c];
     }
   }
-  __syncthreads();
+  gsync(G);
 }
 
 // Forward substitution (Algorithm 2) for one segment; the top level (P = 1)
 // also solves the corner and runs its own backward sweep (Algorithm 3,
 // sequential phase). `skip`: per-system flags; a set flag returns at once.
 template <typename TS>
-__global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __restrict__ descs,
-                                                           const Task* __restrict__ tasks, double* b,
-                                                           int ldb, int nr, const int* skip) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const Task tk = tasks[blockIdx.x];
+__device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs, double* b, int ldb, int nr,
+                             const int* skip, unsigned char* smraw, Grp G) {
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
   const int n = d.n, m = d.m;
@@ -1094,18 +1291,18 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
   auto rhs = [&](int j, TS* dst) {  // this level's right-hand side of stage j
     if (d.level == 1) {
       const VecView v = level_vec(d, b, ldb, j);
-      load_vec(dst, S.ldV, v.p, v.ld, (const double*)nullptr, n, nr);
+      load_vec(dst, S.ldV, v.p, v.ld, (const double*)nullptr, n, nr, G);
     } else {
       load_vec(dst, S.ldV, d.RA + (size_t)j * n * kRhsChunk, kRhsChunk,
-               d.RB + (size_t)j * n * kRhsChunk, n, nr);
+               d.RB + (size_t)j * n * kRhsChunk, n, nr, G);
     }
   };
   int r0, r1;
   stage_rows(g, 0, n, m, r0, r1);
-  prefetch_stage_factor(S, 0, d, g.f, r0, r1, false);
+  prefetch_stage_factor(S, 0, d, g.f, r0, r1, false, G);
   // V_G <- 0, V_W <- rhs of the separator, t <- rhs of the first stage
-  for (int e = threadIdx.x; e < (2 * n + m) * S.ldV; e += blockDim.x) S.V[e] = TS(0);
-  __syncthreads();
+  for (int e = G.tid; e < (2 * n + m) * S.ldV; e += G.nt) S.V[e] = TS(0);
+  gsync(G);
   if (g.hasW) rhs(g.f - 1, S.V + oW * S.ldV);
   rhs(g.f, S.t);
   for (int i = 0; i < g.len; ++i) {
@@ -1113,21 +1310,21 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
     stage_rows(g, i, n, m, r0, r1);
     if (i + 1 < g.len) rhs(j + 1, S.V);  // V_E <- next stage's rhs (else 0: F-hat term)
     cp_async_wait_all();
-    __syncthreads();
+    gsync(G);
     if (i + 1 < g.len) {
       int p0, p1;
       stage_rows(g, i + 1, n, m, p0, p1);
-      prefetch_stage_factor(S, q ^ 1, d, j + 1, p0, p1, false);
+      prefetch_stage_factor(S, q ^ 1, d, j + 1, p0, p1, false, G);
     }
-    trsv_warp(S.t, S.ldV, S.L[q], S.ldL, S.rinv[q], n, nr, false);
+    trsv_warp(S.t, S.ldV, S.L(q), S.ldL, S.rinv(q), n, nr, false, G);
     const VecView y = level_vec(d, b, ldb, j);
-    store_vec(y.p, y.ld, S.t, S.ldV, n, nr);
+    store_vec(y.p, y.ld, S.t, S.ldV, n, nr, G);
     // [V_E; V_G; V_W] -= Z y over the active panel rows: four lanes per output
     // (each a quarter of the dot product, two partial sums), shuffle-reduced
-    const TS* Z = S.Z[q];
+    const TS* Z = S.Z(q);
     {
       const int outs = (r1 - r0) * nr, span = (outs * 4 + 31) & ~31;
-      for (int e = threadIdx.x; e < span; e += blockDim.x) {
+      for (int e = G.tid; e < span; e += G.nt) {
         const int o = e >> 2, qq = e & 3;
         const bool act = o < outs;
         const int oo = act ? o : 0;
@@ -1148,21 +1345,21 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
         if (act && qq == 0) S.V[r * S.ldV + c] -= a;
       }
     }
-    __syncthreads();
+    gsync(G);
     if (i + 1 < g.len) {
-      for (int e = threadIdx.x; e < n * nr; e += blockDim.x) {
+      for (int e = G.tid; e < n * nr; e += G.nt) {
         const int r = e / nr, c = e - r * nr;
         S.t[r * S.ldV + c] = S.V[r * S.ldV + c];
         S.V[r * S.ldV + c] = TS(0);
       }
-      __syncthreads();  // V_E is reloaded at the top of the next stage
+      gsync(G);  // V_E is reloaded at the top of the next stage
     }
   }
-  __syncthreads();
+  gsync(G);
   if (!d.is_top) {
-    if (g.hasF) store_vec(d.YB + (size_t)k * n * kRhsChunk, kRhsChunk, S.V, S.ldV, n, nr);
-    if (g.hasW) store_vec(d.YA + (size_t)(k - 1) * n * kRhsChunk, kRhsChunk, S.V + oW * S.ldV, S.ldV, n, nr);
-    if (m) store_vec(d.ygpart + (size_t)k * m * kRhsChunk, kRhsChunk, S.V + oG * S.ldV, S.ldV, m, nr);
+    if (g.hasF) store_vec(d.YB + (size_t)k * n * kRhsChunk, kRhsChunk, S.V, S.ldV, n, nr, G);
+    if (g.hasW) store_vec(d.YA + (size_t)(k - 1) * n * kRhsChunk, kRhsChunk, S.V + oW * S.ldV, S.ldV, n, nr, G);
+    if (m) store_vec(d.ygpart + (size_t)k * m * kRhsChunk, kRhsChunk, S.V + oG * S.ldV, S.ldV, m, nr, G);
     return;
   }
   // top level: corner y_g = R-hat^{-1} (r_g + sum of every yg partial + own),
@@ -1172,42 +1369,39 @@ __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __re
     TS* gv = S.t;
     const int ldR = odd(m);
     sum_partials(
-        m * nr, d.nyg_all,
+        G, m * nr, d.nyg_all,
         [&](int p, int o) { return d.yg_all[((size_t)p * m + o / nr) * kRhsChunk + o % nr]; },
         [&](int o, double v) {
           const int r = o / nr, c = o - r * nr;
           gv[r * S.ldV + c] = (TS)((bg[(size_t)r * ldb + c] + v) + (double)S.V[(oG + r) * S.ldV + c]);
         });
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {  // R-hat: columns scaled, rows scaled
+    for (int e = G.tid; e < m * m; e += G.nt) {  // R-hat: columns scaled, rows scaled
       const int r = e / m, c = e - r * m;
-      S.L[0][r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[c]);
-      S.L[1][r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[r]);
+      S.L(0)[r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[c]);
+      S.L(1)[r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[r]);
     }
-    for (int e = threadIdx.x; e < m; e += blockDim.x) S.rinv[0][e] = (TS)d.Rri[e];
-    __syncthreads();
-    trsv_warp(gv, S.ldV, S.L[0], ldR, S.rinv[0], m, nr, false);
-    trsv_warp(gv, S.ldV, S.L[1], ldR, S.rinv[0], m, nr, true);
-    store_vec(bg, ldb, gv, S.ldV, m, nr);
+    for (int e = G.tid; e < m; e += G.nt) S.rinv(0)[e] = (TS)d.Rri[e];
+    gsync(G);
+    trsv_warp(gv, S.ldV, S.L(0), ldR, S.rinv(0), m, nr, false, G);
+    trsv_warp(gv, S.ldV, S.L(1), ldR, S.rinv(0), m, nr, true, G);
+    store_vec(bg, ldb, gv, S.ldV, m, nr, G);
   }
   // V <- [0; x_g; -] for the backward sweep of the top level
-  for (int e = threadIdx.x; e < (2 * n + m) * S.ldV; e += blockDim.x) {
+  for (int e = G.tid; e < (2 * n + m) * S.ldV; e += G.nt) {
     const int r = e / S.ldV;
     if (r < oG || r >= oW) S.V[e] = TS(0);
     else S.V[e] = S.t[(r - oG) * S.ldV + (e - r * S.ldV)];
   }
-  __syncthreads();
-  backward_segment(S, d, g, b, ldb, nr);
+  gsync(G);
+  backward_segment(S, d, g, b, ldb, nr, G);
 }
 
 // Backward substitution (Algorithm 3, parallel phase) for one segment below
 // the top level: needs x_g (already in b), the separator solutions of the
 // next level (x at s_k and s_{k+1}), and this level's y.
 template <typename TS>
-__global__ void __launch_bounds__(kSolveThreads) k_backward(const LevelDesc* __restrict__ descs,
-                                                            const Task* __restrict__ tasks, double* b,
-                                                            int ldb, int nr, const int* skip) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const Task tk = tasks[blockIdx.x];
+__device__ void backward_task(const Task tk, const LevelDesc* __restrict__ descs, double* b, int ldb, int nr,
+                              const int* skip, unsigned char* smraw, Grp G) {
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
   const int n = d.n, m = d.m;
@@ -1216,19 +1410,57 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(const LevelDesc* __r
   const SegGeom g = seg_geom(d, tk.seg);
   const int k = tk.seg;
   const double* none = nullptr;
-  for (int e = threadIdx.x; e < (2 * n + m) * S.ldV; e += blockDim.x) S.V[e] = TS(0);
-  __syncthreads();
-  if (g.hasF) load_vec(S.V, S.ldV, d.Xnext + (size_t)k * n * kRhsChunk, kRhsChunk, none, n, nr);
-  if (m) load_vec(S.V + oG * S.ldV, S.ldV, b + (size_t)d.rowG * ldb, ldb, none, m, nr);
+  for (int e = G.tid; e < (2 * n + m) * S.ldV; e += G.nt) S.V[e] = TS(0);
+  gsync(G);
+  if (g.hasF) load_vec(S.V, S.ldV, d.Xnext + (size_t)k * n * kRhsChunk, kRhsChunk, none, n, nr, G);
+  if (m) load_vec(S.V + oG * S.ldV, S.ldV, b + (size_t)d.rowG * ldb, ldb, none, m, nr, G);
   if (g.hasW) {
     load_vec(S.V + oW * S.ldV, S.ldV, d.Xnext + (size_t)(k - 1) * n * kRhsChunk, kRhsChunk, none, n,
-             nr);
-    __syncthreads();
+             nr, G);
+    gsync(G);
     const VecView xs = level_vec(d, b, ldb, g.f - 1);  // this level's copy of x at s_k
-    store_vec(xs.p, xs.ld, S.V + oW * S.ldV, S.ldV, n, nr);
+    store_vec(xs.p, xs.ld, S.V + oW * S.ldV, S.ldV, n, nr, G);
   }
-  __syncthreads();
-  backward_segment(S, d, g, b, ldb, nr);
+  gsync(G);
+  backward_segment(S, d, g, b, ldb, nr, G);
+}
+
+
+// One CTA per task (blocks above kWarpMaxN), or one warp per task with a
+// shared-memory slice each (small blocks; `slice` bytes per warp).
+template <typename TS>
+__global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __restrict__ descs,
+                                                           const Task* __restrict__ tasks, double* b,
+                                                           int ldb, int nr, const int* skip) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  forward_task<TS>(tasks[blockIdx.x], descs, b, ldb, nr, skip, smraw, cta_grp());
+}
+template <typename TS>
+__global__ void __launch_bounds__(kSolveThreads) k_backward(const LevelDesc* __restrict__ descs,
+                                                            const Task* __restrict__ tasks, double* b,
+                                                            int ldb, int nr, const int* skip) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  backward_task<TS>(tasks[blockIdx.x], descs, b, ldb, nr, skip, smraw, cta_grp());
+}
+template <typename TS>
+__global__ void __launch_bounds__(256) k_forward_w(const LevelDesc* __restrict__ descs,
+                                                   const Task* __restrict__ tasks, int ntasks, double* b,
+                                                   int ldb, int nr, const int* skip, int slice) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int wid = threadIdx.x >> 5, t = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (t >= ntasks) return;  // whole warp
+  forward_task<TS>(tasks[t], descs, b, ldb, nr, skip, smraw + (size_t)wid * slice,
+                   Grp{(int)(threadIdx.x & 31), 32, -1});
+}
+template <typename TS>
+__global__ void __launch_bounds__(256) k_backward_w(const LevelDesc* __restrict__ descs,
+                                                    const Task* __restrict__ tasks, int ntasks, double* b,
+                                                    int ldb, int nr, const int* skip, int slice) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int wid = threadIdx.x >> 5, t = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (t >= ntasks) return;  // whole warp
+  backward_task<TS>(tasks[t], descs, b, ldb, nr, skip, smraw + (size_t)wid * slice,
+                    Grp{(int)(threadIdx.x & 31), 32, -1});
 }
 
 // ---------------------------------------------------------------------------
@@ -1260,8 +1492,9 @@ __global__ void k_axpy(const LevelDesc* __restrict__ descs, const ResTask* __res
 }
 
 // FP64 residual c = b - Psi x (blocks of Eq. (3)) over the stage rows of one
-// residual task (kResChunk consecutive stages of one system) per warp: lane
-// i owns row i of the stage (and row i + 32 when n > 32) and forms
+// residual task (kResChunk consecutive stages of one system) per warp: a lane
+// owns one row of a stage (row i and i + 32 when n > 32; for n <= 16 the warp
+// takes floor(32/n) stages at a time, lane = (stage, row)) and forms
 //   (E_{j-1} x_{j-1} + D_j x_j + E_j^T x_{j+1} + G_j^T x_g)_i
 // from the blocks in global memory (lower triangle of D_j by symmetry), with
 // x_k broadcast by shuffles, so every FP64 instruction has a lane per row
@@ -1292,72 +1525,64 @@ __global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ 
   const double* E = uE ? uE + d.offE : nullptr;
   const double* G = m ? uG + d.offG : nullptr;
   double* part = parts + (size_t)t * kResPartDoubles;
-  const int i0 = lane, i1 = lane + 32;
-  const bool r0ok = i0 < n, r1ok = i1 < n, two = n > 32;  // `two` is warp-uniform
-  const int a0 = r0ok ? i0 : 0, a1 = r1ok ? i1 : 0;     // clamped rows for the loads
+  const bool packed = n <= 16;            // several stages per pass
+  const int spw = packed ? 32 / n : 1;    // stages per pass
+  const int sj = packed ? lane / n : 0;   // this lane's stage within a pass
+  const int i0 = packed ? lane - sj * n : lane, i1 = lane + 32;
+  const bool lane_ok = packed ? sj < spw : lane < n;
+  const bool two = n > 32;  // warp-uniform: a second row per lane
+  const int src0 = packed ? sj * n : 0;  // lane holding row 0 of this lane's stage
   double mr = 0.0, mx = 0.0, mb = 0.0, mrow = 0.0;
-  double gab = 0.0;  // |G| sum of g row `lane` (lane < m)
   auto xat = [&](long long row, int col) { return x[(size_t)row * ldx + col]; };
   for (int col = 0; col < nr; ++col) {
-    double xg_l = lane < m ? xat(d.rowG + lane, col) : 0.0;  // x_g, lane q holds row q
+    const double xg_l = lane < m ? xat(d.rowG + lane, col) : 0.0;  // x_g, lane q holds row q
     double gacc[kMaxM];  // this lane's terms of sum_j G_j x_j per g row
 #pragma unroll
     for (int q = 0; q < kMaxM; ++q) gacc[q] = 0.0;
-    for (int j = j0; j < j1; ++j) {
-      const long long rb = d.offB + (long long)j * n;
-      const double* Dj = D + (size_t)j * nn;
-      const double* Ep = (j > 0 && E) ? E + (size_t)(j - 1) * nn : nullptr;
-      const double* En = (j < N - 1 && E) ? E + (size_t)j * nn : nullptr;
-      const double xc0 = r0ok ? xat(rb + i0, col) : 0.0, xc1 = r1ok ? xat(rb + i1, col) : 0.0;
-      const double xp0 = (Ep && r0ok) ? xat(rb - n + i0, col) : 0.0, xp1 = (Ep && r1ok) ? xat(rb - n + i1, col) : 0.0;
-      const double xn0 = (En && r0ok) ? xat(rb + n + i0, col) : 0.0, xn1 = (En && r1ok) ? xat(rb + n + i1, col) : 0.0;
+    for (int jb = j0; jb < j1; jb += spw) {
+      const int j = jb + sj;
+      const bool ok0 = lane_ok && j < j1, ok1 = two && j < j1 && i1 < n;
+      const int jc = ok0 ? j : jb;                 // a valid stage for the addresses
+      const int a0 = ok0 ? i0 : 0, a1 = ok1 ? i1 : 0;
+      const long long rb = d.offB + (long long)jc * n;
+      const double* Dj = D + (size_t)jc * nn;
+      const bool hp = E && jc > 0, hn = E && jc < N - 1;
+      const double* Ep = hp ? E + (size_t)(jc - 1) * nn : D;
+      const double* En = hn ? E + (size_t)jc * nn : D;
+      const double xc0 = ok0 ? xat(rb + i0, col) : 0.0, xc1 = ok1 ? xat(rb + i1, col) : 0.0;
+      const double xp0 = (ok0 && hp) ? xat(rb - n + i0, col) : 0.0, xp1 = (ok1 && hp) ? xat(rb - n + i1, col) : 0.0;
+      const double xn0 = (ok0 && hn) ? xat(rb + n + i0, col) : 0.0, xn1 = (ok1 && hn) ? xat(rb + n + i1, col) : 0.0;
       double acc0 = 0.0, acc1 = 0.0, rs0 = 0.0, rs1 = 0.0;
+      // D_j x_j (lower triangle by symmetry), E_{j-1} x_{j-1}, E_j^T x_{j+1}
       for (int k = 0; k < n; ++k) {
-        const double xk = __shfl_sync(0xffffffffu, k < 32 ? xc0 : xc1, k & 31);
+        const int sl = packed ? src0 + k : (k & 31);
+        const double xk = __shfl_sync(0xffffffffu, k < 32 ? xc0 : xc1, sl);
+        const double xpk = __shfl_sync(0xffffffffu, k < 32 ? xp0 : xp1, sl);
+        const double xnk = __shfl_sync(0xffffffffu, k < 32 ? xn0 : xn1, sl);
         const double d0 = k <= a0 ? Dj[a0 * n + k] : Dj[k * n + a0];
+        const double p0 = hp ? Ep[a0 * n + k] : 0.0, q0 = hn ? En[k * n + a0] : 0.0;
         acc0 = fma(d0, xk, acc0);
-        if (norms) rs0 += fabs(d0);
+        acc0 = fma(p0, xpk, acc0);
+        acc0 = fma(q0, xnk, acc0);
+        if (norms) rs0 += (fabs(d0) + fabs(p0)) + fabs(q0);
         if (two) {
           const double d1 = k <= a1 ? Dj[a1 * n + k] : Dj[k * n + a1];
+          const double p1 = hp ? Ep[a1 * n + k] : 0.0, q1 = hn ? En[k * n + a1] : 0.0;
           acc1 = fma(d1, xk, acc1);
-          if (norms) rs1 += fabs(d1);
-        }
-      }
-      if (Ep) {
-        for (int k = 0; k < n; ++k) {
-          const double xk = __shfl_sync(0xffffffffu, k < 32 ? xp0 : xp1, k & 31);
-          const double e0 = Ep[a0 * n + k];
-          acc0 = fma(e0, xk, acc0);
-          if (norms) rs0 += fabs(e0);
-          if (two) {
-            const double e1 = Ep[a1 * n + k];
-            acc1 = fma(e1, xk, acc1);
-            if (norms) rs1 += fabs(e1);
-          }
-        }
-      }
-      if (En) {
-        for (int k = 0; k < n; ++k) {
-          const double xk = __shfl_sync(0xffffffffu, k < 32 ? xn0 : xn1, k & 31);
-          const double e0 = En[k * n + a0];
-          acc0 = fma(e0, xk, acc0);
-          if (norms) rs0 += fabs(e0);
-          if (two) {
-            const double e1 = En[k * n + a1];
-            acc1 = fma(e1, xk, acc1);
-            if (norms) rs1 += fabs(e1);
-          }
+          acc1 = fma(p1, xpk, acc1);
+          acc1 = fma(q1, xnk, acc1);
+          if (norms) rs1 += (fabs(d1) + fabs(p1)) + fabs(q1);
         }
       }
       if (m) {
-        const double* Gj = G + (size_t)j * mn;
+        const double* Gj = G + (size_t)jc * mn;
 #pragma unroll
         for (int q = 0; q < kMaxM; ++q) {
           if (q >= m) break;  // warp-uniform; full unrolling keeps gacc in registers
           const double xq = __shfl_sync(0xffffffffu, xg_l, q);
           const double g0 = Gj[q * n + a0];
           acc0 = fma(g0, xq, acc0);
-          gacc[q] = fma(g0, xc0, gacc[q]);
+          gacc[q] = fma(g0, xc0, gacc[q]);  // xc0 = 0 on idle lanes
           if (norms) rs0 += fabs(g0);
           if (two) {
             const double g1 = Gj[q * n + a1];
@@ -1367,13 +1592,13 @@ __global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ 
           }
         }
       }
-      if (r0ok) {
+      if (ok0) {
         const double bv = b[(size_t)(rb + i0) * ldb + col], r = bv - acc0;
         c[(size_t)(rb + i0) * kRhsChunk + col] = r;
         mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xc0));
         if (norms) mrow = fmax(mrow, rs0);
       }
-      if (r1ok) {
+      if (ok1) {
         const double bv = b[(size_t)(rb + i1) * ldb + col], r = bv - acc1;
         c[(size_t)(rb + i1) * kRhsChunk + col] = r;
         mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xc1));
@@ -1384,19 +1609,17 @@ __global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ 
 #pragma unroll
     for (int q = 0; q < kMaxM; ++q) {
       if (q >= m) break;
-      double v = gacc[q];  // rows beyond n hold x = 0
+      double v = gacc[q];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (lane == 0) part[q * kRhsChunk + col] = v;
     }
   }
-  if (norms && m) {
-    // |G| sums of the g rows over the task's stages: lane q sums row q
+  double gab = 0.0;  // |G| sum of g row `lane` (lane < m) over the task's stages
+  if (norms && m && lane < m)
     for (int j = j0; j < j1; ++j) {
       const double* Gj = G + (size_t)j * mn;
-      if (lane < m)
-        for (int i = 0; i < n; ++i) gab += fabs(Gj[lane * n + i]);
+      for (int i = 0; i < n; ++i) gab += fabs(Gj[lane * n + i]);
     }
-  }
   for (int o = 16; o > 0; o >>= 1) {
     mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
     mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -1553,6 +1776,24 @@ size_t solve_smem_bytes(int n, int m, int single) {
   return (size_t)sol_layout(n, m, single ? 4 : 8).total;
 }
 
+int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
+                    const double* D, const double* E, const double* G, const double* R, Info* info,
+                    void* stream) {
+  if (ntasks <= 0) return 0;
+  const int slice = fac_layout_w(maxn, maxm, mixed ? 4 : 8).total;
+  const int wpc = std::max(1, std::min(8, (200 * 1024) / slice));  // tasks (warps) per CTA
+  const size_t sm = (size_t)wpc * slice;
+  const void* fn = mixed ? (const void*)k_factor_w<float> : (const void*)k_factor_w<double>;
+  int e = set_smem(fn, sm);
+  if (e) return e;
+  const int grid = (ntasks + wpc - 1) / wpc;
+  if (mixed)
+    k_factor_w<float><<<grid, 32 * wpc, sm, (cudaStream_t)stream>>>(d, t, ntasks, D, E, G, R, info, slice);
+  else
+    k_factor_w<double><<<grid, 32 * wpc, sm, (cudaStream_t)stream>>>(d, t, ntasks, D, E, G, R, info, slice);
+  return (int)cudaGetLastError();
+}
+
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
                   void* stream) {
@@ -1605,6 +1846,29 @@ int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
     k_backward<float><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip);
   else
     k_backward<double><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip);
+  return (int)cudaGetLastError();
+}
+
+// warp-per-task substitutions (blocks n <= kWarpMaxN)
+int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
+                   double* b, int ldb, int nrhs, const int* skip, void* stream) {
+  if (ntasks <= 0) return 0;
+  const int slice = (int)solve_smem_bytes(maxn, maxm, single);
+  const int wpc = std::max(1, std::min(8, (200 * 1024) / slice));
+  const size_t sm = (size_t)wpc * slice;
+  const void* fn = backward ? (single ? (const void*)k_backward_w<float> : (const void*)k_backward_w<double>)
+                            : (single ? (const void*)k_forward_w<float> : (const void*)k_forward_w<double>);
+  int e = set_smem(fn, sm);
+  if (e) return e;
+  const int grid = (ntasks + wpc - 1) / wpc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (backward) {
+    if (single) k_backward_w<float><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice);
+    else k_backward_w<double><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice);
+  } else {
+    if (single) k_forward_w<float><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice);
+    else k_forward_w<double><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice);
+  }
   return (int)cudaGetLastError();
 }
 

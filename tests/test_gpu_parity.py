@@ -60,6 +60,8 @@ def gpu_solve(kkt, D, E, G, R, b, P=1, levels=None, want_factor=False, balanced=
         info = kkt.kkt_get_info(h)
         assert info["status"] == 0, info
         F = kkt.kkt_get_factor(h, N, n, m) if want_factor else None
+        if F is not None:
+            F["seg"] = kkt.kkt_partition(h, 0, 1)     # the handle's level-1 segment lengths
         return bd.cpu().numpy(), F
     finally:
         kkt.kkt_destroy(h)
@@ -222,13 +224,12 @@ def test_balanced_partition_solution(kkt, orc, N, n, m, levels):
 def test_balanced_two_level_blocks(kkt, orc):
     """Two balanced levels: the factor blocks are Algorithm 1's on the
     oracle's run with the same segment lengths."""
-    import torch
     N, n, m, P = 40, 5, 2, 9
     D, E, G, R, _ = gen.known_factor(N, n, m, seed=3)
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    seg = kkt.kkt_partition_balanced(N, n, m, P, paired=2 * P <= sms)
     b = gen.rhs(N * n + m, 1, seed=4)
     x, F = gpu_solve(kkt, D, E, G, R, b, P=P, want_factor=True, balanced=True)
+    seg = F["seg"]
+    assert seg in (kkt.kkt_partition_balanced(N, n, m, P, False), kkt.kkt_partition_balanced(N, n, m, P, True))
     Fo = orc.par_factor(D, E, G, R, seg_len=seg)
     for key in ("Ld", "Le", "Lw", "Lh", "Lg", "Lr"):
         scale = max(1.0, np.abs(Fo[key]).max() if Fo[key].size else 1.0)
