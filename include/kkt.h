@@ -186,6 +186,23 @@ kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const dou
  * columns. nrhs >= 1. Asynchronous on `stream`. */
 kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream);
 
+/* Factor Psi and solve Psi x = b in one pass (kkt_factor followed by
+ * kkt_solve, with the same result up to rounding): the right-hand side is
+ * bordered onto the arrow, i.e. the matrix [[Psi, b], [b^T, .]] is factored,
+ * so the forward substitution (Algorithm 2) is carried by the factorization
+ * (its extra arrow row is y = L-hat^{-1} b, stage by stage and across the
+ * levels through the same slots) and only the corner and the backward
+ * substitution (Algorithm 3) follow. b (device, ldb >= nrhs) is overwritten
+ * with x. Used for FP64 handles with nrhs = 1 and an arrow of at most 15 rows
+ * (room for the bordered row); otherwise it runs kkt_factor and kkt_solve.
+ * The factor stays usable for kkt_solve, kkt_solve_refined and
+ * kkt_solve_adjoint; kkt_get_factor then reports KKT_ERR_STATE. Launches
+ * recorded by kkt_set_launch_events: the copy of the bordered arrow, the
+ * factor launches, the top level's corner and backward sweep, then the
+ * backward launches. */
+kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, const double* G,
+                            const double* R, double* b, int nrhs, int ldb, void* stream);
+
 /* Mixed-precision iterative refinement: x = Psi^{-1} b by x_0 = 0,
  * c <- b; then `sweeps` times: c <- (L-hat L-hat^T)^{-1} c with the current
  * factor (FP32 substitutions on mixed levels), x <- x + c, c <- b - Psi x in

@@ -26,7 +26,7 @@ RHS_CHUNK = 16
 
 EXPORTED = [
     "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_batch_create_tuned", "kkt_destroy",
-    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta",
+    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_factor_solve", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta",
     "kkt_get_info",
     "kkt_get_factor", "kkt_set_pairing", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
 ]
@@ -63,6 +63,7 @@ _sig = {
     "kkt_batch_offsets": [_vp, _szp, _szp, _szp, _szp, _szp],
     "kkt_factor": [_vp, _vp, _vp, _vp, _vp, _vp],
     "kkt_solve": [_vp, _vp, _i, _i, _vp],
+    "kkt_factor_solve": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp],
     "kkt_solve_refined": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i, _i, _i, ctypes.c_double, _vp],
     "kkt_refine_eta": [_vp, _i, _dp],
     "kkt_solve_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _vp, _vp, _i, _vp],
@@ -206,6 +207,17 @@ def kkt_solve(h: int, b, nrhs: int | None = None, ldb: int | None = None, stream
     if ldb is None:
         ldb = 1 if b.dim() == 1 else b.shape[1]
     _check(_lib.kkt_solve(h, _ptr(b), nrhs, ldb, _stream(stream)), "kkt_solve")
+
+
+def kkt_factor_solve(h: int, D, E, G, R, b, nrhs: int | None = None, ldb: int | None = None, stream=None):
+    """Factor and solve in one pass (the right-hand side bordered onto the
+    arrow, see the C header); b is overwritten with x."""
+    if nrhs is None:
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+    if ldb is None:
+        ldb = 1 if b.dim() == 1 else b.shape[1]
+    _check(_lib.kkt_factor_solve(h, _ptr(D), _ptr(E), _ptr(G), _ptr(R), _ptr(b), nrhs, ldb, _stream(stream)),
+           "kkt_factor_solve")
 
 
 def kkt_solve_refined(h: int, D, E, G, R, b, x, nrhs: int | None = None, ldb: int | None = None,

@@ -176,6 +176,15 @@ struct kkt_handle {
   double* deta = nullptr;                    // eta history [kMaxSweeps][count]
   std::vector<int> level_mixed;              // per level index (all systems alike)
   std::vector<int> level_pair;               // factor tasks of this level run as CTA pairs
+  // fused factor-and-solve (kkt_factor_solve): one right-hand side bordered
+  // onto the arrow; storage has room for m + border arrow rows
+  int border = 0;                            // 1 when the fused pass is available
+  LevelDesc* ddesc_b = nullptr;              // bordered descriptors (m + 1 arrow rows, mr = 1)
+  double* Gb = nullptr;                      // bordered level-1 arrow blocks [sum N][m+1][n]
+  double* Rb = nullptr;                      // bordered corners [sum (m+1)^2]
+  bool cur_b = false;                        // the current factor is the bordered one
+  long long max_gb = 0;                      // largest bordered arrow of one system (elements)
+  std::vector<int> level_top;                // some system's top level is this level
   int pair_policy = KKT_PAIR_AUTO;
 };
 
@@ -296,6 +305,11 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
   h->level_pair.assign(h->maxL, 0);
   for (int l = 0; l < h->maxL && l < (int)pair_lv.size(); ++l) h->level_pair[l] = pair_lv[l];
   if (kkt::factor_smem_bytes(h->maxn, h->maxm, 0) > size_t(optin)) { delete h; return KKT_ERR_ARG; }
+  // room for one bordered right-hand side (FP64 handles whose arrow has a spare row)
+  h->border = (precision == KKT_FP64 && h->maxm + 1 <= kkt::kMaxM &&
+               kkt::factor_smem_bytes(h->maxn, h->maxm + 1, 0) <= size_t(optin))
+                  ? 1 : 0;
+  const int bc = h->border;
   h->level_mixed.assign(h->maxL, 0);
   for (const SysPlan& sp : h->sys)
     for (size_t l = 0; l < sp.lv.size(); ++l) h->level_mixed[l] = sp.lv[l].mixed;
@@ -309,9 +323,16 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
   };
   std::vector<std::vector<Offs>> lo(count);
   std::vector<size_t> rhat(count), rri(count), rpart(count), ygall(count);
+  std::vector<size_t> offGb(count), offRb(count);
+  size_t tot_Gb = 0, tot_Rb = 0;
   for (int s = 0; s < count; ++s) {
     const SysPlan& sp = h->sys[s];
-    const size_t nn = size_t(sp.n) * sp.n, mn = size_t(sp.m) * sp.n, R = 2 * sp.n + sp.m;
+    const int ma = sp.m + bc;  // arrow rows with room for a bordered right-hand side
+    const size_t nn = size_t(sp.n) * sp.n, mn = size_t(ma) * sp.n, R = 2 * sp.n + ma;
+    offGb[s] = tot_Gb; offRb[s] = tot_Rb;
+    tot_Gb += size_t(sp.N) * ma * sp.n;
+    h->max_gb = std::max<long long>(h->max_gb, (long long)sp.N * ma * sp.n);
+    tot_Rb += size_t(ma) * ma;
     size_t nparts = 0;
     for (const LevelPlan& L : sp.lv) {
       Offs o{};
@@ -342,11 +363,13 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       o.seg = cv.take(sizeof(int) * (L.P + 1));
       lo[s].push_back(o);
     }
-    rhat[s] = cv.take(D8 * std::max(sp.m * sp.m, 1));
-    rri[s] = cv.take(D8 * std::max(sp.m, 1));
-    rpart[s] = cv.take(D8 * std::max<size_t>(nparts * sp.m * sp.m, 1));
-    ygall[s] = cv.take(D8 * std::max<size_t>(nparts * sp.m * CH, 1));
+    rhat[s] = cv.take(D8 * std::max(ma * ma, 1));
+    rri[s] = cv.take(D8 * std::max(ma, 1));
+    rpart[s] = cv.take(D8 * std::max<size_t>(nparts * ma * ma, 1));
+    ygall[s] = cv.take(D8 * std::max<size_t>(nparts * ma * CH, 1));
   }
+  const size_t gb_off = bc ? cv.take(D8 * std::max<size_t>(tot_Gb, 1)) : 0;
+  const size_t rb_off = bc ? cv.take(D8 * std::max<size_t>(tot_Rb, 1)) : 0;
   // descriptors and tasks
   std::vector<Task> tasks;
   h->desc_of.assign(count, {});
@@ -356,6 +379,7 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       h->hdesc.push_back(LevelDesc{});
     }
   const size_t desc_off = cv.take(sizeof(LevelDesc) * h->hdesc.size());
+  const size_t descb_off2 = bc ? cv.take(sizeof(LevelDesc) * h->hdesc.size()) : 0;
   // task lists: factor/forward per level, then backward per level
   h->fac_off.assign(h->maxL, 0); h->fac_cnt.assign(h->maxL, 0);
   h->bwd_off.assign(h->maxL, 0); h->bwd_cnt.assign(h->maxL, 0);
@@ -463,6 +487,35 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       d.nyg_all = (int)part_cursor;
     }
   }
+  // bordered descriptors: the same storage, the arrow one row longer (the
+  // right-hand side), level 1 reading the bordered copies of G and R
+  std::vector<LevelDesc> hdesc_b;
+  if (bc) {
+    hdesc_b = h->hdesc;
+    for (int s = 0; s < count; ++s) {
+      const SysPlan& sp = h->sys[s];
+      const int ma = sp.m + 1;
+      size_t cursor = 0;
+      for (size_t l = 0; l < sp.lv.size(); ++l) {
+        LevelDesc& d = hdesc_b[h->desc_of[s][l]];
+        d.m = ma;
+        d.mr = 1;
+        d.offGu = sp.offG;
+        d.offRu = sp.offR;
+        d.offG = (long long)offGb[s];
+        d.offR = (long long)offRb[s];
+        if (!d.is_top) {
+          d.Rpart = dp(rpart[s]) + cursor * ma * ma;
+          d.ygpart = dp(ygall[s]) + cursor * ma * kkt::kRhsChunk;
+          cursor += sp.lv[l].P;
+        }
+        if (l > 0) {
+          d.Gw = dp(lo[s][l - 1].GA);
+          d.G2w = dp(lo[s][l - 1].GB);
+        }
+      }
+    }
+  }
   h->dres = (kkt::ResTask*)(base + res_off);
   h->dsys_desc = (int*)(base + sysd_off);
   h->dpart0 = (int*)(base + part0_off);
@@ -471,11 +524,21 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
   h->dconv = (int*)(base + conv_off);
   h->deta = (double*)(base + eta_off);
   h->ddesc = (LevelDesc*)(base + desc_off);
+  if (bc) {
+    h->ddesc_b = (LevelDesc*)(base + descb_off2);
+    h->Gb = dp(gb_off);
+    h->Rb = dp(rb_off);
+  }
   h->dtasks = (Task*)(base + task_off);
   h->dinfo = (kkt::Info*)(base + info_off);
   bool ok = cudaMemset(h->dmem, 0, h->dbytes) == cudaSuccess;
   ok = ok && cudaMemcpy(h->ddesc, h->hdesc.data(), sizeof(LevelDesc) * h->hdesc.size(),
                         cudaMemcpyHostToDevice) == cudaSuccess;
+  if (bc)
+    ok = ok && cudaMemcpy(h->ddesc_b, hdesc_b.data(), sizeof(LevelDesc) * hdesc_b.size(),
+                          cudaMemcpyHostToDevice) == cudaSuccess;
+  h->level_top.assign(h->maxL, 0);
+  for (const SysPlan& sp : h->sys) h->level_top[sp.lv.size() - 1] = 1;
   if (!tasks.empty())
     ok = ok && cudaMemcpy(h->dtasks, tasks.data(), sizeof(Task) * tasks.size(),
                           cudaMemcpyHostToDevice) == cudaSuccess;
@@ -748,28 +811,35 @@ kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const dou
       if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
     }
   h->factored = true;
+  h->cur_b = false;
   return KKT_OK;
 }
 
 namespace {
-// One forward/backward sweep over every level for up to kRhsChunk columns.
-kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* skip, void* stream,
-                       int* li) {
+// One forward/backward sweep over every level for up to kRhsChunk columns,
+// with the descriptors of the current factor. fwd_done: the factorization
+// carried the forward sweep (bordered pass), so only the top levels' corner
+// and backward sweep run among the forward launches.
+kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* skip, void* stream, int* li,
+                       int fwd_done = 0) {
+  const LevelDesc* dd = h->cur_b ? h->ddesc_b : h->ddesc;
+  const int dm = h->cur_b ? 1 : 0;  // arrow rows beyond each group's m
   // one launch per group: small blocks one warp per task, the others one CTA per task
   auto run = [&](bool backward, int l, const std::vector<kkt_handle::Group>& groups) -> bool {
     for (const kkt_handle::Group& gr : groups) {
       const Task* t = h->dtasks + gr.off;
-      const int mx = h->level_mixed[l];
-      const int e = gr.warp ? kkt::launch_solve_w(backward, h->ddesc, t, gr.cnt, gr.n, gr.m, mx, b, ldb, nr, skip,
-                                                  stream)
-                    : backward ? kkt::launch_backward(h->ddesc, t, gr.cnt, gr.n, gr.m, mx, b, ldb, nr, skip, stream)
-                               : kkt::launch_forward(h->ddesc, t, gr.cnt, gr.n, gr.m, mx, b, ldb, nr, skip, stream);
+      const int mx = h->level_mixed[l], gm = gr.m + dm;
+      const int e = gr.warp ? kkt::launch_solve_w(backward, dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip,
+                                                  stream, fwd_done)
+                    : backward ? kkt::launch_backward(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip, stream)
+                               : kkt::launch_forward(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip, stream,
+                                                     fwd_done);
       if (e || (li && !mark(h, (*li)++, stream))) return false;
     }
     return true;
   };
   for (int l = 0; l < h->maxL; ++l)
-    if (!run(false, l, h->fac_groups[l])) return KKT_ERR_CUDA;
+    if ((!fwd_done || h->level_top[l]) && !run(false, l, h->fac_groups[l])) return KKT_ERR_CUDA;
   for (int l = h->maxL - 2; l >= 0; --l)
     if (!run(true, l, h->bwd_groups[l])) return KKT_ERR_CUDA;
   return KKT_OK;
@@ -789,6 +859,34 @@ kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream) 
     if (st != KKT_OK) return st;
   }
   return KKT_OK;
+}
+
+kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, const double* G,
+                            const double* R, double* b, int nrhs, int ldb, void* stream) {
+  if (!h || !D || !b || nrhs < 1 || ldb < nrhs) return KKT_ERR_ARG;
+  if (h->tot_E > 0 && !E) return KKT_ERR_ARG;
+  if (h->maxm > 0 && (!G || !R)) return KKT_ERR_ARG;
+  if (!h->border || nrhs != 1) {  // no room for the bordered row: the two passes
+    const kkt_status st = kkt_factor(h, D, E, G, R, stream);
+    return st != KKT_OK ? st : kkt_solve(h, b, nrhs, ldb, stream);
+  }
+  // the right-hand side bordered onto the arrow: the factorization carries the
+  // forward substitution and writes y where the backward sweep reads it
+  int li = 0;
+  if (kkt::launch_border(h->ddesc_b, h->dsys_desc, h->count, h->max_gb, G, R, b, ldb, h->Gb, h->Rb, stream) ||
+      !mark(h, li++, stream))
+    return KKT_ERR_CUDA;
+  for (int l = 0; l < h->maxL; ++l)
+    for (const kkt_handle::Group& gr : h->fac_groups[l]) {
+      const int e = gr.warp ? kkt::launch_factor_w(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0, D, E,
+                                                   h->Gb, h->Rb, h->dinfo, stream, b, ldb)
+                            : kkt::launch_factor(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0,
+                                                 level_paired(h, l), D, E, h->Gb, h->Rb, h->dinfo, stream, b, ldb);
+      if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
+    }
+  h->factored = true;
+  h->cur_b = true;
+  return solve_chunk(h, b, ldb, 1, nullptr, stream, &li, 1);
 }
 
 kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, const double* G,
@@ -884,7 +982,7 @@ kkt_status kkt_get_factor(kkt_handle* h, int system, double* Ld, double* Le, dou
   if (!h || system < 0 || system >= h->count) return KKT_ERR_ARG;
   const SysPlan& sp = h->sys[system];
   if (sp.lv.size() > 2) return KKT_ERR_ARG;
-  if (!h->factored) return KKT_ERR_STATE;
+  if (!h->factored || h->cur_b) return KKT_ERR_STATE;
   if (cudaDeviceSynchronize() != cudaSuccess) return KKT_ERR_CUDA;
   const int N = sp.N, n = sp.n, m = sp.m, R = 2 * n + m;
   const size_t nn = size_t(n) * n, mn = size_t(m) * n;

@@ -49,6 +49,11 @@ struct LevelDesc {
   int is_top;     // P == 1 and no deeper level: also factors/solves the corner
   int sys;        // system index in the batch
   int precision;  // kkt_precision
+  // right-hand sides bordered onto the arrow (0, or 1 in a fused factor-and-solve
+  // pass): the last mr of the m arrow rows then hold b, the factorization carries
+  // the forward substitution, and the real arrow has m - mr rows
+  int mr;
+  long long offGu, offRu;  // bordered level 1: the caller's G and R (offG, offR index the bordered copies)
   // inputs: level 1 reads the caller's arrays at these element offsets;
   // deeper levels read the slots the level above wrote (D = Dw + D2w, etc.)
   long long offD, offE, offG, offR, offB;
@@ -197,19 +202,24 @@ constexpr int kResPartDoubles = kMaxM * kRhsChunk + 4 * kRhsChunk;
 // with the FP32 factor copy (mixed levels only); `skip`: per-system flags
 // (null = never skip), a set flag makes the system's CTAs return at once.
 // one warp per task (blocks n <= kWarpMaxN), several tasks per CTA
+// (b, ldb: where the forward solution y of a bordered pass is written; unused otherwise)
 int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
                     const double* D, const double* E, const double* G, const double* R, Info* info,
-                    void* stream);
+                    void* stream, double* b = nullptr, int ldb = 1);
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
-                  void* stream);
+                  void* stream, double* b = nullptr, int ldb = 1);
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                   double* b, int ldb, int nrhs, const int* skip, void* stream);
+                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0);
 int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
                     double* b, int ldb, int nrhs, const int* skip, void* stream);
 // one warp per task (blocks n <= kWarpMaxN), forward or backward substitution
 int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                   double* b, int ldb, int nrhs, const int* skip, void* stream);
+                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0);
+// bordered inputs of a fused factor-and-solve pass, for every system: Gb_j =
+// [G_j; b_j^T] ((m+1) x n per stage), Rb = [[R, b_g], [b_g^T, 0]] ((m+1)^2)
+int launch_border(const LevelDesc* db, const int* sys_desc, int count, long long max_elems, const double* G,
+                  const double* R, const double* b, int ldb, double* Gb, double* Rb, void* stream);
 // x += c (stage rows per residual task, g rows by each system's first task)
 int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int ldx, const double* c,
                 int nr, const int* skip, void* stream);

@@ -498,6 +498,84 @@ constexpr int kWhole = 0, kSplit = 1, kPair = 2;
 constexpr int kBarProd = 2, kBarCons = 3, kBarFullM = 4, kBarFreeM = 5, kBarFullZ = 6, kBarFreeZ = 7;
 constexpr int kRoleThreads = 128;
 
+// Pairs (i, k) with 1 <= k <= i < n ordered by k descending (packed
+// i << 16 | k): the updates by column j are the prefix of length
+// (n-1-j)(n-j)/2.
+__device__ void pair_table_w(int* tab, int n, int lane) {
+  const int np = (n - 1) * n / 2;
+  for (int e = lane; e < np; e += 32) {
+    int a, b;
+    tri_rc(e, a, b);
+    const int k = n - 1 - a;
+    tab[e] = (k + b) << 16 | k;
+  }
+  __syncwarp();
+}
+
+// In-place lower Cholesky of A (n x n, FP64, n <= kWarpMaxN) by one warp,
+// right-looking: pivot by lane 0, column scaled by the lanes, then the
+// trailing update by column j over the pair table. Returns the first bad
+// column + 1 (0 if every pivot was positive) in lane 0.
+__device__ int potrf_w(double* A, int ld, int n, double* rinv, const int* tab, int lane) {
+  int bad = 0;
+  for (int j = 0; j < n; ++j) {
+    double r = 0.0;
+    if (lane == 0) {
+      const double dj = A[j * ld + j];
+      if (not_positive(dj) && bad == 0) bad = j + 1;
+      r = pivot_rsqrt(dj);
+      A[j * ld + j] = dj * r;
+      rinv[j] = r;
+    }
+    r = __shfl_sync(0xffffffffu, r, 0);
+    for (int i = j + 1 + lane; i < n; i += 32) A[i * ld + j] *= r;
+    __syncwarp();
+    const int cnt = (n - 1 - j) * (n - j) / 2;
+    for (int e = lane; e < cnt; e += 32) {
+      const int p = tab[e], i = p >> 16, k = p & 0xffff;
+      A[i * ld + k] = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
+    }
+    __syncwarp();
+  }
+  return bad;
+}
+
+// Corner of the top level: R-hat = chol(Rs) on the leading m - mr rows (Rs, ld
+// ldR, m x m, in shared memory, already summed); the last mr rows hold
+// bordered right-hand sides, which are solved against it instead of pivoted
+// (their diagonal is never formed): row r gets (Rs[r][k] - sum_{t<k}
+// Rs[r][t] R-hat[k][t]) / R-hat[k][k], the forward solution y_g of the
+// corner. Writes R-hat (m x m, upper part zero) and 1/diag; group G; the
+// pivot factorization uses warps 0-3 (potrf_sm) or one warp (potrf_w).
+template <bool WARP>
+__device__ void corner_factor(double* Rs, int ldR, int m, int mr, double* rinv, int* tab, const LevelDesc& d,
+                              Info* info, int* bad, Grp G) {
+  const int mk = m - mr;
+  if (WARP) {
+    pair_table_w(tab, mk, G.tid);
+    const int bd = potrf_w(Rs, ldR, mk, rinv, tab, G.tid);
+    if (G.tid == 0 && bd) record_breakdown(info, d.sys, d.Nnat, d.level);
+  } else if (mk > 0) {
+    potrf_table(tab, mk);
+    __syncthreads();
+    potrf_sm(Rs, ldR, mk, rinv, tab, bad);
+    if (*bad && threadIdx.x == 0) record_breakdown(info, d.sys, d.Nnat, d.level);
+  }
+  // bordered rows: a forward substitution with the corner factor, one row per thread
+  for (int r = mk + G.tid; r < m; r += G.nt) {
+    double* z = Rs + r * ldR;
+    for (int k = 0; k < mk; ++k) {
+      double a = z[k];
+      for (int t = 0; t < k; ++t) a = fma(-z[t], Rs[k * ldR + t], a);
+      z[k] = a * rinv[k];
+    }
+    for (int k = mk; k < m; ++k) z[k] = 0.0;
+  }
+  gsync(G);
+  store_blk(d.Rhat, Rs, ldR, m, m, false, true, G);
+  for (int e = G.tid; e < m; e += G.nt) d.Rri[e] = e < mk ? rinv[e] : 0.0;
+}
+
 // Shared-memory view and per-stage bookkeeping of one segment task of
 // Algorithm 1: where the stage's blocks live, the loads of its inputs (the
 // caller's arrays at level 1, the slots of the level below otherwise), the
@@ -588,6 +666,18 @@ struct FacCtx {
     for (int e = G.tid; e < n; e += G.nt) d->Lri[(size_t)j * n + e] = rv[e];
   }
 
+  // bordered pass: the last arrow row of the solved panel is y_j^T (the
+  // forward substitution of stage j), written where the solve keeps it
+  // (the caller's b at level 1, this level's X otherwise)
+  __device__ void store_y(int j, double* b, int ldb, Grp G) const {
+    const TZ* yr = Z + (oG + m - d->mr) * ldZ;
+    double* dst;
+    long long ld;
+    if (d->level == 1) { dst = b + (size_t)(d->offB + (long long)j * n) * ldb; ld = ldb; }
+    else { dst = d->X + (size_t)j * n * kRhsChunk; ld = kRhsChunk; }
+    for (int e = G.tid; e < n; e += G.nt) dst[(size_t)e * ld] = (double)yr[e];
+  }
+
   // panel rows [0, rows) of Lp for stage j: rows outside [r0, r1) are zero
   // (a consumer writes the W-rows of a split or paired segment)
   __device__ void store_panel(int j, int r0, int r1, int rows, Grp G) const {
@@ -642,7 +732,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
                                                            const double* __restrict__ uE,
                                                            const double* __restrict__ uG,
                                                            const double* __restrict__ uR,
-                                                           Info* info, int pair) {
+                                                           Info* info, int pair, double* yb, int ldyb) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
   const unsigned rank = pair ? cluster_rank() : 0u;
@@ -727,6 +817,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
       group_arrive(kBarFullM, kFactorThreads);
       trsm_panel(Z, ldZ, r0, pr1, M, ldD, n, rinvZ, P);
       group_arrive(kBarFullZ, kFactorThreads);
+      if (d.mr) cx.store_y(j, yb, ldyb, P);
       store_pivot(j, Dfac, rinv, M, P);
       store_panel(j, r0, pr1, pr1, P);
       syrk_trap(T, ldT, Z, Z, 0, ldZ, r0, pr1, r0, n, P);
@@ -768,6 +859,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
       }
       __syncthreads();
       if (threadIdx.x == 0 && bad) { record_breakdown(info, d.sys, d.nat[j], d.level); bad = 0; }
+      if (d.mr) cx.store_y(j, yb, ldyb, P);
       if (push) {
         for (int e = P.tid; e < n; e += P.nt) rinvZ[e] = (TZ)rvbuf(cur)[e];
         __syncthreads();
@@ -856,12 +948,8 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
       const int r = e / m, c = e - r * m;
       Rs[r * ldR + c] = (Ru[e] + Psum[e]) + T[(oG + r) * ldT + oG + c];
     }
-    potrf_table(tab, m);
     __syncthreads();
-    potrf_sm(Rs, ldR, m, rinv, tab, &bad);
-    if (bad && threadIdx.x == 0) record_breakdown(info, d.sys, d.Nnat, d.level);
-    store_blk(d.Rhat, Rs, ldR, m, m, false, true);
-    for (int e = threadIdx.x; e < m; e += blockDim.x) d.Rri[e] = rinv[e];
+    corner_factor<false>(Rs, ldR, m, d.mr, rinv, tab, d, info, &bad, cta_grp());
   }
   if (mode == kPair) {
     // a segment without fill-in leaves its consumer idle; every CTA of the
@@ -880,48 +968,6 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
 // many independent stage chains an SM interleaves. The operations per
 // element are those of the CTA kernel, in the same order.
 // ---------------------------------------------------------------------------
-
-// Pairs (i, k) with 1 <= k <= i < n ordered by k descending (packed
-// i << 16 | k): the updates by column j are the prefix of length
-// (n-1-j)(n-j)/2.
-__device__ void pair_table_w(int* tab, int n, int lane) {
-  const int np = (n - 1) * n / 2;
-  for (int e = lane; e < np; e += 32) {
-    int a, b;
-    tri_rc(e, a, b);
-    const int k = n - 1 - a;
-    tab[e] = (k + b) << 16 | k;
-  }
-  __syncwarp();
-}
-
-// In-place lower Cholesky of A (n x n, FP64, n <= kWarpMaxN) by one warp,
-// right-looking: pivot by lane 0, column scaled by the lanes, then the
-// trailing update by column j over the pair table. Returns the first bad
-// column + 1 (0 if every pivot was positive) in lane 0.
-__device__ int potrf_w(double* A, int ld, int n, double* rinv, const int* tab, int lane) {
-  int bad = 0;
-  for (int j = 0; j < n; ++j) {
-    double r = 0.0;
-    if (lane == 0) {
-      const double dj = A[j * ld + j];
-      if (not_positive(dj) && bad == 0) bad = j + 1;
-      r = pivot_rsqrt(dj);
-      A[j * ld + j] = dj * r;
-      rinv[j] = r;
-    }
-    r = __shfl_sync(0xffffffffu, r, 0);
-    for (int i = j + 1 + lane; i < n; i += 32) A[i * ld + j] *= r;
-    __syncwarp();
-    const int cnt = (n - 1 - j) * (n - j) / 2;
-    for (int e = lane; e < cnt; e += 32) {
-      const int p = tab[e], i = p >> 16, k = p & 0xffff;
-      A[i * ld + k] = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
-    }
-    __syncwarp();
-  }
-  return bad;
-}
 
 // Z[r0:r1) <- Z[r0:r1) L^{-T} by one warp, one panel row per lane: the
 // division-free substitution of trsm_panel, in the same order per element.
@@ -943,7 +989,7 @@ __global__ void __launch_bounds__(256) k_factor_w(const LevelDesc* __restrict__ 
                                                   const Task* __restrict__ tasks, int ntasks,
                                                   const double* __restrict__ uD, const double* __restrict__ uE,
                                                   const double* __restrict__ uG, const double* __restrict__ uR,
-                                                  Info* info, int slice) {
+                                                  Info* info, int slice, double* yb, int ldyb) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int t = blockIdx.x * (blockDim.x >> 5) + wid;
@@ -971,6 +1017,7 @@ __global__ void __launch_bounds__(256) k_factor_w(const LevelDesc* __restrict__ 
     for (int e = lane; e < n; e += 32) cx.rinvZ[e] = (TZ)cx.rinv[e];
     __syncwarp();
     trsm_w(cx.Z, ldZ, r0, pr1, cx.M, ldD, n, cx.rinvZ, lane);
+    if (d.mr) cx.store_y(j, yb, ldyb, W);
     cx.store_pivot(j, cx.Dfac, cx.rinv, cx.M, W);
     cx.store_panel(j, r0, pr1, R, W);
     syrk_trap(cx.T, ldT, cx.Z, cx.Z, 0, ldZ, r0, pr1, r0, n, W);
@@ -1004,11 +1051,8 @@ __global__ void __launch_bounds__(256) k_factor_w(const LevelDesc* __restrict__ 
       const int r = e / m, c = e - r * m;
       Rs[r * ldR + c] = (Ru[e] + Psum[e]) + cx.T[(oG + r) * ldT + oG + c];
     }
-    pair_table_w(cx.tab, m, lane);
-    const int bad = potrf_w(Rs, ldR, m, cx.rinv, cx.tab, lane);
-    if (lane == 0 && bad) record_breakdown(info, d.sys, d.Nnat, d.level);
-    store_blk(d.Rhat, Rs, ldR, m, m, false, true, W);
-    for (int e = lane; e < m; e += 32) d.Rri[e] = cx.rinv[e];
+    __syncwarp();
+    corner_factor<true>(Rs, ldR, m, d.mr, cx.rinv, cx.tab, d, info, nullptr, W);
   }
 }
 
@@ -1280,10 +1324,11 @@ __device__ void backward_segment(const SolveSmem<TS>& S, const LevelDesc& d, con
 // sequential phase). `skip`: per-system flags; a set flag returns at once.
 template <typename TS>
 __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs, double* b, int ldb, int nr,
-                             const int* skip, unsigned char* smraw, Grp G) {
+                             const int* skip, unsigned char* smraw, Grp G, int fwd_done) {
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
-  const int n = d.n, m = d.m;
+  if (fwd_done && !d.is_top) return;  // the factorization carried this forward sweep
+  const int n = d.n, m = d.m, mg = d.m - d.mr;  // mg: rows of the real arrow
   const SolveSmem<TS> S = solve_smem<TS>(smraw, n, m);
   const int oG = n, oW = n + m;
   const SegGeom g = seg_geom(d, tk.seg);
@@ -1299,13 +1344,14 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
   };
   int r0, r1;
   stage_rows(g, 0, n, m, r0, r1);
-  prefetch_stage_factor(S, 0, d, g.f, r0, r1, false, G);
+  if (!fwd_done) prefetch_stage_factor(S, 0, d, g.f, r0, r1, false, G);
   // V_G <- 0, V_W <- rhs of the separator, t <- rhs of the first stage
   for (int e = G.tid; e < (2 * n + m) * S.ldV; e += G.nt) S.V[e] = TS(0);
   gsync(G);
   if (g.hasW) rhs(g.f - 1, S.V + oW * S.ldV);
   rhs(g.f, S.t);
-  for (int i = 0; i < g.len; ++i) {
+  // a bordered factorization already carried this forward sweep (fwd_done)
+  for (int i = 0; i < (fwd_done ? 0 : g.len); ++i) {
     const int j = g.f + i, q = i & 1;
     stage_rows(g, i, n, m, r0, r1);
     if (i + 1 < g.len) rhs(j + 1, S.V);  // V_E <- next stage's rhs (else 0: F-hat term)
@@ -1364,32 +1410,40 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
   }
   // top level: corner y_g = R-hat^{-1} (r_g + sum of every yg partial + own),
   // x_g = R-hat^{-T} y_g, written to the caller's b; then the backward sweep.
-  if (m) {
+  // After a bordered factorization y_g is the bordered row of R-hat itself.
+  if (mg) {
     double* bg = b + (size_t)d.rowG * ldb;
     TS* gv = S.t;
-    const int ldR = odd(m);
-    sum_partials(
-        G, m * nr, d.nyg_all,
-        [&](int p, int o) { return d.yg_all[((size_t)p * m + o / nr) * kRhsChunk + o % nr]; },
-        [&](int o, double v) {
-          const int r = o / nr, c = o - r * nr;
-          gv[r * S.ldV + c] = (TS)((bg[(size_t)r * ldb + c] + v) + (double)S.V[(oG + r) * S.ldV + c]);
-        });
-    for (int e = G.tid; e < m * m; e += G.nt) {  // R-hat: columns scaled, rows scaled
-      const int r = e / m, c = e - r * m;
-      S.L(0)[r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[c]);
-      S.L(1)[r * ldR + c] = (TS)(d.Rhat[e] * d.Rri[r]);
+    const int ldR = odd(mg);
+    if (fwd_done) {
+      for (int e = G.tid; e < mg * nr; e += G.nt) {
+        const int r = e / nr, c = e - r * nr;
+        gv[r * S.ldV + c] = (TS)d.Rhat[(size_t)(mg + c) * m + r];
+      }
+    } else {
+      sum_partials(
+          G, mg * nr, d.nyg_all,
+          [&](int p, int o) { return d.yg_all[((size_t)p * m + o / nr) * kRhsChunk + o % nr]; },
+          [&](int o, double v) {
+            const int r = o / nr, c = o - r * nr;
+            gv[r * S.ldV + c] = (TS)((bg[(size_t)r * ldb + c] + v) + (double)S.V[(oG + r) * S.ldV + c]);
+          });
     }
-    for (int e = G.tid; e < m; e += G.nt) S.rinv(0)[e] = (TS)d.Rri[e];
+    for (int e = G.tid; e < mg * mg; e += G.nt) {  // R-hat: columns scaled, rows scaled
+      const int r = e / mg, c = e - r * mg;
+      S.L(0)[r * ldR + c] = (TS)(d.Rhat[r * m + c] * d.Rri[c]);
+      S.L(1)[r * ldR + c] = (TS)(d.Rhat[r * m + c] * d.Rri[r]);
+    }
+    for (int e = G.tid; e < mg; e += G.nt) S.rinv(0)[e] = (TS)d.Rri[e];
     gsync(G);
-    trsv_warp(gv, S.ldV, S.L(0), ldR, S.rinv(0), m, nr, false, G);
-    trsv_warp(gv, S.ldV, S.L(1), ldR, S.rinv(0), m, nr, true, G);
-    store_vec(bg, ldb, gv, S.ldV, m, nr, G);
+    if (!fwd_done) trsv_warp(gv, S.ldV, S.L(0), ldR, S.rinv(0), mg, nr, false, G);
+    trsv_warp(gv, S.ldV, S.L(1), ldR, S.rinv(0), mg, nr, true, G);
+    store_vec(bg, ldb, gv, S.ldV, mg, nr, G);
   }
-  // V <- [0; x_g; -] for the backward sweep of the top level
+  // V <- [0; x_g; 0; -] for the backward sweep of the top level (bordered rows 0)
   for (int e = G.tid; e < (2 * n + m) * S.ldV; e += G.nt) {
     const int r = e / S.ldV;
-    if (r < oG || r >= oW) S.V[e] = TS(0);
+    if (r < oG || r >= oG + mg) S.V[e] = TS(0);
     else S.V[e] = S.t[(r - oG) * S.ldV + (e - r * S.ldV)];
   }
   gsync(G);
@@ -1413,7 +1467,7 @@ __device__ void backward_task(const Task tk, const LevelDesc* __restrict__ descs
   for (int e = G.tid; e < (2 * n + m) * S.ldV; e += G.nt) S.V[e] = TS(0);
   gsync(G);
   if (g.hasF) load_vec(S.V, S.ldV, d.Xnext + (size_t)k * n * kRhsChunk, kRhsChunk, none, n, nr, G);
-  if (m) load_vec(S.V + oG * S.ldV, S.ldV, b + (size_t)d.rowG * ldb, ldb, none, m, nr, G);
+  if (d.m - d.mr) load_vec(S.V + oG * S.ldV, S.ldV, b + (size_t)d.rowG * ldb, ldb, none, d.m - d.mr, nr, G);
   if (g.hasW) {
     load_vec(S.V + oW * S.ldV, S.ldV, d.Xnext + (size_t)(k - 1) * n * kRhsChunk, kRhsChunk, none, n,
              nr, G);
@@ -1431,9 +1485,9 @@ __device__ void backward_task(const Task tk, const LevelDesc* __restrict__ descs
 template <typename TS>
 __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __restrict__ descs,
                                                            const Task* __restrict__ tasks, double* b,
-                                                           int ldb, int nr, const int* skip) {
+                                                           int ldb, int nr, const int* skip, int fwd_done) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  forward_task<TS>(tasks[blockIdx.x], descs, b, ldb, nr, skip, smraw, cta_grp());
+  forward_task<TS>(tasks[blockIdx.x], descs, b, ldb, nr, skip, smraw, cta_grp(), fwd_done);
 }
 template <typename TS>
 __global__ void __launch_bounds__(kSolveThreads) k_backward(const LevelDesc* __restrict__ descs,
@@ -1445,12 +1499,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward(const LevelDesc* __r
 template <typename TS>
 __global__ void __launch_bounds__(256) k_forward_w(const LevelDesc* __restrict__ descs,
                                                    const Task* __restrict__ tasks, int ntasks, double* b,
-                                                   int ldb, int nr, const int* skip, int slice) {
+                                                   int ldb, int nr, const int* skip, int slice, int fwd_done) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int wid = threadIdx.x >> 5, t = blockIdx.x * (blockDim.x >> 5) + wid;
   if (t >= ntasks) return;  // whole warp
   forward_task<TS>(tasks[t], descs, b, ldb, nr, skip, smraw + (size_t)wid * slice,
-                   Grp{(int)(threadIdx.x & 31), 32, -1});
+                   Grp{(int)(threadIdx.x & 31), 32, -1}, fwd_done);
 }
 template <typename TS>
 __global__ void __launch_bounds__(256) k_backward_w(const LevelDesc* __restrict__ descs,
@@ -1762,6 +1816,34 @@ __global__ void k_fill_identity(const LevelDesc* __restrict__ descs, const int* 
   for (int e = threadIdx.x; e < d.m * d.m; e += blockDim.x) R[d.offR + e] = (e % (d.m + 1) == 0) ? 1.0 : 0.0;
 }
 
+// Bordered inputs for a fused factor-and-solve pass: Gb_j = [G_j; b_j^T],
+// Rb = [[R, b_g], [b_g^T, 0]]; db holds the bordered level-1 descriptors (m + 1
+// arrow rows, offG and offR into Gb and Rb). Grid: x strides over a system's
+// elements (one stage's row per 32-lane chunk), y = system.
+__global__ void k_border(const LevelDesc* __restrict__ descs, const int* __restrict__ sys_desc,
+                         const double* __restrict__ G, const double* __restrict__ R, const double* __restrict__ b,
+                         int ldb, double* Gb, double* Rb) {
+  const LevelDesc& d = descs[sys_desc[blockIdx.y]];
+  const int n = d.n, mb = d.m, m = mb - 1, N = d.N;
+  const long long offG = d.offGu, offR = d.offRu;  // the caller's arrays
+  const long long rows = (long long)N * mb;         // rows of Gb for this system
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < rows * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / n, j = row / mb;
+    const int r = (int)(row - j * mb), c = (int)(e - row * n);
+    Gb[d.offG + e] = r < m ? G[offG + (j * m + r) * n + c] : b[(size_t)(d.offB + j * n + c) * ldb];
+  }
+  if (blockIdx.x == 0)
+    for (int e = threadIdx.x; e < mb * mb; e += blockDim.x) {
+      const int r = e / mb, c = e - r * mb;
+      double v = 0.0;
+      if (r < m && c < m) v = R[offR + r * m + c];
+      else if (r == m && c < m) v = b[(size_t)(d.rowG + c) * ldb];
+      else if (c == m && r < m) v = b[(size_t)(d.rowG + r) * ldb];
+      Rb[d.offR + e] = v;
+    }
+}
+
 int set_smem(const void* fn, size_t bytes) {
   return (int)cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
@@ -1778,7 +1860,7 @@ size_t solve_smem_bytes(int n, int m, int single) {
 
 int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
                     const double* D, const double* E, const double* G, const double* R, Info* info,
-                    void* stream) {
+                    void* stream, double* b, int ldb) {
   if (ntasks <= 0) return 0;
   const int slice = fac_layout_w(maxn, maxm, mixed ? 4 : 8).total;
   const int wpc = std::max(1, std::min(8, (200 * 1024) / slice));  // tasks (warps) per CTA
@@ -1788,15 +1870,15 @@ int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
   if (e) return e;
   const int grid = (ntasks + wpc - 1) / wpc;
   if (mixed)
-    k_factor_w<float><<<grid, 32 * wpc, sm, (cudaStream_t)stream>>>(d, t, ntasks, D, E, G, R, info, slice);
+    k_factor_w<float><<<grid, 32 * wpc, sm, (cudaStream_t)stream>>>(d, t, ntasks, D, E, G, R, info, slice, b, ldb);
   else
-    k_factor_w<double><<<grid, 32 * wpc, sm, (cudaStream_t)stream>>>(d, t, ntasks, D, E, G, R, info, slice);
+    k_factor_w<double><<<grid, 32 * wpc, sm, (cudaStream_t)stream>>>(d, t, ntasks, D, E, G, R, info, slice, b, ldb);
   return (int)cudaGetLastError();
 }
 
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
-                  void* stream) {
+                  void* stream, double* b, int ldb) {
   if (ntasks <= 0) return 0;
   const size_t sm = factor_smem_bytes(maxn, maxm, mixed);
   const void* fn = mixed ? (const void*)k_factor<float> : (const void*)k_factor<double>;
@@ -1817,21 +1899,21 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
     cfg.numAttrs = 1;
   }
   const int p = pair ? 1 : 0;
-  if (mixed) return (int)cudaLaunchKernelEx(&cfg, k_factor<float>, d, t, D, E, G, R, info, p);
-  return (int)cudaLaunchKernelEx(&cfg, k_factor<double>, d, t, D, E, G, R, info, p);
+  if (mixed) return (int)cudaLaunchKernelEx(&cfg, k_factor<float>, d, t, D, E, G, R, info, p, b, ldb);
+  return (int)cudaLaunchKernelEx(&cfg, k_factor<double>, d, t, D, E, G, R, info, p, b, ldb);
 }
 
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                   double* b, int ldb, int nrhs, const int* skip, void* stream) {
+                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done) {
   if (ntasks <= 0) return 0;
   const size_t sm = solve_smem_bytes(maxn, maxm, single);
   const void* fn = single ? (const void*)k_forward<float> : (const void*)k_forward<double>;
   int e = set_smem(fn, sm);
   if (e) return e;
   if (single)
-    k_forward<float><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip);
+    k_forward<float><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip, fwd_done);
   else
-    k_forward<double><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip);
+    k_forward<double><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip, fwd_done);
   return (int)cudaGetLastError();
 }
 
@@ -1851,7 +1933,7 @@ int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
 
 // warp-per-task substitutions (blocks n <= kWarpMaxN)
 int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                   double* b, int ldb, int nrhs, const int* skip, void* stream) {
+                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done) {
   if (ntasks <= 0) return 0;
   const int slice = (int)solve_smem_bytes(maxn, maxm, single);
   const int wpc = std::max(1, std::min(8, (200 * 1024) / slice));
@@ -1866,8 +1948,8 @@ int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks,
     if (single) k_backward_w<float><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice);
     else k_backward_w<double><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice);
   } else {
-    if (single) k_forward_w<float><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice);
-    else k_forward_w<double><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice);
+    if (single) k_forward_w<float><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice, fwd_done);
+    else k_forward_w<double><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice, fwd_done);
   }
   return (int)cudaGetLastError();
 }
@@ -1883,6 +1965,15 @@ int launch_fill_identity(const LevelDesc* d, const int* sys_desc, int count, dou
                          void* stream) {
   if (count <= 0) return 0;
   k_fill_identity<<<count, 256, 0, (cudaStream_t)stream>>>(d, sys_desc, D, R);
+  return (int)cudaGetLastError();
+}
+
+int launch_border(const LevelDesc* db, const int* sys_desc, int count, long long max_elems, const double* G,
+                  const double* R, const double* b, int ldb, double* Gb, double* Rb, void* stream) {
+  if (count <= 0) return 0;
+  const long long bx = std::min<long long>(std::max<long long>((max_elems + 255) / 256, 1), 2048);
+  k_border<<<dim3((unsigned)bx, (unsigned)count), 256, 0, (cudaStream_t)stream>>>(db, sys_desc, G, R, b, ldb, Gb,
+                                                                                  Rb);
   return (int)cudaGetLastError();
 }
 

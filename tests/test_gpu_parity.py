@@ -485,3 +485,88 @@ def test_tuned_plans_follow_the_batch(kkt):
         assert lv[0] >= 2 and len(kkt.kkt_partition(h, 0, 1)) > 1
     finally:
         kkt.kkt_destroy(h)
+
+
+# ------------------------------------------------------------- fused factor + solve
+
+@pytest.mark.parametrize("pairing", PAIRINGS)
+@pytest.mark.parametrize("N,n,m,levels", [(16, 8, 4, [4, 1]), (128, 32, 8, [16, 4, 1]), (200, 24, 4, [20, 5, 1]),
+                                          (64, 6, 2, [16, 4, 1]), (40, 12, 0, [6, 1]), (30, 20, 3, [1]),
+                                          (1024, 32, 8, [152, 38, 10, 3, 1])])
+def test_factor_solve_fused(kkt, orc, N, n, m, levels, pairing):
+    """The right-hand side bordered onto the arrow: one pass gives the
+    solution of factor + solve (to rounding), and the factor it leaves
+    solves further right-hand sides and refines like kkt_factor's."""
+    import torch
+    D, E, G, R = gen.ipm(N, n, m, seed=41)
+    b = gen.rhs(N * n + m, 1, seed=42)
+    b2 = gen.rhs(N * n + m, 1, seed=43)
+    h = kkt.kkt_create_plan(N, n, m, levels, kkt.KKT_PARTITION_BALANCED)
+    try:
+        kkt.kkt_set_pairing(h, kkt.KKT_PAIR_OFF if pairing == "off" else kkt.KKT_PAIR_ON)
+        Dd, Ed, Gd, Rd = dev(D), dev(E) if N > 1 else None, dev(G) if m else None, dev(R) if m else None
+        x_two = dev(b)
+        kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+        kkt.kkt_solve(h, x_two)
+        x_one = dev(b)
+        kkt.kkt_factor_solve(h, Dd, Ed, Gd, Rd, x_one)
+        x_again = dev(b2)
+        kkt.kkt_solve(h, x_again)                     # the fused pass's factor, a new right-hand side
+        xr = torch.zeros_like(x_again)
+        kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, dev(b2), xr, sweeps=1, tol=0.0)
+        torch.cuda.synchronize()
+        assert kkt.kkt_get_info(h)["status"] == 0
+        with pytest.raises(kkt.KKTError):
+            kkt.kkt_get_factor(h, N, n, m)            # blocks of the bordered pass are not exported
+    finally:
+        kkt.kkt_destroy(h)
+    x_two, x_one, x_again, xr = (t.cpu().numpy() for t in (x_two, x_one, x_again, xr))
+    xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b)
+    check_solution(orc, D, E, G, R, x_one, b, xo, fwd_tol=1e-5)
+    np.testing.assert_allclose(x_one, x_two, rtol=0, atol=1e-9 * np.abs(x_two).max())
+    xo2 = orc.seq_solve(orc.seq_factor(D, E, G, R), b2)
+    check_solution(orc, D, E, G, R, x_again, b2, xo2, fwd_tol=1e-5)
+    check_solution(orc, D, E, G, R, xr, b2, xo2, fwd_tol=1e-5)
+
+
+def test_factor_solve_fused_batch(kkt, orc):
+    """Uneven batch, systems of different depths and block sizes."""
+    import torch
+    sy = gen.uneven_batch(9, seed=12, N_range=(6, 50))
+    Ns = [s[0].shape[0] for s in sy]
+    ns = [s[0].shape[1] for s in sy]
+    ms = [s[3].shape[0] for s in sy]
+    Ps = [max(1, min(5, (N + 1) // 2)) if i % 3 else 1 for i, N in enumerate(Ns)]
+    h = kkt.kkt_batch_create(Ns, ns, ms, Ps)
+    try:
+        off = kkt.kkt_batch_offsets(h, len(sy))
+        cat = lambda i: dev(np.concatenate([s[i].ravel() for s in sy] + [np.zeros(1)]))
+        bs = [gen.rhs(N * n + m, 1, seed=70 + i) for i, (N, n, m) in enumerate(zip(Ns, ns, ms))]
+        b = dev(np.concatenate(bs))
+        kkt.kkt_factor_solve(h, cat(0), cat(1), cat(2), cat(3), b)
+        torch.cuda.synchronize()
+        assert kkt.kkt_get_info(h)["status"] == 0
+        x = b.cpu().numpy()
+    finally:
+        kkt.kkt_destroy(h)
+    for i, s in enumerate(sy):
+        xi = x[off["b"][i]:off["b"][i + 1]]
+        xo = orc.seq_solve(orc.seq_factor(*s), bs[i])
+        check_solution(orc, *s, xi, bs[i], xo, fwd_tol=1e-6)
+
+
+def test_factor_solve_reports_breakdown(kkt):
+    """A bordered pass reports a non-SPD pivot block like kkt_factor."""
+    import torch
+    N, n, m = 16, 4, 2
+    D, E, G, R, _ = gen.known_factor(N, n, m, seed=0)
+    D = D.copy()
+    D[9] = -D[9]
+    h = kkt.kkt_create(N, n, m, 4)
+    try:
+        kkt.kkt_factor_solve(h, dev(D), dev(E), dev(G), dev(R), dev(gen.rhs(N * n + m, 1, seed=1)))
+        torch.cuda.synchronize()
+        info = kkt.kkt_get_info(h)
+        assert info["status"] == kkt.KKT_ERR_NOT_SPD and info["stage"] == 9
+    finally:
+        kkt.kkt_destroy(h)
