@@ -38,7 +38,7 @@ import gen  # noqa: E402
 METRIC = "KKT factor+solve systems/sec at stated error vs plain FP64 GPU; % FLOP roofline"
 UNIT = "systems/s"
 N_STAGES, N_BLOCK, M_ARROW = 1024, 32, 8
-WORKLOAD = f"ipm-shaped KKT, one system: N={N_STAGES}, n={N_BLOCK}, m={M_ARROW}, FP64, nrhs=1"
+WORKLOAD = f"ipm-shaped KKT, one system: N={N_STAGES}, n={N_BLOCK}, m={M_ARROW}, FP64, nrhs={{nrhs}}"
 # FP64 peak from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 L2_FLUSH_BYTES = 256 << 20
@@ -190,9 +190,9 @@ def kernel_source_sha() -> str:
     return h.hexdigest()
 
 
-def workload(seed: int):
+def workload(seed: int, nrhs: int = 1):
     D, E, G, R = gen.ipm(N_STAGES, N_BLOCK, M_ARROW, seed=seed)
-    b = gen.rhs(N_STAGES * N_BLOCK + M_ARROW, 1, seed=seed + 1)
+    b = gen.rhs(N_STAGES * N_BLOCK + M_ARROW, nrhs, seed=seed + 1)
     return D, E, G, R, b
 
 
@@ -218,7 +218,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    D, E, G, R, b = workload(0)
+    D, E, G, R, b = workload(0, args.nrhs)
     per_step = []
     total_sys = 0
     for _ in range(args.warmup):
@@ -233,7 +233,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "method": "FP64 CPU oracle, sequential block Cholesky"},
+        "config": {"workload": WORKLOAD.format(nrhs=args.nrhs), "method": "FP64 CPU oracle, sequential block Cholesky"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{total_sys} factor+solve runs of the workload system, "
                                    f"{args.steps} steps of about {args.ref_seconds:.0f} s"},
@@ -246,41 +246,55 @@ def device_sms() -> int:
     return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
-def per_launch_flops(kkt, plan):
+def per_launch_flops(kkt, plan, partition, nrhs=1):
     """Names and algorithmic FP64 flops (standard convention, as executed) of
-    the launches of one fused factor-and-solve step (kkt_factor_solve), in
-    launch order: factor levels 1..L with the right-hand side bordered onto the
-    arrow (the flop model with m + 1 arrow rows: the factorization plus the
-    forward substitution it carries), the top level's corner and backward
-    sweep, backward levels L-1..1."""
+    the launches of one factor-and-solve step, in launch order. With one
+    right-hand side (kkt_factor_solve, the right-hand side bordered onto the
+    arrow): factor levels 1..L with the flop model of m + 1 arrow rows (the
+    factorization plus the forward substitution it carries), the top level's
+    corner and backward sweep, backward levels L-1..1. With several (the two
+    passes): factor levels 1..L, forward levels 1..L (the top one also solves
+    the corner and runs its backward sweep), backward levels L-1..1."""
     L = len(plan)
     Ns = [N_STAGES]
     for p in plan[:-1]:
         Ns.append(p - 1)
     sms = device_sms()
-    sufb = [kkt.kkt_plan_flops(Ns[l], N_BLOCK, M_ARROW + 1, plan[l:], kkt.KKT_PARTITION_BALANCED, sms)
-            for l in range(L)]
-    suf = [kkt.kkt_plan_flops(Ns[l], N_BLOCK, M_ARROW, plan[l:], kkt.KKT_PARTITION_BALANCED, sms)
-           for l in range(L)]
+    fused = nrhs == 1
+    ma = M_ARROW + 1 if fused else M_ARROW
+    sufb = [kkt.kkt_plan_flops(Ns[l], N_BLOCK, ma, plan[l:], partition, sms) for l in range(L)]
+    suf = [kkt.kkt_plan_flops(Ns[l], N_BLOCK, M_ARROW, plan[l:], partition, sms) for l in range(L)]
     fac = [sufb[l]["factor"] - (sufb[l + 1]["factor"] if l + 1 < L else 0.0) for l in range(L)]
-    sol = [suf[l]["solve"] - (suf[l + 1]["solve"] if l + 1 < L else 0.0) for l in range(L)]
-    names = ["k_border (bordered arrow copy)"] + [f"k_factor level {l + 1} (+forward)" for l in range(L)]
-    flops = [0.0] + list(fac)
-    names.append(f"k_forward level {L} (corner, backward)")
-    flops.append(sol[L - 1] / 2.0)
+    sol = [nrhs * (suf[l]["solve"] - (suf[l + 1]["solve"] if l + 1 < L else 0.0)) for l in range(L)]
+    names, flops = [], []
+    if fused:
+        names.append("k_border (bordered arrow copy)")
+        flops.append(0.0)
+    tag = " (+forward)" if fused else ""
+    names += [f"k_factor level {l + 1}{tag}" for l in range(L)]
+    flops += list(fac)
+    if not fused:
+        for l in range(L - 1):
+            names.append(f"k_forward level {l + 1}")
+            flops.append(sol[l] / 2.0)
+        names.append(f"k_forward level {L} (forward, corner, backward)")
+        flops.append(sol[L - 1])
+    else:
+        names.append(f"k_forward level {L} (corner, backward)")
+        flops.append(sol[L - 1] / 2.0)
     for l in range(L - 2, -1, -1):
         names.append(f"k_backward level {l + 1}")
         flops.append(sol[l] / 2.0)
     return names, flops
 
 
-def candidate_plans(kkt):
+def candidate_plans(kkt, partition):
     plans = [[304, 76, 19, 6, 2, 1], [256, 64, 16, 4, 1], [304, 76, 19, 5, 1], [256, 64, 16, 4, 2, 1],
-             [152, 38, 10, 3, 1], [228, 57, 14, 3, 1]]
+             [304, 76, 19, 9, 3, 1], [304, 76, 25, 8, 2, 1], [152, 38, 10, 3, 1], [228, 57, 14, 3, 1]]
     ok = []
     for p in plans:
         try:
-            kkt.kkt_plan_flops(N_STAGES, N_BLOCK, M_ARROW, p, kkt.KKT_PARTITION_BALANCED)
+            kkt.kkt_plan_flops(N_STAGES, N_BLOCK, M_ARROW, p, partition)
             ok.append(p)
         except kkt.KKTError:
             pass
@@ -375,7 +389,12 @@ def run_batch(args):
     for path in spec["paths"]:
         prec = kkt.KKT_MIXED_FP32_ALL if path == "mixed" else kkt.KKT_FP64
         t0 = time.perf_counter()
-        h, lv = kkt.kkt_batch_create_tuned(Ns, ns, ms, prec)
+        if args.P:
+            # the paper's two-phase method with P segments in every system
+            h = kkt.kkt_batch_create(Ns, ns, ms, [args.P] * count, prec)
+            lv = [2 if args.P > 1 else 1] * count
+        else:
+            h, lv = kkt.kkt_batch_create_tuned(Ns, ns, ms, prec)
         tune_s = time.perf_counter() - t0
         b = b0.clone()
         x = torch.zeros_like(b0)
@@ -457,6 +476,7 @@ def run_batch(args):
         "warmup": args.warmup, "ms_per_step": br["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if bp != "mixed" else "f32+f64", "data": "synthetic",
         "config": {"workload": spec["desc"], "name": name, "path": bp, "systems": count,
+                   "plan": f"two levels, P = {args.P} per system" if args.P else "autotuned per system",
                    "refinement_sweeps": sweeps if "mixed" in spec["paths"] else None,
                    "l2": "inputs larger than L2", "graph": "one CUDA graph per step"},
         "error": {"max_backward_error": br["max_eta"], "gate": 1e-14},
@@ -486,6 +506,11 @@ def main():
     ap.add_argument("--workload", default="ipm1024", choices=["ipm1024"] + sorted(BATCHES),
                     help="ipm1024: the single-system workload (default); the others are the batched ones")
     ap.add_argument("--sweeps", type=int, default=4, help="refinement sweeps of the mixed path (at most)")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (ipm1024)")
+    ap.add_argument("--P", type=int, default=0,
+                    help="batched workloads: the two-level method with P segments per system (default: tuned)")
+    ap.add_argument("--partition", default="balanced", choices=["balanced", "paper"],
+                    help="segment lengths: pairing-aware balanced, or Eq. (13) of the paper")
     ap.add_argument("--tol", type=float, default=1e-14,
                     help="refinement stop of the mixed path: a system stops once its eta is below this")
     args = ap.parse_args()
@@ -506,7 +531,8 @@ def main():
         dist.init_process_group("nccl")
     import paper_2511_00946_gb300 as kkt
 
-    D, E, G, R, b = workload(rank)
+    D, E, G, R, b = workload(rank, args.nrhs)
+    part = kkt.KKT_PARTITION_BALANCED if args.partition == "balanced" else kkt.KKT_PARTITION_PAPER
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     Dd, Ed, Gd, Rd, b0 = dev(D), dev(E), dev(G), dev(R), dev(b)
     bd = b0.clone()
@@ -518,8 +544,8 @@ def main():
         plan = [int(v) for v in args.levels.split(",")]
     else:
         best = None
-        for p in candidate_plans(kkt):
-            h = kkt.kkt_create_plan(N_STAGES, N_BLOCK, M_ARROW, p, kkt.KKT_PARTITION_BALANCED)
+        for p in candidate_plans(kkt, part):
+            h = kkt.kkt_create_plan(N_STAGES, N_BLOCK, M_ARROW, p, part)
             ts = []
             for it in range(9):
                 bd.copy_(b0)
@@ -536,9 +562,9 @@ def main():
             if best is None or t < best[0]:
                 best = (t, p)
         plan = best[1]
-    h = kkt.kkt_create_plan(N_STAGES, N_BLOCK, M_ARROW, plan, kkt.KKT_PARTITION_BALANCED)
+    h = kkt.kkt_create_plan(N_STAGES, N_BLOCK, M_ARROW, plan, part)
     fl = kkt.kkt_flops(h)
-    launch_names, launch_flops = per_launch_flops(kkt, plan)
+    launch_names, launch_flops = per_launch_flops(kkt, plan, part, args.nrhs)
     nl = len(launch_names)
 
     launch_ev = [torch.cuda.Event(enable_timing=True) for _ in range(nl)]
@@ -548,7 +574,8 @@ def main():
     kkt.kkt_set_launch_events(h, launch_ev)
 
     def launch_step():
-        # factor + solve in one pass: the right-hand side bordered onto the arrow
+        # factor + solve: with one right-hand side in one pass (bordered onto
+        # the arrow), with several the factorization and then the solve
         kkt.kkt_factor_solve(h, Dd, Ed, Gd, Rd, bd)
 
     # one step (factor + solve, every level) captured once in a CUDA graph and
@@ -608,7 +635,9 @@ def main():
         ms = float(t.item())
     value = world * 1000.0 / ms
     x = bd.cpu().numpy()
-    eta, relres = backward_error(D, E, G, R, x, b)
+    errs = [backward_error(D, E, G, R, x.reshape(x.shape[0], -1)[:, c], b.reshape(b.shape[0], -1)[:, c])
+            for c in range(args.nrhs)]
+    eta, relres = max(e[0] for e in errs), max(e[1] for e in errs)
 
     # --- end to end through the public API with host buffers (pinned)
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -652,7 +681,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "levels": plan, "partition": "balanced", "precision": "fp64",
+            "config": {"workload": WORKLOAD.format(nrhs=args.nrhs), "levels": plan, "partition": args.partition,
+                       "precision": "fp64",
                        "l2": "flushed before every timed step (256 MiB write)",
                        "replicas": world},
             "error": {"backward_error": eta, "relative_residual": relres},

@@ -357,9 +357,10 @@ __device__ void trsm_panel(TZ* Z, int ldz, int r0, int r1, const TZ* M, int ldm,
 // T[a][b] -= sum_t Z[a][t] Z[b][t] for ra0 <= a < ra1, cb0 <= b <= a (cb0 <=
 // ra0: a rectangle of full rows beside a lower triangle; ra0 = cb0 is a plain
 // lower triangle). Panel rows below `zsplit` are read from Zlo, the others
-// from Z (same leading dimension and row numbering). The dot product is
-// formed in TZ (FP64, or FP32 in the mixed variant) and subtracted from the
-// FP64 accumulator once.
+// from Z (same leading dimension and row numbering). FP64 panels: T_ab takes
+// the rank-1 updates of the columns t = 0, 1, .. in turn, each one fma. FP32
+// panels (mixed variant): the dot product is formed in FP32 and subtracted
+// from the FP64 accumulator once.
 template <typename TZ>
 __device__ void syrk_trap(double* T, int ldt, const TZ* Zlo, const TZ* Z, int zsplit, int ldz, int ra0,
                           int ra1, int cb0, int n, Grp g) {
@@ -375,16 +376,25 @@ __device__ void syrk_trap(double* T, int ldt, const TZ* Zlo, const TZ* Z, int zs
     }
     const TZ* zi = (a < zsplit ? Zlo : Z) + a * ldz;
     const TZ* zj = (b < zsplit ? Zlo : Z) + b * ldz;
-    TZ s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    int t = 0;
-    for (; t + 3 < n; t += 4) {
-      s0 = fma(zi[t], zj[t], s0);
-      s1 = fma(zi[t + 1], zj[t + 1], s1);
-      s2 = fma(zi[t + 2], zj[t + 2], s2);
-      s3 = fma(zi[t + 3], zj[t + 3], s3);
+    if (sizeof(TZ) == 8) {
+      // FP64: rank-1 updates in column order, T_ab = fma(-z_at, z_bt, T_ab): no
+      // partial sums to combine, and one dependent chain per element already
+      // keeps an FP64 pipe busy on this part
+      double acc = T[a * ldt + b];
+      for (int t = 0; t < n; ++t) acc = fma(-(double)zi[t], (double)zj[t], acc);
+      T[a * ldt + b] = acc;
+    } else {
+      TZ s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      int t = 0;
+      for (; t + 3 < n; t += 4) {
+        s0 = fma(zi[t], zj[t], s0);
+        s1 = fma(zi[t + 1], zj[t + 1], s1);
+        s2 = fma(zi[t + 2], zj[t + 2], s2);
+        s3 = fma(zi[t + 3], zj[t + 3], s3);
+      }
+      for (; t < n; ++t) s0 = fma(zi[t], zj[t], s0);
+      T[a * ldt + b] -= (double)((s0 + s1) + (s2 + s3));
     }
-    for (; t < n; ++t) s0 = fma(zi[t], zj[t], s0);
-    T[a * ldt + b] -= (double)((s0 + s1) + (s2 + s3));
   }
   gsync(g);
 }
