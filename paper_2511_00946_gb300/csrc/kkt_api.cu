@@ -154,6 +154,7 @@ struct kkt_handle {
   struct Group {
     int off, cnt, n, m;
     bool warp;
+    bool fill;  // some task has fill-in rows (its system has P > 1 at this level)
   };
   std::vector<std::vector<Group>> fac_groups, bwd_groups;
   std::vector<int> bwd_off, bwd_cnt;         // task ranges per level (backward)
@@ -388,12 +389,18 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
     std::vector<int> sys_at;
     for (int s = 0; s < count; ++s)
       if ((backward ? l + 1 : l) < (int)h->sys[s].lv.size()) sys_at.push_back(s);
-    std::stable_sort(sys_at.begin(), sys_at.end(), [&](int a, int b) { return h->sys[a].n < h->sys[b].n; });
+    // one launch per block-size class and per layout: levels with P = 1 (no
+    // fill-in rows) get the compact shared-memory layout and more CTAs per SM
+    auto fill_of = [&](int s) { return h->sys[s].lv[l].P > 1; };
+    std::stable_sort(sys_at.begin(), sys_at.end(), [&](int a, int b) {
+      return h->sys[a].n != h->sys[b].n ? h->sys[a].n < h->sys[b].n : fill_of(a) < fill_of(b);
+    });
     for (int s : sys_at) {
       const SysPlan& sp = h->sys[s];
-      const bool warp = sp.n <= kkt::kWarpMaxN;
-      if (groups.empty() || groups.back().warp != warp || (!warp && groups.back().n != sp.n))
-        groups.push_back(kkt_handle::Group{(int)tasks.size(), 0, sp.n, sp.m, warp});
+      const bool warp = sp.n <= kkt::kWarpMaxN, fill = fill_of(s);
+      if (groups.empty() || groups.back().warp != warp || (!warp && groups.back().n != sp.n) ||
+          groups.back().fill != fill)
+        groups.push_back(kkt_handle::Group{(int)tasks.size(), 0, sp.n, sp.m, warp, fill});
       kkt_handle::Group& gr = groups.back();
       for (int k = 0; k < sp.lv[l].P; ++k) tasks.push_back(Task{h->desc_of[s][l], k});
       gr.cnt += sp.lv[l].P;
@@ -804,10 +811,11 @@ kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const dou
   for (int l = 0; l < h->maxL; ++l)
     for (const kkt_handle::Group& gr : h->fac_groups[l]) {
       const int e = gr.warp ? kkt::launch_factor_w(h->ddesc, h->dtasks + gr.off, gr.cnt, gr.n, gr.m,
-                                                   h->level_mixed[l], D, E, G, R, h->dinfo, stream)
+                                                   h->level_mixed[l], D, E, G, R, h->dinfo, stream, nullptr, 1,
+                                                   gr.fill)
                             : kkt::launch_factor(h->ddesc, h->dtasks + gr.off, gr.cnt, gr.n, gr.m,
                                                  h->level_mixed[l], level_paired(h, l), D, E, G, R,
-                                                 h->dinfo, stream);
+                                                 h->dinfo, stream, nullptr, 1, gr.fill);
       if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
     }
   h->factored = true;
@@ -879,9 +887,10 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
   for (int l = 0; l < h->maxL; ++l)
     for (const kkt_handle::Group& gr : h->fac_groups[l]) {
       const int e = gr.warp ? kkt::launch_factor_w(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0, D, E,
-                                                   h->Gb, h->Rb, h->dinfo, stream, b, ldb)
+                                                   h->Gb, h->Rb, h->dinfo, stream, b, ldb, gr.fill)
                             : kkt::launch_factor(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0,
-                                                 level_paired(h, l), D, E, h->Gb, h->Rb, h->dinfo, stream, b, ldb);
+                                                 level_paired(h, l), D, E, h->Gb, h->Rb, h->dinfo, stream, b, ldb,
+                                                 gr.fill);
       if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
     }
   h->factored = true;

@@ -118,24 +118,30 @@ struct Info {
 // FP64 buffers are sized for q = max(n, m) because the corner (m x m) reuses
 // them. zb = bytes per panel element (8: FP64 path, 4: mixed). Odd leading
 // dimensions keep row- and column-wise accesses free of bank conflicts.
+// `fill`: the level has fill-in rows (P > 1). A level without them (P = 1,
+// the last level of its systems) keeps only the E- and G-rows of the panel
+// and of T in shared memory (Rs = n + m instead of R = 2n + m rows), which
+// lets more CTAs share an SM; R stays the panel height of the factor in
+// global memory.
 struct FacLayout {
-  int q, R, ldD, ldZ, ldT, oDfac, oM, oRinv, oRinvZ, oZ, oT, oTab, oDfac2, oRinv2, oCorner, total;
+  int q, R, Rs, ldD, ldZ, ldT, oDfac, oM, oRinv, oRinvZ, oZ, oT, oTab, oDfac2, oRinv2, oCorner, total;
 };
 __host__ __device__ inline int kkt_align16(int b) { return (b + 15) & ~15; }
-__host__ __device__ inline FacLayout fac_layout(int n, int m, int zb) {
+__host__ __device__ inline FacLayout fac_layout(int n, int m, int zb, bool fill = true) {
   FacLayout L;
   L.q = n > m ? n : m;
   L.R = 2 * n + m;
+  L.Rs = fill ? L.R : n + m;
   L.ldD = L.q | 1;
   L.ldZ = n | 1;
-  L.ldT = L.R | 1;
+  L.ldT = L.Rs | 1;
   L.oDfac = 0;
   L.oM = L.oDfac + kkt_align16(8 * L.q * L.ldD);
   L.oRinv = L.oM + kkt_align16(zb * n * L.ldD);
   L.oRinvZ = L.oRinv + kkt_align16(8 * L.q);
   L.oZ = L.oRinvZ + kkt_align16(zb * L.q);
-  L.oT = L.oZ + kkt_align16(zb * L.R * L.ldZ);
-  L.oTab = L.oT + kkt_align16(8 * L.R * L.ldT);  // potrf element table, q(q-1)/2 ints
+  L.oT = L.oZ + kkt_align16(zb * L.Rs * L.ldZ);
+  L.oTab = L.oT + kkt_align16(8 * L.Rs * L.ldT);  // potrf element table, q(q-1)/2 ints
   // second pivot block and rinv: the next stage's pivot factorization runs
   // while the current stage's factor blocks are still being written
   L.oDfac2 = L.oTab + kkt_align16(4 * (L.q * (L.q - 1) / 2 + 1));
@@ -147,8 +153,8 @@ __host__ __device__ inline FacLayout fac_layout(int n, int m, int zb) {
 }
 // One warp's slice for a small-block segment task (k_factor_w): the same
 // blocks without the second pivot buffer, and an m x m corner sum.
-__host__ __device__ inline FacLayout fac_layout_w(int n, int m, int zb) {
-  FacLayout L = fac_layout(n, m, zb);
+__host__ __device__ inline FacLayout fac_layout_w(int n, int m, int zb, bool fill = true) {
+  FacLayout L = fac_layout(n, m, zb, fill);
   L.oDfac2 = L.oRinv2 = 0;
   L.oCorner = L.oTab + kkt_align16(4 * (L.q * (L.q - 1) / 2 + 1));
   L.total = L.oCorner + kkt_align16(8 * (m * m > 0 ? m * m : 1));
@@ -203,12 +209,14 @@ constexpr int kResPartDoubles = kMaxM * kRhsChunk + 4 * kRhsChunk;
 // (null = never skip), a set flag makes the system's CTAs return at once.
 // one warp per task (blocks n <= kWarpMaxN), several tasks per CTA
 // (b, ldb: where the forward solution y of a bordered pass is written; unused otherwise)
+// (fill: some task of the launch has fill-in rows; 0 sizes shared memory for
+// the compact layout of levels with P = 1)
 int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
                     const double* D, const double* E, const double* G, const double* R, Info* info,
-                    void* stream, double* b = nullptr, int ldb = 1);
+                    void* stream, double* b = nullptr, int ldb = 1, int fill = 1);
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
-                  void* stream, double* b = nullptr, int ldb = 1);
+                  void* stream, double* b = nullptr, int ldb = 1, int fill = 1);
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
                    double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0);
 int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
@@ -242,7 +250,7 @@ int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const 
 // D (every system's stage blocks) <- identity blocks, R <- identity corners
 int launch_fill_identity(const LevelDesc* d, const int* sys_desc, int count, double* D, double* R,
                          void* stream);
-size_t factor_smem_bytes(int maxn, int maxm, int mixed);
+size_t factor_smem_bytes(int maxn, int maxm, int mixed, int fill = 1);
 size_t solve_smem_bytes(int maxn, int maxm, int single);
 
 }  // namespace kkt

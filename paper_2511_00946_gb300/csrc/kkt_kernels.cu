@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
   const Task tk = tasks[pair ? blockIdx.x >> 1 : blockIdx.x];
   const LevelDesc& d = descs[tk.desc];
   constexpr bool mixed = sizeof(TZ) == 4;
-  const FacLayout lay = fac_layout(d.n, d.m, (int)sizeof(TZ));
+  const FacLayout lay = fac_layout(d.n, d.m, (int)sizeof(TZ), d.P > 1);
   const FacCtx<TZ> cx(d, tk.seg, smraw, lay, uD, uE, uG);
   const int n = cx.n, m = cx.m, R = cx.R, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG, oW = cx.oW;
   double* const Dfac = cx.Dfac;
@@ -771,7 +771,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __re
   const bool wr = g.hasW && (mode != kPair || rank == 1);  // this CTA holds the W rows
 
   if (threadIdx.x == 0) bad = 0;
-  for (int e = threadIdx.x; e < R * ldT; e += blockDim.x) T[e] = 0.0;
+  for (int e = threadIdx.x; e < lay.Rs * ldT; e += blockDim.x) T[e] = 0.0;
   if (eg) potrf_table(tab, n);
   __syncthreads();
   cx.load_first(eg, wr, cta_grp());
@@ -1007,12 +1007,12 @@ __global__ void __launch_bounds__(256) k_factor_w(const LevelDesc* __restrict__ 
   const Task tk = tasks[t];
   const LevelDesc& d = descs[tk.desc];
   unsigned char* sm = smraw + (size_t)wid * slice;
-  const FacLayout lay = fac_layout_w(d.n, d.m, (int)sizeof(TZ));
+  const FacLayout lay = fac_layout_w(d.n, d.m, (int)sizeof(TZ), d.P > 1);
   const FacCtx<TZ> cx(d, tk.seg, sm, lay, uD, uE, uG);
   const int n = cx.n, m = cx.m, R = cx.R, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG;
   const SegGeom g = cx.g;
   const Grp W{lane, 32, -1};
-  for (int e = lane; e < R * ldT; e += 32) cx.T[e] = 0.0;
+  for (int e = lane; e < lay.Rs * ldT; e += 32) cx.T[e] = 0.0;
   pair_table_w(cx.tab, n, lane);
   cx.load_first(true, g.hasW, W);
   __syncwarp();
@@ -1860,8 +1860,8 @@ int set_smem(const void* fn, size_t bytes) {
 
 }  // namespace
 
-size_t factor_smem_bytes(int n, int m, int mixed) {
-  return (size_t)fac_layout(n, m, mixed ? 4 : 8).total;
+size_t factor_smem_bytes(int n, int m, int mixed, int fill) {
+  return (size_t)fac_layout(n, m, mixed ? 4 : 8, fill != 0).total;
 }
 
 size_t solve_smem_bytes(int n, int m, int single) {
@@ -1870,9 +1870,9 @@ size_t solve_smem_bytes(int n, int m, int single) {
 
 int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
                     const double* D, const double* E, const double* G, const double* R, Info* info,
-                    void* stream, double* b, int ldb) {
+                    void* stream, double* b, int ldb, int fill) {
   if (ntasks <= 0) return 0;
-  const int slice = fac_layout_w(maxn, maxm, mixed ? 4 : 8).total;
+  const int slice = fac_layout_w(maxn, maxm, mixed ? 4 : 8, fill != 0).total;
   const int wpc = std::max(1, std::min(8, (200 * 1024) / slice));  // tasks (warps) per CTA
   const size_t sm = (size_t)wpc * slice;
   const void* fn = mixed ? (const void*)k_factor_w<float> : (const void*)k_factor_w<double>;
@@ -1888,9 +1888,9 @@ int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
 
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
-                  void* stream, double* b, int ldb) {
+                  void* stream, double* b, int ldb, int fill) {
   if (ntasks <= 0) return 0;
-  const size_t sm = factor_smem_bytes(maxn, maxm, mixed);
+  const size_t sm = factor_smem_bytes(maxn, maxm, mixed, fill);
   const void* fn = mixed ? (const void*)k_factor<float> : (const void*)k_factor<double>;
   int e = set_smem(fn, sm);
   if (e) return e;
