@@ -735,8 +735,12 @@ struct FacCtx {
   }
 };
 
-template <typename TZ>
-__global__ void __launch_bounds__(kFactorThreads) k_factor(const LevelDesc* __restrict__ descs,
+// MINB: CTAs per SM the register allocation must allow. Launches of CTA pairs
+// (one CTA per SM, latency-bound) take the unconstrained allocation (1);
+// the others four (at most 64 registers), so that several segment CTAs share
+// an SM when shared memory allows it.
+template <typename TZ, int MINB>
+__global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc* __restrict__ descs,
                                                            const Task* __restrict__ tasks,
                                                            const double* __restrict__ uD,
                                                            const double* __restrict__ uE,
@@ -995,7 +999,7 @@ __device__ void trsm_w(TZ* Z, int ldz, int r0, int r1, const TZ* M, int ldm, int
 }
 
 template <typename TZ>
-__global__ void __launch_bounds__(256) k_factor_w(const LevelDesc* __restrict__ descs,
+__global__ void __launch_bounds__(256, 4) k_factor_w(const LevelDesc* __restrict__ descs,
                                                   const Task* __restrict__ tasks, int ntasks,
                                                   const double* __restrict__ uD, const double* __restrict__ uE,
                                                   const double* __restrict__ uG, const double* __restrict__ uR,
@@ -1891,7 +1895,8 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
                   void* stream, double* b, int ldb, int fill) {
   if (ntasks <= 0) return 0;
   const size_t sm = factor_smem_bytes(maxn, maxm, mixed, fill);
-  const void* fn = mixed ? (const void*)k_factor<float> : (const void*)k_factor<double>;
+  const void* fn = mixed ? (pair ? (const void*)k_factor<float, 1> : (const void*)k_factor<float, 4>)
+                          : (pair ? (const void*)k_factor<double, 1> : (const void*)k_factor<double, 4>);
   int e = set_smem(fn, sm);
   if (e) return e;
   cudaLaunchConfig_t cfg = {};
@@ -1909,8 +1914,11 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
     cfg.numAttrs = 1;
   }
   const int p = pair ? 1 : 0;
-  if (mixed) return (int)cudaLaunchKernelEx(&cfg, k_factor<float>, d, t, D, E, G, R, info, p, b, ldb);
-  return (int)cudaLaunchKernelEx(&cfg, k_factor<double>, d, t, D, E, G, R, info, p, b, ldb);
+  if (mixed)
+    return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<float, 1>, d, t, D, E, G, R, info, p, b, ldb)
+                : (int)cudaLaunchKernelEx(&cfg, k_factor<float, 4>, d, t, D, E, G, R, info, p, b, ldb);
+  return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<double, 1>, d, t, D, E, G, R, info, p, b, ldb)
+              : (int)cudaLaunchKernelEx(&cfg, k_factor<double, 4>, d, t, D, E, G, R, info, p, b, ldb);
 }
 
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
