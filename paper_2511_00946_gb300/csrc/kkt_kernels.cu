@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 
 #include "kkt_internal.h"
 
@@ -1858,8 +1860,18 @@ __global__ void k_border(const LevelDesc* __restrict__ descs, const int* __restr
     }
 }
 
+// Raises a kernel's dynamic shared memory limit to `bytes` (never lowers it:
+// a captured graph replays earlier launches of the same kernel, which may
+// need more than the latest one).
 int set_smem(const void* fn, size_t bytes) {
-  return (int)cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> granted;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& g = granted[fn];
+  if (bytes <= g) return 0;
+  const int e = (int)cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (!e) g = bytes;
+  return e;
 }
 
 }  // namespace
