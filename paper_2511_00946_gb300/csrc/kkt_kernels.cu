@@ -1540,6 +1540,18 @@ __global__ void __launch_bounds__(256) k_backward_w(const LevelDesc* __restrict_
 // sides of the system together.
 // ---------------------------------------------------------------------------
 
+// |v| as a float for the |Psi| row sums that scale eta: the exponent rebased
+// and the mantissa cut to 20 bits with integer operations only (no FP64
+// instruction), so never above |v|; 0 below the float range, the largest
+// float above it. The sums then run in FP32: about 1e-6 relative, ample for
+// the scale of a backward error.
+__device__ __forceinline__ float abs_lo(double v) {
+  const int hi = __double2hiint(v) & 0x7fffffff;
+  const int e = hi - (896 << 20);  // exponent bias 1023 -> 127
+  if (e >= (255 << 20)) return 3.4028234e38f;
+  return e > 0 ? __int_as_float(e << 3) : 0.0f;
+}
+
 // x += c over the stage rows of one chunk; each system's first chunk also
 // does the g rows. c has leading dimension kRhsChunk.
 __global__ void k_axpy(const LevelDesc* __restrict__ descs, const ResTask* __restrict__ tasks,
@@ -1602,7 +1614,8 @@ __global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ 
   const bool lane_ok = packed ? sj < spw : lane < n;
   const bool two = n > 32;  // warp-uniform: a second row per lane
   const int src0 = packed ? sj * n : 0;  // lane holding row 0 of this lane's stage
-  double mr = 0.0, mx = 0.0, mb = 0.0, mrow = 0.0;
+  double mr = 0.0, mx = 0.0, mb = 0.0;
+  float mrow = 0.0f;
   auto xat = [&](long long row, int col) { return x[(size_t)row * ldx + col]; };
   for (int col = 0; col < nr; ++col) {
     const double xg_l = lane < m ? xat(d.rowG + lane, col) : 0.0;  // x_g, lane q holds row q
@@ -1622,7 +1635,8 @@ __global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ 
       const double xc0 = ok0 ? xat(rb + i0, col) : 0.0, xc1 = ok1 ? xat(rb + i1, col) : 0.0;
       const double xp0 = (ok0 && hp) ? xat(rb - n + i0, col) : 0.0, xp1 = (ok1 && hp) ? xat(rb - n + i1, col) : 0.0;
       const double xn0 = (ok0 && hn) ? xat(rb + n + i0, col) : 0.0, xn1 = (ok1 && hn) ? xat(rb + n + i1, col) : 0.0;
-      double acc0 = 0.0, acc1 = 0.0, rs0 = 0.0, rs1 = 0.0;
+      double acc0 = 0.0, acc1 = 0.0;
+      float rs0 = 0.0f, rs1 = 0.0f;
       // D_j x_j (lower triangle by symmetry), E_{j-1} x_{j-1}, E_j^T x_{j+1}
       for (int k = 0; k < n; ++k) {
         const int sl = packed ? src0 + k : (k & 31);
@@ -1634,14 +1648,14 @@ __global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ 
         acc0 = fma(d0, xk, acc0);
         acc0 = fma(p0, xpk, acc0);
         acc0 = fma(q0, xnk, acc0);
-        if (norms) rs0 += (fabs(d0) + fabs(p0)) + fabs(q0);
+        if (norms) rs0 += (abs_lo(d0) + abs_lo(p0)) + abs_lo(q0);
         if (two) {
           const double d1 = k <= a1 ? Dj[a1 * n + k] : Dj[k * n + a1];
           const double p1 = hp ? Ep[a1 * n + k] : 0.0, q1 = hn ? En[k * n + a1] : 0.0;
           acc1 = fma(d1, xk, acc1);
           acc1 = fma(p1, xpk, acc1);
           acc1 = fma(q1, xnk, acc1);
-          if (norms) rs1 += (fabs(d1) + fabs(p1)) + fabs(q1);
+          if (norms) rs1 += (abs_lo(d1) + abs_lo(p1)) + abs_lo(q1);
         }
       }
       if (m) {
@@ -1653,12 +1667,12 @@ __global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ 
           const double g0 = Gj[q * n + a0];
           acc0 = fma(g0, xq, acc0);
           gacc[q] = fma(g0, xc0, gacc[q]);  // xc0 = 0 on idle lanes
-          if (norms) rs0 += fabs(g0);
+          if (norms) rs0 += abs_lo(g0);
           if (two) {
             const double g1 = Gj[q * n + a1];
             acc1 = fma(g1, xq, acc1);
             gacc[q] = fma(g1, xc1, gacc[q]);
-            if (norms) rs1 += fabs(g1);
+            if (norms) rs1 += abs_lo(g1);
           }
         }
       }
@@ -1666,13 +1680,13 @@ __global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ 
         const double bv = b[(size_t)(rb + i0) * ldb + col], r = bv - acc0;
         c[(size_t)(rb + i0) * kRhsChunk + col] = r;
         mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xc0));
-        if (norms) mrow = fmax(mrow, rs0);
+        if (norms) mrow = fmaxf(mrow, rs0);
       }
       if (ok1) {
         const double bv = b[(size_t)(rb + i1) * ldb + col], r = bv - acc1;
         c[(size_t)(rb + i1) * kRhsChunk + col] = r;
         mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xc1));
-        if (norms) mrow = fmax(mrow, rs1);
+        if (norms) mrow = fmaxf(mrow, rs1);
       }
     }
     // g-row partials of this column: lane sums, then a shuffle tree
@@ -1684,24 +1698,24 @@ __global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ 
       if (lane == 0) part[q * kRhsChunk + col] = v;
     }
   }
-  double gab = 0.0;  // |G| sum of g row `lane` (lane < m) over the task's stages
+  float gab = 0.0f;  // |G| sum of g row `lane` (lane < m) over the task's stages
   if (norms && m && lane < m)
     for (int j = j0; j < j1; ++j) {
       const double* Gj = G + (size_t)j * mn;
-      for (int i = 0; i < n; ++i) gab += fabs(Gj[lane * n + i]);
+      for (int i = 0; i < n; ++i) gab += abs_lo(Gj[lane * n + i]);
     }
   for (int o = 16; o > 0; o >>= 1) {
     mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
     mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-    if (norms) mrow = fmax(mrow, __shfl_xor_sync(0xffffffffu, mrow, o));
+    if (norms) mrow = fmaxf(mrow, __shfl_xor_sync(0xffffffffu, mrow, o));
   }
   double* pm = part + kMaxM * kRhsChunk;
   if (lane == 0) {
     pm[0] = mr; pm[1] = mx; pm[2] = mb;
-    if (norms) pm[3] = mrow;
+    if (norms) pm[3] = (double)mrow;
   }
-  if (norms && lane < m) pm[4 + lane] = gab;
+  if (norms && lane < m) pm[4 + lane] = (double)gab;
 }
 
 // Finish the g rows of one system from the chunk partials, then eta and the
