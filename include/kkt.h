@@ -203,6 +203,24 @@ kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream);
 kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, const double* G,
                             const double* R, double* b, int nrhs, int ldb, void* stream);
 
+/* kkt_factor_solve from HOST buffers: D, E, G, R and b are host pointers in
+ * the layout above (page-locked memory lets the copies run asynchronously);
+ * x is written back to b (ldb >= nrhs) when the stream reaches the end of the
+ * call. The handle keeps device copies of the inputs (allocated by the first
+ * call, which therefore must not run inside a stream capture; later calls
+ * may be captured). For one system with the bordered pass (FP64, nrhs = 1,
+ * P >= 2 level-1 segments) the copy of the stage blocks is split at separator
+ * stages into up to four chunks on an internal stream, and each chunk's
+ * level-1 segments start on a stream of their own as soon as their blocks
+ * have arrived (the segments of Algorithm 1 are independent), so the
+ * transfer overlaps the level-1 factorization; the arrow blocks, the corner
+ * and b are copied first (the bordered arrow needs them whole). Otherwise
+ * the inputs are copied on `stream` and kkt_factor_solve runs on the device
+ * copies. The result is that of kkt_factor_solve on the same inputs, bit for
+ * bit. Launch events are not recorded. */
+kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E, const double* G,
+                                 const double* R, double* b, int nrhs, int ldb, void* stream);
+
 /* Mixed-precision iterative refinement: x = Psi^{-1} b by x_0 = 0,
  * c <- b; then `sweeps` times: c <- (L-hat L-hat^T)^{-1} c with the current
  * factor (FP32 substitutions on mixed levels), x <- x + c, c <- b - Psi x in

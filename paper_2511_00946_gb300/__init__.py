@@ -26,7 +26,7 @@ RHS_CHUNK = 16
 
 EXPORTED = [
     "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_batch_create_tuned", "kkt_destroy",
-    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_factor_solve", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta",
+    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_factor_solve", "kkt_factor_solve_host", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta",
     "kkt_get_info",
     "kkt_get_factor", "kkt_set_pairing", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
 ]
@@ -64,6 +64,7 @@ _sig = {
     "kkt_factor": [_vp, _vp, _vp, _vp, _vp, _vp],
     "kkt_solve": [_vp, _vp, _i, _i, _vp],
     "kkt_factor_solve": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp],
+    "kkt_factor_solve_host": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp],
     "kkt_solve_refined": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i, _i, _i, ctypes.c_double, _vp],
     "kkt_refine_eta": [_vp, _i, _dp],
     "kkt_solve_adjoint": [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i, _vp, _i, _i, _vp, _vp, _vp, _vp, _i, _vp],
@@ -218,6 +219,34 @@ def kkt_factor_solve(h: int, D, E, G, R, b, nrhs: int | None = None, ldb: int | 
         ldb = 1 if b.dim() == 1 else b.shape[1]
     _check(_lib.kkt_factor_solve(h, _ptr(D), _ptr(E), _ptr(G), _ptr(R), _ptr(b), nrhs, ldb, _stream(stream)),
            "kkt_factor_solve")
+
+
+def _host_ptr(x):
+    """Host pointer of a contiguous float64 CPU tensor or NumPy array (None
+    passes through); page-locked torch tensors let the copies run async."""
+    if x is None:
+        return None
+    import numpy as _np
+    if isinstance(x, _np.ndarray):
+        if x.dtype != _np.float64 or not x.flags.c_contiguous:
+            raise TypeError("expected a C-contiguous float64 array")
+        return x.ctypes.data
+    import torch
+    if not isinstance(x, torch.Tensor) or x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+        raise TypeError("expected a contiguous float64 host tensor or array")
+    return x.data_ptr()
+
+
+def kkt_factor_solve_host(h: int, D, E, G, R, b, nrhs: int | None = None, ldb: int | None = None, stream=None):
+    """kkt_factor_solve from host buffers (see the C header): the transfer of
+    the stage blocks overlaps the level-1 factorization; b (host) receives x
+    when `stream` reaches the end of the call."""
+    if nrhs is None:
+        nrhs = 1 if b.ndim == 1 else b.shape[1]
+    if ldb is None:
+        ldb = 1 if b.ndim == 1 else b.shape[1]
+    _check(_lib.kkt_factor_solve_host(h, _host_ptr(D), _host_ptr(E), _host_ptr(G), _host_ptr(R), _host_ptr(b),
+                                      nrhs, ldb, _stream(stream)), "kkt_factor_solve_host")
 
 
 def kkt_solve_refined(h: int, D, E, G, R, b, x, nrhs: int | None = None, ldb: int | None = None,

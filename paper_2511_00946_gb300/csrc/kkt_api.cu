@@ -187,6 +187,14 @@ struct kkt_handle {
   long long max_gb = 0;                      // largest bordered arrow of one system (elements)
   std::vector<int> level_top;                // some system's top level is this level
   int pair_policy = KKT_PAIR_AUTO;
+  // kkt_factor_solve_host: device copies of the inputs and the streams and
+  // events of the overlapped transfer (created by the first call)
+  static constexpr int kHostChunks = 4;
+  void* hs_mem = nullptr;
+  double *hsD = nullptr, *hsE = nullptr, *hsG = nullptr, *hsR = nullptr, *hsB = nullptr;
+  int hs_nrhs = 0;                           // columns the b copy has room for
+  cudaStream_t hs_copy = nullptr, hs_lvl[kHostChunks] = {};
+  cudaEvent_t hs_ev_border = nullptr, hs_ev_copy[kHostChunks] = {}, hs_ev_lvl[kHostChunks] = {};
 };
 
 constexpr int kMaxSweeps = 16;
@@ -740,6 +748,14 @@ kkt_status kkt_batch_create_tuned(int count, const int* N, const int* n, const i
 kkt_status kkt_destroy(kkt_handle* h) {
   if (!h) return KKT_OK;
   if (h->dmem) cudaFree(h->dmem);
+  if (h->hs_mem) cudaFree(h->hs_mem);
+  if (h->hs_copy) cudaStreamDestroy(h->hs_copy);
+  if (h->hs_ev_border) cudaEventDestroy(h->hs_ev_border);
+  for (int c = 0; c < kkt_handle::kHostChunks; ++c) {
+    if (h->hs_lvl[c]) cudaStreamDestroy(h->hs_lvl[c]);
+    if (h->hs_ev_copy[c]) cudaEventDestroy(h->hs_ev_copy[c]);
+    if (h->hs_ev_lvl[c]) cudaEventDestroy(h->hs_ev_lvl[c]);
+  }
   delete h;
   return KKT_OK;
 }
@@ -896,6 +912,127 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
   h->factored = true;
   h->cur_b = true;
   return solve_chunk(h, b, ldb, 1, nullptr, stream, &li, 1);
+}
+
+namespace {
+// Device copies of the inputs and the overlap streams of kkt_factor_solve_host.
+kkt_status host_prepare(kkt_handle* h, int nrhs) {
+  if (h->hs_mem && h->hs_nrhs >= nrhs) return KKT_OK;
+  if (h->hs_mem) {
+    cudaFree(h->hs_mem);
+    h->hs_mem = nullptr;
+  }
+  const size_t d8 = sizeof(double);
+  const size_t tot = h->tot_D + h->tot_E + h->tot_G + h->tot_R + h->tot_B * (size_t)nrhs;
+  if (cudaMalloc(&h->hs_mem, std::max<size_t>(tot, 1) * d8) != cudaSuccess) {
+    h->hs_mem = nullptr;
+    return KKT_ERR_CUDA;
+  }
+  double* p = (double*)h->hs_mem;
+  h->hsD = p; p += h->tot_D;
+  h->hsE = p; p += h->tot_E;
+  h->hsG = p; p += h->tot_G;
+  h->hsR = p; p += h->tot_R;
+  h->hsB = p;
+  h->hs_nrhs = nrhs;
+  if (!h->hs_copy) {
+    if (cudaStreamCreateWithFlags(&h->hs_copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->hs_ev_border, cudaEventDisableTiming) != cudaSuccess)
+      return KKT_ERR_CUDA;
+    for (int c = 0; c < kkt_handle::kHostChunks; ++c)
+      if (cudaStreamCreateWithFlags(&h->hs_lvl[c], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->hs_ev_copy[c], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->hs_ev_lvl[c], cudaEventDisableTiming) != cudaSuccess)
+        return KKT_ERR_CUDA;
+  }
+  return KKT_OK;
+}
+}  // namespace
+
+kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E, const double* G,
+                                 const double* R, double* b, int nrhs, int ldb, void* stream) {
+  if (!h || !D || !b || nrhs < 1 || ldb < nrhs) return KKT_ERR_ARG;
+  if (h->tot_E > 0 && !E) return KKT_ERR_ARG;
+  if (h->maxm > 0 && (!G || !R)) return KKT_ERR_ARG;
+  const kkt_status ps = host_prepare(h, nrhs);
+  if (ps != KKT_OK) return ps;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t d8 = sizeof(double);
+  auto h2d = [&](double* dst, const double* src, size_t cnt, cudaStream_t st) {
+    return cnt == 0 || cudaMemcpyAsync(dst, src, cnt * d8, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  };
+  // b: (N n + m) rows of ldb on the host, nrhs packed columns on the device
+  const bool b_in = cudaMemcpy2DAsync(h->hsB, nrhs * d8, b, ldb * d8, nrhs * d8, h->tot_B,
+                                      cudaMemcpyHostToDevice, s) == cudaSuccess;
+  auto b_out = [&]() {
+    return cudaMemcpy2DAsync(b, ldb * d8, h->hsB, nrhs * d8, nrhs * d8, h->tot_B, cudaMemcpyDeviceToHost, s) ==
+                   cudaSuccess
+               ? KKT_OK
+               : KKT_ERR_CUDA;
+  };
+  if (!b_in) return KKT_ERR_CUDA;
+  const bool chunked = h->count == 1 && h->border && nrhs == 1 && h->sys[0].lv[0].P >= 2 &&
+                       h->fac_groups[0].size() == 1;
+  if (!chunked) {
+    if (!h2d(h->hsD, D, h->tot_D, s) || !h2d(h->hsE, E, h->tot_E, s) || !h2d(h->hsG, G, h->tot_G, s) ||
+        !h2d(h->hsR, R, h->tot_R, s))
+      return KKT_ERR_CUDA;
+    std::vector<cudaEvent_t> ev;
+    ev.swap(h->events);  // no launch events on this path
+    const kkt_status st = kkt_factor_solve(h, h->hsD, h->tot_E ? h->hsE : nullptr, h->maxm ? h->hsG : nullptr,
+                                           h->maxm ? h->hsR : nullptr, h->hsB, nrhs, nrhs, stream);
+    h->events.swap(ev);
+    return st != KKT_OK ? st : b_out();
+  }
+  // one system, bordered pass: the arrow blocks, the corner and b first (the
+  // bordered arrow copy needs them whole), then the stage blocks in chunks
+  // that end at separator stages, each chunk's level-1 segments on a stream
+  // of their own as soon as their blocks have arrived
+  const SysPlan& sp = h->sys[0];
+  const LevelPlan& L1 = sp.lv[0];
+  const int P = L1.P, K = std::min(kkt_handle::kHostChunks, P);
+  const size_t nn = (size_t)sp.n * sp.n;
+  if (!h2d(h->hsG, G, h->tot_G, s) || !h2d(h->hsR, R, h->tot_R, s)) return KKT_ERR_CUDA;
+  if (kkt::launch_border(h->ddesc_b, h->dsys_desc, h->count, h->max_gb, h->hsG, h->hsR, h->hsB, 1, h->Gb, h->Rb,
+                         stream) ||
+      cudaEventRecord(h->hs_ev_border, s) != cudaSuccess ||
+      cudaStreamWaitEvent(h->hs_copy, h->hs_ev_border, 0) != cudaSuccess)
+    return KKT_ERR_CUDA;
+  const kkt_handle::Group& g1 = h->fac_groups[0][0];
+  for (int c = 0; c < K; ++c) {
+    const int k0 = (int)((long long)P * c / K), k1 = (int)((long long)P * (c + 1) / K);
+    // stages [lo, hi): segments k0..k1-1 with the separator in front of k0
+    const int lo = k0 ? L1.start[k0] - 1 : 0, hi = k1 < P ? L1.start[k1] - 1 : sp.N;
+    const int ehi = std::min(hi, sp.N - 1);
+    if (!h2d(h->hsD + lo * nn, D + lo * nn, (size_t)(hi - lo) * nn, h->hs_copy) ||
+        (ehi > lo && !h2d(h->hsE + lo * nn, E + lo * nn, (size_t)(ehi - lo) * nn, h->hs_copy)) ||
+        cudaEventRecord(h->hs_ev_copy[c], h->hs_copy) != cudaSuccess)
+      return KKT_ERR_CUDA;
+    cudaStream_t ls = h->hs_lvl[c];
+    if (cudaStreamWaitEvent(ls, h->hs_ev_copy[c], 0) != cudaSuccess) return KKT_ERR_CUDA;
+    const Task* t = h->dtasks + g1.off + k0;
+    const int e = g1.warp ? kkt::launch_factor_w(h->ddesc_b, t, k1 - k0, g1.n, g1.m + 1, 0, h->hsD, h->hsE, h->Gb,
+                                                 h->Rb, h->dinfo, ls, h->hsB, 1, g1.fill)
+                          : kkt::launch_factor(h->ddesc_b, t, k1 - k0, g1.n, g1.m + 1, 0, level_paired(h, 0),
+                                               h->hsD, h->hsE, h->Gb, h->Rb, h->dinfo, ls, h->hsB, 1, g1.fill);
+    if (e || cudaEventRecord(h->hs_ev_lvl[c], ls) != cudaSuccess ||
+        cudaStreamWaitEvent(s, h->hs_ev_lvl[c], 0) != cudaSuccess)
+      return KKT_ERR_CUDA;
+  }
+  for (int l = 1; l < h->maxL; ++l)
+    for (const kkt_handle::Group& gr : h->fac_groups[l]) {
+      const int e = gr.warp ? kkt::launch_factor_w(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0,
+                                                   h->hsD, h->hsE, h->Gb, h->Rb, h->dinfo, stream, h->hsB, 1,
+                                                   gr.fill)
+                            : kkt::launch_factor(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0,
+                                                 level_paired(h, l), h->hsD, h->hsE, h->Gb, h->Rb, h->dinfo,
+                                                 stream, h->hsB, 1, gr.fill);
+      if (e) return KKT_ERR_CUDA;
+    }
+  h->factored = true;
+  h->cur_b = true;
+  const kkt_status st = solve_chunk(h, h->hsB, 1, 1, nullptr, stream, nullptr, 1);
+  return st != KKT_OK ? st : b_out();
 }
 
 kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, const double* G,

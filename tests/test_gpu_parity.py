@@ -570,3 +570,45 @@ def test_factor_solve_reports_breakdown(kkt):
         assert info["status"] == kkt.KKT_ERR_NOT_SPD and info["stage"] == 9
     finally:
         kkt.kkt_destroy(h)
+
+
+@pytest.mark.parametrize("N,n,m,levels,nrhs", [
+    (120, 24, 6, [12, 3, 1], 1),     # one system, bordered pass: chunked transfer, 4 level-1 streams
+    (40, 20, 3, [3, 1], 1),          # fewer segments than chunks
+    (60, 8, 4, [6, 1], 1),           # warp-per-task blocks
+    (50, 17, 0, [1], 1),             # one level: the plain path
+    (90, 24, 6, [9, 1], 3),          # several right-hand sides: the plain path
+])
+def test_factor_solve_host_matches_device(kkt, orc, N, n, m, levels, nrhs):
+    """kkt_factor_solve from host buffers (page-locked torch tensors and plain
+    NumPy arrays) returns, bit for bit, what kkt_factor_solve returns on device
+    copies of the same inputs: the chunked transfer only reorders launches of
+    independent segments."""
+    import torch
+    D, E, G, R = gen.ipm(N, n, m, seed=81)
+    b = gen.rhs(N * n + m, nrhs, seed=82).reshape(N * n + m, -1) if nrhs > 1 else gen.rhs(N * n + m, 1, seed=82)
+    h = kkt.kkt_create_plan(N, n, m, levels, kkt.KKT_PARTITION_BALANCED)
+    try:
+        bd = dev(b)
+        kkt.kkt_factor_solve(h, dev(D), dev(E) if N > 1 else None, dev(G) if m else None, dev(R) if m else None, bd)
+        torch.cuda.synchronize()
+        x_dev = bd.cpu().numpy()
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hb = pin(b)
+        kkt.kkt_factor_solve_host(h, pin(D), pin(E) if N > 1 else None, pin(G) if m else None,
+                                  pin(R) if m else None, hb)
+        torch.cuda.synchronize()
+        x_pinned = hb.numpy().copy()
+        nb = np.ascontiguousarray(b).copy()
+        kkt.kkt_factor_solve_host(h, np.ascontiguousarray(D), np.ascontiguousarray(E) if N > 1 else None,
+                                  np.ascontiguousarray(G) if m else None, np.ascontiguousarray(R) if m else None, nb)
+        torch.cuda.synchronize()
+        assert kkt.kkt_get_info(h)["status"] == 0
+    finally:
+        kkt.kkt_destroy(h)
+    np.testing.assert_array_equal(x_pinned, x_dev)
+    np.testing.assert_array_equal(nb, x_dev)
+    for c in range(nrhs):
+        bc = b.reshape(b.shape[0], -1)[:, c]
+        xc = x_dev.reshape(x_dev.shape[0], -1)[:, c]
+        check_solution(orc, D, E, G, R, xc, bc, orc.seq_solve(orc.seq_factor(D, E, G, R), bc), fwd_tol=1e-5)
