@@ -209,12 +209,13 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
  * call. The handle keeps device copies of the inputs (allocated by the first
  * call, which therefore must not run inside a stream capture; later calls
  * may be captured). For one system with the bordered pass (FP64, nrhs = 1,
- * P >= 2 level-1 segments) the copy of the stage blocks is split at separator
- * stages into up to four chunks on an internal stream, and each chunk's
- * level-1 segments start on a stream of their own as soon as their blocks
- * have arrived (the segments of Algorithm 1 are independent), so the
- * transfer overlaps the level-1 factorization; the arrow blocks, the corner
- * and b are copied first (the bordered arrow needs them whole). Otherwise
+ * P >= 2 level-1 segments) the copy of the stage rows of D, E, G and b is
+ * split at separator stages into up to eight chunks on an internal stream,
+ * and each chunk's bordered arrow copy and level-1 segments start on a
+ * stream of their own as soon as its rows have arrived (the segments of
+ * Algorithm 1 are independent), so the transfer overlaps the level-1
+ * factorization; the corner and the g-rows of b travel with the first
+ * chunk. Otherwise
  * the inputs are copied on `stream` and kkt_factor_solve runs on the device
  * copies. The result is that of kkt_factor_solve on the same inputs, bit for
  * bit. Launch events are not recorded. */

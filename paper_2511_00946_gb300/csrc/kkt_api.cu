@@ -189,12 +189,12 @@ struct kkt_handle {
   int pair_policy = KKT_PAIR_AUTO;
   // kkt_factor_solve_host: device copies of the inputs and the streams and
   // events of the overlapped transfer (created by the first call)
-  static constexpr int kHostChunks = 4;
+  static constexpr int kHostChunks = 8;
   void* hs_mem = nullptr;
   double *hsD = nullptr, *hsE = nullptr, *hsG = nullptr, *hsR = nullptr, *hsB = nullptr;
   int hs_nrhs = 0;                           // columns the b copy has room for
   cudaStream_t hs_copy = nullptr, hs_lvl[kHostChunks] = {};
-  cudaEvent_t hs_ev_border = nullptr, hs_ev_copy[kHostChunks] = {}, hs_ev_lvl[kHostChunks] = {};
+  cudaEvent_t hs_ev_start = nullptr, hs_ev_copy[kHostChunks] = {}, hs_ev_lvl[kHostChunks] = {};
 };
 
 constexpr int kMaxSweeps = 16;
@@ -750,7 +750,7 @@ kkt_status kkt_destroy(kkt_handle* h) {
   if (h->dmem) cudaFree(h->dmem);
   if (h->hs_mem) cudaFree(h->hs_mem);
   if (h->hs_copy) cudaStreamDestroy(h->hs_copy);
-  if (h->hs_ev_border) cudaEventDestroy(h->hs_ev_border);
+  if (h->hs_ev_start) cudaEventDestroy(h->hs_ev_start);
   for (int c = 0; c < kkt_handle::kHostChunks; ++c) {
     if (h->hs_lvl[c]) cudaStreamDestroy(h->hs_lvl[c]);
     if (h->hs_ev_copy[c]) cudaEventDestroy(h->hs_ev_copy[c]);
@@ -937,7 +937,7 @@ kkt_status host_prepare(kkt_handle* h, int nrhs) {
   h->hs_nrhs = nrhs;
   if (!h->hs_copy) {
     if (cudaStreamCreateWithFlags(&h->hs_copy, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->hs_ev_border, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&h->hs_ev_start, cudaEventDisableTiming) != cudaSuccess)
       return KKT_ERR_CUDA;
     for (int c = 0; c < kkt_handle::kHostChunks; ++c)
       if (cudaStreamCreateWithFlags(&h->hs_lvl[c], cudaStreamNonBlocking) != cudaSuccess ||
@@ -962,19 +962,20 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
     return cnt == 0 || cudaMemcpyAsync(dst, src, cnt * d8, cudaMemcpyHostToDevice, st) == cudaSuccess;
   };
   // b: (N n + m) rows of ldb on the host, nrhs packed columns on the device
-  const bool b_in = cudaMemcpy2DAsync(h->hsB, nrhs * d8, b, ldb * d8, nrhs * d8, h->tot_B,
-                                      cudaMemcpyHostToDevice, s) == cudaSuccess;
+  auto b_in = [&]() {
+    return cudaMemcpy2DAsync(h->hsB, nrhs * d8, b, ldb * d8, nrhs * d8, h->tot_B, cudaMemcpyHostToDevice, s) ==
+           cudaSuccess;
+  };
   auto b_out = [&]() {
     return cudaMemcpy2DAsync(b, ldb * d8, h->hsB, nrhs * d8, nrhs * d8, h->tot_B, cudaMemcpyDeviceToHost, s) ==
                    cudaSuccess
                ? KKT_OK
                : KKT_ERR_CUDA;
   };
-  if (!b_in) return KKT_ERR_CUDA;
   const bool chunked = h->count == 1 && h->border && nrhs == 1 && h->sys[0].lv[0].P >= 2 &&
                        h->fac_groups[0].size() == 1;
   if (!chunked) {
-    if (!h2d(h->hsD, D, h->tot_D, s) || !h2d(h->hsE, E, h->tot_E, s) || !h2d(h->hsG, G, h->tot_G, s) ||
+    if (!b_in() || !h2d(h->hsD, D, h->tot_D, s) || !h2d(h->hsE, E, h->tot_E, s) || !h2d(h->hsG, G, h->tot_G, s) ||
         !h2d(h->hsR, R, h->tot_R, s))
       return KKT_ERR_CUDA;
     std::vector<cudaEvent_t> ev;
@@ -984,19 +985,17 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
     h->events.swap(ev);
     return st != KKT_OK ? st : b_out();
   }
-  // one system, bordered pass: the arrow blocks, the corner and b first (the
-  // bordered arrow copy needs them whole), then the stage blocks in chunks
-  // that end at separator stages, each chunk's level-1 segments on a stream
-  // of their own as soon as their blocks have arrived
+  // one system, bordered pass: the stage rows of D, E, G and b in chunks that
+  // end at separator stages, on the copy stream; each chunk's bordered arrow
+  // copy and level-1 segments on a stream of their own as soon as its rows
+  // have arrived (the first chunk also brings the corner and the g-rows of b)
   const SysPlan& sp = h->sys[0];
   const LevelPlan& L1 = sp.lv[0];
   const int P = L1.P, K = std::min(kkt_handle::kHostChunks, P);
-  const size_t nn = (size_t)sp.n * sp.n;
-  if (!h2d(h->hsG, G, h->tot_G, s) || !h2d(h->hsR, R, h->tot_R, s)) return KKT_ERR_CUDA;
-  if (kkt::launch_border(h->ddesc_b, h->dsys_desc, h->count, h->max_gb, h->hsG, h->hsR, h->hsB, 1, h->Gb, h->Rb,
-                         stream) ||
-      cudaEventRecord(h->hs_ev_border, s) != cudaSuccess ||
-      cudaStreamWaitEvent(h->hs_copy, h->hs_ev_border, 0) != cudaSuccess)
+  const size_t nn = (size_t)sp.n * sp.n, mn = (size_t)sp.m * sp.n;
+  // the copy stream starts after the work already queued on `stream`
+  if (cudaEventRecord(h->hs_ev_start, s) != cudaSuccess ||
+      cudaStreamWaitEvent(h->hs_copy, h->hs_ev_start, 0) != cudaSuccess)
     return KKT_ERR_CUDA;
   const kkt_handle::Group& g1 = h->fac_groups[0][0];
   for (int c = 0; c < K; ++c) {
@@ -1004,12 +1003,24 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
     // stages [lo, hi): segments k0..k1-1 with the separator in front of k0
     const int lo = k0 ? L1.start[k0] - 1 : 0, hi = k1 < P ? L1.start[k1] - 1 : sp.N;
     const int ehi = std::min(hi, sp.N - 1);
-    if (!h2d(h->hsD + lo * nn, D + lo * nn, (size_t)(hi - lo) * nn, h->hs_copy) ||
-        (ehi > lo && !h2d(h->hsE + lo * nn, E + lo * nn, (size_t)(ehi - lo) * nn, h->hs_copy)) ||
-        cudaEventRecord(h->hs_ev_copy[c], h->hs_copy) != cudaSuccess)
+    cudaStream_t cs = h->hs_copy;
+    if (!h2d(h->hsD + lo * nn, D + lo * nn, (size_t)(hi - lo) * nn, cs) ||
+        (ehi > lo && !h2d(h->hsE + lo * nn, E + lo * nn, (size_t)(ehi - lo) * nn, cs)) ||
+        !h2d(h->hsG + lo * mn, G + lo * mn, (size_t)(hi - lo) * mn, cs) ||
+        cudaMemcpy2DAsync(h->hsB + (size_t)lo * sp.n, d8, b + (size_t)lo * sp.n * ldb, ldb * d8, d8,
+                          (size_t)(hi - lo) * sp.n, cudaMemcpyHostToDevice, cs) != cudaSuccess)
       return KKT_ERR_CUDA;
+    if (c == 0 && sp.m > 0 &&
+        (!h2d(h->hsR, R, h->tot_R, cs) ||
+         cudaMemcpy2DAsync(h->hsB + (size_t)sp.N * sp.n, d8, b + (size_t)sp.N * sp.n * ldb, ldb * d8, d8,
+                           (size_t)sp.m, cudaMemcpyHostToDevice, cs) != cudaSuccess))
+      return KKT_ERR_CUDA;
+    if (cudaEventRecord(h->hs_ev_copy[c], cs) != cudaSuccess) return KKT_ERR_CUDA;
     cudaStream_t ls = h->hs_lvl[c];
-    if (cudaStreamWaitEvent(ls, h->hs_ev_copy[c], 0) != cudaSuccess) return KKT_ERR_CUDA;
+    if (cudaStreamWaitEvent(ls, h->hs_ev_copy[c], 0) != cudaSuccess ||
+        kkt::launch_border(h->ddesc_b, h->dsys_desc, 1, (long long)(hi - lo) * (sp.m + 1) * sp.n, h->hsG, h->hsR,
+                           h->hsB, 1, h->Gb, h->Rb, ls, lo, hi, c == 0))
+      return KKT_ERR_CUDA;
     const Task* t = h->dtasks + g1.off + k0;
     const int e = g1.warp ? kkt::launch_factor_w(h->ddesc_b, t, k1 - k0, g1.n, g1.m + 1, 0, h->hsD, h->hsE, h->Gb,
                                                  h->Rb, h->dinfo, ls, h->hsB, 1, g1.fill)

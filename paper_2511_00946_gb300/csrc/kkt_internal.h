@@ -226,8 +226,10 @@ int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks,
                    double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0);
 // bordered inputs of a fused factor-and-solve pass, for every system: Gb_j =
 // [G_j; b_j^T] ((m+1) x n per stage), Rb = [[R, b_g], [b_g^T, 0]] ((m+1)^2)
+// (stages [j0, j1) of every system's arrow, and with `corner` the bordered corners)
 int launch_border(const LevelDesc* db, const int* sys_desc, int count, long long max_elems, const double* G,
-                  const double* R, const double* b, int ldb, double* Gb, double* Rb, void* stream);
+                  const double* R, const double* b, int ldb, double* Gb, double* Rb, void* stream, int j0 = 0,
+                  int j1 = 1 << 30, int corner = 1);
 // x += c (stage rows per residual task, g rows by each system's first task)
 int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int ldx, const double* c,
                 int nr, const int* skip, void* stream);

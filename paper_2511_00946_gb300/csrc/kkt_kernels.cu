@@ -1852,18 +1852,20 @@ __global__ void k_fill_identity(const LevelDesc* __restrict__ descs, const int* 
 // elements (one stage's row per 32-lane chunk), y = system.
 __global__ void k_border(const LevelDesc* __restrict__ descs, const int* __restrict__ sys_desc,
                          const double* __restrict__ G, const double* __restrict__ R, const double* __restrict__ b,
-                         int ldb, double* Gb, double* Rb) {
+                         int ldb, double* Gb, double* Rb, int j0, int j1, int corner) {
   const LevelDesc& d = descs[sys_desc[blockIdx.y]];
   const int n = d.n, mb = d.m, m = mb - 1, N = d.N;
   const long long offG = d.offGu, offR = d.offRu;  // the caller's arrays
-  const long long rows = (long long)N * mb;         // rows of Gb for this system
+  const int je = min(j1, N);
+  const long long rows = je > j0 ? (long long)(je - j0) * mb : 0;  // rows of Gb of stages [j0, je)
+  const long long base = (long long)j0 * mb * n;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < rows * n;
        e += (long long)gridDim.x * blockDim.x) {
-    const long long row = e / n, j = row / mb;
-    const int r = (int)(row - j * mb), c = (int)(e - row * n);
-    Gb[d.offG + e] = r < m ? G[offG + (j * m + r) * n + c] : b[(size_t)(d.offB + j * n + c) * ldb];
+    const long long row = e / n, j = j0 + row / mb;
+    const int r = (int)(row - (j - j0) * mb), c = (int)(e - row * n);
+    Gb[d.offG + base + e] = r < m ? G[offG + (j * m + r) * n + c] : b[(size_t)(d.offB + j * n + c) * ldb];
   }
-  if (blockIdx.x == 0)
+  if (corner && blockIdx.x == 0)
     for (int e = threadIdx.x; e < mb * mb; e += blockDim.x) {
       const int r = e / mb, c = e - r * mb;
       double v = 0.0;
@@ -2013,11 +2015,12 @@ int launch_fill_identity(const LevelDesc* d, const int* sys_desc, int count, dou
 }
 
 int launch_border(const LevelDesc* db, const int* sys_desc, int count, long long max_elems, const double* G,
-                  const double* R, const double* b, int ldb, double* Gb, double* Rb, void* stream) {
+                  const double* R, const double* b, int ldb, double* Gb, double* Rb, void* stream, int j0, int j1,
+                  int corner) {
   if (count <= 0) return 0;
   const long long bx = std::min<long long>(std::max<long long>((max_elems + 255) / 256, 1), 2048);
   k_border<<<dim3((unsigned)bx, (unsigned)count), 256, 0, (cudaStream_t)stream>>>(db, sys_desc, G, R, b, ldb, Gb,
-                                                                                  Rb);
+                                                                                  Rb, j0, j1, corner);
   return (int)cudaGetLastError();
 }
 
