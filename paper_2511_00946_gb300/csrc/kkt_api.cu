@@ -187,6 +187,7 @@ struct kkt_handle {
   long long max_gb = 0;                      // largest bordered arrow of one system (elements)
   std::vector<int> level_top;                // some system's top level is this level
   int pair_policy = KKT_PAIR_AUTO;
+  int sms = 0;                               // SMs of the device the handle was built on
   // kkt_factor_solve_host: device copies of the inputs and the streams and
   // events of the overlapped transfer (created by the first call)
   static constexpr int kHostChunks = 8;
@@ -269,6 +270,7 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
   auto* h = new kkt_handle();
   h->count = count;
   h->precision = precision;
+  h->sms = sms;
   h->sys.resize(count);
   for (int s = 0; s < count; ++s) {
     SysPlan& sp = h->sys[s];
@@ -853,11 +855,16 @@ kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* ski
     for (const kkt_handle::Group& gr : groups) {
       const Task* t = h->dtasks + gr.off;
       const int mx = h->level_mixed[l], gm = gr.m + dm;
+      // several right-hand sides on a level with few tasks: the columns are
+      // split over up to four CTAs per task (at least four columns each) while
+      // the CTAs fit one wave (three substitution CTAs per SM)
+      const int slots = 3 * std::max(h->sms, 1);
+      const int split = std::max(1, std::min(nr / 4, slots / std::max(gr.cnt, 1)));
       const int e = gr.warp ? kkt::launch_solve_w(backward, dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip,
                                                   stream, fwd_done)
-                    : backward ? kkt::launch_backward(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip, stream)
+                    : backward ? kkt::launch_backward(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip, stream, split)
                                : kkt::launch_forward(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip, stream,
-                                                     fwd_done);
+                                                     fwd_done, split);
       if (e || (li && !mark(h, (*li)++, stream))) return false;
     }
     return true;

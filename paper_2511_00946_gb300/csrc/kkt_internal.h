@@ -217,10 +217,11 @@ int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
                   void* stream, double* b = nullptr, int ldb = 1, int fill = 1);
+// (split: CTAs per task, each on its own group of right-hand-side columns)
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0);
+                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0, int split = 1);
 int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                    double* b, int ldb, int nrhs, const int* skip, void* stream);
+                    double* b, int ldb, int nrhs, const int* skip, void* stream, int split = 1);
 // one warp per task (blocks n <= kWarpMaxN), forward or backward substitution
 int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
                    double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0);

@@ -1085,10 +1085,10 @@ struct VecView {
   int ld;
 };
 
-__device__ __forceinline__ VecView level_vec(const LevelDesc& d, double* b, int ldb, int j) {
+__device__ __forceinline__ VecView level_vec(const LevelDesc& d, double* b, int ldb, int j, int c0) {
   VecView v;
   if (d.level == 1) { v.p = b + (size_t)(d.offB + (long long)j * d.n) * ldb; v.ld = ldb; }
-  else { v.p = d.X + (size_t)j * d.n * kRhsChunk; v.ld = kRhsChunk; }
+  else { v.p = d.X + (size_t)j * d.n * kRhsChunk + c0; v.ld = kRhsChunk; }
   return v;
 }
 
@@ -1282,7 +1282,7 @@ __device__ __forceinline__ void stage_rows(const SegGeom& g, int i, int n, int m
 // blocks of the next stage stream in while the current one is solved.
 template <typename TS>
 __device__ void backward_segment(const SolveSmem<TS>& S, const LevelDesc& d, const SegGeom& g,
-                                 double* b, int ldb, int nr, Grp G) {
+                                 double* b, int ldb, int nr, int c0, Grp G) {
   const int n = d.n, m = d.m;
   int r0, r1;
   stage_rows(g, g.len - 1, n, m, r0, r1);
@@ -1290,7 +1290,7 @@ __device__ void backward_segment(const SolveSmem<TS>& S, const LevelDesc& d, con
   for (int i = g.len - 1; i >= 0; --i) {
     const int j = g.f + i, q = (g.len - 1 - i) & 1;
     stage_rows(g, i, n, m, r0, r1);
-    const VecView y = level_vec(d, b, ldb, j);
+    const VecView y = level_vec(d, b, ldb, j, c0);
     cp_async_wait_all();
     gsync(G);
     if (i > 0) {
@@ -1340,7 +1340,7 @@ __device__ void backward_segment(const SolveSmem<TS>& S, const LevelDesc& d, con
 // sequential phase). `skip`: per-system flags; a set flag returns at once.
 template <typename TS>
 __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs, double* b, int ldb, int nr,
-                             const int* skip, unsigned char* smraw, Grp G, int fwd_done) {
+                             const int* skip, unsigned char* smraw, Grp G, int fwd_done, int c0 = 0) {
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
   if (fwd_done && !d.is_top) return;  // the factorization carried this forward sweep
@@ -1351,11 +1351,11 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
   const int k = tk.seg;
   auto rhs = [&](int j, TS* dst) {  // this level's right-hand side of stage j
     if (d.level == 1) {
-      const VecView v = level_vec(d, b, ldb, j);
+      const VecView v = level_vec(d, b, ldb, j, c0);
       load_vec(dst, S.ldV, v.p, v.ld, (const double*)nullptr, n, nr, G);
     } else {
-      load_vec(dst, S.ldV, d.RA + (size_t)j * n * kRhsChunk, kRhsChunk,
-               d.RB + (size_t)j * n * kRhsChunk, n, nr, G);
+      load_vec(dst, S.ldV, d.RA + (size_t)j * n * kRhsChunk + c0, kRhsChunk,
+               d.RB + (size_t)j * n * kRhsChunk + c0, n, nr, G);
     }
   };
   int r0, r1;
@@ -1379,7 +1379,7 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
       prefetch_stage_factor(S, q ^ 1, d, j + 1, p0, p1, false, G);
     }
     trsv_warp(S.t, S.ldV, S.L(q), S.ldL, S.rinv(q), n, nr, false, G);
-    const VecView y = level_vec(d, b, ldb, j);
+    const VecView y = level_vec(d, b, ldb, j, c0);
     store_vec(y.p, y.ld, S.t, S.ldV, n, nr, G);
     // [V_E; V_G; V_W] -= Z y over the active panel rows: four lanes per output
     // (each a quarter of the dot product, two partial sums), shuffle-reduced
@@ -1419,9 +1419,10 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
   }
   gsync(G);
   if (!d.is_top) {
-    if (g.hasF) store_vec(d.YB + (size_t)k * n * kRhsChunk, kRhsChunk, S.V, S.ldV, n, nr, G);
-    if (g.hasW) store_vec(d.YA + (size_t)(k - 1) * n * kRhsChunk, kRhsChunk, S.V + oW * S.ldV, S.ldV, n, nr, G);
-    if (m) store_vec(d.ygpart + (size_t)k * m * kRhsChunk, kRhsChunk, S.V + oG * S.ldV, S.ldV, m, nr, G);
+    if (g.hasF) store_vec(d.YB + (size_t)k * n * kRhsChunk + c0, kRhsChunk, S.V, S.ldV, n, nr, G);
+    if (g.hasW)
+      store_vec(d.YA + (size_t)(k - 1) * n * kRhsChunk + c0, kRhsChunk, S.V + oW * S.ldV, S.ldV, n, nr, G);
+    if (m) store_vec(d.ygpart + (size_t)k * m * kRhsChunk + c0, kRhsChunk, S.V + oG * S.ldV, S.ldV, m, nr, G);
     return;
   }
   // top level: corner y_g = R-hat^{-1} (r_g + sum of every yg partial + own),
@@ -1439,7 +1440,7 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
     } else {
       sum_partials(
           G, mg * nr, d.nyg_all,
-          [&](int p, int o) { return d.yg_all[((size_t)p * m + o / nr) * kRhsChunk + o % nr]; },
+          [&](int p, int o) { return d.yg_all[((size_t)p * m + o / nr) * kRhsChunk + c0 + o % nr]; },
           [&](int o, double v) {
             const int r = o / nr, c = o - r * nr;
             gv[r * S.ldV + c] = (TS)((bg[(size_t)r * ldb + c] + v) + (double)S.V[(oG + r) * S.ldV + c]);
@@ -1463,7 +1464,7 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
     else S.V[e] = S.t[(r - oG) * S.ldV + (e - r * S.ldV)];
   }
   gsync(G);
-  backward_segment(S, d, g, b, ldb, nr, G);
+  backward_segment(S, d, g, b, ldb, nr, c0, G);
 }
 
 // Backward substitution (Algorithm 3, parallel phase) for one segment below
@@ -1471,7 +1472,7 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
 // next level (x at s_k and s_{k+1}), and this level's y.
 template <typename TS>
 __device__ void backward_task(const Task tk, const LevelDesc* __restrict__ descs, double* b, int ldb, int nr,
-                              const int* skip, unsigned char* smraw, Grp G) {
+                              const int* skip, unsigned char* smraw, Grp G, int c0 = 0) {
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
   const int n = d.n, m = d.m;
@@ -1482,17 +1483,17 @@ __device__ void backward_task(const Task tk, const LevelDesc* __restrict__ descs
   const double* none = nullptr;
   for (int e = G.tid; e < (2 * n + m) * S.ldV; e += G.nt) S.V[e] = TS(0);
   gsync(G);
-  if (g.hasF) load_vec(S.V, S.ldV, d.Xnext + (size_t)k * n * kRhsChunk, kRhsChunk, none, n, nr, G);
+  if (g.hasF) load_vec(S.V, S.ldV, d.Xnext + (size_t)k * n * kRhsChunk + c0, kRhsChunk, none, n, nr, G);
   if (d.m - d.mr) load_vec(S.V + oG * S.ldV, S.ldV, b + (size_t)d.rowG * ldb, ldb, none, d.m - d.mr, nr, G);
   if (g.hasW) {
-    load_vec(S.V + oW * S.ldV, S.ldV, d.Xnext + (size_t)(k - 1) * n * kRhsChunk, kRhsChunk, none, n,
+    load_vec(S.V + oW * S.ldV, S.ldV, d.Xnext + (size_t)(k - 1) * n * kRhsChunk + c0, kRhsChunk, none, n,
              nr, G);
     gsync(G);
-    const VecView xs = level_vec(d, b, ldb, g.f - 1);  // this level's copy of x at s_k
+    const VecView xs = level_vec(d, b, ldb, g.f - 1, c0);  // this level's copy of x at s_k
     store_vec(xs.p, xs.ld, S.V + oW * S.ldV, S.ldV, n, nr, G);
   }
   gsync(G);
-  backward_segment(S, d, g, b, ldb, nr, G);
+  backward_segment(S, d, g, b, ldb, nr, c0, G);
 }
 
 
@@ -1501,16 +1502,22 @@ __device__ void backward_task(const Task tk, const LevelDesc* __restrict__ descs
 template <typename TS>
 __global__ void __launch_bounds__(kSolveThreads) k_forward(const LevelDesc* __restrict__ descs,
                                                            const Task* __restrict__ tasks, double* b,
-                                                           int ldb, int nr, const int* skip, int fwd_done) {
+                                                           int ldb, int nr, const int* skip, int fwd_done,
+                                                           int split) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  forward_task<TS>(tasks[blockIdx.x], descs, b, ldb, nr, skip, smraw, cta_grp(), fwd_done);
+  // `split` CTAs per task, each on its own group of right-hand-side columns
+  const int cg = blockIdx.x % split, nc = (nr + split - 1) / split, c0 = cg * nc, cn = min(nc, nr - c0);
+  if (cn <= 0) return;
+  forward_task<TS>(tasks[blockIdx.x / split], descs, b + c0, ldb, cn, skip, smraw, cta_grp(), fwd_done, c0);
 }
 template <typename TS>
 __global__ void __launch_bounds__(kSolveThreads) k_backward(const LevelDesc* __restrict__ descs,
                                                             const Task* __restrict__ tasks, double* b,
-                                                            int ldb, int nr, const int* skip) {
+                                                            int ldb, int nr, const int* skip, int split) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  backward_task<TS>(tasks[blockIdx.x], descs, b, ldb, nr, skip, smraw, cta_grp());
+  const int cg = blockIdx.x % split, nc = (nr + split - 1) / split, c0 = cg * nc, cn = min(nc, nr - c0);
+  if (cn <= 0) return;
+  backward_task<TS>(tasks[blockIdx.x / split], descs, b + c0, ldb, cn, skip, smraw, cta_grp(), c0);
 }
 template <typename TS>
 __global__ void __launch_bounds__(256) k_forward_w(const LevelDesc* __restrict__ descs,
@@ -1950,30 +1957,34 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
 }
 
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done) {
+                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done, int split) {
   if (ntasks <= 0) return 0;
   const size_t sm = solve_smem_bytes(maxn, maxm, single);
   const void* fn = single ? (const void*)k_forward<float> : (const void*)k_forward<double>;
   int e = set_smem(fn, sm);
   if (e) return e;
+  split = std::max(1, std::min(split, nrhs));
+  const unsigned grid = (unsigned)(ntasks * split);
   if (single)
-    k_forward<float><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip, fwd_done);
+    k_forward<float><<<grid, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip, fwd_done, split);
   else
-    k_forward<double><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip, fwd_done);
+    k_forward<double><<<grid, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip, fwd_done, split);
   return (int)cudaGetLastError();
 }
 
 int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                    double* b, int ldb, int nrhs, const int* skip, void* stream) {
+                    double* b, int ldb, int nrhs, const int* skip, void* stream, int split) {
   if (ntasks <= 0) return 0;
   const size_t sm = solve_smem_bytes(maxn, maxm, single);
   const void* fn = single ? (const void*)k_backward<float> : (const void*)k_backward<double>;
   int e = set_smem(fn, sm);
   if (e) return e;
+  split = std::max(1, std::min(split, nrhs));
+  const unsigned grid = (unsigned)(ntasks * split);
   if (single)
-    k_backward<float><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip);
+    k_backward<float><<<grid, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip, split);
   else
-    k_backward<double><<<ntasks, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip);
+    k_backward<double><<<grid, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip, split);
   return (int)cudaGetLastError();
 }
 

@@ -169,6 +169,45 @@ def test_multiple_rhs(kkt, orc, nrhs, ldb):
     np.testing.assert_array_equal(x[:, nrhs:], b[:, nrhs:])   # untouched columns
 
 
+@pytest.mark.parametrize("N,n,m,levels,nrhs,ldb", [
+    (200, 24, 4, [20, 4, 1], 16, 16),   # columns split over four CTAs per task on the deep levels
+    (120, 32, 8, [12, 1], 17, 20),      # two chunks (16 + 1), a leading dimension above nrhs
+    (90, 20, 0, [9, 2, 1], 40, 40),     # three chunks
+])
+def test_multiple_rhs_column_split(kkt, orc, N, n, m, levels, nrhs, ldb):
+    """Several right-hand sides with CTA-size blocks: a level with few
+    segment tasks spreads the columns of a chunk over several CTAs. Each
+    column's arithmetic is its own, so the columns agree bit for bit with
+    single-column solves, and with the oracle to the parity tolerance."""
+    import torch
+    D, E, G, R = gen.ipm(N, n, m, seed=91)
+    b = gen.rhs(N * n + m, ldb, seed=92).reshape(N * n + m, ldb)
+    h = kkt.kkt_create_plan(N, n, m, levels, kkt.KKT_PARTITION_BALANCED)
+    try:
+        Dd, Ed, Gd, Rd = dev(D), dev(E), dev(G) if m else None, dev(R) if m else None
+        kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+        bd = dev(b)
+        kkt.kkt_solve(h, bd, nrhs=nrhs, ldb=ldb)
+        cols = []
+        for c in (0, nrhs // 2, nrhs - 1):
+            bc = dev(np.ascontiguousarray(b[:, c]))
+            kkt.kkt_solve(h, bc)
+            cols.append((c, bc))
+        torch.cuda.synchronize()
+        assert kkt.kkt_get_info(h)["status"] == 0
+        x = bd.cpu().numpy()
+        cols = [(c, v.cpu().numpy()) for c, v in cols]
+    finally:
+        kkt.kkt_destroy(h)
+    for c, v in cols:
+        np.testing.assert_array_equal(x[:, c], v)
+    np.testing.assert_array_equal(x[:, nrhs:], b[:, nrhs:])   # untouched columns
+    F = orc.seq_factor(D, E, G, R)
+    xo = orc.seq_solve(F, np.ascontiguousarray(b[:, :nrhs]))
+    for c in range(0, nrhs, 7):
+        check_solution(orc, D, E, G, R, x[:, c], b[:, c], xo[:, c], fwd_tol=1e-5)
+
+
 # ------------------------------------------------------------- IPM-shaped
 
 @pytest.mark.parametrize("pairing", PAIRINGS)
