@@ -162,3 +162,33 @@ def test_mixed_uneven_batch(kkt, orc):
     for i, s in enumerate(sy):
         xi = x[off["b"][i]:off["b"][i + 1]]
         assert eta(orc, *s, xi, bs[i]) <= 1e-14, (i, etas)
+
+
+def test_refinement_multiple_rhs_cta_blocks(kkt, orc):
+    """Mixed factor, CTA-size blocks and 20 right-hand sides (two chunks): the
+    FP32 correction solves split a chunk's columns over several CTAs per task
+    on the reduced levels; every column reaches the FP64 gate and agrees, bit
+    for bit, with its own single-column refinement."""
+    import torch
+    N, n, m = 150, 24, 4
+    D, E, G, R = gen.ipm(N, n, m, seed=21, sigma_decades=4.0)
+    b = gen.rhs(N * n + m, 20, seed=22).reshape(N * n + m, 20)
+    h = kkt.kkt_create_plan(N, n, m, [15, 3, 1], kkt.KKT_PARTITION_BALANCED, kkt.KKT_MIXED_FP32_ALL)
+    try:
+        Dd, Ed, Gd, Rd = dev(D), dev(E), dev(G), dev(R)
+        kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+        x = torch.zeros((N * n + m, 20), dtype=torch.float64, device="cuda")
+        kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, dev(b), x, sweeps=5, tol=0.0)
+        x1 = torch.zeros(N * n + m, dtype=torch.float64, device="cuda")
+        kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, dev(np.ascontiguousarray(b[:, 13])), x1, sweeps=5, tol=0.0)
+        torch.cuda.synchronize()
+        assert kkt.kkt_get_info(h)["status"] == 0
+        x, x1 = x.cpu().numpy(), x1.cpu().numpy()
+    finally:
+        kkt.kkt_destroy(h)
+    np.testing.assert_array_equal(x[:, 13], x1)
+    for c in (0, 13, 19):
+        r = b[:, c] - orc.block_matvec(D, E, G, R, x[:, c])
+        xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b[:, c])
+        assert np.abs(x[:, c] - xo).max() <= 1e-5 * np.abs(xo).max()
+        assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(b[:, c])

@@ -651,3 +651,35 @@ def test_factor_solve_host_matches_device(kkt, orc, N, n, m, levels, nrhs):
         bc = b.reshape(b.shape[0], -1)[:, c]
         xc = x_dev.reshape(x_dev.shape[0], -1)[:, c]
         check_solution(orc, D, E, G, R, xc, bc, orc.seq_solve(orc.seq_factor(D, E, G, R), bc), fwd_tol=1e-5)
+
+
+def test_factor_solve_host_other_handles(kkt, orc):
+    """The host entry point on handles without the chunked transfer: a batch,
+    a mixed-precision handle (no bordered pass) and a system of one stage;
+    each returns what kkt_factor_solve returns on device copies."""
+    import torch
+    sy = gen.uneven_batch(5, seed=31, N_range=(6, 40))
+    Ns = [s[0].shape[0] for s in sy]
+    ns = [s[0].shape[1] for s in sy]
+    ms = [s[3].shape[0] for s in sy]
+    cat = lambda i: np.concatenate([s[i].ravel() for s in sy] + [np.zeros(1)])
+    bs = np.concatenate([gen.rhs(N * n + m, 1, seed=90 + i) for i, (N, n, m) in enumerate(zip(Ns, ns, ms))])
+    cases = [(kkt.kkt_batch_create(Ns, ns, ms, [max(1, min(3, (N + 1) // 2)) for N in Ns]),
+              [cat(0), cat(1), cat(2), cat(3)], bs)]
+    D, E, G, R = gen.ipm(64, 24, 4, seed=33)
+    cases.append((kkt.kkt_create_plan(64, 24, 4, [8, 1], kkt.KKT_PARTITION_BALANCED, kkt.KKT_MIXED_FP32),
+                  [D, E, G, R], gen.rhs(64 * 24 + 4, 1, seed=34)))
+    D1, E1, G1, R1 = gen.ipm(1, 20, 3, seed=35)
+    cases.append((kkt.kkt_create(1, 20, 3, 1), [D1, None, G1, R1], gen.rhs(23, 1, seed=36)))
+    for h, arrs, b in cases:
+        try:
+            bd = dev(b)
+            kkt.kkt_factor_solve(h, *[dev(a) if a is not None else None for a in arrs], bd)
+            torch.cuda.synchronize()
+            hb = np.ascontiguousarray(b).copy()
+            kkt.kkt_factor_solve_host(h, *[np.ascontiguousarray(a) if a is not None else None for a in arrs], hb)
+            torch.cuda.synchronize()
+            assert kkt.kkt_get_info(h)["status"] == 0
+            np.testing.assert_array_equal(hb, bd.cpu().numpy())
+        finally:
+            kkt.kkt_destroy(h)
