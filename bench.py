@@ -251,8 +251,9 @@ def per_launch_flops(kkt, plan, partition, nrhs=1):
     the launches of one factor-and-solve step, in launch order. With one
     right-hand side (kkt_factor_solve, the right-hand side bordered onto the
     arrow): factor levels 1..L with the flop model of m + 1 arrow rows (the
-    factorization plus the forward substitution it carries), the top level's
-    corner and backward sweep, backward levels L-1..1. With several (the two
+    factorization plus the forward substitution it carries; the top level's
+    launch also runs the corner solve and the top level's backward sweep),
+    backward levels L-1..1. With several (the two
     passes): factor levels 1..L, forward levels 1..L (the top one also solves
     the corner and runs its backward sweep), backward levels L-1..1."""
     L = len(plan)
@@ -280,8 +281,8 @@ def per_launch_flops(kkt, plan, partition, nrhs=1):
         names.append(f"k_forward level {L} (forward, corner, backward)")
         flops.append(sol[L - 1])
     else:
-        names.append(f"k_forward level {L} (corner, backward)")
-        flops.append(sol[L - 1] / 2.0)
+        names[-1] = f"k_factor level {L} (+forward, corner, corner solve, backward)"
+        flops[-1] += sol[L - 1] / 2.0
     for l in range(L - 2, -1, -1):
         names.append(f"k_backward level {l + 1}")
         flops.append(sol[l] / 2.0)

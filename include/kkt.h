@@ -198,8 +198,10 @@ kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream);
  * The factor stays usable for kkt_solve, kkt_solve_refined and
  * kkt_solve_adjoint; kkt_get_factor then reports KKT_ERR_STATE. Launches
  * recorded by kkt_set_launch_events: the copy of the bordered arrow, the
- * factor launches, the top level's corner and backward sweep, then the
- * backward launches. */
+ * factor launches, then the backward launches. With blocks n > 16 the top
+ * level's factor launch also runs the corner solve x_g = R-hat^{-T} y_g and
+ * the top level's backward sweep (when the top level has at most one task
+ * per SM); otherwise a launch of their own follows the factor launches. */
 kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, const double* G,
                             const double* R, double* b, int nrhs, int ldb, void* stream);
 

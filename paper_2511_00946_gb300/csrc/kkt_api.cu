@@ -812,6 +812,14 @@ int level_paired(const kkt_handle* h, int l) {
   if (h->pair_policy == KKT_PAIR_ON) return 1;
   return h->level_pair[l];
 }
+
+// A bordered pass runs the top level's corner solve and backward sweep at the
+// end of the top level's factor kernel (CTA-size blocks, and few enough top
+// tasks that the larger shared-memory request costs no occupancy); the
+// separate launch of that step is then left out.
+bool top_in_factor(const kkt_handle* h, int l, const kkt_handle::Group& gr) {
+  return h->level_top[l] && !gr.warp && gr.cnt <= h->sms;
+}
 }  // namespace
 
 kkt_status kkt_set_pairing(kkt_handle* h, int policy) {
@@ -853,6 +861,7 @@ kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* ski
   // one launch per group: small blocks one warp per task, the others one CTA per task
   auto run = [&](bool backward, int l, const std::vector<kkt_handle::Group>& groups) -> bool {
     for (const kkt_handle::Group& gr : groups) {
+      if (fwd_done && !backward && top_in_factor(h, l, gr)) continue;  // done by the factor kernel
       const Task* t = h->dtasks + gr.off;
       const int mx = h->level_mixed[l], gm = gr.m + dm;
       // several right-hand sides on a level with few tasks: the columns are
@@ -913,7 +922,7 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
                                                    h->Gb, h->Rb, h->dinfo, stream, b, ldb, gr.fill)
                             : kkt::launch_factor(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0,
                                                  level_paired(h, l), D, E, h->Gb, h->Rb, h->dinfo, stream, b, ldb,
-                                                 gr.fill);
+                                                 gr.fill, top_in_factor(h, l, gr));
       if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
     }
   h->factored = true;
@@ -1044,7 +1053,7 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
                                                    gr.fill)
                             : kkt::launch_factor(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0,
                                                  level_paired(h, l), h->hsD, h->hsE, h->Gb, h->Rb, h->dinfo,
-                                                 stream, h->hsB, 1, gr.fill);
+                                                 stream, h->hsB, 1, gr.fill, top_in_factor(h, l, gr));
       if (e) return KKT_ERR_CUDA;
     }
   h->factored = true;

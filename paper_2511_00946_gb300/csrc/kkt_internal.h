@@ -214,9 +214,11 @@ constexpr int kResPartDoubles = kMaxM * kRhsChunk + 4 * kRhsChunk;
 int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
                     const double* D, const double* E, const double* G, const double* R, Info* info,
                     void* stream, double* b = nullptr, int ldb = 1, int fill = 1);
+// (top_solve: on a bordered pass the top level's tasks also run their corner
+// solve and backward sweep at the end of the factor kernel)
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
-                  void* stream, double* b = nullptr, int ldb = 1, int fill = 1);
+                  void* stream, double* b = nullptr, int ldb = 1, int fill = 1, int top_solve = 0);
 // (split: CTAs per task, each on its own group of right-hand-side columns)
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
                    double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0, int split = 1);

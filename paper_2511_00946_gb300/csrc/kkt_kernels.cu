@@ -737,6 +737,13 @@ struct FacCtx {
   }
 };
 
+// Forward substitution task of the solve kernels (defined below); the factor
+// kernel of a bordered pass runs it for the top level (corner solve and the
+// backward sweep of the top level) right after the corner.
+template <typename TS>
+__device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs, double* b, int ldb, int nr,
+                             const int* skip, unsigned char* smraw, Grp G, int fwd_done, int c0 = 0);
+
 // MINB: CTAs per SM the register allocation must allow. Launches of CTA pairs
 // (one CTA per SM, latency-bound) take the unconstrained allocation (1);
 // the others four (at most 64 registers), so that several segment CTAs share
@@ -748,7 +755,8 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
                                                            const double* __restrict__ uE,
                                                            const double* __restrict__ uG,
                                                            const double* __restrict__ uR,
-                                                           Info* info, int pair, double* yb, int ldyb) {
+                                                           Info* info, int pair, double* yb, int ldyb,
+                                                           int top_solve) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
   const unsigned rank = pair ? cluster_rank() : 0u;
@@ -966,6 +974,16 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
     }
     __syncthreads();
     corner_factor<false>(Rs, ldR, m, d.mr, rinv, tab, d, info, &bad, cta_grp());
+  }
+  if constexpr (!mixed) {
+    // bordered pass, top level: the corner solve x_g = R-hat^{-T} y_g and the
+    // backward sweep of the top level's stages (Algorithm 3, sequential
+    // phase) here instead of in a launch of their own; the blocks it reads
+    // were written by this CTA, and the shared memory is free by now
+    if (top_solve && d.is_top && d.mr && yb && eg) {
+      __syncthreads();
+      forward_task<double>(tk, descs, yb, ldyb, 1, nullptr, smraw, cta_grp(), 1);
+    }
   }
   if (mode == kPair) {
     // a segment without fill-in leaves its consumer idle; every CTA of the
@@ -1340,7 +1358,7 @@ __device__ void backward_segment(const SolveSmem<TS>& S, const LevelDesc& d, con
 // sequential phase). `skip`: per-system flags; a set flag returns at once.
 template <typename TS>
 __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs, double* b, int ldb, int nr,
-                             const int* skip, unsigned char* smraw, Grp G, int fwd_done, int c0 = 0) {
+                             const int* skip, unsigned char* smraw, Grp G, int fwd_done, int c0) {
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
   if (fwd_done && !d.is_top) return;  // the factorization carried this forward sweep
@@ -1927,9 +1945,11 @@ int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
 
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
-                  void* stream, double* b, int ldb, int fill) {
+                  void* stream, double* b, int ldb, int fill, int top_solve) {
   if (ntasks <= 0) return 0;
-  const size_t sm = factor_smem_bytes(maxn, maxm, mixed, fill);
+  top_solve = top_solve && b && !mixed;
+  size_t sm = factor_smem_bytes(maxn, maxm, mixed, fill);
+  if (top_solve) sm = std::max(sm, solve_smem_bytes(maxn, maxm, 0));
   const void* fn = mixed ? (pair ? (const void*)k_factor<float, 1> : (const void*)k_factor<float, 4>)
                           : (pair ? (const void*)k_factor<double, 1> : (const void*)k_factor<double, 4>);
   int e = set_smem(fn, sm);
@@ -1950,10 +1970,10 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
   }
   const int p = pair ? 1 : 0;
   if (mixed)
-    return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<float, 1>, d, t, D, E, G, R, info, p, b, ldb)
-                : (int)cudaLaunchKernelEx(&cfg, k_factor<float, 4>, d, t, D, E, G, R, info, p, b, ldb);
-  return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<double, 1>, d, t, D, E, G, R, info, p, b, ldb)
-              : (int)cudaLaunchKernelEx(&cfg, k_factor<double, 4>, d, t, D, E, G, R, info, p, b, ldb);
+    return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<float, 1>, d, t, D, E, G, R, info, p, b, ldb, top_solve)
+                : (int)cudaLaunchKernelEx(&cfg, k_factor<float, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve);
+  return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<double, 1>, d, t, D, E, G, R, info, p, b, ldb, top_solve)
+              : (int)cudaLaunchKernelEx(&cfg, k_factor<double, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve);
 }
 
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
