@@ -305,8 +305,8 @@ def kkt_set_launch_events(h: int, events) -> None:
     """events: list of torch.cuda.Event (created with enable_timing=True and
     already recorded once so that they own a CUDA event) or raw handles."""
     handles = []
-    for ev in events or []:
-        handles.append(ev if isinstance(ev, int) else ev.cuda_event)
+    for ev in events or []:  # None: no event after that launch
+        handles.append(None if ev is None else ev if isinstance(ev, int) else ev.cuda_event)
     arr = (_vp * max(len(handles), 1))(*handles)
     _check(_lib.kkt_set_launch_events(h, arr if handles else None, len(handles)), "kkt_set_launch_events")
 
