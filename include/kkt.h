@@ -22,7 +22,8 @@
  *        b [N*n+m][ldb] right-hand sides in the first nrhs columns
  *  - Matrix and vector pointers passed to kkt_factor/kkt_solve* are DEVICE
  *    pointers owned by the caller; the library only reads them (b is
- *    overwritten with the solution). The factor and all scratch space are
+ *    overwritten with the solution). kkt_factor_solve_host alone takes HOST
+ *    pointers (see there). The factor and all scratch space are
  *    device memory owned by the handle, allocated by kkt_create* and freed
  *    by kkt_destroy.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
@@ -217,9 +218,8 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
  * stream of their own as soon as its rows have arrived (the segments of
  * Algorithm 1 are independent), so the transfer overlaps the level-1
  * factorization; the corner and the g-rows of b travel with the first
- * chunk. Otherwise
- * the inputs are copied on `stream` and kkt_factor_solve runs on the device
- * copies. The result is that of kkt_factor_solve on the same inputs, bit for
+ * chunk. Otherwise the inputs are copied on `stream` and kkt_factor_solve
+ * runs on the device copies. The result is that of kkt_factor_solve on the same inputs, bit for
  * bit. Launch events are not recorded. */
 kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E, const double* G,
                                  const double* R, double* b, int nrhs, int ldb, void* stream);
