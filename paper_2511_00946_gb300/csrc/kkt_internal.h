@@ -127,7 +127,10 @@ struct FacLayout {
   int q, R, Rs, ldD, ldZ, ldT, oDfac, oM, oRinv, oRinvZ, oZ, oT, oTab, oDfac2, oRinv2, oCorner, total;
 };
 __host__ __device__ inline int kkt_align16(int b) { return (b + 15) & ~15; }
-__host__ __device__ inline FacLayout fac_layout(int n, int m, int zb, bool fill = true) {
+// `dbl`: a second pivot buffer (and rinv) so that warp 4 can write the
+// previous stage's pivot blocks while the next ones are being factored; a
+// launch goes without it when that lets more CTAs share an SM.
+__host__ __device__ inline FacLayout fac_layout(int n, int m, int zb, bool fill = true, bool dbl = true) {
   FacLayout L;
   L.q = n > m ? n : m;
   L.R = 2 * n + m;
@@ -145,9 +148,9 @@ __host__ __device__ inline FacLayout fac_layout(int n, int m, int zb, bool fill 
   // second pivot block and rinv: the next stage's pivot factorization runs
   // while the current stage's factor blocks are still being written
   L.oDfac2 = L.oTab + kkt_align16(4 * (L.q * (L.q - 1) / 2 + 1));
-  L.oRinv2 = L.oDfac2 + kkt_align16(8 * L.q * L.ldD);
+  L.oRinv2 = L.oDfac2 + (dbl ? kkt_align16(8 * L.q * L.ldD) : 0);
   // sum of the lower levels' corner partials (m x m), formed before the corner
-  L.oCorner = L.oRinv2 + kkt_align16(8 * L.q);
+  L.oCorner = L.oRinv2 + (dbl ? kkt_align16(8 * L.q) : 0);
   L.total = L.oCorner + kkt_align16(8 * kMaxM * kMaxM);
   return L;
 }
@@ -255,7 +258,7 @@ int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const 
 // D (every system's stage blocks) <- identity blocks, R <- identity corners
 int launch_fill_identity(const LevelDesc* d, const int* sys_desc, int count, double* D, double* R,
                          void* stream);
-size_t factor_smem_bytes(int maxn, int maxm, int mixed, int fill = 1);
+size_t factor_smem_bytes(int maxn, int maxm, int mixed, int fill = 1, int dbl = 1);
 size_t solve_smem_bytes(int maxn, int maxm, int single);
 
 }  // namespace kkt

@@ -756,14 +756,14 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
                                                            const double* __restrict__ uG,
                                                            const double* __restrict__ uR,
                                                            Info* info, int pair, double* yb, int ldyb,
-                                                           int top_solve) {
+                                                           int top_solve, int dbl) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
   const unsigned rank = pair ? cluster_rank() : 0u;
   const Task tk = tasks[pair ? blockIdx.x >> 1 : blockIdx.x];
   const LevelDesc& d = descs[tk.desc];
   constexpr bool mixed = sizeof(TZ) == 4;
-  const FacLayout lay = fac_layout(d.n, d.m, (int)sizeof(TZ), d.P > 1);
+  const FacLayout lay = fac_layout(d.n, d.m, (int)sizeof(TZ), d.P > 1, dbl != 0);
   const FacCtx<TZ> cx(d, tk.seg, smraw, lay, uD, uE, uG);
   const int n = cx.n, m = cx.m, R = cx.R, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG, oW = cx.oW;
   double* const Dfac = cx.Dfac;
@@ -869,20 +869,23 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
     const bool push = mode == kPair && g.hasW;
     double* const Dfac2 = (double*)(smraw + lay.oDfac2);
     double* const rinv2 = (double*)(smraw + lay.oRinv2);
-    auto Dbuf = [&](int b) { return b ? Dfac2 : Dfac; };
-    auto rvbuf = [&](int b) { return b ? rinv2 : rinv; };
+    // without the second pivot buffer (dbl = 0) the pivot blocks of a stage
+    // are written by the whole CTA right after its sweep
+    auto Dbuf = [&](int b) { return b && dbl ? Dfac2 : Dfac; };
+    auto rvbuf = [&](int b) { return b && dbl ? rinv2 : rinv; };
     for (int i = 0; i < g.len; ++i) {
       const int j = g.f + i;
       const int cur = i & 1;
       const bool eRows = (i < g.len - 1) || g.hasF;
       const int r0 = eRows ? 0 : n;
       if (w4) {
-        if (i > 0) store_pivot(j - 1, Dbuf(cur ^ 1), rvbuf(cur ^ 1), nullptr, W4);
+        if (i > 0 && dbl) store_pivot(j - 1, Dbuf(cur ^ 1), rvbuf(cur ^ 1), nullptr, W4);
       } else {
         potrf_trsm_sm(Dbuf(cur), ldD, n, rvbuf(cur), M, tab, &bad, Z, ldZ, r0, pr1);
       }
       __syncthreads();
       if (threadIdx.x == 0 && bad) { record_breakdown(info, d.sys, d.nat[j], d.level); bad = 0; }
+      if (!dbl) store_pivot(j, Dfac, rinv, nullptr, P);  // read before the copy of D_{i+1} below
       if (d.mr) cx.store_y(j, yb, ldyb, P);
       if (push) {
         for (int e = P.tid; e < n; e += P.nt) rinvZ[e] = (TZ)rvbuf(cur)[e];
@@ -896,7 +899,7 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
       if (i + 1 < g.len) {
         copy_blk(Dbuf(cur ^ 1), ldD, T, ldT, n, n, P);                      // D_{i+1}
         rotate(i, j, mode == kWhole && g.hasW, P);
-      } else {
+      } else if (dbl) {
         store_pivot(j, Dbuf(cur), rvbuf(cur), nullptr, P);
       }
     }
@@ -1917,8 +1920,8 @@ int set_smem(const void* fn, size_t bytes) {
 
 }  // namespace
 
-size_t factor_smem_bytes(int n, int m, int mixed, int fill) {
-  return (size_t)fac_layout(n, m, mixed ? 4 : 8, fill != 0).total;
+size_t factor_smem_bytes(int n, int m, int mixed, int fill, int dbl) {
+  return (size_t)fac_layout(n, m, mixed ? 4 : 8, fill != 0, dbl != 0).total;
 }
 
 size_t solve_smem_bytes(int n, int m, int single) {
@@ -1954,6 +1957,19 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
                           : (pair ? (const void*)k_factor<double, 1> : (const void*)k_factor<double, 4>);
   int e = set_smem(fn, sm);
   if (e) return e;
+  // unpaired launches drop the second pivot buffer when that lets more CTAs
+  // share an SM (the occupancy of this kernel with either request)
+  int dbl = 1;
+  if (!pair && !top_solve) {
+    const size_t sm1 = factor_smem_bytes(maxn, maxm, mixed, fill, 0);
+    int occ = 0, occ1 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFactorThreads, sm) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, fn, kFactorThreads, sm1) == cudaSuccess &&
+        occ1 > occ) {
+      dbl = 0;
+      sm = sm1;
+    }
+  }
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   cfg.gridDim = dim3((unsigned)(pair ? 2 * ntasks : ntasks));
@@ -1970,10 +1986,14 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
   }
   const int p = pair ? 1 : 0;
   if (mixed)
-    return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<float, 1>, d, t, D, E, G, R, info, p, b, ldb, top_solve)
-                : (int)cudaLaunchKernelEx(&cfg, k_factor<float, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve);
-  return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<double, 1>, d, t, D, E, G, R, info, p, b, ldb, top_solve)
-              : (int)cudaLaunchKernelEx(&cfg, k_factor<double, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve);
+    return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<float, 1>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
+                                          dbl)
+                : (int)cudaLaunchKernelEx(&cfg, k_factor<float, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
+                                          dbl);
+  return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<double, 1>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
+                                        dbl)
+              : (int)cudaLaunchKernelEx(&cfg, k_factor<double, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
+                                        dbl);
 }
 
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
