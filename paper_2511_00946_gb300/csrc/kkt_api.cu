@@ -870,10 +870,11 @@ kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* ski
       const int slots = 3 * std::max(h->sms, 1);
       const int split = std::max(1, std::min(nr / 4, slots / std::max(gr.cnt, 1)));
       const int e = gr.warp ? kkt::launch_solve_w(backward, dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip,
-                                                  stream, fwd_done)
-                    : backward ? kkt::launch_backward(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip, stream, split)
+                                                  stream, fwd_done, gr.fill)
+                    : backward ? kkt::launch_backward(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip, stream, split,
+                                                      gr.fill)
                                : kkt::launch_forward(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip, stream,
-                                                     fwd_done, split);
+                                                     fwd_done, split, gr.fill);
       if (e || (li && !mark(h, (*li)++, stream))) return false;
     }
     return true;

@@ -169,10 +169,12 @@ constexpr int kWarpMaxN = 16;  // largest stage block of the warp-per-task kerne
 struct SolLayout {
   int q, R, ldL, ldZ, ldV, oL[2], oRinv[2], oZ[2], oV, oT, total;
 };
-__host__ __device__ inline SolLayout sol_layout(int n, int m, int sb) {
+// (fill: as for fac_layout; a level with P = 1 keeps only the E- and G-rows of
+// the panel and of V)
+__host__ __device__ inline SolLayout sol_layout(int n, int m, int sb, bool fill = true) {
   SolLayout L;
   L.q = n > m ? n : m;
-  L.R = 2 * n + m;
+  L.R = fill ? 2 * n + m : n + m;
   L.ldL = L.q | 1;
   L.ldZ = n | 1;
   L.ldV = kRhsChunk | 1;
@@ -223,13 +225,16 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
                   const double* D, const double* E, const double* G, const double* R, Info* info,
                   void* stream, double* b = nullptr, int ldb = 1, int fill = 1, int top_solve = 0);
 // (split: CTAs per task, each on its own group of right-hand-side columns)
+// (fill: some task's level has P > 1; 0 sizes shared memory for the compact
+// layout of levels with P = 1)
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0, int split = 1);
+                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0, int split = 1,
+                   int fill = 1);
 int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                    double* b, int ldb, int nrhs, const int* skip, void* stream, int split = 1);
+                    double* b, int ldb, int nrhs, const int* skip, void* stream, int split = 1, int fill = 1);
 // one warp per task (blocks n <= kWarpMaxN), forward or backward substitution
 int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0);
+                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0, int fill = 1);
 // bordered inputs of a fused factor-and-solve pass, for every system: Gb_j =
 // [G_j; b_j^T] ((m+1) x n per stage), Rb = [[R, b_g], [b_g^T, 0]] ((m+1)^2)
 // (stages [j0, j1) of every system's arrow, and with `corner` the bordered corners)
@@ -259,6 +264,6 @@ int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const 
 int launch_fill_identity(const LevelDesc* d, const int* sys_desc, int count, double* D, double* R,
                          void* stream);
 size_t factor_smem_bytes(int maxn, int maxm, int mixed, int fill = 1, int dbl = 1);
-size_t solve_smem_bytes(int maxn, int maxm, int single);
+size_t solve_smem_bytes(int maxn, int maxm, int single, int fill = 1);
 
 }  // namespace kkt

@@ -1234,16 +1234,17 @@ __device__ void trsv_warp(TS* t, int ldt, const TS* M, int ldl, const TS* rinv, 
 template <typename TS>
 struct SolveSmem {
   TS *L0, *L1, *ri0, *ri1, *Z0, *Z1, *V, *t;
-  int ldL, ldZ, ldV;
+  int ldL, ldZ, ldV, Rs;  // Rs: panel rows held (2n + m, or n + m on a level with P = 1)
   __device__ TS* L(int q) const { return q ? L1 : L0; }
   __device__ TS* rinv(int q) const { return q ? ri1 : ri0; }
   __device__ TS* Z(int q) const { return q ? Z1 : Z0; }
 };
 
 template <typename TS>
-__device__ __forceinline__ SolveSmem<TS> solve_smem(unsigned char* sm, int n, int m) {
+__device__ __forceinline__ SolveSmem<TS> solve_smem(unsigned char* sm, int n, int m, bool fill) {
   SolveSmem<TS> S;
-  const SolLayout L = sol_layout(n, m, (int)sizeof(TS));
+  const SolLayout L = sol_layout(n, m, (int)sizeof(TS), fill);
+  S.Rs = L.R;
   S.ldL = odd(n);
   S.ldZ = L.ldZ;
   S.ldV = L.ldV;
@@ -1366,7 +1367,7 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
   if (skip && skip[d.sys]) return;
   if (fwd_done && !d.is_top) return;  // the factorization carried this forward sweep
   const int n = d.n, m = d.m, mg = d.m - d.mr;  // mg: rows of the real arrow
-  const SolveSmem<TS> S = solve_smem<TS>(smraw, n, m);
+  const SolveSmem<TS> S = solve_smem<TS>(smraw, n, m, d.P > 1);
   const int oG = n, oW = n + m;
   const SegGeom g = seg_geom(d, tk.seg);
   const int k = tk.seg;
@@ -1383,7 +1384,7 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
   stage_rows(g, 0, n, m, r0, r1);
   if (!fwd_done) prefetch_stage_factor(S, 0, d, g.f, r0, r1, false, G);
   // V_G <- 0, V_W <- rhs of the separator, t <- rhs of the first stage
-  for (int e = G.tid; e < (2 * n + m) * S.ldV; e += G.nt) S.V[e] = TS(0);
+  for (int e = G.tid; e < S.Rs * S.ldV; e += G.nt) S.V[e] = TS(0);
   gsync(G);
   if (g.hasW) rhs(g.f - 1, S.V + oW * S.ldV);
   rhs(g.f, S.t);
@@ -1479,7 +1480,7 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
     store_vec(bg, ldb, gv, S.ldV, mg, nr, G);
   }
   // V <- [0; x_g; 0; -] for the backward sweep of the top level (bordered rows 0)
-  for (int e = G.tid; e < (2 * n + m) * S.ldV; e += G.nt) {
+  for (int e = G.tid; e < S.Rs * S.ldV; e += G.nt) {
     const int r = e / S.ldV;
     if (r < oG || r >= oG + mg) S.V[e] = TS(0);
     else S.V[e] = S.t[(r - oG) * S.ldV + (e - r * S.ldV)];
@@ -1497,12 +1498,12 @@ __device__ void backward_task(const Task tk, const LevelDesc* __restrict__ descs
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
   const int n = d.n, m = d.m;
-  const SolveSmem<TS> S = solve_smem<TS>(smraw, n, m);
+  const SolveSmem<TS> S = solve_smem<TS>(smraw, n, m, d.P > 1);
   const int oG = n, oW = n + m;
   const SegGeom g = seg_geom(d, tk.seg);
   const int k = tk.seg;
   const double* none = nullptr;
-  for (int e = G.tid; e < (2 * n + m) * S.ldV; e += G.nt) S.V[e] = TS(0);
+  for (int e = G.tid; e < S.Rs * S.ldV; e += G.nt) S.V[e] = TS(0);
   gsync(G);
   if (g.hasF) load_vec(S.V, S.ldV, d.Xnext + (size_t)k * n * kRhsChunk + c0, kRhsChunk, none, n, nr, G);
   if (d.m - d.mr) load_vec(S.V + oG * S.ldV, S.ldV, b + (size_t)d.rowG * ldb, ldb, none, d.m - d.mr, nr, G);
@@ -1924,8 +1925,8 @@ size_t factor_smem_bytes(int n, int m, int mixed, int fill, int dbl) {
   return (size_t)fac_layout(n, m, mixed ? 4 : 8, fill != 0, dbl != 0).total;
 }
 
-size_t solve_smem_bytes(int n, int m, int single) {
-  return (size_t)sol_layout(n, m, single ? 4 : 8).total;
+size_t solve_smem_bytes(int n, int m, int single, int fill) {
+  return (size_t)sol_layout(n, m, single ? 4 : 8, fill != 0).total;
 }
 
 int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed,
@@ -1952,7 +1953,7 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
   if (ntasks <= 0) return 0;
   top_solve = top_solve && b && !mixed;
   size_t sm = factor_smem_bytes(maxn, maxm, mixed, fill);
-  if (top_solve) sm = std::max(sm, solve_smem_bytes(maxn, maxm, 0));
+  if (top_solve) sm = std::max(sm, solve_smem_bytes(maxn, maxm, 0, fill));
   const void* fn = mixed ? (pair ? (const void*)k_factor<float, 1> : (const void*)k_factor<float, 4>)
                           : (pair ? (const void*)k_factor<double, 1> : (const void*)k_factor<double, 4>);
   int e = set_smem(fn, sm);
@@ -1997,9 +1998,9 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
 }
 
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done, int split) {
+                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done, int split, int fill) {
   if (ntasks <= 0) return 0;
-  const size_t sm = solve_smem_bytes(maxn, maxm, single);
+  const size_t sm = solve_smem_bytes(maxn, maxm, single, fill);
   const void* fn = single ? (const void*)k_forward<float> : (const void*)k_forward<double>;
   int e = set_smem(fn, sm);
   if (e) return e;
@@ -2013,9 +2014,9 @@ int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int 
 }
 
 int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                    double* b, int ldb, int nrhs, const int* skip, void* stream, int split) {
+                    double* b, int ldb, int nrhs, const int* skip, void* stream, int split, int fill) {
   if (ntasks <= 0) return 0;
-  const size_t sm = solve_smem_bytes(maxn, maxm, single);
+  const size_t sm = solve_smem_bytes(maxn, maxm, single, fill);
   const void* fn = single ? (const void*)k_backward<float> : (const void*)k_backward<double>;
   int e = set_smem(fn, sm);
   if (e) return e;
@@ -2030,9 +2031,9 @@ int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
 
 // warp-per-task substitutions (blocks n <= kWarpMaxN)
 int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
-                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done) {
+                   double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done, int fill) {
   if (ntasks <= 0) return 0;
-  const int slice = (int)solve_smem_bytes(maxn, maxm, single);
+  const int slice = (int)solve_smem_bytes(maxn, maxm, single, fill);
   const int wpc = std::max(1, std::min(8, (200 * 1024) / slice));
   const size_t sm = (size_t)wpc * slice;
   const void* fn = backward ? (single ? (const void*)k_backward_w<float> : (const void*)k_backward_w<double>)
