@@ -1617,7 +1617,7 @@ __global__ void k_axpy(const LevelDesc* __restrict__ descs, const ResTask* __res
 // writes the g-row partials sum_j G_j x_j (m x nr), max|c|, max|x|, max|b|
 // and, with `norms`, the largest stage-row sum of |Psi| and the |G| sums of
 // the g rows; k_residual_final combines them per system.
-__global__ void __launch_bounds__(256) k_residual(const LevelDesc* __restrict__ descs,
+__global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict__ descs,
                                                   const ResTask* __restrict__ tasks, int ntasks,
                                                   const double* __restrict__ uD, const double* __restrict__ uE,
                                                   const double* __restrict__ uG, const double* __restrict__ b,
