@@ -44,6 +44,69 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 L2_FLUSH_BYTES = 256 << 20
 
 
+# --- one process per GPU (torchrun). Every workload partitions into
+# independent systems, so ranks exchange no data: rank r solves its own share
+# of the global batch, and the only collectives are the barriers around the
+# timed region and one MAX reduction of the per-rank step times.
+
+def rank_env():
+    """(world, rank, local_rank) from the torchrun environment; (1, 0, 0) alone."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def init_ranks(backend: str = "nccl"):
+    """Join the process group when launched with more than one rank."""
+    world, rank, local = rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+    return world, rank, local
+
+
+def _grouped() -> bool:
+    import torch.distributed as dist
+    return dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+
+
+def barrier():
+    if _grouped():
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(values):
+    """Elementwise maximum over all ranks of a list of floats (the slowest
+    rank's times); the list itself when running alone."""
+    vals = [float(v) for v in values]
+    if not _grouped():
+        return vals
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu().tolist()]
+
+
+def whole_job_rate(systems_per_rank: int, ms_max: float, world: int) -> float:
+    """Systems per second of the whole job: every rank solves systems_per_rank
+    systems per step, and a step takes the slowest rank's time ms_max."""
+    return world * systems_per_rank * 1000.0 / ms_max
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Seed of rank's share of the global batch (distinct systems per rank)."""
+    return base + 7919 * rank
+
+
+def finish_ranks():
+    if _grouped():
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def backward_error(D, E, G, R, x, b):
     """||b - Psi x||_inf / (||Psi||_inf ||x||_inf + ||b||_inf), blocks of Eq. (3)."""
     N, n, _ = D.shape
@@ -215,7 +278,7 @@ def cpu_oracle_rate(D, E, G, R, b, budget_s: float):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return
     D, E, G, R, b = workload(0, args.nrhs)
@@ -377,13 +440,17 @@ def run_batch(args):
     import gen.device as gdev
     name = args.workload
     spec = BATCHES[name]
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    world, rank, local = rank_env()
+    torch.cuda.set_device(local)
+    init_ranks("nccl")
     Ns, ns, ms = batch_shapes(name)
     count = len(Ns)
-    D, E, G, R = gdev.batch(Ns, ns, ms, seed=11, kind=spec["kind"], sigma_decades=spec["sigma"],
-                            psd_couplings=spec.get("psd", False))
+    # rank r holds systems [r * count, (r + 1) * count) of the global batch:
+    # the same shapes, its own draws
+    D, E, G, R = gdev.batch(Ns, ns, ms, seed=rank_seed(11, rank), kind=spec["kind"],
+                            sigma_decades=spec["sigma"], psd_couplings=spec.get("psd", False))
     rows = int(sum(N * n + m for N, n, m in zip(Ns, ns, ms)))
-    b0 = gdev.rhs(rows, 1, seed=12)
+    b0 = gdev.rhs(rows, 1, seed=rank_seed(12, rank))
     stream = torch.cuda.current_stream()
     sweeps = args.sweeps
     results = {}
@@ -434,7 +501,9 @@ def run_batch(args):
             graph.replay()
         torch.cuda.synchronize()
         ms_list = []
-        with ClockSampler(0) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
             for _ in range(args.steps):
                 reset()
                 e0 = torch.cuda.Event(enable_timing=True)
@@ -444,6 +513,7 @@ def run_batch(args):
                 e1.record(stream)
                 e1.synchronize()
                 ms_list.append(e0.elapsed_time(e1))
+        barrier()
         info = kkt.kkt_get_info(h)
         if info["status"] != 0:
             raise RuntimeError(f"{name}/{path}: factorization failed: {info}")
@@ -457,10 +527,10 @@ def run_batch(args):
             eta = kkt.kkt_refine_eta(h, 0, count)
             eta_raw = eta
         fl = kkt.kkt_flops(h)
-        t_ms = statistics.median(ms_list)
+        t_ms, max_eta = max_over_ranks([statistics.median(ms_list), float(np.max(eta))])
         P1 = [len(kkt.kkt_partition(h, s, 1)) for s in range(count)]
         results[path] = dict(
-            ms_per_step=t_ms, value=count * 1000.0 / t_ms, max_eta=float(np.max(eta)),
+            ms_per_step=t_ms, value=whole_job_rate(count, t_ms, world), max_eta=max_eta,
             max_eta_unrefined=float(np.max(eta_raw)), levels_max=int(max(lv)),
             level1_segments_total=int(sum(P1)), tune_s=tune_s,
             factor_flops=fl["factor"], sequential_factor_flops=fl["sequential_factor"],
@@ -472,11 +542,15 @@ def run_batch(args):
     best = min(ok.items(), key=lambda kv: kv[1]["ms_per_step"]) if ok else min(
         results.items(), key=lambda kv: kv[1]["ms_per_step"])
     bp, br = best
+    if rank != 0:
+        finish_ranks()
+        return
     line = {
-        "metric": METRIC, "value": br["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": br["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": br["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if bp != "mixed" else "f32+f64", "data": "synthetic",
-        "config": {"workload": spec["desc"], "name": name, "path": bp, "systems": count,
+        "config": {"workload": spec["desc"], "name": name, "path": bp, "systems": count * world,
+                   "systems_per_rank": count,
                    "plan": f"two levels, P = {args.P} per system" if args.P else "autotuned per system",
                    "refinement_sweeps": sweeps if "mixed" in spec["paths"] else None,
                    "l2": "inputs larger than L2", "graph": "one CUDA graph per step"},
@@ -489,9 +563,10 @@ def run_batch(args):
         "clocks": br["clocks"],
     }
     line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
-    if not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = batch_cpu_baseline(name, Ns, ns, ms, args.cpu_seconds)
     print(json.dumps(line), flush=True)
+    finish_ranks()
 
 
 def main():
@@ -523,13 +598,9 @@ def main():
         return
 
     import torch
-    import torch.distributed as dist
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
+    init_ranks("nccl")
     import paper_2511_00946_gb300 as kkt
 
     D, E, G, R, b = workload(rank, args.nrhs)
@@ -641,8 +712,7 @@ def main():
         raise RuntimeError(f"factorization failed: {info}")
 
     step_ms, dom_ms = [], []
-    if world > 1:
-        dist.barrier()
+    barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
@@ -659,14 +729,9 @@ def main():
             dom_ms.append((dom_ev[0] if dom > 0 else e0).elapsed_time(dom_ev[1]))
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
-    if world > 1:
-        dist.barrier()
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1000.0 / ms
+    barrier()
+    ms = max_over_ranks([statistics.mean(step_ms)])[0]
+    value = whole_job_rate(1, ms, world)
     x = bd.cpu().numpy()
     errs = [backward_error(D, E, G, R, x.reshape(x.shape[0], -1)[:, c], b.reshape(b.shape[0], -1)[:, c])
             for c in range(args.nrhs)]
@@ -698,6 +763,7 @@ def main():
     stream.wait_stream(cap)
     torch.cuda.synchronize()
     e2e_ms = []
+    barrier()
     for it in range(args.steps + 2):
         hx.copy_(hb)            # host copy of b: x overwrites it
         flush.zero_()
@@ -708,7 +774,8 @@ def main():
         e1.synchronize()
         if it >= 2:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
+    barrier()
+    e2e_val = whole_job_rate(1, max_over_ranks([statistics.mean(e2e_ms)])[0], world)
     e2e_same = bool(np.array_equal(hx.numpy(), x))  # the device path's solution, bit for bit
 
     # --- roofline of the dominant kernel (largest share of the step), timed
@@ -756,8 +823,7 @@ def main():
             out["cpu_baseline"] = cpu
         print(json.dumps(out), flush=True)
     kkt.kkt_destroy(h)
-    if world > 1:
-        dist.destroy_process_group()
+    finish_ranks()
 
 
 if __name__ == "__main__":
