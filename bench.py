@@ -101,6 +101,26 @@ def rank_seed(base: int, rank: int) -> int:
     return base + 7919 * rank
 
 
+def step_stats(ms_list):
+    """Mean, standard deviation, median and extremes of the per-step times (ms)."""
+    return {"mean": statistics.mean(ms_list), "std": statistics.pstdev(ms_list),
+            "median": statistics.median(ms_list), "min": min(ms_list), "max": max(ms_list), "n": len(ms_list)}
+
+
+def host_cpu() -> str:
+    """Model name of the host CPU (as /proc/cpuinfo or the platform reports it)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k, _, v = ln.partition(":")
+                if k.strip() in ("model name", "Model", "CPU part") and v.strip():
+                    return v.strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def finish_ranks():
     if _grouped():
         import torch.distributed as dist
@@ -297,7 +317,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD.format(nrhs=args.nrhs), "method": "FP64 CPU oracle, sequential block Cholesky"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "ms_stats": step_stats([1000.0 * t for t in per_step]),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": host_cpu(),
                          "sample": f"{total_sys} factor+solve runs of the workload system, "
                                    f"{args.steps} steps of about {args.ref_seconds:.0f} s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -430,7 +451,7 @@ def batch_cpu_baseline(name: str, Ns, ns, ms, budget_s: float):
         for _ in range(reps):
             list(ex.map(one, systems))
         dt = time.perf_counter() - t0
-    return dict(value=reps * len(systems) / dt, unit=UNIT, cores=cores, kind="oracle",
+    return dict(value=reps * len(systems) / dt, unit=UNIT, cores=cores, kind="oracle", cpu=host_cpu(),
                 sample=f"{reps} x {len(systems)} systems drawn from the batch on {cores} threads ({dt:.1f} s)")
 
 
@@ -530,7 +551,8 @@ def run_batch(args):
         t_ms, max_eta = max_over_ranks([statistics.median(ms_list), float(np.max(eta))])
         P1 = [len(kkt.kkt_partition(h, s, 1)) for s in range(count)]
         results[path] = dict(
-            ms_per_step=t_ms, value=whole_job_rate(count, t_ms, world), max_eta=max_eta,
+            ms_per_step=t_ms, ms_stats=step_stats(ms_list), value=whole_job_rate(count, t_ms, world),
+            max_eta=max_eta,
             max_eta_unrefined=float(np.max(eta_raw)), levels_max=int(max(lv)),
             level1_segments_total=int(sum(P1)), tune_s=tune_s,
             factor_flops=fl["factor"], sequential_factor_flops=fl["sequential_factor"],
@@ -789,13 +811,14 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, reps, dt = cpu_oracle_rate(D, E, G, R, b, budget_s=args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": host_cpu(),
                "sample": f"{reps} sequential FP64 factor+solve runs of the workload system ({dt:.1f} s)"}
 
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "ms_stats": step_stats(step_ms),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD.format(nrhs=args.nrhs), "levels": plan, "partition": args.partition,
                        "precision": "fp64",
