@@ -683,3 +683,47 @@ def test_factor_solve_host_other_handles(kkt, orc):
             np.testing.assert_array_equal(hb, bd.cpu().numpy())
         finally:
             kkt.kkt_destroy(h)
+
+
+def test_bench_workload_every_candidate_plan(kkt, orc):
+    """The single-system workload exactly as the benchmark times it: its
+    seeds and shapes, every level plan its search may pick, kkt_factor_solve
+    captured into a CUDA graph and replayed after an L2-evicting write. Each
+    plan's x against the oracle's sequential solution, and two replays
+    bitwise equal."""
+    import torch
+    import bench
+    D, E, G, R, b = bench.workload(0)
+    xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b)
+    Dd, Ed, Gd, Rd, b0 = (dev(a) for a in (D, E, G, R, b))
+    flush = torch.empty(bench.L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    part = kkt.KKT_PARTITION_BALANCED
+    plans = bench.candidate_plans(kkt, part)
+    assert plans
+    for plan in plans:
+        h = kkt.kkt_create_plan(bench.N_STAGES, bench.N_BLOCK, bench.M_ARROW, plan, part)
+        try:
+            bd = b0.clone()
+            for _ in range(2):
+                bd.copy_(b0)
+                kkt.kkt_factor_solve(h, Dd, Ed, Gd, Rd, bd)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            cap = torch.cuda.Stream()
+            cap.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(cap):
+                with torch.cuda.graph(g, stream=cap):
+                    kkt.kkt_factor_solve(h, Dd, Ed, Gd, Rd, bd)
+            torch.cuda.current_stream().wait_stream(cap)
+            xs = []
+            for _ in range(2):
+                bd.copy_(b0)
+                flush.zero_()
+                g.replay()
+                torch.cuda.synchronize()
+                xs.append(bd.cpu().numpy())
+            assert kkt.kkt_get_info(h)["status"] == 0, plan
+            np.testing.assert_array_equal(xs[0], xs[1])
+            check_solution(orc, D, E, G, R, xs[0], b, xo, fwd_tol=1e-5)
+        finally:
+            kkt.kkt_destroy(h)
