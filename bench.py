@@ -760,9 +760,10 @@ def main():
     eta, relres = max(e[0] for e in errs), max(e[1] for e in errs)
 
     # --- end to end through the public API with host buffers (pinned): the
-    # host entry point copies the inputs in (the stage blocks in chunks that
-    # overlap the level-1 factorization), factors, solves and copies x back;
-    # the call is captured once into a CUDA graph and replayed
+    # host entry point reads the inputs from host memory (the factor launches
+    # load the page-locked blocks in place; b is copied in), factors, solves
+    # and copies x back; the call is captured once into a CUDA graph and
+    # replayed
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     hD, hE, hG, hR, hb = pin(D), pin(E), pin(G), pin(R), pin(b)
     hx = hb.clone().pin_memory()
@@ -826,7 +827,9 @@ def main():
                        "replicas": world},
             "error": {"backward_error": eta, "relative_residual": relres},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "api": "kkt_factor_solve_host (page-locked host buffers, graph replay)",
+                    "api": "kkt_factor_solve_host (page-locked host buffers, graph replay): the factor "
+                           "launches read D, E, G, R from host memory over the host link, b is copied in and "
+                           "x copied out; the byte counts are every input and output crossing per step",
                     "same_x_as_device_path": e2e_same},
             "gpu_launches": args.steps * nl,
             "launches_per_step": {names[i] if i < len(names) else f"launch {i}": round(a, 4)

@@ -207,20 +207,28 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
                             const double* R, double* b, int nrhs, int ldb, void* stream);
 
 /* kkt_factor_solve from HOST buffers: D, E, G, R and b are host pointers in
- * the layout above (page-locked memory lets the copies run asynchronously);
- * x is written back to b (ldb >= nrhs) when the stream reaches the end of the
- * call. The handle keeps device copies of the inputs (allocated by the first
- * call, which therefore must not run inside a stream capture; later calls
- * may be captured). For one system with the bordered pass (FP64, nrhs = 1,
- * P >= 2 level-1 segments) the copy of the stage rows of D, E, G and b is
- * split at separator stages into up to eight chunks on an internal stream,
- * and each chunk's bordered arrow copy and level-1 segments start on a
- * stream of their own as soon as its rows have arrived (the segments of
- * Algorithm 1 are independent), so the transfer overlaps the level-1
- * factorization; the corner and the g-rows of b travel with the first
- * chunk. Otherwise the inputs are copied on `stream` and kkt_factor_solve
- * runs on the device copies. The result is that of kkt_factor_solve on the same inputs, bit for
- * bit. Launch events are not recorded. */
+ * the layout above; x is written back to b (ldb >= nrhs) when the stream
+ * reaches the end of the call. The handle keeps device buffers (allocated by
+ * the first call, which therefore must not run inside a stream capture;
+ * later calls may be captured). Three ways, by the memory the inputs live in:
+ *  - D, E, G and R all page-locked and addressable by the device
+ *    (cudaHostAlloc or cudaHostRegister; torch pin_memory): the factor
+ *    launches read them in place over the host link, each element once, and
+ *    only b is copied in and x out. The host arrays must stay alive and
+ *    unchanged until the stream has passed the call (for a captured call:
+ *    every replay reads them again).
+ *  - Otherwise, for one system with the bordered pass (FP64, nrhs = 1,
+ *    P >= 2 level-1 segments): the copy of the stage rows of D, E, G and b is
+ *    split at separator stages into up to eight chunks on an internal
+ *    stream, and each chunk's bordered arrow copy and level-1 segments start
+ *    on a stream of their own as soon as its rows have arrived (the segments
+ *    of Algorithm 1 are independent), so the transfer overlaps the level-1
+ *    factorization; the corner and the g-rows of b travel with the first
+ *    chunk.
+ *  - Otherwise the inputs are copied on `stream` and kkt_factor_solve runs on
+ *    the device copies.
+ * The result is that of kkt_factor_solve on the same inputs, bit for bit.
+ * Launch events are not recorded. */
 kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E, const double* G,
                                  const double* R, double* b, int nrhs, int ldb, void* stream);
 

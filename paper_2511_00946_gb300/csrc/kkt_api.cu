@@ -964,6 +964,25 @@ kkt_status host_prepare(kkt_handle* h, int nrhs) {
   }
   return KKT_OK;
 }
+
+// The device address of host array p when it is page-locked memory that the
+// current device can read (cudaHostAlloc / cudaHostRegister with unified
+// addressing); nullptr for pageable memory and anything else. The query
+// enqueues nothing; the thread's capture mode is relaxed around it so that it
+// is also allowed while the caller captures a graph.
+const double* device_view(const double* p) {
+  if (!p) return nullptr;
+  cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+  if (cudaThreadExchangeStreamCaptureMode(&mode) != cudaSuccess) return nullptr;
+  cudaPointerAttributes a;
+  const bool ok = cudaPointerGetAttributes(&a, p) == cudaSuccess;
+  cudaThreadExchangeStreamCaptureMode(&mode);  // back to the caller's mode
+  if (!ok) {
+    cudaGetLastError();  // clear the error an unknown pointer may leave
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost && a.devicePointer ? (const double*)a.devicePointer : nullptr;
+}
 }  // namespace
 
 kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E, const double* G,
@@ -989,6 +1008,20 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
                ? KKT_OK
                : KKT_ERR_CUDA;
   };
+  // page-locked inputs: the factorization reads D, E, G and R in place over
+  // the host link (each element once, by the launch that factors its stage),
+  // so only b is copied in and x out
+  const double *vD = device_view(D), *vE = h->tot_E ? device_view(E) : nullptr,
+               *vG = h->tot_G ? device_view(G) : nullptr, *vR = h->tot_R ? device_view(R) : nullptr;
+  if (vD && (vE || !h->tot_E) && (vG || !h->tot_G) && (vR || !h->tot_R)) {
+    if (!b_in()) return KKT_ERR_CUDA;
+    std::vector<cudaEvent_t> ev;
+    ev.swap(h->events);  // no launch events on this path
+    const kkt_status st = kkt_factor_solve(h, vD, vE, h->maxm ? vG : nullptr, h->maxm ? vR : nullptr, h->hsB,
+                                           nrhs, nrhs, stream);
+    h->events.swap(ev);
+    return st != KKT_OK ? st : b_out();
+  }
   const bool chunked = h->count == 1 && h->border && nrhs == 1 && h->sys[0].lv[0].P >= 2 &&
                        h->fac_groups[0].size() == 1;
   if (!chunked) {

@@ -619,9 +619,10 @@ def test_factor_solve_reports_breakdown(kkt):
     (90, 24, 6, [9, 1], 3),          # several right-hand sides: the plain path
 ])
 def test_factor_solve_host_matches_device(kkt, orc, N, n, m, levels, nrhs):
-    """kkt_factor_solve from host buffers (page-locked torch tensors and plain
-    NumPy arrays) returns, bit for bit, what kkt_factor_solve returns on device
-    copies of the same inputs: the chunked transfer only reorders launches of
+    """kkt_factor_solve from host buffers (page-locked torch tensors, read in
+    place by the factorization, and plain NumPy arrays, copied in chunks)
+    returns, bit for bit, what kkt_factor_solve returns on device copies of
+    the same inputs: the chunked transfer only reorders launches of
     independent segments."""
     import torch
     D, E, G, R = gen.ipm(N, n, m, seed=81)
@@ -727,3 +728,47 @@ def test_bench_workload_every_candidate_plan(kkt, orc):
             check_solution(orc, D, E, G, R, xs[0], b, xo, fwd_tol=1e-5)
         finally:
             kkt.kkt_destroy(h)
+
+
+@pytest.mark.parametrize("N,n,m,levels", [(120, 24, 6, [12, 3, 1]), (60, 8, 4, [6, 1]), (50, 17, 0, [1])])
+def test_factor_solve_host_page_locked_graph(kkt, N, n, m, levels):
+    """Page-locked inputs read in place, captured into a CUDA graph: two
+    replays give the device path's x bit for bit. With only some inputs
+    page-locked the call falls back to copying, with the same result."""
+    import torch
+    D, E, G, R = gen.ipm(N, n, m, seed=83)
+    b = gen.rhs(N * n + m, 1, seed=84)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h = kkt.kkt_create_plan(N, n, m, levels, kkt.KKT_PARTITION_BALANCED)
+    try:
+        bd = dev(b)
+        kkt.kkt_factor_solve(h, dev(D), dev(E) if N > 1 else None, dev(G) if m else None, dev(R) if m else None, bd)
+        torch.cuda.synchronize()
+        x_dev = bd.cpu().numpy()
+        hD, hE, hG, hR = pin(D), pin(E) if N > 1 else None, pin(G) if m else None, pin(R) if m else None
+        hb0, hb = pin(b), pin(b)
+        kkt.kkt_factor_solve_host(h, hD, hE, hG, hR, hb)      # eager, before capture
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(hb.numpy(), x_dev)
+        g = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(g, stream=cap):
+                kkt.kkt_factor_solve_host(h, hD, hE, hG, hR, hb)
+        torch.cuda.current_stream().wait_stream(cap)
+        for _ in range(2):
+            hb.copy_(hb0)
+            g.replay()
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(hb.numpy(), x_dev)
+        del g
+        # D page-locked, the rest pageable: the copy path
+        nb = np.ascontiguousarray(b).copy()
+        kkt.kkt_factor_solve_host(h, hD, np.ascontiguousarray(E) if N > 1 else None,
+                                  np.ascontiguousarray(G) if m else None, np.ascontiguousarray(R) if m else None, nb)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(nb, x_dev)
+        assert kkt.kkt_get_info(h)["status"] == 0
+    finally:
+        kkt.kkt_destroy(h)
