@@ -74,7 +74,11 @@ __device__ __forceinline__ void gsync(const Grp& g) {
 // loads zeros. Coalesced over the global array.
 // The three source cases are separate loops: a predicated-off FP64 add still
 // holds the FP64 pipe on this part.
-template <typename T>
+// U > 1: every thread issues U loads before their stores. The stores go to
+// shared memory, which the compiler cannot prove disjoint from A and B, so
+// with U = 1 each load's latency is waited out in turn (U = 1 keeps the
+// register footprint of the warp kernels).
+template <int U = 1, typename T>
 __device__ void load_blk(T* dst, int ld, const double* A, const double* B, int rows, int cols,
                          bool trans, Grp g = cta_grp()) {
   const int tot = rows * cols;
@@ -84,10 +88,27 @@ __device__ void load_blk(T* dst, int ld, const double* A, const double* B, int r
     else { r = e / cols; c = e - r * cols; }
     return r * ld + c;
   };
+  auto batched = [&](auto get) {
+    for (int e0 = g.tid; e0 < tot; e0 += U * g.nt) {
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * g.nt;
+        v[u] = e < tot ? get(e) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * g.nt;
+        if (e < tot) dst[at(e)] = (T)v[u];
+      }
+    }
+  };
   if (A && B) {
-    for (int e = g.tid; e < tot; e += g.nt) dst[at(e)] = (T)(A[e] + B[e]);
+    if constexpr (U > 1) batched([&](int e) { return A[e] + B[e]; });
+    else for (int e = g.tid; e < tot; e += g.nt) dst[at(e)] = (T)(A[e] + B[e]);
   } else if (A) {
-    for (int e = g.tid; e < tot; e += g.nt) dst[at(e)] = (T)A[e];
+    if constexpr (U > 1) batched([&](int e) { return A[e]; });
+    else for (int e = g.tid; e < tot; e += g.nt) dst[at(e)] = (T)A[e];
   } else {
     for (int e = g.tid; e < tot; e += g.nt) dst[at(e)] = T(0);
   }
@@ -593,7 +614,7 @@ __device__ void corner_factor(double* Rs, int ldR, int m, int mr, double* rinv, 
 // caller's arrays at level 1, the slots of the level below otherwise), the
 // stores of its factor blocks and the next level's slots. Used by the CTA
 // kernel (k_factor) and the warp kernel (k_factor_w) alike.
-template <typename TZ>
+template <typename TZ, int LU>
 struct FacCtx {
   static constexpr bool mixed = sizeof(TZ) == 4;
   const LevelDesc* d;
@@ -635,18 +656,18 @@ struct FacCtx {
   __device__ void load_first(bool eg, bool wr, Grp G) const {
     const double* none = nullptr;
     if (eg) {
-      load_blk(Dfac, ldD, Dp(Din, g.f), Dp(D2, g.f), n, n, false, G);
-      if (g.len > 1 || g.hasF) load_blk(Z, ldZ, Dp(Ein, g.f), none, n, n, false, G);
-      if (m) load_blk(Z + oG * ldZ, ldZ, Gp(Gin, g.f), Gp(G2, g.f), m, n, false, G);
+      load_blk<LU>(Dfac, ldD, Dp(Din, g.f), Dp(D2, g.f), n, n, false, G);
+      if (g.len > 1 || g.hasF) load_blk<LU>(Z, ldZ, Dp(Ein, g.f), none, n, n, false, G);
+      if (m) load_blk<LU>(Z + oG * ldZ, ldZ, Gp(Gin, g.f), Gp(G2, g.f), m, n, false, G);
       if (g.len > 1) {
-        load_blk(T, ldT, Dp(Din, g.f + 1), Dp(D2, g.f + 1), n, n, false, G);          // D_{2}
-        if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, g.f + 1), Gp(G2, g.f + 1), m, n, false, G);
+        load_blk<LU>(T, ldT, Dp(Din, g.f + 1), Dp(D2, g.f + 1), n, n, false, G);          // D_{2}
+        if (m) load_blk<LU>(T + oG * ldT, ldT, Gp(Gin, g.f + 1), Gp(G2, g.f + 1), m, n, false, G);
       }
     }
     if (wr) {
-      load_blk(Z + oW * ldZ, ldZ, Dp(Ein, s), none, n, n, true, G);                 // W_1 = B_k = E[s]^T
-      load_blk(T + oW * ldT + oW, ldT, Dp(Din, s), Dp(D2, s), n, n, false, G);       // A_k
-      if (m) load_blk(T + oW * ldT + oG, ldT, Gp(Gin, s), Gp(G2, s), n, m, true, G);  // Q_k^T
+      load_blk<LU>(Z + oW * ldZ, ldZ, Dp(Ein, s), none, n, n, true, G);                 // W_1 = B_k = E[s]^T
+      load_blk<LU>(T + oW * ldT + oW, ldT, Dp(Din, s), Dp(D2, s), n, n, false, G);       // A_k
+      if (m) load_blk<LU>(T + oW * ldT + oG, ldT, Gp(Gin, s), Gp(G2, s), n, m, true, G);  // Q_k^T
     }
   }
 
@@ -709,15 +730,15 @@ struct FacCtx {
     const double* none = nullptr;
     if (m) copy_blk(Z + oG * ldZ, ldZ, T + oG * ldT, ldT, m, n, G);          // G_{i+1}
     if (withW) copy_blk(Z + oW * ldZ, ldZ, T + oW * ldT, ldT, n, n, G);      // W_{i+1}
-    if ((i + 1 < g.len - 1) || g.hasF) load_blk(Z, ldZ, Dp(Ein, j + 1), none, n, n, false, G);
+    if ((i + 1 < g.len - 1) || g.hasF) load_blk<LU>(Z, ldZ, Dp(Ein, j + 1), none, n, n, false, G);
     gsync(G);
-    if (withW) load_blk(T + oW * ldT, ldT, none, none, n, n, false, G);     // W_{i+2} <- 0
+    if (withW) load_blk<LU>(T + oW * ldT, ldT, none, none, n, n, false, G);     // W_{i+2} <- 0
     if (i + 2 < g.len) {
-      load_blk(T, ldT, Dp(Din, j + 2), Dp(D2, j + 2), n, n, false, G);
-      if (m) load_blk(T + oG * ldT, ldT, Gp(Gin, j + 2), Gp(G2, j + 2), m, n, false, G);
+      load_blk<LU>(T, ldT, Dp(Din, j + 2), Dp(D2, j + 2), n, n, false, G);
+      if (m) load_blk<LU>(T + oG * ldT, ldT, Gp(Gin, j + 2), Gp(G2, j + 2), m, n, false, G);
     } else {
-      load_blk(T, ldT, none, none, n, n, false, G);
-      if (m) load_blk(T + oG * ldT, ldT, none, none, m, n, false, G);
+      load_blk<LU>(T, ldT, none, none, n, n, false, G);
+      if (m) load_blk<LU>(T + oG * ldT, ldT, none, none, m, n, false, G);
     }
     gsync(G);
   }
@@ -764,7 +785,7 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
   const LevelDesc& d = descs[tk.desc];
   constexpr bool mixed = sizeof(TZ) == 4;
   const FacLayout lay = fac_layout(d.n, d.m, (int)sizeof(TZ), d.P > 1, dbl != 0);
-  const FacCtx<TZ> cx(d, tk.seg, smraw, lay, uD, uE, uG);
+  const FacCtx<TZ, 4> cx(d, tk.seg, smraw, lay, uD, uE, uG);
   const int n = cx.n, m = cx.m, R = cx.R, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG, oW = cx.oW;
   double* const Dfac = cx.Dfac;
   double* const rinv = cx.rinv;
@@ -1035,7 +1056,7 @@ __global__ void __launch_bounds__(256, 4) k_factor_w(const LevelDesc* __restrict
   const LevelDesc& d = descs[tk.desc];
   unsigned char* sm = smraw + (size_t)wid * slice;
   const FacLayout lay = fac_layout_w(d.n, d.m, (int)sizeof(TZ), d.P > 1);
-  const FacCtx<TZ> cx(d, tk.seg, sm, lay, uD, uE, uG);
+  const FacCtx<TZ, 1> cx(d, tk.seg, sm, lay, uD, uE, uG);
   const int n = cx.n, m = cx.m, R = cx.R, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG;
   const SegGeom g = cx.g;
   const Grp W{lane, 32, -1};
