@@ -997,16 +997,18 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
   auto h2d = [&](double* dst, const double* src, size_t cnt, cudaStream_t st) {
     return cnt == 0 || cudaMemcpyAsync(dst, src, cnt * d8, cudaMemcpyHostToDevice, st) == cudaSuccess;
   };
-  // b: (N n + m) rows of ldb on the host, nrhs packed columns on the device
-  auto b_in = [&]() {
-    return cudaMemcpy2DAsync(h->hsB, nrhs * d8, b, ldb * d8, nrhs * d8, h->tot_B, cudaMemcpyHostToDevice, s) ==
-           cudaSuccess;
+  // b: (N n + m) rows of ldb on the host, nrhs packed columns on the device;
+  // one linear copy when the host rows are packed too (a pitched copy of
+  // 8-byte rows moves one row at a time)
+  auto rows_copy = [&](double* dst, size_t dld, const double* src, size_t sld, size_t rows, cudaMemcpyKind kind,
+                       cudaStream_t st) {
+    if (dld == (size_t)nrhs && sld == (size_t)nrhs)
+      return cudaMemcpyAsync(dst, src, rows * nrhs * d8, kind, st) == cudaSuccess;
+    return cudaMemcpy2DAsync(dst, dld * d8, src, sld * d8, nrhs * d8, rows, kind, st) == cudaSuccess;
   };
+  auto b_in = [&]() { return rows_copy(h->hsB, nrhs, b, ldb, h->tot_B, cudaMemcpyHostToDevice, s); };
   auto b_out = [&]() {
-    return cudaMemcpy2DAsync(b, ldb * d8, h->hsB, nrhs * d8, nrhs * d8, h->tot_B, cudaMemcpyDeviceToHost, s) ==
-                   cudaSuccess
-               ? KKT_OK
-               : KKT_ERR_CUDA;
+    return rows_copy(b, ldb, h->hsB, nrhs, h->tot_B, cudaMemcpyDeviceToHost, s) ? KKT_OK : KKT_ERR_CUDA;
   };
   // page-locked inputs: the factorization reads D, E, G and R in place over
   // the host link (each element once, by the launch that factors its stage),
@@ -1057,13 +1059,13 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
     if (!h2d(h->hsD + lo * nn, D + lo * nn, (size_t)(hi - lo) * nn, cs) ||
         (ehi > lo && !h2d(h->hsE + lo * nn, E + lo * nn, (size_t)(ehi - lo) * nn, cs)) ||
         !h2d(h->hsG + lo * mn, G + lo * mn, (size_t)(hi - lo) * mn, cs) ||
-        cudaMemcpy2DAsync(h->hsB + (size_t)lo * sp.n, d8, b + (size_t)lo * sp.n * ldb, ldb * d8, d8,
-                          (size_t)(hi - lo) * sp.n, cudaMemcpyHostToDevice, cs) != cudaSuccess)
+        !rows_copy(h->hsB + (size_t)lo * sp.n, 1, b + (size_t)lo * sp.n * ldb, ldb, (size_t)(hi - lo) * sp.n,
+                   cudaMemcpyHostToDevice, cs))
       return KKT_ERR_CUDA;
     if (c == 0 && sp.m > 0 &&
         (!h2d(h->hsR, R, h->tot_R, cs) ||
-         cudaMemcpy2DAsync(h->hsB + (size_t)sp.N * sp.n, d8, b + (size_t)sp.N * sp.n * ldb, ldb * d8, d8,
-                           (size_t)sp.m, cudaMemcpyHostToDevice, cs) != cudaSuccess))
+         !rows_copy(h->hsB + (size_t)sp.N * sp.n, 1, b + (size_t)sp.N * sp.n * ldb, ldb, (size_t)sp.m,
+                    cudaMemcpyHostToDevice, cs)))
       return KKT_ERR_CUDA;
     if (cudaEventRecord(h->hs_ev_copy[c], cs) != cudaSuccess) return KKT_ERR_CUDA;
     cudaStream_t ls = h->hs_lvl[c];
