@@ -208,9 +208,12 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
 
 /* kkt_factor_solve from HOST buffers: D, E, G, R and b are host pointers in
  * the layout above; x is written back to b (ldb >= nrhs) when the stream
- * reaches the end of the call. The handle keeps device buffers (allocated by
- * the first call, which therefore must not run inside a stream capture;
- * later calls may be captured). Three ways, by the memory the inputs live in:
+ * reaches the end of the call. The handle keeps device buffers: a copy of b
+ * (allocated by the first call, and again by a call with more right-hand
+ * sides than any before) and copies of D, E, G, R (allocated by the first
+ * call that copies them). A call that allocates must not run inside a stream
+ * capture and invalidates graphs captured before it; the others may be
+ * captured. Three ways, by the memory the inputs live in:
  *  - D, E, G and R all page-locked and addressable by the device
  *    (cudaHostAlloc or cudaHostRegister; torch pin_memory): the factor
  *    launches read them in place over the host link, each element once, and

@@ -191,7 +191,8 @@ struct kkt_handle {
   // kkt_factor_solve_host: device copies of the inputs and the streams and
   // events of the overlapped transfer (created by the first call)
   static constexpr int kHostChunks = 8;
-  void* hs_mem = nullptr;
+  void* hs_mem = nullptr;                    // device copies of D, E, G, R (only when a call copies them)
+  void* hs_bmem = nullptr;                   // device copy of b
   double *hsD = nullptr, *hsE = nullptr, *hsG = nullptr, *hsR = nullptr, *hsB = nullptr;
   int hs_nrhs = 0;                           // columns the b copy has room for
   cudaStream_t hs_copy = nullptr, hs_lvl[kHostChunks] = {};
@@ -751,6 +752,7 @@ kkt_status kkt_destroy(kkt_handle* h) {
   if (!h) return KKT_OK;
   if (h->dmem) cudaFree(h->dmem);
   if (h->hs_mem) cudaFree(h->hs_mem);
+  if (h->hs_bmem) cudaFree(h->hs_bmem);
   if (h->hs_copy) cudaStreamDestroy(h->hs_copy);
   if (h->hs_ev_start) cudaEventDestroy(h->hs_ev_start);
   for (int c = 0; c < kkt_handle::kHostChunks; ++c) {
@@ -932,26 +934,34 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
 }
 
 namespace {
-// Device copies of the inputs and the overlap streams of kkt_factor_solve_host.
-kkt_status host_prepare(kkt_handle* h, int nrhs) {
-  if (h->hs_mem && h->hs_nrhs >= nrhs) return KKT_OK;
-  if (h->hs_mem) {
-    cudaFree(h->hs_mem);
-    h->hs_mem = nullptr;
-  }
+// Device buffers and the overlap streams of kkt_factor_solve_host: the copy
+// of b always, copies of D, E, G, R only for inputs that are not read in
+// place (`inputs`).
+kkt_status host_prepare(kkt_handle* h, int nrhs, bool inputs) {
   const size_t d8 = sizeof(double);
-  const size_t tot = h->tot_D + h->tot_E + h->tot_G + h->tot_R + h->tot_B * (size_t)nrhs;
-  if (cudaMalloc(&h->hs_mem, std::max<size_t>(tot, 1) * d8) != cudaSuccess) {
-    h->hs_mem = nullptr;
-    return KKT_ERR_CUDA;
+  if (!h->hs_bmem || h->hs_nrhs < nrhs) {
+    if (h->hs_bmem) cudaFree(h->hs_bmem);
+    h->hs_bmem = nullptr;
+    if (cudaMalloc(&h->hs_bmem, std::max<size_t>(h->tot_B * (size_t)nrhs, 1) * d8) != cudaSuccess) {
+      h->hs_bmem = nullptr;
+      h->hs_nrhs = 0;
+      return KKT_ERR_CUDA;
+    }
+    h->hsB = (double*)h->hs_bmem;
+    h->hs_nrhs = nrhs;
   }
-  double* p = (double*)h->hs_mem;
-  h->hsD = p; p += h->tot_D;
-  h->hsE = p; p += h->tot_E;
-  h->hsG = p; p += h->tot_G;
-  h->hsR = p; p += h->tot_R;
-  h->hsB = p;
-  h->hs_nrhs = nrhs;
+  if (inputs && !h->hs_mem) {
+    const size_t tot = h->tot_D + h->tot_E + h->tot_G + h->tot_R;
+    if (cudaMalloc(&h->hs_mem, std::max<size_t>(tot, 1) * d8) != cudaSuccess) {
+      h->hs_mem = nullptr;
+      return KKT_ERR_CUDA;
+    }
+    double* p = (double*)h->hs_mem;
+    h->hsD = p; p += h->tot_D;
+    h->hsE = p; p += h->tot_E;
+    h->hsG = p; p += h->tot_G;
+    h->hsR = p;
+  }
   if (!h->hs_copy) {
     if (cudaStreamCreateWithFlags(&h->hs_copy, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->hs_ev_start, cudaEventDisableTiming) != cudaSuccess)
@@ -990,8 +1000,6 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
   if (!h || !D || !b || nrhs < 1 || ldb < nrhs) return KKT_ERR_ARG;
   if (h->tot_E > 0 && !E) return KKT_ERR_ARG;
   if (h->maxm > 0 && (!G || !R)) return KKT_ERR_ARG;
-  const kkt_status ps = host_prepare(h, nrhs);
-  if (ps != KKT_OK) return ps;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t d8 = sizeof(double);
   auto h2d = [&](double* dst, const double* src, size_t cnt, cudaStream_t st) {
@@ -1015,7 +1023,10 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
   // so only b is copied in and x out
   const double *vD = device_view(D), *vE = h->tot_E ? device_view(E) : nullptr,
                *vG = h->tot_G ? device_view(G) : nullptr, *vR = h->tot_R ? device_view(R) : nullptr;
-  if (vD && (vE || !h->tot_E) && (vG || !h->tot_G) && (vR || !h->tot_R)) {
+  const bool in_place = vD && (vE || !h->tot_E) && (vG || !h->tot_G) && (vR || !h->tot_R);
+  const kkt_status ps = host_prepare(h, nrhs, !in_place);
+  if (ps != KKT_OK) return ps;
+  if (in_place) {
     if (!b_in()) return KKT_ERR_CUDA;
     std::vector<cudaEvent_t> ev;
     ev.swap(h->events);  // no launch events on this path

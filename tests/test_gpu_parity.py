@@ -772,3 +772,31 @@ def test_factor_solve_host_page_locked_graph(kkt, N, n, m, levels):
         assert kkt.kkt_get_info(h)["status"] == 0
     finally:
         kkt.kkt_destroy(h)
+
+
+def test_factor_solve_host_page_locked_allocates_no_input_copies(kkt):
+    """With page-locked inputs the host entry point keeps only a device copy
+    of b: the device's free memory drops by far less than the 19 MB of D, E,
+    G, R (a copy of them is made only by a call that needs one)."""
+    import torch
+    N, n, m = 1024, 32, 8
+    D, E, G, R = gen.ipm(N, n, m, seed=85)
+    b = gen.rhs(N * n + m, 1, seed=86)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h = kkt.kkt_create_plan(N, n, m, [152, 38, 10, 1], kkt.KKT_PARTITION_BALANCED)
+    try:
+        bd = dev(b)
+        kkt.kkt_factor_solve(h, dev(D), dev(E), dev(G), dev(R), bd)   # modules loaded, handle warm
+        torch.cuda.synchronize()
+        hD, hE, hG, hR, hb = pin(D), pin(E), pin(G), pin(R), pin(b)
+        free0 = torch.cuda.mem_get_info()[0]
+        kkt.kkt_factor_solve_host(h, hD, hE, hG, hR, hb)
+        torch.cuda.synchronize()
+        drop = free0 - torch.cuda.mem_get_info()[0]
+        inputs = sum(a.nbytes for a in (D, E, G, R))
+        assert inputs > 16 << 20
+        assert drop <= 8 << 20, (drop, inputs)
+        np.testing.assert_array_equal(hb.numpy(), bd.cpu().numpy())
+        assert kkt.kkt_get_info(h)["status"] == 0
+    finally:
+        kkt.kkt_destroy(h)
