@@ -107,16 +107,27 @@ def step_stats(ms_list):
             "median": statistics.median(ms_list), "min": min(ms_list), "max": max(ms_list), "n": len(ms_list)}
 
 
+# Arm cores report an implementer and a part number instead of a model name
+ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd49": "Arm Neoverse N2",
+             "0xd0c": "Arm Neoverse N1", "0xd8e": "Arm Neoverse N3", "0xd84": "Arm Neoverse V3"}
+
+
 def host_cpu() -> str:
     """Model name of the host CPU (as /proc/cpuinfo or the platform reports it)."""
+    part = None
     try:
         with open("/proc/cpuinfo") as f:
             for ln in f:
                 k, _, v = ln.partition(":")
-                if k.strip() in ("model name", "Model", "CPU part") and v.strip():
-                    return v.strip()
+                k, v = k.strip(), v.strip()
+                if k in ("model name", "Model") and v:
+                    return v
+                if k == "CPU part" and v and part is None:
+                    part = v.lower()
     except OSError:
         pass
+    if part:
+        return ARM_PARTS.get(part, f"Arm CPU part {part}")
     import platform
     return platform.processor() or platform.machine()
 
