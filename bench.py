@@ -112,11 +112,11 @@ ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd49": "A
              "0xd0c": "Arm Neoverse N1", "0xd8e": "Arm Neoverse N3", "0xd84": "Arm Neoverse V3"}
 
 
-def host_cpu() -> str:
+def host_cpu(cpuinfo: str = "/proc/cpuinfo") -> str:
     """Model name of the host CPU (as /proc/cpuinfo or the platform reports it)."""
     part = None
     try:
-        with open("/proc/cpuinfo") as f:
+        with open(cpuinfo) as f:
             for ln in f:
                 k, _, v = ln.partition(":")
                 k, v = k.strip(), v.strip()

@@ -105,3 +105,19 @@ def test_reference_arm_under_torchrun_prints_one_line():
     rec = json.loads(lines[0])
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["value"] > 0
     assert rec["e2e"]["h2d_bytes_per_step"] == 0 and rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_host_cpu_names_x86_and_arm(tmp_path):
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    x86 = tmp_path / "x86"
+    x86.write_text("processor\t: 0\nmodel name\t: Some Xeon @ 2.70GHz\nflags\t\t: fpu\n")
+    arm = tmp_path / "arm"
+    arm.write_text("processor\t: 0\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n\nprocessor\t: 1\nCPU part\t: 0xd4f\n")
+    odd = tmp_path / "odd"
+    odd.write_text("processor\t: 0\nCPU part\t: 0xabc\n")
+    assert bench.host_cpu(str(x86)) == "Some Xeon @ 2.70GHz"
+    assert bench.host_cpu(str(arm)) == "Arm Neoverse V2"
+    assert bench.host_cpu(str(odd)) == "Arm CPU part 0xabc"
+    assert bench.host_cpu(str(tmp_path / "missing"))      # falls back to the platform's name
