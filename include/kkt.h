@@ -131,7 +131,10 @@ kkt_status kkt_create_plan(int N, int n, int m, int nlevels, const int* P_levels
                            int precision, kkt_handle** out);
 
 /* Batch of `count` independent systems; system s has N[s], n[s], m[s] and
- * P[s] segments (P = NULL: P = 1, the sequential method, for every system).
+ * P[s] segments (the two-phase method of kkt_create; P[s] = 1 is the
+ * sequential method). P = NULL lets the autotuner pick every system's level
+ * plan: the call is then kkt_batch_create_tuned (it blocks while the
+ * candidates are timed and must be made outside any graph capture).
  * Limits per system as for kkt_create. */
 kkt_status kkt_batch_create(int count, const int* N, const int* n, const int* m, const int* P,
                             int precision, kkt_handle** out);
@@ -346,10 +349,11 @@ kkt_status kkt_plan_flops(int N, int n, int m, int nlevels, const int* P_levels,
 
 /* Factor and solve ONE system without allocating any memory (the paper has
  * no counterpart: this serves callers that cannot allocate device memory
- * where they solve, e.g. code inside a CUDA-graph capture region or a
- * real-time loop that must not touch an allocator, or a plugin whose host
- * owns all allocations). Same method as kkt_create(N, n, m, P, KKT_FP64)
- * followed by kkt_factor and kkt_solve, with the same results.
+ * where they solve, e.g. a real-time control loop that must not touch an
+ * allocator, a plugin whose host framework owns every allocation, or a
+ * process whose memory pool is exhausted). Same method as
+ * kkt_create(N, n, m, P, KKT_FP64) followed by kkt_factor and kkt_solve,
+ * with the same results.
  *  - D, E, G, R, b: device pointers as for kkt_factor / kkt_solve; b is
  *    overwritten with the solution. `info`: optional device pointer to 4
  *    ints that receive the kkt_info record of a breakdown (zeroed first by
@@ -362,13 +366,15 @@ kkt_status kkt_plan_flops(int N, int n, int m, int nlevels, const int* P_levels,
  *    or P > 1024, returns KKT_ERR_CAPACITY before any work is enqueued.
  *  - The first call on a device (with that device current) looks up the
  *    array's device address with cudaGetSymbolAddress; make that first call
- *    before any stream capture. Each call copies a few small tables from
- *    host memory with cudaMemcpyAsync (pageable, so it synchronizes with
- *    `stream` first) and clears the breakdown record with cudaMemsetAsync.
+ *    before any stream capture. Every call stages its small tables
+ *    (descriptors, tasks, index maps) from host memory into the array with
+ *    cudaMemcpyAsync from a pageable buffer, which may block the host until
+ *    the data is staged, and clears the breakdown record with
+ *    cudaMemsetAsync.
  *  - Every call on a device shares the one array and leaves its contents
  *    behind. Calls whose work overlaps on the GPU (other streams, other
- *    host threads, other processes' contexts excluded) race on it and give
- *    undefined results: serialize them, e.g. on one stream.
+ *    host threads) race on it and give undefined results: serialize them,
+ *    e.g. on one stream.
  * Returns KKT_ERR_ARG for invalid sizes or pointers, KKT_ERR_PARTITION when
  * P > floor((N+1)/2). */
 kkt_status kkt_solve_noalloc(int N, int n, int m, int P, const double* D, const double* E,

@@ -338,6 +338,14 @@ def kkt_solve_noalloc(N: int, n: int, m: int, P: int, D, E, G, R, b, nrhs: int |
         nrhs = 1 if b.dim() == 1 else b.shape[1]
     if ldb is None:
         ldb = 1 if b.dim() == 1 else b.shape[1]
+    # the kernels read and write every element of these extents: a smaller
+    # tensor would be accessed out of bounds
+    need = {"D": (D, N * n * n), "E": (E, (N - 1) * n * n), "G": (G, N * m * n), "R": (R, m * m),
+            "b": (b, ((N * n + m - 1) * ldb + nrhs) if N * n + m > 0 else 0)}
+    for name, (t, count) in need.items():
+        if count > 0 and (t is None or t.numel() < count):
+            raise ValueError(f"kkt_solve_noalloc: {name} needs at least {count} elements for N={N}, n={n}, "
+                             f"m={m}, nrhs={nrhs}, ldb={ldb}")
     ip = None
     if info is not None:
         import torch

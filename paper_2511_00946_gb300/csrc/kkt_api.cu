@@ -630,10 +630,11 @@ kkt_status kkt_create_plan(int N, int n, int m, int nlevels, const int* P_levels
 
 kkt_status kkt_batch_create(int count, const int* N, const int* n, const int* m, const int* P,
                             int precision, kkt_handle** out) {
+  if (!P) return kkt_batch_create_tuned(count, N, n, m, precision, nullptr, out);
   if (count < 1 || !N || !n || !m) return KKT_ERR_ARG;
   std::vector<std::vector<int>> Ps(count);
   for (int s = 0; s < count; ++s) {
-    const int p = P ? P[s] : 1;
+    const int p = P[s];
     if (p < 1) return KKT_ERR_PARTITION;
     Ps[s] = (p == 1) ? std::vector<int>{1} : std::vector<int>{p, 1};
   }

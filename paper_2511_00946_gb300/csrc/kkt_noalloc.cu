@@ -1,17 +1,20 @@
 // kkt_solve_noalloc: factor and solve one system without allocating memory.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// solve: code running inside a CUDA-graph capture region or a real-time
-// control loop that must not touch the allocator, plugins whose host
-// framework owns every allocation, or processes whose memory pool is already
-// exhausted. For them this entry point keeps its factor and scratch space in
-// a fixed, library-owned device array instead of a handle's cudaMalloc.
+// solve: a real-time control loop that must not touch the allocator, a
+// plugin whose host framework owns every allocation, or a process whose
+// memory pool is already exhausted. For them this entry point keeps its
+// factor and scratch space in a fixed, library-owned device array instead of
+// a handle's cudaMalloc.
 //
 // The array is a file-scope __device__ variable of kNoallocBytes (16 MiB).
 // Every GPU on which the library is loaded holds it until the process exits.
 // Its host-side name is only a stand-in, not a device address: the device
 // address is looked up with cudaGetSymbolAddress once per device (on the
-// first call made with that device current) and cached.
+// first call made with that device current) and cached. Each call stages a
+// few small tables (level descriptors, task list, index maps) from a static
+// host buffer into the array with cudaMemcpyAsync from pageable memory, which
+// may block the host until the data is staged.
 #include <cuda_runtime.h>
 
 #include <cstring>

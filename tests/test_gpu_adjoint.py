@@ -55,16 +55,24 @@ def test_adjoint_matches_oracle(kkt, orc, N, n, m, levels, precision, nrhs):
                                    err_msg=name)
 
 
-def test_autograd_function_and_finite_differences(kkt):
+@pytest.mark.parametrize("sigma,levels,abs_tol", [(1.0, [16, 1], 1e-6), (8.0, [1], 1e-5)])
+def test_autograd_function_and_finite_differences(kkt, sigma, levels, abs_tol):
     """L = 1/2 ||x||^2 through the differentiable solve (the differentiable-MPC
     workload shape: N = 256, n = 32, m = 8): autograd gradients against
     central differences (h = 1e-6) of the same GPU forward on 64 sampled
-    entries of D (lower), E, G, R and b."""
+    entries of D (lower), E, G, R and b. With Sigma over 16 decades (the
+    workload's, kappa ~ 1e9) the rounding of the forward solve moves L by
+    far more than h^2 terms do, and the central difference itself is only
+    good to a few 1e-6 absolute (measured with the FP64 oracle's forward
+    on the same samples: at most 3.2e-6, where Richardson extrapolation does
+    not help, so it is noise, not truncation); the exact check at that
+    conditioning is the comparison with the oracle's adjoint
+    (test_gpu_bench_shapes)."""
     import torch
     N, n, m = 256, 32, 8
-    D, E, G, R = gen.ipm(N, n, m, seed=3, sigma_decades=1.0)
+    D, E, G, R = gen.ipm(N, n, m, seed=3, sigma_decades=sigma)
     b = gen.rhs(N * n + m, 1, seed=4)
-    solver = kkt.KKTSolver(N, n, m, levels=[16, 1])
+    solver = kkt.KKTSolver(N, n, m, levels=levels)
     try:
         Dd, Ed, Gd, Rd, bd = (dev(a).requires_grad_() for a in (D, E, G, R, b))
         x = kkt.kkt_solve_differentiable(solver, Dd, Ed, Gd, Rd, bd)
@@ -80,6 +88,7 @@ def test_autograd_function_and_finite_differences(kkt):
         rng = np.random.default_rng(1)
         base = [D, E, G, R, b]
         hstep = 1e-6
+        L0 = L(base)
         for s in range(64):
             which = s % 5
             a = base[which]
@@ -97,6 +106,6 @@ def test_autograd_function_and_finite_differences(kkt):
             minus[which][pos] -= hstep
             fd = (L(plus) - L(minus)) / (2 * hstep)
             g = grads[which][pos]
-            assert fd == pytest.approx(g, rel=1e-4, abs=1e-6 * max(1.0, abs(L(base)))), (which, pos, fd, g)
+            assert fd == pytest.approx(g, rel=1e-4, abs=abs_tol * max(1.0, abs(L0))), (which, pos, fd, g)
     finally:
         solver.close()

@@ -285,3 +285,93 @@ def test_adjoint_matches_central_differences(orc):
         assert fd(4, (i,)) == pytest.approx(bbar[i], rel=1e-6, abs=1e-9)
     # the upper triangles are not parameters
     assert np.all(np.triu(dD, 1) == 0) and np.all(np.triu(dR, 1) == 0)
+
+
+# ----------------------------------------------------------- norms, error and condition estimates
+
+@pytest.mark.parametrize("m,nrhs", [(0, 1), (3, 1), (2, 4)])
+def test_block_backward_error_is_the_dense_definition(orc, m, nrhs):
+    """The block-wise backward error equals the dense definition on Psi
+    assembled from its blocks (x perturbed so that the residual is far above
+    rounding)."""
+    D, E, G, R = gen.ipm(12, 5, m, seed=3, sigma_decades=2.0)
+    A = orc.assemble_dense(D, E, G, R)
+    b = gen.rhs(A.shape[0], nrhs, seed=5)
+    x = np.linalg.solve(A, b)
+    x = x + 1e-6 * np.abs(x).max() * gen.rhs(A.shape[0], nrhs, seed=6)
+    dense = np.abs(b - A @ x).max() / (np.abs(A).sum(axis=1).max() * np.abs(x).max() + np.abs(b).max())
+    assert orc.block_backward_error(D, E, G, R, x, b) == pytest.approx(dense, rel=1e-12)
+    assert orc.block_norm_inf(D, E, G, R) == pytest.approx(np.abs(A).sum(axis=1).max(), rel=1e-15)
+    if nrhs == 1:
+        assert orc.backward_error(A, x, b) == pytest.approx(dense, rel=1e-12)
+
+
+@pytest.mark.parametrize("N,n,m,sigma", [(8, 3, 2, 2.0), (10, 4, 0, 6.0), (6, 5, 3, 8.0), (12, 2, 1, 4.0)])
+def test_cond_est_brackets_the_exact_condition_number(orc, N, n, m, sigma):
+    """Hager's estimate is a lower bound of kappa_1 and, on these matrices,
+    within a factor of 3 of it (exact kappa_1 from the dense inverse)."""
+    D, E, G, R = gen.ipm(N, n, m, seed=N * n + m, sigma_decades=sigma)
+    A = orc.assemble_dense(D, E, G, R)
+    exact = np.abs(A).sum(axis=0).max() * np.abs(np.linalg.inv(A)).sum(axis=0).max()
+    est = orc.cond_est(D, E, G, R)
+    assert est <= exact * (1 + 1e-8)
+    assert est >= exact / 3.0
+
+
+# ----------------------------------------------------------- flop counters in the standard convention
+
+def _potrf_std(k):
+    return k ** 3 / 3.0 + k ** 2 / 2.0 + k / 6.0
+
+
+def _seq_closed_form(N, n, m):
+    """Standard-convention flops of the sequential block method, stage by
+    stage: potrf of the n x n pivot, the panel of r = n + m rows (E_j and
+    G_j; r = m at the last stage) solved against it (r n^2) and its syrk
+    update of the next pivot, the next G and the corner (r (r + 1) n), then
+    the m x m corner's potrf."""
+    stage = lambda r: _potrf_std(n) + r * n * n + r * (r + 1) * n
+    return (N - 1) * stage(n + m) + stage(m) + (_potrf_std(m) if m else 0.0)
+
+
+@pytest.mark.parametrize("N,n,m", [(1024, 32, 8), (16, 8, 4), (200, 48, 4), (8192, 6, 2), (5, 3, 0), (1, 7, 2)])
+def test_standard_flop_counter_sequential_closed_form(orc, N, n, m):
+    """The oracle's standard-convention counter (the roofline numerator via the
+    library's flop model) equals the closed form of the sequential method; for
+    N = 1024, n = 32, m = 8 that is 107,314,380 flops."""
+    D, E, G, R = gen.ipm(N, n, m, seed=1) if N * n <= 4096 else (None,) * 4
+    if D is None:    # large shapes: the counter is what matters, any SPD values do
+        D = np.broadcast_to(np.eye(n) * 4.0, (N, n, n)).copy()
+        E = np.zeros((N - 1, n, n))
+        G = np.zeros((N, m, n))
+        R = np.eye(m) * 4.0
+    orc.flops_reset()
+    orc.seq_factor(D, E, G, R)
+    _, std = orc.flops_get()
+    assert std == pytest.approx(_seq_closed_form(N, n, m), rel=1e-14)
+    if (N, n, m) == (1024, 32, 8):
+        assert round(std) == 107314380
+
+
+@pytest.mark.parametrize("N,P", [(16, 4), (40, 6), (30, 3), (9, 5)])
+def test_standard_flop_counter_leading_terms_are_table1(orc, N, P):
+    """Per segment, the standard-convention factor count is a cubic in the
+    block size b (no arrow); its b^3 coefficient is Table 1's, which counts
+    potrf as b^3/3, trsm as r b^2 and syrk as r^2 k: the two conventions
+    differ only in lower-order terms. The coefficient is the third finite
+    difference over b = 1..4 divided by 6."""
+    rows = {r[0]: [Fraction(v) for v in r[2:]] for r in _read_rows("table1_flops.txt")}
+    counts = []
+    for b in (1, 2, 3, 4):
+        D, E, G, R, _ = gen.known_factor(N, b, 0, seed=1)
+        F = orc.par_factor(D, E, G, R, P=P, flops=True)
+        counts.append(F["flops_std"])
+    c = np.array(counts)
+    c3 = (c[3] - 3 * c[2] + 3 * c[1] - c[0]) / 6.0
+    seg = orc.partition(N, P)
+    parts = ["first_segment"] + ["other_segment"] * (P - 2) + ["last_segment"]
+    for k, part in enumerate(parts):
+        c1, c0 = rows[part][0], rows[part][1]
+        assert c3[k] == pytest.approx(float(c1 * seg[k] + c0), abs=1e-9)
+    c1, c0 = rows["sequential_phase"][0], rows["sequential_phase"][1]
+    assert c3[P] == pytest.approx(float(c1 * P + c0), abs=1e-9)
