@@ -466,25 +466,50 @@ def batch_cpu_baseline(name: str, Ns, ns, ms, budget_s: float):
                 sample=f"{reps} x {len(systems)} systems drawn from the batch on {cores} threads ({dt:.1f} s)")
 
 
-def run_batch(args):
+def _plan_is_sequential(kkt, h, count):
+    return all(len(kkt.kkt_partition(h, s, 1)) == 1 for s in range(count))
+
+
+def _factor_launch_groups(Ns, ns, ms):
+    """Factor launches of a batch whose systems are all sequential (P = 1),
+    in launch order: one per block size, small blocks (one warp per system)
+    first, each with the indices of its systems."""
+    groups = {}
+    for s, n in enumerate(ns):
+        groups.setdefault(n, []).append(s)
+    return [(n, groups[n]) for n in sorted(groups)]
+
+
+def measure_batch(name, args, world, rank, local, host_check=64):
+    """Time one batched workload, FP64 and (where listed) mixed, each step a
+    CUDA graph of factor + solve (FP64) or factor + refinement (mixed).
+    Returns (results per path, shapes). Besides the step time: the device's
+    eta; a host FP64 check of the residual of `host_check` sampled systems
+    for both paths on the same inputs; and, on sequential plans, the time of
+    every factor launch over diagnostic replays and of the dominant one over
+    the timed steps (two event nodes in the timed graph)."""
     import torch
     import paper_2511_00946_gb300 as kkt
     import gen.device as gdev
-    name = args.workload
     spec = BATCHES[name]
-    world, rank, local = rank_env()
-    torch.cuda.set_device(local)
-    init_ranks("nccl")
     Ns, ns, ms = batch_shapes(name)
     count = len(Ns)
     # rank r holds systems [r * count, (r + 1) * count) of the global batch:
     # the same shapes, its own draws
     D, E, G, R = gdev.batch(Ns, ns, ms, seed=rank_seed(11, rank), kind=spec["kind"],
                             sigma_decades=spec["sigma"], psd_couplings=spec.get("psd", False))
-    rows = int(sum(N * n + m for N, n, m in zip(Ns, ns, ms)))
-    b0 = gdev.rhs(rows, 1, seed=rank_seed(12, rank))
+    off = gdev.offsets(Ns, ns, ms)
+    b0 = gdev.rhs(int(off["b"][-1]), 1, seed=rank_seed(12, rank))
     stream = torch.cuda.current_stream()
-    sweeps = args.sweeps
+    sample = sorted(np.random.default_rng(3).choice(count, size=min(host_check, count), replace=False).tolist())
+    host_blocks = []
+    for s in sample:
+        N, n, m = Ns[s], ns[s], ms[s]
+        host_blocks.append((D[off["D"][s]:off["D"][s + 1]].cpu().numpy().reshape(N, n, n),
+                            E[off["E"][s]:off["E"][s + 1]].cpu().numpy().reshape(max(N - 1, 0), n, n),
+                            G[off["G"][s]:off["G"][s + 1]].cpu().numpy().reshape(N, m, n),
+                            R[off["R"][s]:off["R"][s + 1]].cpu().numpy().reshape(m, m),
+                            b0[off["b"][s]:off["b"][s + 1]].cpu().numpy()))
     results = {}
     for path in spec["paths"]:
         prec = kkt.KKT_MIXED_FP32_ALL if path == "mixed" else kkt.KKT_FP64
@@ -498,14 +523,15 @@ def run_batch(args):
         tune_s = time.perf_counter() - t0
         b = b0.clone()
         x = torch.zeros_like(b0)
-        xb = torch.empty_like(b0)
         bb = torch.empty_like(b0)
         gD, gE, gG, gR = (torch.empty_like(t) for t in (D, E, G, R))
+        seq = _plan_is_sequential(kkt, h, count)
+        fgroups = _factor_launch_groups(Ns, ns, ms) if seq else []
 
         def launch_step():
             kkt.kkt_factor(h, D, E, G, R)
             if path == "mixed":
-                kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=sweeps, tol=args.tol)
+                kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=args.sweeps, tol=args.tol)
             else:
                 kkt.kkt_solve(h, b)
                 if path == "fp64_adjoint":
@@ -516,23 +542,63 @@ def run_batch(args):
             if path != "mixed":
                 b.copy_(b0)
 
-        for _ in range(2):
-            reset()
-            launch_step()
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        cap = torch.cuda.Stream()
-        cap.wait_stream(stream)
-        with torch.cuda.stream(cap):
-            with torch.cuda.graph(graph, stream=cap):
+        def capture(events):
+            kkt.kkt_set_launch_events(h, events)
+            for _ in range(2):
+                reset()
                 launch_step()
-        stream.wait_stream(cap)
-        torch.cuda.synchronize()
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            cap = torch.cuda.Stream()
+            cap.wait_stream(stream)
+            with torch.cuda.stream(cap):
+                with torch.cuda.graph(g, stream=cap):
+                    launch_step()
+            stream.wait_stream(cap)
+            torch.cuda.synchronize()
+            return g
+
+        def new_events(k):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+            for ev in evs:
+                ev.record()
+            torch.cuda.synchronize()
+            return evs
+
+        # diagnostic replays: an event after every factor launch
+        split, dom = None, None
+        if fgroups:
+            nf = len(fgroups)
+            diag = new_events(nf)
+            graph = capture(diag)
+            per = [[] for _ in range(nf)]
+            for it in range(8):
+                reset()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                graph.replay()
+                torch.cuda.synchronize()
+                if it >= 2:
+                    prev = e0
+                    for i, ev in enumerate(diag):
+                        per[i].append(prev.elapsed_time(ev))
+                        prev = ev
+            split = [statistics.mean(v) for v in per]
+            dom = int(np.argmax(split))
+            del graph
+        dom_ev = new_events(2) if dom is not None else None
+        evs = None
+        if dom is not None:
+            evs = [None] * len(fgroups)
+            if dom > 0:
+                evs[dom - 1] = dom_ev[0]
+            evs[dom] = dom_ev[1]
+        graph = capture(evs or [])
         for _ in range(max(args.warmup, 3)):
             reset()
             graph.replay()
         torch.cuda.synchronize()
-        ms_list = []
+        ms_list, dom_ms = [], []
         barrier()
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
@@ -545,33 +611,96 @@ def run_batch(args):
                 e1.record(stream)
                 e1.synchronize()
                 ms_list.append(e0.elapsed_time(e1))
+                if dom is not None:
+                    dom_ms.append((dom_ev[0] if dom > 0 else e0).elapsed_time(dom_ev[1]))
         barrier()
+        kkt.kkt_set_launch_events(h, [])
         info = kkt.kkt_get_info(h)
         if info["status"] != 0:
             raise RuntimeError(f"{name}/{path}: factorization failed: {info}")
-        # error of the returned solution: eta per system (FP64 residual)
+        # error of the returned solution: the device's eta per system, and a
+        # host FP64 residual of the sampled systems
+        xs = (x if path == "mixed" else b).cpu().numpy()
         if path == "mixed":
-            eta = kkt.kkt_refine_eta(h, sweeps - 1, count)
+            eta_dev = kkt.kkt_refine_eta(h, args.sweeps - 1, count)
             eta_raw = kkt.kkt_refine_eta(h, 0, count)
         else:
             x1 = torch.zeros_like(b0)
             kkt.kkt_solve_refined(h, D, E, G, R, b0, x1, sweeps=1, tol=0.0)
-            eta = kkt.kkt_refine_eta(h, 0, count)
-            eta_raw = eta
+            eta_dev = kkt.kkt_refine_eta(h, 0, count)
+            eta_raw = eta_dev
+        host = []
+        for s, (Dh, Eh, Gh, Rh, bh) in zip(sample, host_blocks):
+            host.append(backward_error(Dh, Eh, Gh, Rh, xs[off["b"][s]:off["b"][s + 1]], bh))
         fl = kkt.kkt_flops(h)
-        t_ms, max_eta = max_over_ranks([statistics.median(ms_list), float(np.max(eta))])
+        t_ms, max_eta = max_over_ranks([statistics.median(ms_list), float(np.max(eta_dev))])
         P1 = [len(kkt.kkt_partition(h, s, 1)) for s in range(count)]
-        results[path] = dict(
-            ms_per_step=t_ms, ms_stats=step_stats(ms_list), value=whole_job_rate(count, t_ms, world),
-            max_eta=max_eta,
-            max_eta_unrefined=float(np.max(eta_raw)), levels_max=int(max(lv)),
-            level1_segments_total=int(sum(P1)), tune_s=tune_s,
-            factor_flops=fl["factor"], sequential_factor_flops=fl["sequential_factor"],
-            clocks=clk.summary())
+        r = dict(ms_per_step=t_ms, ms_stats=step_stats(ms_list), value=whole_job_rate(count, t_ms, world),
+                 max_eta=max_eta, max_eta_unrefined=float(np.max(eta_raw)),
+                 host_check={"systems": len(sample), "max_backward_error": max(e for e, _ in host),
+                             "relres": [rr for _, rr in host]},
+                 levels_max=int(max(lv)), level1_segments_total=int(sum(P1)), tune_s=tune_s,
+                 factor_flops=fl["factor"], sequential_factor_flops=fl["sequential_factor"],
+                 clocks=clk.summary())
+        if path == "mixed":
+            r["refinement"] = {"sweeps_max": args.sweeps, "tol": args.tol,
+                               "stop": "eta <= tol, or a sweep that does not halve eta (rounding floor)"}
+        if split is not None:
+            names = [f"{'k_factor_w' if n <= 16 else 'k_factor'} n={n} ({len(sy)} systems)" for n, sy in fgroups]
+            r["factor_launch_ms"] = {nm: round(v, 4) for nm, v in zip(names, split)}
+            dom_avg = statistics.mean(dom_ms)
+            r["dominant_factor_launch"] = {"kernel": names[dom], "launch_ms": dom_avg}
+            if path != "mixed":
+                flops = 0.0
+                cache = {}
+                for s in fgroups[dom][1]:
+                    key = (Ns[s], ns[s], ms[s])
+                    if key not in cache:
+                        cache[key] = kkt.kkt_plan_flops(*key, [1])["factor"]
+                    flops += cache[key]
+                ach = flops / (dom_avg * 1e-3) / 1e12
+                peak = FP64_PEAK_GFLOPS / 1000.0
+                r["roofline"] = {"bound": "alu", "kernel": names[dom], "launch_ms": dom_avg, "achieved": ach,
+                                 "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                                 "flops_per_launch": flops, "traffic": None,
+                                 "note": "FP64 sequential factor flops of the launch's systems (standard "
+                                         "convention) over its event-timed duration in the timed graph"}
+        results[path] = r
         kkt.kkt_destroy(h)
         del graph
         torch.cuda.synchronize()
-    ok = {p: r for p, r in results.items() if r["max_eta"] <= 1e-14}
+    return results, (Ns, ns, ms)
+
+
+def compare_paths(results):
+    """Equal-accuracy comparison of the mixed path with the FP64 path on the
+    same inputs: the ratio of the sampled systems' relative residuals (mixed
+    over FP64, the worst system) and of the step rates."""
+    if "fp64" not in results or "mixed" not in results:
+        return None
+    a, m = results["fp64"], results["mixed"]
+    ratios = [rm / ra for rm, ra in zip(m["host_check"]["relres"], a["host_check"]["relres"])]
+    return {"rate_mixed_over_fp64": m["value"] / a["value"], "ms_fp64": a["ms_per_step"],
+            "ms_mixed": m["ms_per_step"], "worst_relres_ratio_mixed_over_fp64": max(ratios),
+            "median_relres_ratio_mixed_over_fp64": statistics.median(ratios),
+            "max_eta_fp64": a["max_eta"], "max_eta_mixed": m["max_eta"],
+            "equal_accuracy": bool(max(ratios) <= 10.0 and m["max_eta"] <= 1e-14)}
+
+
+def run_batch(args):
+    import torch
+    name = args.workload
+    spec = BATCHES[name]
+    world, rank, local = rank_env()
+    torch.cuda.set_device(local)
+    init_ranks("nccl")
+    results, (Ns, ns, ms) = measure_batch(name, args, world, rank, local)
+    count = len(Ns)
+    # value: the fastest path that meets the error gates (eta <= 1e-14 and,
+    # for the mixed path, residuals within 10x the FP64 path's)
+    cmp_ = compare_paths(results)
+    ok = {p: r for p, r in results.items()
+          if r["max_eta"] <= 1e-14 and (p != "mixed" or (cmp_ and cmp_["equal_accuracy"]))}
     best = min(ok.items(), key=lambda kv: kv[1]["ms_per_step"]) if ok else min(
         results.items(), key=lambda kv: kv[1]["ms_per_step"])
     bp, br = best
@@ -585,17 +714,14 @@ def run_batch(args):
         "config": {"workload": spec["desc"], "name": name, "path": bp, "systems": count * world,
                    "systems_per_rank": count,
                    "plan": f"two levels, P = {args.P} per system" if args.P else "autotuned per system",
-                   "refinement_sweeps": sweeps if "mixed" in spec["paths"] else None,
+                   "refinement": {"sweeps_max": args.sweeps, "tol": args.tol} if "mixed" in spec["paths"] else None,
                    "l2": "inputs larger than L2", "graph": "one CUDA graph per step"},
         "error": {"max_backward_error": br["max_eta"], "gate": 1e-14},
         "paths": results,
-        "roofline": {"bound": "alu", "achieved": results.get("fp64", results.get("fp64_adjoint"))["factor_flops"]
-                     / (results.get("fp64", results.get("fp64_adjoint"))["ms_per_step"] * 1e9),
-                     "peak": FP64_PEAK_GFLOPS / 1000.0, "unit": "TFLOP/s",
-                     "note": "FP64 path: executed factor flops per step over the whole step time"},
+        "comparison": cmp_,
+        "roofline": results.get("fp64", results.get("fp64_adjoint")).get("roofline"),
         "clocks": br["clocks"],
     }
-    line["roofline"]["frac"] = line["roofline"]["achieved"] / line["roofline"]["peak"]
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = batch_cpu_baseline(name, Ns, ns, ms, args.cpu_seconds)
     print(json.dumps(line), flush=True)
@@ -612,16 +738,20 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=3.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched FP64-vs-mixed comparison in the default line")
     ap.add_argument("--workload", default="ipm1024", choices=["ipm1024"] + sorted(BATCHES),
                     help="ipm1024: the single-system workload (default); the others are the batched ones")
-    ap.add_argument("--sweeps", type=int, default=4, help="refinement sweeps of the mixed path (at most)")
+    ap.add_argument("--sweeps", type=int, default=8, help="refinement sweeps of the mixed path (at most)")
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per step (ipm1024)")
     ap.add_argument("--P", type=int, default=0,
                     help="batched workloads: the two-level method with P segments per system (default: tuned)")
     ap.add_argument("--partition", default="balanced", choices=["balanced", "paper"],
                     help="segment lengths: pairing-aware balanced, or Eq. (13) of the paper")
-    ap.add_argument("--tol", type=float, default=1e-14,
-                    help="refinement stop of the mixed path: a system stops once its eta is below this")
+    ap.add_argument("--tol", type=float, default=1e-16,
+                    help="refinement stop of the mixed path: a system stops once its eta is below this (or "
+                         "once a sweep fails to halve it); 1e-16 gives residuals within a few times the "
+                         "FP64 path's")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -811,6 +941,27 @@ def main():
     barrier()
     e2e_val = whole_job_rate(1, max_over_ranks([statistics.mean(e2e_ms)])[0], world)
     e2e_same = bool(np.array_equal(hx.numpy(), x))  # the device path's solution, bit for bit
+    del e2e_graph
+    # the same call made eagerly (no graph): the host work of every call
+    # (pointer queries, chunk plan, launches) is paid each step; host wall
+    # clock from the call to the synchronization that makes x readable
+    for _ in range(3):
+        hx.copy_(hb)
+        e2e_step()
+        torch.cuda.synchronize()
+    eager_ms = []
+    barrier()
+    for _ in range(args.steps):
+        hx.copy_(hb)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_step()
+        stream.synchronize()
+        eager_ms.append(1000.0 * (time.perf_counter() - t0))
+    barrier()
+    eager_val = whole_job_rate(1, max_over_ranks([statistics.mean(eager_ms)])[0], world)
+    eager_same = bool(np.array_equal(hx.numpy(), x))
 
     # --- roofline of the dominant kernel (largest share of the step), timed
     # live over the timed steps
@@ -819,6 +970,17 @@ def main():
     achieved = launch_flops[dom] / (dom_avg * 1e-3) / 1e12
     peak = FP64_PEAK_GFLOPS / 1000.0
     traffic = read_traffic(kernel_source_sha())
+
+    # the batched comparison the metric names (mixed precision against the
+    # plain FP64 path at equal accuracy), measured in the same run
+    batched = None
+    if not args.no_batched:
+        bres, (bN, bn, bm) = measure_batch("uneven4096", args, world, rank, local)
+        batched = {"workload": BATCHES["uneven4096"]["desc"], "systems": len(bN) * world,
+                   "paths": bres, "comparison": compare_paths(bres),
+                   "roofline": bres["fp64"].get("roofline")}
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            batched["cpu_baseline"] = batch_cpu_baseline("uneven4096", bN, bn, bm, args.cpu_seconds / 2)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -841,7 +1003,12 @@ def main():
                     "api": "kkt_factor_solve_host (page-locked host buffers, graph replay): the factor "
                            "launches read D, E, G, R from host memory over the host link, b is copied in and "
                            "x copied out; the byte counts are every input and output crossing per step",
-                    "same_x_as_device_path": e2e_same},
+                    "same_x_as_device_path": e2e_same,
+                    "eager": {"value": eager_val, "unit": UNIT, "ms_mean": statistics.mean(eager_ms),
+                              "ms_median": statistics.median(eager_ms),
+                              "how": "the same call without a graph, host wall clock from the call to the "
+                                     "stream synchronization that makes x readable (L2 flushed before)",
+                              "same_x_as_device_path": eager_same}},
             "gpu_launches": args.steps * nl,
             "launches_per_step": {names[i] if i < len(names) else f"launch {i}": round(a, 4)
                                   for i, a in enumerate(diag_avg)},
@@ -858,6 +1025,8 @@ def main():
         }
         if cpu:
             out["cpu_baseline"] = cpu
+        if batched:
+            out["batched"] = batched
         print(json.dumps(out), flush=True)
     kkt.kkt_destroy(h)
     finish_ranks()

@@ -242,9 +242,15 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
  * c <- b; then `sweeps` times: c <- (L-hat L-hat^T)^{-1} c with the current
  * factor (FP32 substitutions on mixed levels), x <- x + c, c <- b - Psi x in
  * FP64 with the blocks of Eq. (3), eta = ||c||_inf / (||Psi||_inf ||x||_inf +
- * ||b||_inf) over the system's right-hand sides together. A system whose eta
- * is <= tol stops (its remaining sweeps return at once on the device: no
- * host synchronization, capturable in a CUDA graph). D, E, G, R must be the
+ * ||b||_inf) over the system's right-hand sides together. A system stops
+ * when its eta is <= tol, or when a sweep fails to halve its eta (the
+ * rounding floor of the FP64 residual has been reached, or refinement
+ * stalls); its remaining sweeps return at once on the device (no host
+ * synchronization, capturable in a CUDA graph). With tol = 0 every system
+ * refines until its eta stops falling; with tol < 0 every sweep runs. A relative residual within a small
+ * factor of the FP64 factorization's needs eta at that level (about 1e-16
+ * on barrier-scaled systems), i.e. tol <= 1e-16; a looser tol stops earlier
+ * at a correspondingly larger residual. D, E, G, R must be the
  * matrix that was factored; b (read-only) and x (written) are device
  * pointers with leading dimensions ldb, ldx >= nrhs. 1 <= sweeps <= 16.
  * Works with any precision (with KKT_FP64 one sweep is a plain solve plus a

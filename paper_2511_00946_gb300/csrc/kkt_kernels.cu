@@ -1707,7 +1707,9 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
 }
 
 // Finish the g rows of one system from the chunk partials, then eta and the
-// convergence flag.
+// stop flag: 1 when eta <= tol, 2 when the sweep failed to halve the previous
+// sweep's eta (refinement has reached the rounding floor of the FP64
+// residual, or stalls); a stopped system skips the remaining sweeps.
 __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int* __restrict__ sys_desc,
                                  const int* __restrict__ part0, const double* __restrict__ uG,
                                  const double* __restrict__ uR, const double* __restrict__ b, int ldb,
@@ -1762,7 +1764,12 @@ __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int*
   if (threadIdx.x == 0) {
     const double eta = red[0][0] / (red[3][0] * red[1][0] + red[2][0]);
     eta_out[s] = eta;
-    if (converged && eta <= tol) converged[s] = 1;
+    // stop: 1 = eta <= tol; 2 = this sweep did not halve eta (the FP64
+    // residual's rounding floor, or a stall)
+    if (converged) {
+      if (eta <= tol) converged[s] = 1;
+      else if (tol >= 0.0 && eta_prev && eta > 0.5 * eta_prev[s]) converged[s] = 2;
+    }
   }
 }
 

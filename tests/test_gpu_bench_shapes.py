@@ -58,9 +58,10 @@ def check_system(orc, s, x, b, xo=None, kappa=None):
     return eta
 
 
-def run_batch(kkt, h, systems, bs, path, sweeps=4, tol=1e-14):
+def run_batch(kkt, h, systems, bs, path, sweeps=8, tol=1e-16):
     """One benchmark step of `path` on handle h: the FP64 path factors and
-    solves, the mixed path factors and refines (as the benchmark does)."""
+    solves, the mixed path factors and refines to the FP64 path's accuracy
+    (eta <= 1e-16 or until eta stops falling), as the benchmark does."""
     import torch
     D, E, G, R = pack(systems)
     b = dev(np.concatenate(bs))
@@ -89,7 +90,9 @@ def test_raceline_batch_on_the_tuned_plan(kkt, orc, path):
     """The race-line workload: 64 systems of N = 8192 stages, n = 6, m = 2,
     Sigma over 16 decades, on the plan the autotuner picks for exactly these
     shapes (a multi-level plan with thousands of level-1 segments); FP64, and
-    FP32 mixed with FP64 refinement to eta <= 1e-14."""
+    FP32 mixed with FP64 refinement to the FP64 path's accuracy (G1 and G2
+    both hold: a refinement stopped at eta <= 1e-14 leaves a residual about
+    100x the FP64 one and fails G2)."""
     count, N, n, m = 64, 8192, 6, 2
     systems = [gen.raceline(N, n, m, seed=s, sigma_decades=8.0) for s in range(count)]
     bs = [gen.rhs(N * n + m, 1, seed=1000 + s) for s in range(count)]
@@ -101,7 +104,7 @@ def test_raceline_batch_on_the_tuned_plan(kkt, orc, path):
         assert P1 >= 1000, P1
         x, _ = run_batch(kkt, h, systems, bs, path)
         xs = split(kkt, h, x, count)
-        eta_dev = kkt.kkt_refine_eta(h, 3, count) if path == "mixed" else None
+        eta_dev = kkt.kkt_refine_eta(h, 7, count) if path == "mixed" else None
     finally:
         kkt.kkt_destroy(h)
     for s in range(count):
@@ -110,7 +113,7 @@ def test_raceline_batch_on_the_tuned_plan(kkt, orc, path):
         kap = orc.cond_est(*systems[s]) if sample else None
         check_system(orc, systems[s], xs[s], bs[s], xo, kap)
     if eta_dev is not None:
-        assert eta_dev.max() <= 1e-14
+        assert eta_dev.max() <= 2e-15
 
 
 # ------------------------------------------------------------ uneven batch (slice of the 4096 shapes)
