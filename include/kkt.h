@@ -57,7 +57,8 @@ typedef enum {
   KKT_ERR_PARTITION = 2,  /* no partition: P < 1 or P > floor((N+1)/2)          */
   KKT_ERR_NOT_SPD = 3,    /* a pivot block was not positive definite            */
   KKT_ERR_CUDA = 4,       /* a CUDA runtime call failed (allocation, launch)   */
-  KKT_ERR_TIMEOUT = 5,    /* reserved: no call waits on the device              */
+  KKT_ERR_TIMEOUT = 5,    /* a bounded wait inside a kernel ran out (reported by
+                             kkt_get_info; the results of that call are invalid) */
   KKT_ERR_STATE = 6,      /* call out of order (solve before factor)           */
   KKT_ERR_CAPACITY = 7    /* problem larger than a fixed-size buffer allows     */
 } kkt_status;
@@ -73,8 +74,23 @@ typedef enum {
  *                      kkt_solve then returns an unrefined solution;
  *                      kkt_solve_refined recovers FP64 accuracy by iterative
  *                      refinement on the FP64 residual.
- *  KKT_MIXED_FP32_ALL  the same arithmetic on every level. */
-typedef enum { KKT_FP64 = 0, KKT_MIXED_FP32 = 1, KKT_MIXED_FP32_ALL = 2 } kkt_precision;
+ *  KKT_MIXED_FP32_ALL  the same arithmetic on every level.
+ *  KKT_MIXED_TF32      KKT_MIXED_FP32 with the Schur-complement products of
+ *                      level-1 blocks n >= 32 (the stacked panel's Z Z^T of
+ *                      Algorithm 1, Eqs. (8a)-(8b)) on the tensor cores:
+ *                      operands rounded to TF32, products accumulated in
+ *                      FP32 and subtracted from the FP64 Schur accumulator;
+ *                      pivots, trsm and smaller blocks as KKT_MIXED_FP32.
+ *  KKT_MIXED_BF16      the same with BF16 operands (FP32 accumulation).
+ *  The lower-precision products need more refinement sweeps for the same
+ *  accuracy (kkt_solve_refined). */
+typedef enum {
+  KKT_FP64 = 0,
+  KKT_MIXED_FP32 = 1,
+  KKT_MIXED_FP32_ALL = 2,
+  KKT_MIXED_TF32 = 3,
+  KKT_MIXED_BF16 = 4
+} kkt_precision;
 
 /* How a level's N stages are split into P segments.
  *  KKT_PARTITION_PAPER     Eq. (13): N_1 and P-1 equal lengths N_k, with the
@@ -99,7 +115,7 @@ typedef struct kkt_handle kkt_handle;
 
 /* First breakdown recorded by the device since the last kkt_factor. */
 typedef struct {
-  int status;  /* KKT_OK or KKT_ERR_NOT_SPD                                     */
+  int status;  /* KKT_OK, KKT_ERR_NOT_SPD or KKT_ERR_TIMEOUT                    */
   int system;  /* system index in the batch                                     */
   int stage;   /* natural stage of the failing pivot block; N for the corner R */
   int level;   /* 1 = stage blocks of Psi, 2.. = reduced (separator) systems    */
@@ -243,9 +259,9 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
  * factor (FP32 substitutions on mixed levels), x <- x + c, c <- b - Psi x in
  * FP64 with the blocks of Eq. (3), eta = ||c||_inf / (||Psi||_inf ||x||_inf +
  * ||b||_inf) over the system's right-hand sides together. A system stops
- * when its eta is <= tol, or when a sweep fails to halve its eta (the
- * rounding floor of the FP64 residual has been reached, or refinement
- * stalls); its remaining sweeps return at once on the device (no host
+ * when its eta is <= tol, or when its eta is at the rounding level of the
+ * FP64 residual (<= 16 u, u = 2^-53) and a sweep cuts it by less than 10 %
+ * (refinement has reached its floor); its remaining sweeps return at once on the device (no host
  * synchronization, capturable in a CUDA graph). With tol = 0 every system
  * refines until its eta stops falling; with tol < 0 every sweep runs. A relative residual within a small
  * factor of the FP64 factorization's needs eta at that level (about 1e-16

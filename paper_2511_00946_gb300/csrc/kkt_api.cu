@@ -142,6 +142,7 @@ bool make_level(int N, int P, int mode, int n, int m, bool paired, LevelPlan* L)
 struct kkt_handle {
   int count = 0;
   int precision = 0;
+  int tc = 0;                                // tensor-core Schur products: 1 = TF32, 2 = BF16
   int maxn = 0, maxm = 0, maxL = 0;
   std::vector<SysPlan> sys;
   std::vector<LevelDesc> hdesc;              // host copy of the descriptors
@@ -266,11 +267,13 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return KKT_ERR_CUDA;
   const std::vector<int> pair_lv = paired_levels(Plev, n, sms);
-  if (precision != KKT_FP64 && precision != KKT_MIXED_FP32 && precision != KKT_MIXED_FP32_ALL)
+  if (precision != KKT_FP64 && precision != KKT_MIXED_FP32 && precision != KKT_MIXED_FP32_ALL &&
+      precision != KKT_MIXED_TF32 && precision != KKT_MIXED_BF16)
     return KKT_ERR_ARG;
   auto* h = new kkt_handle();
   h->count = count;
   h->precision = precision;
+  h->tc = precision == KKT_MIXED_TF32 ? 1 : precision == KKT_MIXED_BF16 ? 2 : 0;
   h->sms = sms;
   h->sys.resize(count);
   for (int s = 0; s < count; ++s) {
@@ -292,7 +295,9 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
         return KKT_ERR_PARTITION;
       }
       L.nat = nat;
-      L.mixed = (precision == KKT_MIXED_FP32_ALL) || (precision == KKT_MIXED_FP32 && l == 0);
+      L.mixed = (precision == KKT_MIXED_FP32_ALL) ||
+                ((precision == KKT_MIXED_FP32 || precision == KKT_MIXED_TF32 || precision == KKT_MIXED_BF16) &&
+                 l == 0);
       sp.lv.push_back(L);
       if (L.P == 1) {
         if (l + 1 != Ps.size()) { delete h; return KKT_ERR_ARG; }
@@ -844,7 +849,8 @@ kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const dou
                                                    gr.fill)
                             : kkt::launch_factor(h->ddesc, h->dtasks + gr.off, gr.cnt, gr.n, gr.m,
                                                  h->level_mixed[l], level_paired(h, l), D, E, G, R,
-                                                 h->dinfo, stream, nullptr, 1, gr.fill);
+                                                 h->dinfo, stream, nullptr, 1, gr.fill, 0,
+                                                 h->level_mixed[l] ? h->tc : 0);
       if (e || !mark(h, li++, stream)) return KKT_ERR_CUDA;
     }
   h->factored = true;
@@ -1190,7 +1196,7 @@ kkt_status kkt_get_info(kkt_handle* h, kkt_info* info, int clear) {
   if (!h || !info) return KKT_ERR_ARG;
   kkt::Info hi{};
   if (cudaMemcpy(&hi, h->dinfo, sizeof(hi), cudaMemcpyDeviceToHost) != cudaSuccess) return KKT_ERR_CUDA;
-  info->status = hi.status == 3 ? KKT_ERR_NOT_SPD : KKT_OK;
+  info->status = hi.status == 3 ? KKT_ERR_NOT_SPD : hi.status == 5 ? KKT_ERR_TIMEOUT : KKT_OK;
   info->system = hi.system;
   info->stage = hi.stage;
   info->level = hi.level;

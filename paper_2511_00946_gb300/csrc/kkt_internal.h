@@ -221,9 +221,11 @@ int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
                     void* stream, double* b = nullptr, int ldb = 1, int fill = 1);
 // (top_solve: on a bordered pass the top level's tasks also run their corner
 // solve and backward sweep at the end of the factor kernel)
+// (tc: Schur products of a mixed launch on the tensor cores, 1 = TF32, 2 = BF16
+// operands, FP32 accumulation; used for blocks n >= 32 where the layout allows)
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
-                  void* stream, double* b = nullptr, int ldb = 1, int fill = 1, int top_solve = 0);
+                  void* stream, double* b = nullptr, int ldb = 1, int fill = 1, int top_solve = 0, int tc = 0);
 // (split: CTAs per task, each on its own group of right-hand-side columns)
 // (fill: some task's level has P > 1; 0 sizes shared memory for the compact
 // layout of levels with P = 1)

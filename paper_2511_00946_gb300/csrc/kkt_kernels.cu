@@ -16,6 +16,7 @@
 // Schur accumulator in FP64: the panel trsm and the dot products of the
 // syrk run in FP32 and each dot product is subtracted from the FP64
 // accumulator once.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +25,7 @@
 
 #include "kkt_internal.h"
 #include "kkt_numerics.cuh"
+#include "kkt_tc.cuh"
 
 namespace kkt {
 namespace {
@@ -42,14 +44,21 @@ __device__ __forceinline__ void tri_rc(int e, int& a, int& b) {
   b = e - r * (r + 1) / 2;
 }
 
-__device__ void record_breakdown(Info* info, int sys, int stage, int level) {
+__device__ void record_status(Info* info, int status, int sys, int stage, int level) {
   if (atomicCAS(&info->status, 0, -1) == 0) {
     info->system = sys;
     info->stage = stage;
     info->level = level;
     __threadfence();
-    atomicExch(&info->status, 3 /* KKT_ERR_NOT_SPD */);
+    atomicExch(&info->status, status);
   }
+}
+__device__ void record_breakdown(Info* info, int sys, int stage, int level) {
+  record_status(info, 3 /* KKT_ERR_NOT_SPD */, sys, stage, level);
+}
+// a bounded device wait ran out (the kernel carries on; its results are invalid)
+__device__ void record_timeout(Info* info, int sys, int stage, int level) {
+  record_status(info, 5 /* KKT_ERR_TIMEOUT */, sys, stage, level);
 }
 
 // A group of threads working on one role of a CTA: thread index within the
@@ -370,6 +379,96 @@ __device__ void syrk_trap(double* T, int ldt, const TZ* Zlo, const TZ* Z, int zs
     }
   }
   gsync(g);
+}
+
+// Tensor-core form of the mixed Schur update (whole-CTA layout, eight warps):
+// T[a][b] -= (Z Z^T)[a][b] for r0 <= b <= a < pr1, with Z (FP32, ld ldz)
+// rounded to TF32 or BF16 and the products accumulated in FP32 by tcgen05
+// MMAs (M = 128 rows, N = pr1 rounded up to 16, K = n padded to the
+// instruction's 8 or 16), then subtracted from the FP64 accumulator once per
+// element, in the element order of syrk_trap. `buf` (shared memory, 16-byte
+// aligned) holds the operand, pr1 rows of K, and afterwards the FP32
+// products as a packed lower triangle; the tensor core reads 128 rows of
+// operand address range from it (rows from pr1 on are arbitrary data inside
+// the CTA's shared memory and feed only accumulator rows that are never
+// read). Returns false when the MMAs did not complete within the bounded
+// wait (T is then left without the update).
+struct TcState {
+  uint32_t tmem;    // accumulator columns in tensor memory
+  uint64_t* bar;    // completion mbarrier
+  uint32_t phase;   // completions so far
+  int mode;         // 1 = TF32, 2 = BF16
+};
+
+__device__ bool syrk_tc(double* T, int ldt, const float* Z, int ldz, int r0, int pr1, int n, unsigned char* buf,
+                        TcState& st) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const bool bf = st.mode == 2;
+  const int kin = bf ? 16 : 8, epc = bf ? 8 : 4, eb = bf ? 2 : 4;
+  const int Kp = (n + kin - 1) / kin * kin;
+  const uint32_t LBO = 128, SBO = (uint32_t)(Kp / epc) * 128;
+  __syncthreads();  // earlier readers of the buffer (the pivot blocks) are done
+  for (int e = tid; e < pr1 * Kp; e += nt) {
+    const int r = e / Kp, k = e - r * Kp;
+    const float v = k < n ? Z[r * ldz + k] : 0.0f;
+    const uint32_t off = (uint32_t)(r >> 3) * SBO + (uint32_t)(k / epc) * LBO + (uint32_t)(r & 7) * 16 +
+                         (uint32_t)(k % epc) * eb;
+    if (bf) *(__nv_bfloat16*)(buf + off) = __float2bfloat16_rn(v);
+    else *(uint32_t*)(buf + off) = tc::to_tf32(v);
+  }
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (tid == 0) {
+    const int N = (pr1 + 15) & ~15;
+    const uint32_t idesc = tc::instr_desc(bf ? 1u : 2u, 128, N);
+    const uint32_t a0 = tc::smem_u32(buf);
+    for (int ks = 0; ks < Kp / kin; ++ks) {
+      const uint64_t d = tc::smem_desc(a0 + (uint32_t)ks * 2 * LBO, LBO, SBO);
+      tc::mma(bf, st.tmem, d, d, idesc, ks > 0);
+    }
+    tc::commit(st.bar);
+  }
+  const bool ok = tc::wait(st.bar, st.phase & 1);
+  st.phase++;
+  tc::fence_after();
+  // products -> packed lower triangle S[a (a + 1) / 2 + b]: warp w reads the
+  // TMEM lanes (rows) 32 (w % 4) .. + 31, warps w and w + 4 take alternate
+  // 8-column chunks
+  float* S = (float*)buf;
+  const int warp = tid >> 5, lane = tid & 31, row0 = 32 * (warp & 3);
+  if (ok && row0 < pr1 && row0 + 31 >= r0) {
+    const int a = row0 + lane;
+    for (int c0 = 8 * (warp >> 2); c0 < pr1 && c0 <= row0 + 31; c0 += 16) {
+      float v[8];
+      tc::ld8(st.tmem + ((uint32_t)row0 << 16) + (uint32_t)c0, v);
+      if (a < pr1 && a >= r0) {
+        float* Sa = S + a * (a + 1) / 2;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (c0 + i >= r0 && c0 + i <= a) Sa[c0 + i] = v[i];
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (ok) {
+    // the subtraction, enumerated like syrk_trap (a rectangle of width 0
+    // beside the triangle of rows and columns [r0, pr1))
+    const int h = pr1 - r0, tot = h * (h + 1) / 2;
+    int a = r0, b = r0 + tid;
+    while (a < pr1 && b > a) { b -= a - r0 + 1; ++a; }
+    for (int e = tid; e < tot; e += nt) {
+      if (e != tid) {
+        b += nt;
+        while (b > a) { b -= a - r0 + 1; ++a; }
+      }
+      T[a * ldt + b] -= (double)S[a * (a + 1) / 2 + b];
+    }
+  }
+  __syncthreads();
+  return ok;
 }
 
 // Thread-block-cluster primitives (a factor task may run as a pair of CTAs).
@@ -727,9 +826,11 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
                                                            const double* __restrict__ uG,
                                                            const double* __restrict__ uR,
                                                            Info* info, int pair, double* yb, int ldyb,
-                                                           int top_solve, int dbl) {
+                                                           int top_solve, int dbl, int tcm) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ int bad;
+  __shared__ uint32_t tslot;               // TMEM address of the tensor-core accumulator
+  __shared__ __align__(8) uint64_t tbar;   // its completion mbarrier
   const unsigned rank = pair ? cluster_rank() : 0u;
   const Task tk = tasks[pair ? blockIdx.x >> 1 : blockIdx.x];
   const LevelDesc& d = descs[tk.desc];
@@ -755,10 +856,24 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
   const bool eg = mode != kPair || rank == 0;       // this CTA holds the E/G rows
   const bool wr = g.hasW && (mode != kPair || rank == 1);  // this CTA holds the W rows
 
+  // tensor-core Schur products (mixed whole-CTA layout without the second
+  // pivot buffer, whose region then stages the operands)
+  const bool use_tc = mixed && tcm && mode == kWhole && !dbl;
+  const uint32_t tc_cols = ((lay.Rs + 15) & ~15) <= 64 ? 64u : 128u;
+  TcState tcs{0u, &tbar, 0u, tcm};
+  if (use_tc) {
+    if (threadIdx.x < 32) tc::alloc(&tslot, tc_cols);
+    if (threadIdx.x == 0) tc::mbar_init(&tbar);
+    tc::fence_before();
+  }
   if (threadIdx.x == 0) bad = 0;
   for (int e = threadIdx.x; e < lay.Rs * ldT; e += blockDim.x) T[e] = 0.0;
   if (eg) potrf_table(tab, n);
   __syncthreads();
+  if (use_tc) {
+    tc::fence_after();
+    tcs.tmem = tslot;
+  }
   cx.load_first(eg, wr, cta_grp());
   __syncthreads();
   if (mode == kPair) {
@@ -866,7 +981,15 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
         cluster_arrive();
       }
       store_panel(j, r0, pr1, mode == kWhole ? R : n + m, P);
-      syrk_trap(T, ldT, Z, Z, 0, ldZ, r0, pr1, r0, n, P);
+      bool tc_done = false;
+      if constexpr (mixed) {
+        if (use_tc) {
+          if (!syrk_tc(T, ldT, (const float*)Z, ldZ, r0, pr1, n, smraw + lay.oDfac, tcs) && threadIdx.x == 0)
+            record_timeout(info, d.sys, d.nat[j], d.level);
+          tc_done = true;
+        }
+      }
+      if (!tc_done) syrk_trap(T, ldT, Z, Z, 0, ldZ, r0, pr1, r0, n, P);
       if (i + 1 < g.len) {
         copy_blk(Dbuf(cur ^ 1), ldD, T, ldT, n, n, P);                      // D_{i+1}
         rotate(i, j, mode == kWhole && g.hasW, P);
@@ -964,6 +1087,11 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
     // pair then meets once more, after which no remote store is in flight
     cluster_arrive();
     cluster_wait();
+  }
+  if (use_tc) {
+    tc::fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tc::dealloc(tcs.tmem, tc_cols);
   }
 }
 
@@ -1707,9 +1835,13 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
 }
 
 // Finish the g rows of one system from the chunk partials, then eta and the
-// stop flag: 1 when eta <= tol, 2 when the sweep failed to halve the previous
-// sweep's eta (refinement has reached the rounding floor of the FP64
-// residual, or stalls); a stopped system skips the remaining sweeps.
+// stop flag: 1 when eta <= tol, 2 when eta is at the rounding level of the
+// FP64 residual (kEtaFloor) and the sweep cut the previous sweep's eta by
+// less than 10 % (refinement has reached its floor; above that level a slow
+// sweep is not taken as the end, since the normwise eta of an
+// ill-conditioned system need not fall monotonically); a stopped system
+// skips the remaining sweeps.
+constexpr double kEtaFloor = 16.0 * 1.1102230246251565e-16;  // 16 u
 __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int* __restrict__ sys_desc,
                                  const int* __restrict__ part0, const double* __restrict__ uG,
                                  const double* __restrict__ uR, const double* __restrict__ b, int ldb,
@@ -1764,11 +1896,11 @@ __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int*
   if (threadIdx.x == 0) {
     const double eta = red[0][0] / (red[3][0] * red[1][0] + red[2][0]);
     eta_out[s] = eta;
-    // stop: 1 = eta <= tol; 2 = this sweep did not halve eta (the FP64
-    // residual's rounding floor, or a stall)
+    // stop: 1 = eta <= tol; 2 = eta is at the rounding level of the FP64
+    // residual (<= 16 u) and this sweep cut it by less than 10 %
     if (converged) {
       if (eta <= tol) converged[s] = 1;
-      else if (tol >= 0.0 && eta_prev && eta > 0.5 * eta_prev[s]) converged[s] = 2;
+      else if (tol >= 0.0 && eta_prev && eta <= kEtaFloor && eta > 0.9 * eta_prev[s]) converged[s] = 2;
     }
   }
 }
@@ -1918,12 +2050,28 @@ int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
   return (int)cudaGetLastError();
 }
 
+// Tensor-core Schur products for a mixed launch of blocks n >= 32 when the
+// pivot-buffer region of the layout without the second pivot buffer can stage
+// the operand (Rs rows of K) and the packed product triangle, and the
+// layout spans the 128 operand rows the MMA addresses; 0 otherwise.
+int tc_mode_for(int tc, int mixed, int pair, int maxn, int maxm, int fill) {
+  if (!tc || !mixed || pair || maxn < 32) return 0;
+  const FacLayout L = fac_layout(maxn, maxm, 4, fill != 0, false);
+  const int kin = tc == 2 ? 16 : 8, eb = tc == 2 ? 2 : 4;
+  const long Kp = (maxn + kin - 1) / kin * kin;
+  const long cap = L.oZ - L.oDfac;
+  const bool fits = L.Rs <= 128 && (long)L.Rs * Kp * eb <= cap && (long)L.Rs * (L.Rs + 1) / 2 * 4 <= cap &&
+                    128 * Kp * eb <= L.total;
+  return fits ? tc : 0;
+}
+
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
-                  void* stream, double* b, int ldb, int fill, int top_solve) {
+                  void* stream, double* b, int ldb, int fill, int top_solve, int tc) {
   if (ntasks <= 0) return 0;
   top_solve = top_solve && b && !mixed;
-  size_t sm = factor_smem_bytes(maxn, maxm, mixed, fill);
+  const int tcm = tc_mode_for(tc, mixed, pair, maxn, maxm, fill);
+  size_t sm = factor_smem_bytes(maxn, maxm, mixed, fill, tcm ? 0 : 1);
   if (top_solve) sm = std::max(sm, solve_smem_bytes(maxn, maxm, 0, fill));
   const void* fn = mixed ? (pair ? (const void*)k_factor<float, 1> : (const void*)k_factor<float, 4>)
                           : (pair ? (const void*)k_factor<double, 1> : (const void*)k_factor<double, 4>);
@@ -1931,8 +2079,8 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
   if (e) return e;
   // unpaired launches drop the second pivot buffer when that lets more CTAs
   // share an SM (the occupancy of this kernel with either request)
-  int dbl = 1;
-  if (!pair && !top_solve) {
+  int dbl = tcm ? 0 : 1;
+  if (!pair && !top_solve && !tcm) {
     const size_t sm1 = factor_smem_bytes(maxn, maxm, mixed, fill, 0);
     int occ = 0, occ1 = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFactorThreads, sm) == cudaSuccess &&
@@ -1959,13 +2107,13 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
   const int p = pair ? 1 : 0;
   if (mixed)
     return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<float, 1>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
-                                          dbl)
+                                          dbl, tcm)
                 : (int)cudaLaunchKernelEx(&cfg, k_factor<float, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
-                                          dbl);
+                                          dbl, tcm);
   return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<double, 1>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
-                                        dbl)
+                                        dbl, 0)
               : (int)cudaLaunchKernelEx(&cfg, k_factor<double, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
-                                        dbl);
+                                        dbl, 0);
 }
 
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,

@@ -1,6 +1,7 @@
 """Mixed precision (FP64 pivots and Schur accumulators, FP32 panel trsm and
-Schur dot products, FP32 substitutions) with FP64 iterative refinement,
-through the C interface, against the FP64 oracle.
+Schur dot products, or TF32/BF16 Schur products on the tensor cores, FP32
+substitutions) with FP64 iterative refinement, through the C interface,
+against the FP64 oracle.
 
 The gate is the FP64 one: after refinement the normwise backward error is
 <= 1e-14 and the solution agrees with the oracle's to the accuracy the
@@ -47,12 +48,14 @@ def eta(orc, D, E, G, R, x, b):
     return np.abs(r).max() / (nrm * np.abs(x).max() + np.abs(b).max())
 
 
-def run(kkt, D, E, G, R, b, levels, precision, sweeps, tol=1e-15):
+def run(kkt, D, E, G, R, b, levels, precision, sweeps, tol=1e-15, pair_off=False):
     import torch
     N, n, _ = D.shape
     m = R.shape[0]
     h = kkt.kkt_create_plan(N, n, m, levels, kkt.KKT_PARTITION_BALANCED, precision)
     try:
+        if pair_off:   # whole-CTA segment tasks (paired tasks keep the CUDA-core products)
+            kkt.kkt_set_pairing(h, kkt.KKT_PAIR_OFF)
         Dd, Ed, Gd, Rd = dev(D), dev(E), dev(G) if m else None, dev(R) if m else None
         kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
         bd = dev(b)
@@ -194,3 +197,26 @@ def test_refinement_multiple_rhs_cta_blocks(kkt, orc):
         xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b[:, c])
         assert np.abs(x[:, c] - xo).max() <= 1e-5 * np.abs(xo).max()
         assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(b[:, c])
+
+
+@pytest.mark.parametrize("N,n,m,levels", [(128, 32, 8, [1]), (90, 48, 4, [1]), (120, 48, 4, [8, 1]),
+                                          (100, 40, 0, [1])])
+@pytest.mark.parametrize("precision", [3, 4])
+def test_tensor_core_schur_products(kkt, orc, N, n, m, levels, precision):
+    """KKT_MIXED_TF32 / KKT_MIXED_BF16: the Schur products of blocks n >= 32
+    on the tensor cores. The unrefined solution differs from the FP32
+    CUDA-core path's (a different product arithmetic ran) and is as accurate
+    as the operand rounding allows; after refinement the FP64 gates hold."""
+    D, E, G, R = gen.ipm(N, n, m, seed=31, sigma_decades=6.0)
+    b = gen.rhs(N * n + m, 1, seed=32)
+    x, raw, etas = run(kkt, D, E, G, R, b, levels, precision, sweeps=12, tol=1e-16, pair_off=True)
+    _, raw32, _ = run(kkt, D, E, G, R, b, levels, kkt.KKT_MIXED_FP32, sweeps=1, tol=1e-16, pair_off=True)
+    assert not np.array_equal(raw, raw32)
+    e_raw = eta(orc, D, E, G, R, raw, b)
+    assert e_raw <= (1e-3 if precision == 4 else 1e-4), e_raw
+    e = eta(orc, D, E, G, R, x, b)
+    assert e <= 1e-14, (e, etas)
+    xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b)
+    r = b - orc.block_matvec(D, E, G, R, x)
+    ro = b - orc.block_matvec(D, E, G, R, xo)
+    assert np.linalg.norm(r) <= max(1e-10 * np.linalg.norm(b), 10 * np.linalg.norm(ro)), etas
