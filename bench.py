@@ -646,7 +646,7 @@ def measure_batch(name, args, world, rank, local, host_check=64):
                  clocks=clk.summary())
         if mixed:
             r["refinement"] = {"sweeps_max": args.sweeps, "tol": args.tol,
-                               "stop": "eta <= tol, or eta <= 16 u and a sweep that cuts it by less than 10 % (rounding floor)"}
+                               "stop": "eta <= tol, or eta <= 4 u and a sweep that cuts it by less than 10 % (rounding floor)"}
         if split is not None:
             names = [f"{'k_factor_w' if n <= 16 else 'k_factor'} n={n} ({len(sy)} systems)" for n, sy in fgroups]
             r["factor_launch_ms"] = {nm: round(v, 4) for nm, v in zip(names, split)}

@@ -260,7 +260,7 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
  * FP64 with the blocks of Eq. (3), eta = ||c||_inf / (||Psi||_inf ||x||_inf +
  * ||b||_inf) over the system's right-hand sides together. A system stops
  * when its eta is <= tol, or when its eta is at the rounding level of the
- * FP64 residual (<= 16 u, u = 2^-53) and a sweep cuts it by less than 10 %
+ * FP64 residual (<= 4 u, u = 2^-53) and a sweep cuts it by less than 10 %
  * (refinement has reached its floor); its remaining sweeps return at once on the device (no host
  * synchronization, capturable in a CUDA graph). With tol = 0 every system
  * refines until its eta stops falling; with tol < 0 every sweep runs. A relative residual within a small

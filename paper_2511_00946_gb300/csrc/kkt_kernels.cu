@@ -391,19 +391,16 @@ __device__ void syrk_trap(double* T, int ldt, const TZ* Zlo, const TZ* Z, int zs
 // products as a packed lower triangle; the tensor core reads 128 rows of
 // operand address range from it (rows from pr1 on are arbitrary data inside
 // the CTA's shared memory and feed only accumulator rows that are never
-// read). Returns false when the MMAs did not complete within the bounded
-// wait (T is then left without the update).
-struct TcState {
-  uint32_t tmem;    // accumulator columns in tensor memory
-  uint64_t* bar;    // completion mbarrier
-  uint32_t phase;   // completions so far
-  int mode;         // 1 = TF32, 2 = BF16
-};
-
-__device__ bool syrk_tc(double* T, int ldt, const float* Z, int ldz, int r0, int pr1, int n, unsigned char* buf,
-                        TcState& st) {
+// read). `tmem`: the accumulator's tensor-memory address; `bar`: the
+// completion mbarrier, waited on with `parity` (its completions so far, mod
+// 2); mode 1 = TF32, 2 = BF16. Returns false when the MMAs did not complete
+// within the bounded wait (T is then left without the update).
+// (out of line: inlined into the stage loop it enlarges the loop's code past
+// what the instruction cache holds, and every mixed launch slowed down)
+__device__ __noinline__ bool syrk_tc(double* T, int ldt, const float* Z, int ldz, int r0, int pr1, int n,
+                                     unsigned char* buf, uint32_t tmem, uint64_t* bar, uint32_t parity, int mode) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const bool bf = st.mode == 2;
+  const bool bf = mode == 2;
   const int kin = bf ? 16 : 8, epc = bf ? 8 : 4, eb = bf ? 2 : 4;
   const int Kp = (n + kin - 1) / kin * kin;
   const uint32_t LBO = 128, SBO = (uint32_t)(Kp / epc) * 128;
@@ -426,12 +423,11 @@ __device__ bool syrk_tc(double* T, int ldt, const float* Z, int ldz, int r0, int
     const uint32_t a0 = tc::smem_u32(buf);
     for (int ks = 0; ks < Kp / kin; ++ks) {
       const uint64_t d = tc::smem_desc(a0 + (uint32_t)ks * 2 * LBO, LBO, SBO);
-      tc::mma(bf, st.tmem, d, d, idesc, ks > 0);
+      tc::mma(bf, tmem, d, d, idesc, ks > 0);
     }
-    tc::commit(st.bar);
+    tc::commit(bar);
   }
-  const bool ok = tc::wait(st.bar, st.phase & 1);
-  st.phase++;
+  const bool ok = tc::wait(bar, parity);
   tc::fence_after();
   // products -> packed lower triangle S[a (a + 1) / 2 + b]: warp w reads the
   // TMEM lanes (rows) 32 (w % 4) .. + 31, warps w and w + 4 take alternate
@@ -442,7 +438,7 @@ __device__ bool syrk_tc(double* T, int ldt, const float* Z, int ldz, int r0, int
     const int a = row0 + lane;
     for (int c0 = 8 * (warp >> 2); c0 < pr1 && c0 <= row0 + 31; c0 += 16) {
       float v[8];
-      tc::ld8(st.tmem + ((uint32_t)row0 << 16) + (uint32_t)c0, v);
+      tc::ld8(tmem + ((uint32_t)row0 << 16) + (uint32_t)c0, v);
       if (a < pr1 && a >= r0) {
         float* Sa = S + a * (a + 1) / 2;
 #pragma unroll
@@ -818,7 +814,9 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
 // (one CTA per SM, latency-bound) take the unconstrained allocation (1);
 // the others four (at most 64 registers), so that several segment CTAs share
 // an SM when shared memory allows it.
-template <typename TZ, int MINB>
+// TC: the instantiation with the tensor-core Schur products (mixed launches
+// that use them); the others carry none of that code.
+template <typename TZ, int MINB, bool TC = false>
 __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc* __restrict__ descs,
                                                            const Task* __restrict__ tasks,
                                                            const double* __restrict__ uD,
@@ -858,21 +856,25 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
 
   // tensor-core Schur products (mixed whole-CTA layout without the second
   // pivot buffer, whose region then stages the operands)
-  const bool use_tc = mixed && tcm && mode == kWhole && !dbl;
+  const bool use_tc = TC && mixed && tcm && mode == kWhole && !dbl;
   const uint32_t tc_cols = ((lay.Rs + 15) & ~15) <= 64 ? 64u : 128u;
-  TcState tcs{0u, &tbar, 0u, tcm};
-  if (use_tc) {
-    if (threadIdx.x < 32) tc::alloc(&tslot, tc_cols);
-    if (threadIdx.x == 0) tc::mbar_init(&tbar);
-    tc::fence_before();
+  uint32_t tmem = 0u, tphase = 0u;
+  if constexpr (TC) {
+    if (use_tc) {
+      if (threadIdx.x < 32) tc::alloc(&tslot, tc_cols);
+      if (threadIdx.x == 0) tc::mbar_init(&tbar);
+      tc::fence_before();
+    }
   }
   if (threadIdx.x == 0) bad = 0;
   for (int e = threadIdx.x; e < lay.Rs * ldT; e += blockDim.x) T[e] = 0.0;
   if (eg) potrf_table(tab, n);
   __syncthreads();
-  if (use_tc) {
-    tc::fence_after();
-    tcs.tmem = tslot;
+  if constexpr (TC) {
+    if (use_tc) {
+      tc::fence_after();
+      tmem = tslot;
+    }
   }
   cx.load_first(eg, wr, cta_grp());
   __syncthreads();
@@ -982,10 +984,12 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
       }
       store_panel(j, r0, pr1, mode == kWhole ? R : n + m, P);
       bool tc_done = false;
-      if constexpr (mixed) {
+      if constexpr (mixed && TC) {
         if (use_tc) {
-          if (!syrk_tc(T, ldT, (const float*)Z, ldZ, r0, pr1, n, smraw + lay.oDfac, tcs) && threadIdx.x == 0)
+          if (!syrk_tc(T, ldT, (const float*)Z, ldZ, r0, pr1, n, smraw + lay.oDfac, tmem, &tbar, tphase & 1, tcm) &&
+              threadIdx.x == 0)
             record_timeout(info, d.sys, d.nat[j], d.level);
+          ++tphase;
           tc_done = true;
         }
       }
@@ -1088,10 +1092,12 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
     cluster_arrive();
     cluster_wait();
   }
-  if (use_tc) {
-    tc::fence_before();
-    __syncthreads();
-    if (threadIdx.x < 32) tc::dealloc(tcs.tmem, tc_cols);
+  if constexpr (TC) {
+    if (use_tc) {
+      tc::fence_before();
+      __syncthreads();
+      if (threadIdx.x < 32) tc::dealloc(tmem, tc_cols);
+    }
   }
 }
 
@@ -1841,7 +1847,7 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
 // sweep is not taken as the end, since the normwise eta of an
 // ill-conditioned system need not fall monotonically); a stopped system
 // skips the remaining sweeps.
-constexpr double kEtaFloor = 16.0 * 1.1102230246251565e-16;  // 16 u
+constexpr double kEtaFloor = 4.0 * 1.1102230246251565e-16;  // 4 u
 __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int* __restrict__ sys_desc,
                                  const int* __restrict__ part0, const double* __restrict__ uG,
                                  const double* __restrict__ uR, const double* __restrict__ b, int ldb,
@@ -1897,7 +1903,7 @@ __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int*
     const double eta = red[0][0] / (red[3][0] * red[1][0] + red[2][0]);
     eta_out[s] = eta;
     // stop: 1 = eta <= tol; 2 = eta is at the rounding level of the FP64
-    // residual (<= 16 u) and this sweep cut it by less than 10 %
+    // residual (<= 4 u) and this sweep cut it by less than 10 %
     if (converged) {
       if (eta <= tol) converged[s] = 1;
       else if (tol >= 0.0 && eta_prev && eta <= kEtaFloor && eta > 0.9 * eta_prev[s]) converged[s] = 2;
@@ -2073,7 +2079,8 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
   const int tcm = tc_mode_for(tc, mixed, pair, maxn, maxm, fill);
   size_t sm = factor_smem_bytes(maxn, maxm, mixed, fill, tcm ? 0 : 1);
   if (top_solve) sm = std::max(sm, solve_smem_bytes(maxn, maxm, 0, fill));
-  const void* fn = mixed ? (pair ? (const void*)k_factor<float, 1> : (const void*)k_factor<float, 4>)
+  const void* fn = mixed ? (pair ? (const void*)k_factor<float, 1>
+                                 : tcm ? (const void*)k_factor<float, 4, true> : (const void*)k_factor<float, 4>)
                           : (pair ? (const void*)k_factor<double, 1> : (const void*)k_factor<double, 4>);
   int e = set_smem(fn, sm);
   if (e) return e;
@@ -2107,9 +2114,11 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
   const int p = pair ? 1 : 0;
   if (mixed)
     return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<float, 1>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
-                                          dbl, tcm)
-                : (int)cudaLaunchKernelEx(&cfg, k_factor<float, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
-                                          dbl, tcm);
+                                          dbl, 0)
+                : tcm ? (int)cudaLaunchKernelEx(&cfg, k_factor<float, 4, true>, d, t, D, E, G, R, info, p, b, ldb,
+                                                top_solve, dbl, tcm)
+                      : (int)cudaLaunchKernelEx(&cfg, k_factor<float, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
+                                                dbl, 0);
   return pair ? (int)cudaLaunchKernelEx(&cfg, k_factor<double, 1>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
                                         dbl, 0)
               : (int)cudaLaunchKernelEx(&cfg, k_factor<double, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
