@@ -349,6 +349,37 @@ kkt_status kkt_set_launch_events(kkt_handle* h, void* const* events, int count);
 typedef enum { KKT_PAIR_AUTO = 0, KKT_PAIR_OFF = 1, KKT_PAIR_ON = 2 } kkt_pair_policy;
 kkt_status kkt_set_pairing(kkt_handle* h, int policy);
 
+/* Schedule of kkt_factor. on = 0 (the default): one launch per level and
+ * block-size class. on = 1: ONE persistent launch for the whole
+ * factorization of every system at every level (Algorithm 1's parallel phase
+ * and, level by level, the reduced systems of Eq. (7)). Its CTAs take work
+ * items by ticket from a queue in topological order (level by level; within
+ * a level the most expensive segment tasks first, i.e. longest processing
+ * time first, so long systems start first and short ones fill the tail;
+ * tasks with blocks n <= 16 in bundles of up to eight, one per warp). A
+ * reduced-system task starts as soon as the lower-level tasks whose slots it
+ * reads have released their per-task ready counters, instead of at a level
+ * boundary; each wait is bounded (kkt_set_wait_limit) and reports
+ * KKT_ERR_TIMEOUT through kkt_get_info instead of hanging. Segment tasks never
+ * run as CTA pairs in this schedule, and mixed levels use FP32 CUDA-core
+ * Schur products. Results are bitwise those of the per-level launches (the
+ * same operations per element). Requires every level of the handle to have
+ * the same arithmetic (KKT_FP64, KKT_MIXED_FP32_ALL, or single-level plans
+ * of any precision), else KKT_ERR_ARG. The first call with on = 1 builds the
+ * work list and allocates a small device buffer (call it outside any graph
+ * capture); kkt_factor then enqueues one memset and one kernel (capturable).
+ * kkt_factor_solve and kkt_factor_solve_host keep the per-level launches. */
+kkt_status kkt_set_persistent(kkt_handle* h, int on);
+
+/* Bounded waits of the persistent schedule: a task gives up waiting for its
+ * feeders after `cycles` SM clock cycles (default 2^31, about a second),
+ * records KKT_ERR_TIMEOUT (system, natural stage and level of the waiting
+ * task) and carries on without its own work, so nothing hangs. unmet != 0
+ * adds one unsatisfiable dependency to every waiting task (a counter no task
+ * ever releases), which makes every wait run out: a test of the timeout path
+ * on the device; unmet = 0 restores the real counts. */
+kkt_status kkt_set_wait_limit(kkt_handle* h, long long cycles, int unmet);
+
 /* Number of kernel launches one kkt_factor / one kkt_solve (per chunk of up
  * to 16 right-hand sides) enqueues for this handle. */
 kkt_status kkt_launch_counts(const kkt_handle* h, int* factor_launches, int* solve_launches);

@@ -29,6 +29,7 @@ EXPORTED = [
     "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_factor_solve", "kkt_factor_solve_host", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta",
     "kkt_get_info",
     "kkt_get_factor", "kkt_set_pairing", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
+    "kkt_set_persistent", "kkt_set_wait_limit",
 ]
 
 
@@ -77,6 +78,8 @@ _sig = {
     "kkt_plan_flops": [_i, _i, _i, _i, _ip, _i, _i, _dp, _dp, _dp],
     "kkt_solve_noalloc": [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp, _vp],
     "kkt_status_string": [_i],
+    "kkt_set_persistent": [_vp, _i],
+    "kkt_set_wait_limit": [_vp, ctypes.c_longlong, _i],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -309,6 +312,18 @@ def kkt_set_launch_events(h: int, events) -> None:
         handles.append(None if ev is None else ev if isinstance(ev, int) else ev.cuda_event)
     arr = (_vp * max(len(handles), 1))(*handles)
     _check(_lib.kkt_set_launch_events(h, arr if handles else None, len(handles)), "kkt_set_launch_events")
+
+
+def kkt_set_persistent(h: int, on: bool = True) -> None:
+    """One persistent launch for the whole factorization (ticket queue in
+    topological, longest-first order; see the C header)."""
+    _check(_lib.kkt_set_persistent(h, int(bool(on))), "kkt_set_persistent")
+
+
+def kkt_set_wait_limit(h: int, cycles: int, unmet: bool = False) -> None:
+    """Clock-cycle bound of the persistent schedule's dependency waits;
+    `unmet` injects an unsatisfiable dependency (tests the timeout path)."""
+    _check(_lib.kkt_set_wait_limit(h, int(cycles), int(bool(unmet))), "kkt_set_wait_limit")
 
 
 def kkt_launch_counts(h: int) -> tuple[int, int]:

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "../../include/kkt.h"
@@ -198,6 +199,18 @@ struct kkt_handle {
   int hs_nrhs = 0;                           // columns the b copy has room for
   cudaStream_t hs_copy = nullptr, hs_lvl[kHostChunks] = {};
   cudaEvent_t hs_ev_start = nullptr, hs_ev_copy[kHostChunks] = {}, hs_ev_lvl[kHostChunks] = {};
+  // persistent factorization (kkt_set_persistent): work items, their tasks,
+  // consumer edges, ready counters + ticket, in one allocation
+  int persistent = 0;
+  void* pmem = nullptr;
+  kkt::PItem* pitems = nullptr;
+  kkt::PCons* pcons = nullptr;
+  Task* ptasks = nullptr;
+  int* pready = nullptr;        // [pn] counters, then the ticket
+  int pn = 0, pgrid = 0, pslice = 0, pdbl = 1, pmixed = 0, punmet = 0;
+  size_t psmem = 0;
+  long long pwait = 1LL << 31;  // clock cycles a dependency wait may take (about a second)
+  std::vector<kkt::PItem> hpitems;
 };
 
 constexpr int kMaxSweeps = 16;
@@ -757,6 +770,7 @@ kkt_status kkt_batch_create_tuned(int count, const int* N, const int* n, const i
 kkt_status kkt_destroy(kkt_handle* h) {
   if (!h) return KKT_OK;
   if (h->dmem) cudaFree(h->dmem);
+  if (h->pmem) cudaFree(h->pmem);
   if (h->hs_mem) cudaFree(h->hs_mem);
   if (h->hs_bmem) cudaFree(h->hs_bmem);
   if (h->hs_copy) cudaStreamDestroy(h->hs_copy);
@@ -836,11 +850,204 @@ kkt_status kkt_set_pairing(kkt_handle* h, int policy) {
   return KKT_OK;
 }
 
+namespace {
+// FP64 flops of one factor task (segment of `len` stages), the LPT cost
+double task_cost(int len, int n, int m, bool hasW, bool hasF) {
+  double f = 0.0, sv = 0.0;
+  seg_flops(len, n, m, hasW, hasF, &f, &sv);
+  return f;
+}
+
+// The work items of the persistent factorization: level by level; within a
+// level the CTA-size tasks one item each and the small-block tasks (n <=
+// kWarpMaxN) in bundles of `wpc`, each group in decreasing cost, the items
+// of the level then merged in decreasing cost (longest processing time
+// first). Segment k' of level l + 1 (stages f'..e', separator f' - 1 when
+// k' >= 1) reads the slots of level-l segments max(f' - 1, 0) .. e' + 1
+// (level-(l+1) stage t is the separator between level-l segments t and
+// t + 1): those are its feeders.
+kkt_status build_persistent(kkt_handle* h) {
+  int mixed = -1;
+  for (int v : h->level_mixed) {
+    if (mixed >= 0 && v != mixed) return KKT_ERR_ARG;  // one precision for every level
+    mixed = v;
+  }
+  mixed = mixed > 0 ? 1 : 0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return KKT_ERR_CUDA;
+  // shared memory: the largest CTA task layout and a bundle of warp slices
+  int cn = 0, cm = 0, wn = 0, wm = 0;
+  bool cfill = false, wfill = false, any_cta = false, any_w = false;
+  for (const SysPlan& sp : h->sys) {
+    bool fill = false;
+    for (const LevelPlan& L : sp.lv) fill = fill || L.P > 1;
+    if (sp.n > kkt::kWarpMaxN) {
+      any_cta = true; cn = std::max(cn, sp.n); cm = std::max(cm, sp.m); cfill = cfill || fill;
+    } else {
+      any_w = true; wn = std::max(wn, sp.n); wm = std::max(wm, sp.m); wfill = wfill || fill;
+    }
+  }
+  const int slice = any_w ? (int)kkt::factor_w_slice_bytes(wn, wm, mixed, wfill) : 0;
+  const int wpc = any_w ? std::max(1, std::min(8, (200 * 1024) / slice)) : 8;
+  int dbl = 1, best_occ = -1;
+  size_t smem = 0;
+  for (int db = 1; db >= 0; --db) {
+    const size_t sc = any_cta ? kkt::factor_smem_bytes(cn, cm, mixed, cfill, db) : 0;
+    const size_t sm = std::max(sc, (size_t)wpc * slice);
+    const int occ = kkt::persist_occupancy(mixed, sm);
+    if (occ > best_occ) { best_occ = occ; dbl = db; smem = sm; }
+    if (!any_cta) break;
+  }
+  if (best_occ < 1) return KKT_ERR_ARG;
+  // items
+  struct Cand { double cost; std::vector<std::pair<int, int>> tasks; bool warp; };
+  std::vector<kkt::PItem> items;
+  std::vector<Task> ptasks;
+  std::vector<std::vector<std::vector<int>>> item_of(h->count);
+  for (int s = 0; s < h->count; ++s) {
+    item_of[s].resize(h->sys[s].lv.size());
+    for (size_t l = 0; l < h->sys[s].lv.size(); ++l) item_of[s][l].assign(h->sys[s].lv[l].P, -1);
+  }
+  for (int l = 0; l < h->maxL; ++l) {
+    std::vector<std::pair<double, std::pair<int, int>>> ct, wt;  // (cost, (system, segment))
+    for (int s = 0; s < h->count; ++s) {
+      const SysPlan& sp = h->sys[s];
+      if (l >= (int)sp.lv.size()) continue;
+      const LevelPlan& L = sp.lv[l];
+      for (int k = 0; k < L.P; ++k) {
+        const double c = task_cost(seg_len(L, k), sp.n, sp.m, k >= 1, k < L.P - 1);
+        (sp.n > kkt::kWarpMaxN ? ct : wt).push_back({c, {s, k}});
+      }
+    }
+    auto desc = [](const std::pair<double, std::pair<int, int>>& a, const std::pair<double, std::pair<int, int>>& b) {
+      return a.first != b.first ? a.first > b.first : a.second < b.second;
+    };
+    std::sort(ct.begin(), ct.end(), desc);
+    std::sort(wt.begin(), wt.end(), desc);
+    std::vector<Cand> cands;
+    for (const auto& t : ct) cands.push_back(Cand{t.first, {t.second}, false});
+    for (size_t i = 0; i < wt.size(); i += wpc) {
+      Cand c{wt[i].first, {}, true};
+      for (size_t j = i; j < std::min(wt.size(), i + (size_t)wpc); ++j) c.tasks.push_back(wt[j].second);
+      cands.push_back(c);
+    }
+    std::stable_sort(cands.begin(), cands.end(), [](const Cand& a, const Cand& b) { return a.cost > b.cost; });
+    for (const Cand& c : cands) {
+      kkt::PItem it{};
+      it.first = (int)ptasks.size();
+      it.cnt = (int)c.tasks.size();
+      it.warp = c.warp ? 1 : 0;
+      for (const auto& t : c.tasks) {
+        ptasks.push_back(Task{h->desc_of[t.first][l], t.second});
+        item_of[t.first][l][t.second] = (int)items.size();
+      }
+      items.push_back(it);
+    }
+  }
+  // dependency edges (producer item, consumer item) -> feeder tasks
+  std::map<std::pair<int, int>, int> w;
+  for (int s = 0; s < h->count; ++s) {
+    const SysPlan& sp = h->sys[s];
+    for (size_t l = 1; l < sp.lv.size(); ++l) {
+      const LevelPlan& L = sp.lv[l];
+      for (int k = 0; k < L.P; ++k) {
+        const int f = seg_first(L, k), e = f + seg_len(L, k) - 1;
+        const int lo = k >= 1 ? f - 1 : f, hi = e + 1;
+        const int ci = item_of[s][l][k];
+        for (int q = lo; q <= hi; ++q) {
+          ++w[{item_of[s][l - 1][q], ci}];
+          ++items[ci].need;
+        }
+      }
+    }
+  }
+  std::vector<kkt::PCons> cons;
+  for (size_t i = 0, pos = 0; i < items.size(); ++i) {
+    items[i].cons0 = (int)cons.size();
+    auto itr = w.lower_bound({(int)i, -1});
+    for (; itr != w.end() && itr->first.first == (int)i; ++itr) cons.push_back(kkt::PCons{itr->first.second, itr->second});
+    items[i].ncons = (int)cons.size() - items[i].cons0;
+    (void)pos;
+  }
+  const size_t n_it = items.size(), n_c = std::max<size_t>(cons.size(), 1), n_t = ptasks.size();
+  Carver cv;
+  const size_t o_it = cv.take(sizeof(kkt::PItem) * n_it), o_c = cv.take(sizeof(kkt::PCons) * n_c),
+               o_t = cv.take(sizeof(Task) * n_t), o_r = cv.take(sizeof(int) * (n_it + 1));
+  if (h->pmem) cudaFree(h->pmem);
+  h->pmem = nullptr;
+  if (cudaMalloc(&h->pmem, cv.off) != cudaSuccess) {
+    h->pmem = nullptr;
+    return KKT_ERR_CUDA;
+  }
+  char* base = (char*)h->pmem;
+  h->pitems = (kkt::PItem*)(base + o_it);
+  h->pcons = (kkt::PCons*)(base + o_c);
+  h->ptasks = (Task*)(base + o_t);
+  h->pready = (int*)(base + o_r);
+  bool ok = cudaMemcpy(h->pitems, items.data(), sizeof(kkt::PItem) * n_it, cudaMemcpyHostToDevice) == cudaSuccess &&
+            (cons.empty() || cudaMemcpy(h->pcons, cons.data(), sizeof(kkt::PCons) * cons.size(),
+                                        cudaMemcpyHostToDevice) == cudaSuccess) &&
+            cudaMemcpy(h->ptasks, ptasks.data(), sizeof(Task) * n_t, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {
+    cudaFree(h->pmem);
+    h->pmem = nullptr;
+    return KKT_ERR_CUDA;
+  }
+  h->hpitems = items;
+  h->pn = (int)n_it;
+  h->pgrid = (int)std::min<long long>((long long)n_it, (long long)best_occ * sms);
+  h->psmem = smem;
+  h->pslice = slice;
+  h->pdbl = dbl;
+  h->pmixed = mixed;
+  h->punmet = 0;
+  return KKT_OK;
+}
+}  // namespace
+
+kkt_status kkt_set_persistent(kkt_handle* h, int on) {
+  if (!h) return KKT_ERR_ARG;
+  if (on && !h->pmem) {
+    const kkt_status st = build_persistent(h);
+    if (st != KKT_OK) return st;
+  }
+  h->persistent = on ? 1 : 0;
+  return KKT_OK;
+}
+
+kkt_status kkt_set_wait_limit(kkt_handle* h, long long cycles, int unmet) {
+  if (!h || cycles < 1) return KKT_ERR_ARG;
+  h->pwait = cycles;
+  unmet = unmet ? 1 : 0;
+  if (h->pmem && unmet != h->punmet) {
+    std::vector<kkt::PItem> it = h->hpitems;
+    if (unmet)
+      for (kkt::PItem& x : it)
+        if (x.need > 0) ++x.need;
+    if (cudaMemcpy(h->pitems, it.data(), sizeof(kkt::PItem) * it.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return KKT_ERR_CUDA;
+  }
+  h->punmet = unmet;
+  return KKT_OK;
+}
+
 kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const double* G,
                       const double* R, void* stream) {
   if (!h || !D) return KKT_ERR_ARG;
   if (h->tot_E > 0 && !E) return KKT_ERR_ARG;
   if (h->maxm > 0 && (!G || !R)) return KKT_ERR_ARG;
+  if (h->persistent) {
+    if (cudaMemsetAsync(h->pready, 0, sizeof(int) * (h->pn + 1), (cudaStream_t)stream) != cudaSuccess ||
+        kkt::launch_factor_persist(h->ddesc, h->ptasks, h->pitems, h->pn, h->pcons, h->pready, h->pmixed, D, E, G, R,
+                                   h->dinfo, h->pgrid, h->psmem, h->pslice, h->pdbl, h->pwait, stream) ||
+        !mark(h, 0, stream))
+      return KKT_ERR_CUDA;
+    h->factored = true;
+    h->cur_b = false;
+    return KKT_OK;
+  }
   int li = 0;
   for (int l = 0; l < h->maxL; ++l)
     for (const kkt_handle::Group& gr : h->fac_groups[l]) {
@@ -902,7 +1109,7 @@ kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream) 
   // attached events: the factor's launches take the first slots, then the
   // solve's launches in order
   int li = 0;
-  for (int l = 0; l < h->maxL; ++l) li += (int)h->fac_groups[l].size();
+  kkt_launch_counts(h, &li, nullptr);
   for (int c0 = 0; c0 < nrhs; c0 += kkt::kRhsChunk) {
     const int nr = std::min(kkt::kRhsChunk, nrhs - c0);
     const kkt_status st = solve_chunk(h, b + c0, ldb, nr, nullptr, stream, &li);
@@ -1273,6 +1480,7 @@ kkt_status kkt_launch_counts(const kkt_handle* h, int* fl, int* sl) {
     f += (int)h->fac_groups[l].size();
     sv += (int)h->fac_groups[l].size() + (int)h->bwd_groups[l].size();
   }
+  if (h->persistent) f = 1;
   if (fl) *fl = f;
   if (sl) *sl = sv;
   return KKT_OK;

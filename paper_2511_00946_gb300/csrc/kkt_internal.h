@@ -109,6 +109,25 @@ struct Task {
   int seg;   // segment index k (0-based)
 };
 
+// Persistent factorization (one launch for every level of every system):
+// work items in topological order (level by level; within a level the most
+// expensive first), each one segment task run by a whole CTA or a bundle of
+// up to eight small-block tasks run one per warp. An item that reads the
+// slots of lower-level tasks starts once its counter in `ready` reaches
+// `need`; a finished item adds `weight` to the counter of each consumer.
+struct PItem {
+  int first;  // first task in the persistent task array
+  int cnt;    // tasks (1 for a CTA item, <= 8 for a warp bundle)
+  int warp;   // 1: one warp per task (blocks n <= kWarpMaxN)
+  int need;   // feeder tasks to wait for
+  int cons0;  // first consumer edge
+  int ncons;  // consumer edges
+};
+struct PCons {
+  int item;    // consumer item
+  int weight;  // feeder tasks of the consumer in this item
+};
+
 // Device-side breakdown record (kkt_info layout).
 struct Info {
   int status, system, stage, level;
@@ -265,7 +284,20 @@ int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const 
 // D (every system's stage blocks) <- identity blocks, R <- identity corners
 int launch_fill_identity(const LevelDesc* d, const int* sys_desc, int count, double* D, double* R,
                          void* stream);
+// Persistent factorization of a handle whose levels share one precision:
+// items [0, nitems) over `grid` CTAs with `smem` bytes of shared memory;
+// ready[0..nitems) and the ticket counter ready[nitems] must be zero; a
+// dependency wait gives up after wait_cycles clock cycles (KKT_ERR_TIMEOUT).
+// `slice`: shared memory of one warp task; `dbl`: the CTA tasks keep the
+// second pivot buffer.
+int launch_factor_persist(const LevelDesc* d, const Task* t, const PItem* items, int nitems, const PCons* cons,
+                          int* ready, int mixed, const double* D, const double* E, const double* G,
+                          const double* R, Info* info, int grid, size_t smem, int slice, int dbl,
+                          long long wait_cycles, void* stream);
+// occupancy (CTAs per SM) of the persistent kernel with `smem` bytes
+int persist_occupancy(int mixed, size_t smem);
 size_t factor_smem_bytes(int maxn, int maxm, int mixed, int fill = 1, int dbl = 1);
+size_t factor_w_slice_bytes(int maxn, int maxm, int mixed, int fill = 1);
 size_t solve_smem_bytes(int maxn, int maxm, int single, int fill = 1);
 
 }  // namespace kkt

@@ -816,21 +816,18 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
 // an SM when shared memory allows it.
 // TC: the instantiation with the tensor-core Schur products (mixed launches
 // that use them); the others carry none of that code.
-template <typename TZ, int MINB, bool TC = false>
-__global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc* __restrict__ descs,
-                                                           const Task* __restrict__ tasks,
-                                                           const double* __restrict__ uD,
-                                                           const double* __restrict__ uE,
-                                                           const double* __restrict__ uG,
-                                                           const double* __restrict__ uR,
-                                                           Info* info, int pair, double* yb, int ldyb,
-                                                           int top_solve, int dbl, int tcm) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  __shared__ int bad;
-  __shared__ uint32_t tslot;               // TMEM address of the tensor-core accumulator
-  __shared__ __align__(8) uint64_t tbar;   // its completion mbarrier
+// One segment task of the factorization by the whole CTA (or, with `pair`,
+// by this CTA's half of a two-CTA cluster): the body of k_factor, also run
+// task after task by the persistent kernel. `bad`, `tslot`, `tbar`: shared
+// variables of the caller (breakdown flag, TMEM address slot, mbarrier).
+template <typename TZ, bool TC>
+__device__ __forceinline__ void factor_task(const Task tk, const LevelDesc* __restrict__ descs,
+                                            const double* __restrict__ uD, const double* __restrict__ uE,
+                                            const double* __restrict__ uG, const double* __restrict__ uR,
+                                            Info* info, int pair, double* yb, int ldyb, int top_solve, int dbl,
+                                            int tcm, unsigned char* smraw, int& bad, uint32_t& tslot,
+                                            uint64_t& tbar) {
   const unsigned rank = pair ? cluster_rank() : 0u;
-  const Task tk = tasks[pair ? blockIdx.x >> 1 : blockIdx.x];
   const LevelDesc& d = descs[tk.desc];
   constexpr bool mixed = sizeof(TZ) == 4;
   const FacLayout lay = fac_layout(d.n, d.m, (int)sizeof(TZ), d.P > 1, dbl != 0);
@@ -1101,6 +1098,23 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
   }
 }
 
+template <typename TZ, int MINB, bool TC = false>
+__global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc* __restrict__ descs,
+                                                           const Task* __restrict__ tasks,
+                                                           const double* __restrict__ uD,
+                                                           const double* __restrict__ uE,
+                                                           const double* __restrict__ uG,
+                                                           const double* __restrict__ uR,
+                                                           Info* info, int pair, double* yb, int ldyb,
+                                                           int top_solve, int dbl, int tcm) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int bad;
+  __shared__ uint32_t tslot;               // TMEM address of the tensor-core accumulator
+  __shared__ __align__(8) uint64_t tbar;   // its completion mbarrier
+  factor_task<TZ, TC>(tasks[pair ? blockIdx.x >> 1 : blockIdx.x], descs, uD, uE, uG, uR, info, pair, yb, ldyb,
+                      top_solve, dbl, tcm, smraw, bad, tslot, tbar);
+}
+
 
 // ---------------------------------------------------------------------------
 // Small blocks (n <= kWarpMaxN): one warp per segment task, every step of a
@@ -1126,19 +1140,14 @@ __device__ void trsm_w(TZ* Z, int ldz, int r0, int r1, const TZ* M, int ldm, int
   __syncwarp();
 }
 
+// One small-block segment task by one warp in its shared-memory slice `sm`:
+// the body of k_factor_w, also run by the persistent kernel.
 template <typename TZ>
-__global__ void __launch_bounds__(256, 4) k_factor_w(const LevelDesc* __restrict__ descs,
-                                                  const Task* __restrict__ tasks, int ntasks,
-                                                  const double* __restrict__ uD, const double* __restrict__ uE,
-                                                  const double* __restrict__ uG, const double* __restrict__ uR,
-                                                  Info* info, int slice, double* yb, int ldyb) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int t = blockIdx.x * (blockDim.x >> 5) + wid;
-  if (t >= ntasks) return;  // whole warp
-  const Task tk = tasks[t];
+__device__ __forceinline__ void factor_task_w(const Task tk, const LevelDesc* __restrict__ descs,
+                                              const double* __restrict__ uD, const double* __restrict__ uE,
+                                              const double* __restrict__ uG, const double* __restrict__ uR,
+                                              Info* info, unsigned char* sm, int lane, double* yb, int ldyb) {
   const LevelDesc& d = descs[tk.desc];
-  unsigned char* sm = smraw + (size_t)wid * slice;
   const FacLayout lay = fac_layout_w(d.n, d.m, (int)sizeof(TZ), d.P > 1);
   const FacCtx<TZ, 1> cx(d, tk.seg, sm, lay, uD, uE, uG);
   const int n = cx.n, m = cx.m, R = cx.R, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG;
@@ -1195,6 +1204,102 @@ __global__ void __launch_bounds__(256, 4) k_factor_w(const LevelDesc* __restrict
     }
     __syncwarp();
     corner_factor<true>(Rs, ldR, m, d.mr, cx.rinv, cx.tab, d, info, nullptr, W);
+  }
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(256, 4) k_factor_w(const LevelDesc* __restrict__ descs,
+                                                  const Task* __restrict__ tasks, int ntasks,
+                                                  const double* __restrict__ uD, const double* __restrict__ uE,
+                                                  const double* __restrict__ uG, const double* __restrict__ uR,
+                                                  Info* info, int slice, double* yb, int ldyb) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int t = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (t >= ntasks) return;  // whole warp
+  factor_task_w<TZ>(tasks[t], descs, uD, uE, uG, uR, info, smraw + (size_t)wid * slice, lane, yb, ldyb);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent factorization: one launch runs every segment task of every level
+// (Algorithm 1's parallel phase and, level by level, the reduced systems of
+// Eq. (7)). CTAs take work items by ticket (atomicAdd) from a list in
+// topological order: level by level, and within a level the most expensive
+// first (longest-processing-time order), so long systems start first and the
+// short ones fill the tail. An item of level >= 2 reads slots written by its
+// feeder tasks one level down; its CTA waits (thread 0, acquire loads with a
+// growing sleep, bounded by wait_cycles) until the feeders' release
+// increments reach `need`. A CTA only ever waits on items with smaller
+// tickets, which CTAs already running hold, so every wait has a producer in
+// progress. A wait that runs out records KKT_ERR_TIMEOUT (with the waiting
+// task's system, natural stage and level), skips its task and still releases
+// its consumers, so nothing waits forever.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <typename TZ>
+__global__ void __launch_bounds__(kFactorThreads, 3)
+    k_factor_persist(const LevelDesc* __restrict__ descs, const Task* __restrict__ tasks,
+                     const PItem* __restrict__ items, int nitems, const PCons* __restrict__ cons, int* ready,
+                     const double* __restrict__ uD, const double* __restrict__ uE, const double* __restrict__ uG,
+                     const double* __restrict__ uR, Info* info, int slice, int dbl, long long wait_cycles) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int bad;
+  __shared__ uint32_t tslot;
+  __shared__ __align__(8) uint64_t tbar;
+  __shared__ int cur, ok;
+  int* const ticket = ready + nitems;
+  for (;;) {
+    if (threadIdx.x == 0) cur = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int it = cur;
+    if (it >= nitems) break;
+    const PItem w = items[it];
+    if (threadIdx.x == 0) {
+      int good = 1;
+      if (w.need > 0) {
+        const long long t0 = clock64();
+        unsigned ns = 64;
+        while (ld_acquire_gpu(ready + it) < w.need) {
+          if (clock64() - t0 > wait_cycles) {
+            good = 0;
+            break;
+          }
+          __nanosleep(ns);
+          if (ns < 2048) ns *= 2;
+        }
+        __threadfence();
+      }
+      ok = good;
+      if (!good) {
+        const Task tk = tasks[w.first];
+        const LevelDesc& d = descs[tk.desc];
+        record_timeout(info, d.sys, d.nat[d.seg[tk.seg]], d.level);
+      }
+    }
+    __syncthreads();
+    if (ok) {
+      if (!w.warp) {
+        factor_task<TZ, false>(tasks[w.first], descs, uD, uE, uG, uR, info, 0, nullptr, 1, 0, dbl, 0, smraw, bad,
+                               tslot, tbar);
+      } else {
+        const int wid = threadIdx.x >> 5;
+        if (wid < w.cnt)
+          factor_task_w<TZ>(tasks[w.first + wid], descs, uD, uE, uG, uR, info, smraw + (size_t)wid * slice,
+                            threadIdx.x & 31, nullptr, 1);
+      }
+    }
+    __syncthreads();
+    // release: every thread's writes of this item precede the barrier; the
+    // fence makes them visible device-wide before the counters move
+    if (threadIdx.x == 0) {
+      __threadfence();
+      for (int c = 0; c < w.ncons; ++c) atomicAdd(ready + cons[w.cons0 + c].item, cons[w.cons0 + c].weight);
+    }
   }
 }
 
@@ -2032,6 +2137,36 @@ int set_smem(const void* fn, size_t bytes) {
 
 size_t factor_smem_bytes(int n, int m, int mixed, int fill, int dbl) {
   return (size_t)fac_layout(n, m, mixed ? 4 : 8, fill != 0, dbl != 0).total;
+}
+
+size_t factor_w_slice_bytes(int n, int m, int mixed, int fill) {
+  return (size_t)fac_layout_w(n, m, mixed ? 4 : 8, fill != 0).total;
+}
+
+int persist_occupancy(int mixed, size_t smem) {
+  const void* fn = mixed ? (const void*)k_factor_persist<float> : (const void*)k_factor_persist<double>;
+  if (set_smem(fn, smem)) return 0;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFactorThreads, smem) != cudaSuccess) return 0;
+  return occ;
+}
+
+int launch_factor_persist(const LevelDesc* d, const Task* t, const PItem* items, int nitems, const PCons* cons,
+                          int* ready, int mixed, const double* D, const double* E, const double* G,
+                          const double* R, Info* info, int grid, size_t smem, int slice, int dbl,
+                          long long wait_cycles, void* stream) {
+  if (nitems <= 0) return 0;
+  const void* fn = mixed ? (const void*)k_factor_persist<float> : (const void*)k_factor_persist<double>;
+  int e = set_smem(fn, smem);
+  if (e) return e;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (mixed)
+    k_factor_persist<float><<<grid, kFactorThreads, smem, st>>>(d, t, items, nitems, cons, ready, D, E, G, R, info,
+                                                                slice, dbl, wait_cycles);
+  else
+    k_factor_persist<double><<<grid, kFactorThreads, smem, st>>>(d, t, items, nitems, cons, ready, D, E, G, R,
+                                                                 info, slice, dbl, wait_cycles);
+  return (int)cudaGetLastError();
 }
 
 size_t solve_smem_bytes(int n, int m, int single, int fill) {
