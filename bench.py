@@ -742,7 +742,7 @@ def run_batch(args):
         "error": {"max_backward_error": br["max_eta"], "gate": 1e-14},
         "paths": results,
         "comparison": cmp_,
-        "roofline": results.get("fp64", results.get("fp64_adjoint")).get("roofline"),
+        "roofline": next((r["roofline"] for r in results.values() if r.get("roofline")), None),
         "clocks": br["clocks"],
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -1003,7 +1003,7 @@ def main():
         bres, (bN, bn, bm) = measure_batch("uneven4096", args, world, rank, local)
         batched = {"workload": BATCHES["uneven4096"]["desc"], "systems": len(bN) * world,
                    "paths": bres, "comparison": compare_paths(bres),
-                   "roofline": bres["fp64"].get("roofline")}
+                   "roofline": next((r["roofline"] for r in bres.values() if r.get("roofline")), None)}
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             batched["cpu_baseline"] = batch_cpu_baseline("uneven4096", bN, bn, bm, args.cpu_seconds / 2)
 

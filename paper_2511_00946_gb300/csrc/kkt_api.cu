@@ -421,8 +421,14 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
     // one launch per block-size class and per layout: levels with P = 1 (no
     // fill-in rows) get the compact shared-memory layout and more CTAs per SM
     auto fill_of = [&](int s) { return h->sys[s].lv[l].P > 1; };
+    // within a launch group the longest segments first (longest processing
+    // time first: CTAs are dispatched in task order, so the long systems of an
+    // uneven batch start in the first wave instead of forming the tail)
+    auto seg_stages = [&](int s) { return (double)h->sys[s].lv[l].N / h->sys[s].lv[l].P; };
     std::stable_sort(sys_at.begin(), sys_at.end(), [&](int a, int b) {
-      return h->sys[a].n != h->sys[b].n ? h->sys[a].n < h->sys[b].n : fill_of(a) < fill_of(b);
+      if (h->sys[a].n != h->sys[b].n) return h->sys[a].n < h->sys[b].n;
+      if (fill_of(a) != fill_of(b)) return fill_of(a) < fill_of(b);
+      return seg_stages(a) > seg_stages(b);
     });
     for (int s : sys_at) {
       const SysPlan& sp = h->sys[s];

@@ -2033,41 +2033,43 @@ __global__ void k_adjoint_grad(const LevelDesc* __restrict__ descs, const ResTas
   const size_t nn = (size_t)n * n, mn = (size_t)m * n;
   auto xr = [&](long long row, int c) { return x[(size_t)row * ldx + c]; };
   auto br = [&](long long row, int c) { return xb[(size_t)row * ldxb + c]; };
+  // Every element costs two FP64 fmas per right-hand side, issued by every
+  // lane alike (a predicated-off FP64 instruction still takes its issue
+  // slot): v = fma(-a_r, b_c, fma(-a'_c, b'_r, v)). On a symmetric block's
+  // diagonal the second term's factor is zeroed by an integer select (the
+  // entry is one parameter: -bbar_r x_r); above it the stored value is 0.
+  auto sym = [&](long long r0, long long c0, int r, int c) {  // dD / dR entry (r, c)
+    double v = 0.0;
+    for (int q = 0; q < nr; ++q) {
+      const double bc = __longlong_as_double(c == r ? 0LL : __double_as_longlong(br(c0 + c, q)));
+      v = fma(-br(r0 + r, q), xr(c0 + c, q), fma(-bc, xr(r0 + r, q), v));
+    }
+    return c > r ? 0.0 : v;
+  };
   for (int j = tk.j0; j < j1; ++j) {
     const long long rj = d.offB + (long long)j * n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       const int r = e / n, c = e - r * n;
-      double v = 0.0;
-      if (c < r)
-        for (int q = 0; q < nr; ++q) v -= br(rj + r, q) * xr(rj + c, q) + br(rj + c, q) * xr(rj + r, q);
-      else if (c == r)
-        for (int q = 0; q < nr; ++q) v -= br(rj + r, q) * xr(rj + r, q);
-      dD[d.offD + (size_t)j * nn + e] = v;
+      dD[d.offD + (size_t)j * nn + e] = sym(rj, rj, r, c);
     }
     if (j < N - 1)
       for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
         const int r = e / n, c = e - r * n;
         double v = 0.0;
-        for (int q = 0; q < nr; ++q) v -= br(rj + n + r, q) * xr(rj + c, q) + xr(rj + n + r, q) * br(rj + c, q);
+        for (int q = 0; q < nr; ++q) v = fma(-br(rj + n + r, q), xr(rj + c, q), fma(-xr(rj + n + r, q), br(rj + c, q), v));
         dE[d.offE + (size_t)j * nn + e] = v;
       }
     for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
       const int r = e / n, c = e - r * n;
       double v = 0.0;
-      for (int q = 0; q < nr; ++q) v -= br(d.rowG + r, q) * xr(rj + c, q) + xr(d.rowG + r, q) * br(rj + c, q);
+      for (int q = 0; q < nr; ++q) v = fma(-br(d.rowG + r, q), xr(rj + c, q), fma(-xr(d.rowG + r, q), br(rj + c, q), v));
       dG[d.offG + (size_t)j * mn + e] = v;
     }
   }
   if (tk.part == 0)
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       const int r = e / m, c = e - r * m;
-      double v = 0.0;
-      if (c < r)
-        for (int q = 0; q < nr; ++q)
-          v -= br(d.rowG + r, q) * xr(d.rowG + c, q) + br(d.rowG + c, q) * xr(d.rowG + r, q);
-      else if (c == r)
-        for (int q = 0; q < nr; ++q) v -= br(d.rowG + r, q) * xr(d.rowG + r, q);
-      dR[d.offR + e] = v;
+      dR[d.offR + e] = sym(d.rowG, d.rowG, r, c);
     }
 }
 
