@@ -294,6 +294,23 @@ kkt_status kkt_solve_adjoint(kkt_handle* h, const double* D, const double* E, co
                              double* bbar, int ldbb, int nrhs, double* dD, double* dE, double* dG,
                              double* dR, int sweeps, void* stream);
 
+/* Fallback of kkt_solve_refined for systems whose refinement stalls:
+ * cg_iters > 0 enables it. A system whose eta, still above the rounding
+ * level, is not at least halved by a sweep is taken out of the classic sweeps
+ * and, after them, together with any system that did not converge within
+ * `sweeps`, runs cg_iters iterations of preconditioned conjugate gradients
+ * on Psi x = b (Psi is SPD) from its refined x, preconditioned by the same
+ * (mixed) factor: the conjugate-gradient form of refinement with a
+ * low-precision preconditioner (Carson and Higham, 2018), which converges
+ * where the stationary iteration stalls because its rate depends on the
+ * spread of the preconditioned spectrum rather than on its distance from 1.
+ * FP64 vectors and products, the factor's substitutions, per-system scalars
+ * on the device: no host synchronization, capturable. kkt_refine_eta of the
+ * last sweep then reports the eta after the fallback. cg_iters = 0 (the
+ * default) disables it; the first call with cg_iters > 0 allocates its
+ * vectors (3 x rows x 16 doubles; call it outside any graph capture). */
+kkt_status kkt_set_refine_fallback(kkt_handle* h, int cg_iters);
+
 /* eta of every system after sweep `sweep` (0-based) of the last
  * kkt_solve_refined (last right-hand-side chunk); eta[count]. Synchronizes.
  * Values after a system converged are those of its converging sweep. */

@@ -29,7 +29,7 @@ EXPORTED = [
     "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_factor_solve", "kkt_factor_solve_host", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta",
     "kkt_get_info",
     "kkt_get_factor", "kkt_set_pairing", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
-    "kkt_set_persistent", "kkt_set_wait_limit",
+    "kkt_set_persistent", "kkt_set_wait_limit", "kkt_set_refine_fallback",
 ]
 
 
@@ -80,6 +80,7 @@ _sig = {
     "kkt_status_string": [_i],
     "kkt_set_persistent": [_vp, _i],
     "kkt_set_wait_limit": [_vp, ctypes.c_longlong, _i],
+    "kkt_set_refine_fallback": [_vp, _i],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -324,6 +325,12 @@ def kkt_set_wait_limit(h: int, cycles: int, unmet: bool = False) -> None:
     """Clock-cycle bound of the persistent schedule's dependency waits;
     `unmet` injects an unsatisfiable dependency (tests the timeout path)."""
     _check(_lib.kkt_set_wait_limit(h, int(cycles), int(bool(unmet))), "kkt_set_wait_limit")
+
+
+def kkt_set_refine_fallback(h: int, cg_iters: int) -> None:
+    """Preconditioned conjugate-gradient fallback of kkt_solve_refined for
+    systems whose refinement stalls (cg_iters = 0 disables it)."""
+    _check(_lib.kkt_set_refine_fallback(h, int(cg_iters)), "kkt_set_refine_fallback")
 
 
 def kkt_launch_counts(h: int) -> tuple[int, int]:

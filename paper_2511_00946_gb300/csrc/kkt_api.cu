@@ -199,6 +199,13 @@ struct kkt_handle {
   int hs_nrhs = 0;                           // columns the b copy has room for
   cudaStream_t hs_copy = nullptr, hs_lvl[kHostChunks] = {};
   cudaEvent_t hs_ev_start = nullptr, hs_ev_copy[kHostChunks] = {}, hs_ev_lvl[kHostChunks] = {};
+  // refinement fallback (kkt_set_refine_fallback): preconditioned conjugate
+  // gradients for stalled systems, its vectors and per-system scalars
+  int cg_iters = 0;
+  void* cg_mem = nullptr;
+  double *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_rho0 = nullptr, *cg_rho1 = nullptr,
+         *cg_pq = nullptr, *cg_eta = nullptr;
+  int* cg_skip = nullptr;
   // persistent factorization (kkt_set_persistent): work items, their tasks,
   // consumer edges, ready counters + ticket, in one allocation
   int persistent = 0;
@@ -777,6 +784,7 @@ kkt_status kkt_destroy(kkt_handle* h) {
   if (!h) return KKT_OK;
   if (h->dmem) cudaFree(h->dmem);
   if (h->pmem) cudaFree(h->pmem);
+  if (h->cg_mem) cudaFree(h->cg_mem);
   if (h->hs_mem) cudaFree(h->hs_mem);
   if (h->hs_bmem) cudaFree(h->hs_bmem);
   if (h->hs_copy) cudaStreamDestroy(h->hs_copy);
@@ -982,6 +990,7 @@ kkt_status build_persistent(kkt_handle* h) {
   const size_t o_it = cv.take(sizeof(kkt::PItem) * n_it), o_c = cv.take(sizeof(kkt::PCons) * n_c),
                o_t = cv.take(sizeof(Task) * n_t), o_r = cv.take(sizeof(int) * (n_it + 1));
   if (h->pmem) cudaFree(h->pmem);
+  if (h->cg_mem) cudaFree(h->cg_mem);
   h->pmem = nullptr;
   if (cudaMalloc(&h->pmem, cv.off) != cudaSuccess) {
     h->pmem = nullptr;
@@ -1329,6 +1338,77 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
   return st != KKT_OK ? st : b_out();
 }
 
+namespace {
+// Preconditioned conjugate gradients for the systems whose refinement stalled
+// or did not converge (flags 0 and 3), started from the refined x and its
+// residual (in dcorr), preconditioned by the factor's solve: r = b - Psi x,
+// z = M^{-1} r, p = z, rho = r.z; then cg_iters times q = Psi p, alpha =
+// rho / p.q, x += alpha p, r -= alpha q, z = M^{-1} r, rho' = r.z, p = z +
+// (rho'/rho) p. The eta of those systems after the last iteration replaces
+// that of the last sweep.
+kkt_status refine_fallback(kkt_handle* h, const double* D, const double* E, const double* G, const double* R,
+                           const double* b, int ldb, double* x, int ldx, int nr, int sweeps, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const int CH = kkt::kRhsChunk, nres = (int)h->hres.size(), cnt = h->count;
+  const size_t vec = sizeof(double) * h->tot_B * CH;
+  auto matvec = [&](const double* v, double* out) {  // out = -Psi v (b = 0)
+    return kkt::launch_residual(h->ddesc, h->dres, nres, D, E, G, nullptr, 1, v, CH, out, nr, h->dparts,
+                                h->cg_skip, 0, stream) == 0 &&
+           kkt::launch_residual_final(h->ddesc, h->dsys_desc, h->dpart0, cnt, G, R, nullptr, 1, v, CH, out, nr,
+                                      h->dparts, -1.0, h->cg_eta, nullptr, h->cg_skip, stream) == 0;
+  };
+  auto precond = [&]() {  // z = M^{-1} r
+    return cudaMemcpyAsync(h->cg_z, h->dcorr, vec, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+           solve_chunk(h, h->cg_z, CH, nr, h->cg_skip, stream, nullptr) == KKT_OK;
+  };
+  bool ok = kkt::launch_pcg_mask(h->dconv, h->cg_skip, cnt, stream) == 0 && precond() &&
+            cudaMemcpyAsync(h->cg_p, h->cg_z, vec, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+            kkt::launch_sys_dot(h->ddesc, h->dsys_desc, h->dconv, cnt, h->dcorr, h->cg_z, nr, h->cg_rho0,
+                                stream) == 0;
+  for (int it = 0; it < h->cg_iters && ok; ++it) {
+    double* rho = (it & 1) ? h->cg_rho1 : h->cg_rho0;
+    double* rho_next = (it & 1) ? h->cg_rho0 : h->cg_rho1;
+    ok = matvec(h->cg_p, h->cg_q) &&
+         kkt::launch_sys_dot(h->ddesc, h->dsys_desc, h->dconv, cnt, h->cg_p, h->cg_q, nr, h->cg_pq, stream) == 0 &&
+         kkt::launch_pcg_update(h->ddesc, h->dres, nres, h->dconv, 0, nr, x, ldx, h->dcorr, h->cg_q, h->cg_p,
+                                nullptr, rho, h->cg_pq, stream) == 0 &&
+         precond() &&
+         kkt::launch_sys_dot(h->ddesc, h->dsys_desc, h->dconv, cnt, h->dcorr, h->cg_z, nr, rho_next, stream) == 0 &&
+         kkt::launch_pcg_update(h->ddesc, h->dres, nres, h->dconv, 1, nr, x, ldx, h->dcorr, h->cg_q, h->cg_p,
+                                h->cg_z, rho_next, rho, stream) == 0;
+  }
+  // the true residual and eta of the fallback's systems
+  ok = ok &&
+       kkt::launch_residual(h->ddesc, h->dres, nres, D, E, G, b, ldb, x, ldx, h->dcorr, nr, h->dparts, h->cg_skip, 0,
+                            stream) == 0 &&
+       kkt::launch_residual_final(h->ddesc, h->dsys_desc, h->dpart0, cnt, G, R, b, ldb, x, ldx, h->dcorr, nr,
+                                  h->dparts, -1.0, h->deta + (size_t)(sweeps - 1) * cnt, nullptr, h->cg_skip,
+                                  stream) == 0;
+  return ok ? KKT_OK : KKT_ERR_CUDA;
+}
+}  // namespace
+
+kkt_status kkt_set_refine_fallback(kkt_handle* h, int cg_iters) {
+  if (!h || cg_iters < 0 || cg_iters > 256) return KKT_ERR_ARG;
+  if (cg_iters > 0 && !h->cg_mem) {
+    const size_t vec = sizeof(double) * h->tot_B * kkt::kRhsChunk, sc = sizeof(double) * h->count * kkt::kRhsChunk;
+    Carver cv;
+    const size_t oz = cv.take(vec), op = cv.take(vec), oq = cv.take(vec), o0 = cv.take(sc), o1 = cv.take(sc),
+                 opq = cv.take(sc), oe = cv.take(sizeof(double) * h->count), os = cv.take(sizeof(int) * h->count);
+    if (cudaMalloc(&h->cg_mem, cv.off) != cudaSuccess) {
+      h->cg_mem = nullptr;
+      return KKT_ERR_CUDA;
+    }
+    char* base = (char*)h->cg_mem;
+    if (cudaMemset(h->cg_mem, 0, cv.off) != cudaSuccess) return KKT_ERR_CUDA;
+    h->cg_z = (double*)(base + oz); h->cg_p = (double*)(base + op); h->cg_q = (double*)(base + oq);
+    h->cg_rho0 = (double*)(base + o0); h->cg_rho1 = (double*)(base + o1); h->cg_pq = (double*)(base + opq);
+    h->cg_eta = (double*)(base + oe); h->cg_skip = (int*)(base + os);
+  }
+  h->cg_iters = cg_iters;
+  return KKT_OK;
+}
+
 kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, const double* G,
                              const double* R, const double* b, int ldb, double* x, int ldx, int nrhs,
                              int sweeps, double tol, void* stream) {
@@ -1360,8 +1440,12 @@ kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, co
                                      x + c0, ldx, h->dcorr, nr, h->dparts, tol,
                                      h->deta + (size_t)sw * h->count,
                                      sw > 0 ? h->deta + (size_t)(sw - 1) * h->count : nullptr, h->dconv,
-                                     stream))
+                                     stream, h->cg_iters > 0))
         return KKT_ERR_CUDA;
+    }
+    if (h->cg_iters > 0) {
+      const kkt_status s3 = refine_fallback(h, D, E, G, R, b + c0, ldb, x + c0, ldx, nr, sweeps, stream);
+      if (s3 != KKT_OK) return s3;
     }
   }
   return KKT_OK;

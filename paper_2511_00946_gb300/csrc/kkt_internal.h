@@ -273,10 +273,21 @@ int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, const doub
                     double* parts, const int* skip, int norms, void* stream);
 // g rows of c, eta per system, converged[s] = (eta <= tol); a system that had
 // converged before copies its eta from eta_prev (the previous sweep's; may be null)
+// (stall: mark systems whose refinement stalls with flag 3 for the fallback)
 int launch_residual_final(const LevelDesc* d, const int* sys_desc, const int* part0, int count,
                           const double* G, const double* R, const double* b, int ldb, const double* x,
                           int ldx, double* c, int nr, const double* parts, double tol, double* eta_out,
-                          const double* eta_prev, int* converged, void* stream);
+                          const double* eta_prev, int* converged, void* stream, int stall = 0);
+// refinement fallback (preconditioned conjugate gradients): per-system dot
+// products of vectors with leading dimension kRhsChunk (systems outside the
+// fallback skipped), the x/r (mode 0) and p (mode 1) updates with per-system
+// scalars num/den, and the skip mask of the fallback's solves and products
+int launch_sys_dot(const LevelDesc* d, const int* sys_desc, const int* conv, int count, const double* u,
+                   const double* v, int nr, double* out, void* stream);
+int launch_pcg_update(const LevelDesc* d, const ResTask* t, int ntasks, const int* conv, int mode, int nr,
+                      double* x, int ldx, double* r, const double* qn, double* p, const double* z,
+                      const double* num, const double* den, void* stream);
+int launch_pcg_mask(const int* conv, int* skip, int count, void* stream);
 // adjoint block gradients (symmetric-entry convention) per residual task
 int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const double* x, int ldx,
                         const double* xb, int ldxb, int nr, double* dD, double* dE, double* dG,

@@ -1904,13 +1904,13 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
         }
       }
       if (ok0) {
-        const double bv = b[(size_t)(rb + i0) * ldb + col], r = bv - acc0;
+        const double bv = b ? b[(size_t)(rb + i0) * ldb + col] : 0.0, r = bv - acc0;
         c[(size_t)(rb + i0) * kRhsChunk + col] = r;
         mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xc0));
         if (norms) mrow = fmaxf(mrow, rs0);
       }
       if (ok1) {
-        const double bv = b[(size_t)(rb + i1) * ldb + col], r = bv - acc1;
+        const double bv = b ? b[(size_t)(rb + i1) * ldb + col] : 0.0, r = bv - acc1;
         c[(size_t)(rb + i1) * kRhsChunk + col] = r;
         mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xc1));
         if (norms) mrow = fmaxf(mrow, rs1);
@@ -1946,19 +1946,21 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
 }
 
 // Finish the g rows of one system from the chunk partials, then eta and the
-// stop flag: 1 when eta <= tol, 2 when eta is at the rounding level of the
+// stop flag (`stall`: the fallback is enabled, flag 3 below): 1 when eta <= tol, 2 when eta is at the rounding level of the
 // FP64 residual (kEtaFloor) and the sweep cut the previous sweep's eta by
 // less than 10 % (refinement has reached its floor; above that level a slow
 // sweep is not taken as the end, since the normwise eta of an
-// ill-conditioned system need not fall monotonically); a stopped system
-// skips the remaining sweeps.
+// ill-conditioned system need not fall monotonically); 3 (only with `stall`)
+// when eta is above that level and the sweep did not halve it (refinement
+// stalls: the system is handed to the preconditioned conjugate-gradient
+// fallback); a stopped system skips the remaining sweeps.
 constexpr double kEtaFloor = 4.0 * 1.1102230246251565e-16;  // 4 u
 __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int* __restrict__ sys_desc,
                                  const int* __restrict__ part0, const double* __restrict__ uG,
                                  const double* __restrict__ uR, const double* __restrict__ b, int ldb,
                                  const double* __restrict__ x, int ldx, double* c, int nr,
                                  const double* __restrict__ parts, double tol, double* eta_out,
-                                 const double* __restrict__ eta_prev, int* converged) {
+                                 const double* __restrict__ eta_prev, int* converged, int stall) {
   __shared__ double red[4][256];
   __shared__ double gsum[kMaxM];
   const int s = blockIdx.x;
@@ -1989,7 +1991,7 @@ __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int*
     for (int k = 0; k < m; ++k)
       acc = fma(k <= q ? R[q * m + k] : R[k * m + q], x[(size_t)(d.rowG + k) * ldx + col], acc);
     const size_t row = (size_t)(d.rowG + q);
-    const double bv = b[row * ldb + col];
+    const double bv = b ? b[row * ldb + col] : 0.0;
     const double r = bv - acc;
     c[row * kRhsChunk + col] = r;
     mr = fmax(mr, fabs(r));
@@ -2012,6 +2014,7 @@ __global__ void k_residual_final(const LevelDesc* __restrict__ descs, const int*
     if (converged) {
       if (eta <= tol) converged[s] = 1;
       else if (tol >= 0.0 && eta_prev && eta <= kEtaFloor && eta > 0.9 * eta_prev[s]) converged[s] = 2;
+      else if (stall && eta_prev && eta > kEtaFloor && eta > 0.5 * eta_prev[s]) converged[s] = 3;
     }
   }
 }
@@ -2071,6 +2074,83 @@ __global__ void k_adjoint_grad(const LevelDesc* __restrict__ descs, const ResTas
       const int r = e / m, c = e - r * m;
       dR[d.offR + e] = sym(d.rowG, d.rowG, r, c);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Fallback of iterative refinement: preconditioned conjugate gradients on
+// Psi x = b (Psi is SPD), preconditioned by the mixed factor, for the systems
+// whose refinement stalled (flag 3) or ran out of sweeps (flag 0), as
+// proposed for GMRES/CG-based refinement with a low-precision factor
+// (Carson and Higham, SIAM J. Sci. Comput. 40, 2018). Vectors are FP64 with
+// leading dimension kRhsChunk; per system and right-hand side the scalars rho
+// and p^T q live in small device arrays, so the iteration needs no host
+// synchronization.
+// ---------------------------------------------------------------------------
+
+// out[s][q] = sum over the system's rows of u[row][q] v[row][q] (rows offB ..
+// offB + N n + m, contiguous), for the systems whose mask entry is set; a
+// fixed-order tree over the CTA
+__global__ void k_sys_dot(const LevelDesc* __restrict__ descs, const int* __restrict__ sys_desc,
+                          const int* __restrict__ conv, const double* __restrict__ u, const double* __restrict__ v,
+                          int nr, double* out) {
+  __shared__ double red[256];
+  const int s = blockIdx.x;
+  if (conv[s] == 1 || conv[s] == 2) return;  // converged: not in the fallback
+  const LevelDesc& d = descs[sys_desc[s]];
+  const long long r0 = d.offB, rows = (long long)d.N * d.n + d.m;
+  for (int q = 0; q < nr; ++q) {
+    double a = 0.0;
+    for (long long r = threadIdx.x; r < rows; r += blockDim.x)
+      a = fma(u[(size_t)(r0 + r) * kRhsChunk + q], v[(size_t)(r0 + r) * kRhsChunk + q], a);
+    red[threadIdx.x] = a;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[(size_t)s * kRhsChunk + q] = red[0];
+    __syncthreads();
+  }
+}
+
+// mode 0: alpha = rho / (p^T Psi p) with Qn = -Psi p and pq = p^T Qn:
+//         x += alpha p, r += alpha Qn (i.e. r -= alpha Psi p)
+// mode 1: beta = rho_new / rho_old: p = z + beta p
+// over the stage rows of each residual task (the g rows with the system's
+// first task); systems outside the fallback are skipped
+__global__ void k_pcg_update(const LevelDesc* __restrict__ descs, const ResTask* __restrict__ tasks,
+                             const int* __restrict__ conv, int mode, int nr, double* x, int ldx, double* rr,
+                             const double* __restrict__ qn, double* p, const double* __restrict__ z,
+                             const double* __restrict__ num, const double* __restrict__ den) {
+  const ResTask tk = tasks[blockIdx.x];
+  const LevelDesc& d = descs[tk.desc];
+  const int cs = conv[d.sys];
+  if (cs == 1 || cs == 2) return;
+  const int j1 = min(tk.j0 + kResChunk, d.N);
+  const long long row0 = d.offB + (long long)tk.j0 * d.n;
+  const int rows = (j1 - tk.j0) * d.n + (tk.part == 0 ? 0 : 0);
+  auto one = [&](long long row, int col) {
+    const size_t sc = (size_t)d.sys * kRhsChunk + col, i = (size_t)row * kRhsChunk + col;
+    const double dn = den[sc];
+    if (mode == 0) {
+      const double alpha = dn != 0.0 ? -num[sc] / dn : 0.0;
+      x[(size_t)row * ldx + col] = fma(alpha, p[i], x[(size_t)row * ldx + col]);
+      rr[i] = fma(alpha, qn[i], rr[i]);
+    } else {
+      const double beta = dn != 0.0 ? num[sc] / dn : 0.0;
+      p[i] = fma(beta, p[i], z[i]);
+    }
+  };
+  for (int e = threadIdx.x; e < rows * nr; e += blockDim.x) one(row0 + e / nr, e % nr);
+  if (tk.part == 0)
+    for (int e = threadIdx.x; e < d.m * nr; e += blockDim.x) one(d.rowG + e / nr, e % nr);
+}
+
+// fallback mask for the solves and the matrix products: skip[s] = 1 unless
+// the system's refinement stalled or did not converge
+__global__ void k_pcg_mask(const int* __restrict__ conv, int* skip, int count) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < count) skip[s] = (conv[s] == 1 || conv[s] == 2) ? 1 : 0;
 }
 
 // Identity pivot blocks and corner for every system of a batch (synthetic
@@ -2341,6 +2421,27 @@ int launch_border(const LevelDesc* db, const int* sys_desc, int count, long long
   return (int)cudaGetLastError();
 }
 
+int launch_sys_dot(const LevelDesc* d, const int* sys_desc, const int* conv, int count, const double* u,
+                   const double* v, int nr, double* out, void* stream) {
+  if (count <= 0) return 0;
+  k_sys_dot<<<count, 256, 0, (cudaStream_t)stream>>>(d, sys_desc, conv, u, v, nr, out);
+  return (int)cudaGetLastError();
+}
+
+int launch_pcg_update(const LevelDesc* d, const ResTask* t, int ntasks, const int* conv, int mode, int nr,
+                      double* x, int ldx, double* r, const double* qn, double* p, const double* z,
+                      const double* num, const double* den, void* stream) {
+  if (ntasks <= 0) return 0;
+  k_pcg_update<<<ntasks, 256, 0, (cudaStream_t)stream>>>(d, t, conv, mode, nr, x, ldx, r, qn, p, z, num, den);
+  return (int)cudaGetLastError();
+}
+
+int launch_pcg_mask(const int* conv, int* skip, int count, void* stream) {
+  if (count <= 0) return 0;
+  k_pcg_mask<<<(count + 255) / 256, 256, 0, (cudaStream_t)stream>>>(conv, skip, count);
+  return (int)cudaGetLastError();
+}
+
 int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const double* x, int ldx,
                         const double* xb, int ldxb, int nr, double* dD, double* dE, double* dG,
                         double* dR, void* stream) {
@@ -2361,10 +2462,10 @@ int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, const doub
 int launch_residual_final(const LevelDesc* d, const int* sys_desc, const int* part0, int count,
                           const double* G, const double* R, const double* b, int ldb, const double* x,
                           int ldx, double* c, int nr, const double* parts, double tol, double* eta_out,
-                          const double* eta_prev, int* converged, void* stream) {
+                          const double* eta_prev, int* converged, void* stream, int stall) {
   if (count <= 0) return 0;
   k_residual_final<<<count, 256, 0, (cudaStream_t)stream>>>(d, sys_desc, part0, G, R, b, ldb, x, ldx, c,
-                                                            nr, parts, tol, eta_out, eta_prev, converged);
+                                                            nr, parts, tol, eta_out, eta_prev, converged, stall);
   return (int)cudaGetLastError();
 }
 

@@ -220,3 +220,41 @@ def test_tensor_core_schur_products(kkt, orc, N, n, m, levels, precision):
     r = b - orc.block_matvec(D, E, G, R, x)
     ro = b - orc.block_matvec(D, E, G, R, xo)
     assert np.linalg.norm(r) <= max(1e-10 * np.linalg.norm(b), 10 * np.linalg.norm(ro)), etas
+
+
+@pytest.mark.parametrize("kind,N,n,m,sigma", [("race", 2048, 6, 2, 10.0), ("ipm", 200, 48, 4, 11.0),
+                                              ("ipm", 200, 32, 8, 12.0)])
+def test_refinement_stall_falls_back_to_pcg(kkt, orc, kind, N, n, m, sigma):
+    """Barrier scaling beyond the workloads' (Sigma over 20-24 decades): the
+    stationary refinement with the FP32 factor stalls well above the FP64
+    level (its residual stays far more than 10x the oracle's); with the
+    fallback enabled the stalled systems continue with conjugate gradients
+    preconditioned by the same factor and reach the FP64 gates."""
+    import torch
+    gen_fn = gen.raceline if kind == "race" else gen.ipm
+    D, E, G, R = gen_fn(N, n, m, seed=5, sigma_decades=sigma)
+    b = gen.rhs(N * n + m, 1, seed=6)
+    xo = orc.seq_solve(orc.seq_factor(D, E, G, R), b)
+    ro = np.linalg.norm(b - orc.block_matvec(D, E, G, R, xo))
+    ratios = {}
+    for cg in (0, 12):
+        h = kkt.kkt_create_plan(N, n, m, [1], kkt.KKT_PARTITION_BALANCED, kkt.KKT_MIXED_FP32_ALL)
+        try:
+            if cg:
+                kkt.kkt_set_refine_fallback(h, cg)
+            Dd, Ed, Gd, Rd = dev(D), dev(E), dev(G), dev(R)
+            kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+            x = torch.zeros(N * n + m, dtype=torch.float64, device="cuda")
+            kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, dev(b), x, sweeps=10, tol=1e-16)
+            torch.cuda.synchronize()
+            assert kkt.kkt_get_info(h)["status"] == 0
+            eta_dev = float(kkt.kkt_refine_eta(h, 9)[0])
+            x = x.cpu().numpy()
+        finally:
+            kkt.kkt_destroy(h)
+        ratios[cg] = np.linalg.norm(b - orc.block_matvec(D, E, G, R, x)) / ro
+        if cg:
+            assert orc.block_backward_error(D, E, G, R, x, b) <= 1e-14
+            assert eta_dev <= 1e-14
+    assert ratios[0] > 10.0, ratios      # the classic sweeps stall
+    assert ratios[12] <= 10.0, ratios    # the fallback reaches the FP64 path's residual
