@@ -751,6 +751,59 @@ def run_batch(args):
     finish_ranks()
 
 
+# Small cases of the batched kernels for ncu captures (inputs larger than L2,
+# about 1 GB on the device): two runs of the path, nothing timed.
+PROFILE_CASES = {
+    "mixed48": "304 ipm-shaped systems N=60, n=48, m=4 (Sigma +-6 decades, PSD couplings), FP32 mixed, "
+               "sequential plan: factor + 2 refinement sweeps",
+    "fp64_48": "the same systems, FP64: factor + solve",
+    "adjoint128": "128 ipm-shaped systems N=256, n=32, m=8 (Sigma +-8 decades), FP64: factor + solve + adjoint",
+    "uneven512": "512 systems of the uneven workload's shapes, FP64, persistent factorization + solve",
+}
+
+
+def run_profile_case(name):
+    import torch
+    import paper_2511_00946_gb300 as kkt
+    import gen.device as gdev
+    torch.cuda.set_device(0)
+    if name in ("mixed48", "fp64_48"):
+        c = 304
+        Ns, ns, ms = [60] * c, [48] * c, [4] * c
+        D, E, G, R = gdev.batch(Ns, ns, ms, seed=1, kind="ipm", sigma_decades=6.0, psd_couplings=True)
+    elif name == "adjoint128":
+        c = 128
+        Ns, ns, ms = [256] * c, [32] * c, [8] * c
+        D, E, G, R = gdev.batch(Ns, ns, ms, seed=1, kind="ipm", sigma_decades=8.0)
+    elif name == "uneven512":
+        Ns, ns, ms = (v[:512] for v in batch_shapes("uneven4096"))
+        c = len(Ns)
+        D, E, G, R = gdev.batch(Ns, ns, ms, seed=1, kind="ipm", sigma_decades=6.0, psd_couplings=True)
+    else:
+        raise ValueError(name)
+    b = gdev.rhs(int(sum(N * n + m for N, n, m in zip(Ns, ns, ms))), 1, seed=2)
+    prec = kkt.KKT_MIXED_FP32_ALL if name == "mixed48" else kkt.KKT_FP64
+    h = kkt.kkt_batch_create(Ns, ns, ms, [1] * c, prec)
+    if name == "uneven512":
+        kkt.kkt_set_persistent(h, True)
+    x = torch.zeros_like(b)
+    gD, gE, gG, gR = (torch.empty_like(t) for t in (D, E, G, R))
+    bb = torch.empty_like(b)
+    for _ in range(2):
+        kkt.kkt_factor(h, D, E, G, R)
+        if name == "mixed48":
+            kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=2, tol=0.0)
+        else:
+            x.copy_(b)
+            kkt.kkt_solve(h, x)
+            if name == "adjoint128":
+                kkt.kkt_solve_adjoint(h, x, x, bb, gD, gE, gG, gR, D=D, E=E, G=G, R=R, sweeps=1)
+    torch.cuda.synchronize()
+    info = kkt.kkt_get_info(h)
+    kkt.kkt_destroy(h)
+    print(json.dumps({"profile_case": name, "desc": PROFILE_CASES[name], "info": info}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -777,7 +830,12 @@ def main():
                     help="refinement stop of the mixed path: a system stops once its eta is below this (or "
                          "once it is at the rounding floor); 1e-16 gives residuals within a few times the "
                          "FP64 path's")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one small case of the batched kernels twice, untimed (for ncu captures)")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

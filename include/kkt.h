@@ -60,7 +60,10 @@ typedef enum {
   KKT_ERR_TIMEOUT = 5,    /* a bounded wait inside a kernel ran out (reported by
                              kkt_get_info; the results of that call are invalid) */
   KKT_ERR_STATE = 6,      /* call out of order (solve before factor)           */
-  KKT_ERR_CAPACITY = 7    /* problem larger than a fixed-size buffer allows     */
+  KKT_ERR_CAPACITY = 7,   /* problem larger than a fixed-size buffer allows     */
+  KKT_ERR_BOUNDS = 8      /* an index check of the debug build (KKT_DEBUG) failed:
+                             a task's geometry or shared-memory layout did not fit;
+                             the task was skipped, nothing trapped              */
 } kkt_status;
 
 /* Arithmetic of the factorization.
@@ -115,7 +118,7 @@ typedef struct kkt_handle kkt_handle;
 
 /* First breakdown recorded by the device since the last kkt_factor. */
 typedef struct {
-  int status;  /* KKT_OK, KKT_ERR_NOT_SPD or KKT_ERR_TIMEOUT                    */
+  int status;  /* KKT_OK, KKT_ERR_NOT_SPD, KKT_ERR_TIMEOUT or KKT_ERR_BOUNDS     */
   int system;  /* system index in the batch                                     */
   int stage;   /* natural stage of the failing pivot block; N for the corner R */
   int level;   /* 1 = stage blocks of Psi, 2.. = reduced (separator) systems    */

@@ -15,10 +15,13 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libkkt.so")
+# KKT_DEBUG=1 in the environment loads the debug build (index checks on every
+# task, reported as KKT_ERR_BOUNDS; build.py --debug builds it)
+DEBUG = os.environ.get("KKT_DEBUG", "0") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "_build_debug" if DEBUG else "_build", "libkkt.so")
 
 (KKT_OK, KKT_ERR_ARG, KKT_ERR_PARTITION, KKT_ERR_NOT_SPD, KKT_ERR_CUDA, KKT_ERR_TIMEOUT, KKT_ERR_STATE,
- KKT_ERR_CAPACITY) = range(8)
+ KKT_ERR_CAPACITY, KKT_ERR_BOUNDS) = range(9)
 KKT_FP64, KKT_MIXED_FP32, KKT_MIXED_FP32_ALL, KKT_MIXED_TF32, KKT_MIXED_BF16 = 0, 1, 2, 3, 4
 KKT_PARTITION_PAPER, KKT_PARTITION_BALANCED = 0, 1
 KKT_PAIR_AUTO, KKT_PAIR_OFF, KKT_PAIR_ON = 0, 1, 2

@@ -1493,7 +1493,11 @@ kkt_status kkt_get_info(kkt_handle* h, kkt_info* info, int clear) {
   if (!h || !info) return KKT_ERR_ARG;
   kkt::Info hi{};
   if (cudaMemcpy(&hi, h->dinfo, sizeof(hi), cudaMemcpyDeviceToHost) != cudaSuccess) return KKT_ERR_CUDA;
-  info->status = hi.status == 3 ? KKT_ERR_NOT_SPD : hi.status == 5 ? KKT_ERR_TIMEOUT : KKT_OK;
+  kkt::Info dbg{};
+  if (kkt::debug_info(&dbg, clear)) return KKT_ERR_CUDA;
+  if (hi.status == 0 && dbg.status == 8) hi = dbg;  // an index check of the debug build failed
+  info->status = hi.status == 3 ? KKT_ERR_NOT_SPD : hi.status == 5 ? KKT_ERR_TIMEOUT
+                 : hi.status == 8 ? KKT_ERR_BOUNDS : KKT_OK;
   info->system = hi.system;
   info->stage = hi.stage;
   info->level = hi.level;
@@ -1632,6 +1636,7 @@ const char* kkt_status_string(int s) {
     case KKT_ERR_TIMEOUT: return "device wait timed out";
     case KKT_ERR_STATE: return "call out of order";
     case KKT_ERR_CAPACITY: return "problem exceeds the fixed buffer capacity";
+    case KKT_ERR_BOUNDS: return "index check failed (debug build)";
     default: return "unknown status";
   }
 }

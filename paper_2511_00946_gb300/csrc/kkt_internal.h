@@ -305,6 +305,9 @@ int launch_factor_persist(const LevelDesc* d, const Task* t, const PItem* items,
                           int* ready, int mixed, const double* D, const double* E, const double* G,
                           const double* R, Info* info, int grid, size_t smem, int slice, int dbl,
                           long long wait_cycles, void* stream);
+// the debug build's index-check record (status 8 on a failed check; zero in
+// the normal build); `clear` resets it
+int debug_info(Info* out, int clear);
 // occupancy (CTAs per SM) of the persistent kernel with `smem` bytes
 int persist_occupancy(int mixed, size_t smem);
 size_t factor_smem_bytes(int maxn, int maxm, int mixed, int fill = 1, int dbl = 1);

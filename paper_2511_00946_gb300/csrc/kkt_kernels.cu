@@ -61,6 +61,46 @@ __device__ void record_timeout(Info* info, int sys, int stage, int level) {
   record_status(info, 5 /* KKT_ERR_TIMEOUT */, sys, stage, level);
 }
 
+// Debug build (compiled with -DKKT_DEBUG): index checks on entry to every
+// segment task and residual task. A task whose geometry does not fit its
+// system (segment index, stage range, separator, block sizes) or whose
+// shared-memory layout does not fit the launch's dynamic shared memory is
+// skipped, and the first such failure is recorded (status 8,
+// KKT_ERR_BOUNDS) in a device record that kkt_get_info reports. Nothing
+// traps. In the normal build the checks compile to nothing.
+#ifdef KKT_DEBUG
+__device__ Info g_debug_info;
+#endif
+extern __shared__ __align__(16) unsigned char kkt_dyn_smem[];
+__device__ __forceinline__ bool dbg_ok(bool cond, const LevelDesc& d) {
+#ifdef KKT_DEBUG
+  if (!cond) record_status(&g_debug_info, 8, d.sys, -1, d.level);
+  return cond;
+#else
+  (void)d;
+  return cond || true;
+#endif
+}
+__device__ __forceinline__ bool task_geometry_ok(const LevelDesc& d, int seg, const void* sm, int bytes) {
+#ifdef KKT_DEBUG
+  unsigned dyn;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  const long long off = (long long)__cvta_generic_to_shared(sm) - (long long)__cvta_generic_to_shared(kkt_dyn_smem);
+  bool ok = d.n >= 1 && d.n <= kMaxN && d.m >= 0 && d.m <= kMaxM && d.N >= 1 && d.P >= 1 && seg >= 0 &&
+            seg < d.P && d.mr >= 0 && d.mr <= d.m;
+  if (ok) {
+    const int f = d.seg[seg], e = d.seg[seg + 1] - 2;  // first and last stage of the segment
+    ok = f >= (seg ? 1 : 0) && e >= f && e < d.N && d.seg[d.P] == d.N + 1;
+    if (ok) ok = d.nat[f] >= 0 && d.nat[e] < d.Nnat && (seg == 0 || d.nat[f - 1] >= 0);
+  }
+  ok = ok && off >= 0 && off + bytes <= (long long)dyn;
+  return dbg_ok(ok, d);
+#else
+  (void)d; (void)seg; (void)sm; (void)bytes;
+  return true;
+#endif
+}
+
 // A group of threads working on one role of a CTA: thread index within the
 // group, group size and the named barrier that synchronizes it (0 = the whole
 // CTA, __syncthreads; -1 = a single warp, __syncwarp).
@@ -831,6 +871,7 @@ __device__ __forceinline__ void factor_task(const Task tk, const LevelDesc* __re
   const LevelDesc& d = descs[tk.desc];
   constexpr bool mixed = sizeof(TZ) == 4;
   const FacLayout lay = fac_layout(d.n, d.m, (int)sizeof(TZ), d.P > 1, dbl != 0);
+  if (!task_geometry_ok(d, tk.seg, smraw, lay.total)) return;  // debug build only (both CTAs of a pair alike)
   const FacCtx<TZ, 4> cx(d, tk.seg, smraw, lay, uD, uE, uG);
   const int n = cx.n, m = cx.m, R = cx.R, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG, oW = cx.oW;
   double* const Dfac = cx.Dfac;
@@ -1149,6 +1190,7 @@ __device__ __forceinline__ void factor_task_w(const Task tk, const LevelDesc* __
                                               Info* info, unsigned char* sm, int lane, double* yb, int ldyb) {
   const LevelDesc& d = descs[tk.desc];
   const FacLayout lay = fac_layout_w(d.n, d.m, (int)sizeof(TZ), d.P > 1);
+  if (!task_geometry_ok(d, tk.seg, sm, lay.total)) return;  // debug build only
   const FacCtx<TZ, 1> cx(d, tk.seg, sm, lay, uD, uE, uG);
   const int n = cx.n, m = cx.m, R = cx.R, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG;
   const SegGeom g = cx.g;
@@ -1576,6 +1618,7 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
   if (fwd_done && !d.is_top) return;  // the factorization carried this forward sweep
+  if (!task_geometry_ok(d, tk.seg, smraw, sol_layout(d.n, d.m, (int)sizeof(TS), d.P > 1).total)) return;
   const int n = d.n, m = d.m, mg = d.m - d.mr;  // mg: rows of the real arrow
   const SolveSmem<TS> S = solve_smem<TS>(smraw, n, m, d.P > 1);
   const int oG = n, oW = n + m;
@@ -1707,6 +1750,7 @@ __device__ void backward_task(const Task tk, const LevelDesc* __restrict__ descs
                               const int* skip, unsigned char* smraw, Grp G, int c0 = 0) {
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
+  if (!task_geometry_ok(d, tk.seg, smraw, sol_layout(d.n, d.m, (int)sizeof(TS), d.P > 1).total)) return;
   const int n = d.n, m = d.m;
   const SolveSmem<TS> S = solve_smem<TS>(smraw, n, m, d.P > 1);
   const int oG = n, oW = n + m;
@@ -1827,6 +1871,7 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
   const ResTask tk = tasks[t];
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
+  if (!dbg_ok(tk.j0 >= 0 && tk.j0 < d.N && d.n <= kMaxN && d.m <= kMaxM && tk.part < tk.nparts, d)) return;
   const int n = d.n, m = d.m, N = d.N;
   const int j0 = tk.j0, j1 = min(tk.j0 + kResChunk, N);
   const size_t nn = (size_t)n * n, mn = (size_t)m * n;
@@ -2219,6 +2264,20 @@ int set_smem(const void* fn, size_t bytes) {
 
 size_t factor_smem_bytes(int n, int m, int mixed, int fill, int dbl) {
   return (size_t)fac_layout(n, m, mixed ? 4 : 8, fill != 0, dbl != 0).total;
+}
+
+int debug_info(Info* out, int clear) {
+#ifdef KKT_DEBUG
+  if (cudaMemcpyFromSymbol(out, g_debug_info, sizeof(Info)) != cudaSuccess) return 1;
+  if (clear) {
+    const Info zero{};
+    if (cudaMemcpyToSymbol(g_debug_info, &zero, sizeof(Info)) != cudaSuccess) return 1;
+  }
+#else
+  *out = Info{};
+  (void)clear;
+#endif
+  return 0;
 }
 
 size_t factor_w_slice_bytes(int n, int m, int mixed, int fill) {
