@@ -301,35 +301,42 @@ __device__ void potrf_sm(double* A, int ld, int n, double* rinv, const int* tab,
 constexpr int kFusedThreads = 224;
 constexpr int kFusedWorkers = 192;  // warps 1-3 and 5-7
 
+// all7: warp 4 works too (seven worker warps, a barrier over the whole CTA).
+// A warp's FP64 instructions issue on sub-partition (warp % 4): with warps
+// 1-3 and 5-7 the workers' FP64 work (trailing updates, panel solve) runs on
+// three of the four FP64 pipes while the pivot chain leaves sub-partition 0's
+// nearly idle; with warp 4 on board all four take a share.
 template <typename TZ>
 __device__ void potrf_trsm_sm(double* A, int ld, int n, double* rinv, TZ* M, const int* tab, int* bad,
-                              TZ* Z, int ldz, int r0, int r1) {
+                              TZ* Z, int ldz, int r0, int r1, bool all7 = false) {
   const int tid = threadIdx.x, lane = tid & 31;
-  if (tid >= kPotrfThreads && tid < kPotrfThreads + 32) return;  // warp 4
-  const int w = tid < kPotrfThreads ? tid - 32 : tid - 64;       // worker index
+  if (!all7 && tid >= kPotrfThreads && tid < kPotrfThreads + 32) return;  // warp 4
+  const int w = all7 ? tid - 32 : (tid < kPotrfThreads ? tid - 32 : tid - 64);  // worker index
+  const int nwk = all7 ? kFactorThreads - 32 : kFusedWorkers;
+  const int nbar = all7 ? kFactorThreads : kFusedThreads;
   const int rows = r1 - r0;
   // panel mapping: `per` workers on a row, each on every per-th column
-  const int per = rows > 0 ? max(1, kFusedWorkers / rows) : 0;
+  const int per = rows > 0 ? max(1, nwk / rows) : 0;
   const bool pact = tid >= 32 && w < rows * per;
   const int pr = pact ? w % rows : 0, pc = pact ? w / rows : 0;
   TZ* zr = Z + (r0 + pr) * ldz;
   if (tid < 32) potrf_col0(A, ld, n, rinv, bad, lane);
-  group_bar(1, kFusedThreads);
+  group_bar(1, nbar);
   for (int j = 0; j < n; ++j) {
     if (tid < 32) {
       if (j + 1 < n) potrf_lookahead(A, ld, n, rinv, bad, j, lane);
     } else {
-      potrf_trailing(A, ld, n, tab, j, w, kFusedWorkers);
-      for (int c = j + 1 + w; c < n; c += kFusedWorkers) M[c * ld + j] = (TZ)(A[c * ld + j] * rinv[j]);
+      potrf_trailing(A, ld, n, tab, j, w, nwk);
+      for (int c = j + 1 + w; c < n; c += nwk) M[c * ld + j] = (TZ)(A[c * ld + j] * rinv[j]);
       if (pact && j >= 1) {
         const TZ zj = zr[j - 1];
         for (int c = j + pc; c < n; c += per) zr[c] = fma(-zj, M[c * ld + j - 1], zr[c]);
       }
     }
-    group_bar(1, kFusedThreads);
+    group_bar(1, nbar);
   }
   if (tid >= 32)
-    for (int e = w; e < rows * n; e += kFusedWorkers) {
+    for (int e = w; e < rows * n; e += nwk) {
       const int r = e / n, c = e - r * n;
       Z[(r0 + r) * ldz + c] *= (TZ)rinv[c];
     }
@@ -1004,8 +1011,10 @@ __device__ __forceinline__ void factor_task(const Task tk, const LevelDesc* __re
       const int cur = i & 1;
       const bool eRows = (i < g.len - 1) || g.hasF;
       const int r0 = eRows ? 0 : n;
-      if (w4) {
-        if (i > 0 && dbl) store_pivot(j - 1, Dbuf(cur ^ 1), rvbuf(cur ^ 1), nullptr, W4);
+      if (!dbl) {
+        potrf_trsm_sm(Dbuf(cur), ldD, n, rvbuf(cur), M, tab, &bad, Z, ldZ, r0, pr1, true);
+      } else if (w4) {
+        if (i > 0) store_pivot(j - 1, Dbuf(cur ^ 1), rvbuf(cur ^ 1), nullptr, W4);
       } else {
         potrf_trsm_sm(Dbuf(cur), ldD, n, rvbuf(cur), M, tab, &bad, Z, ldZ, r0, pr1);
       }
@@ -2353,17 +2362,21 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
   if (ntasks <= 0) return 0;
   top_solve = top_solve && b && !mixed;
   const int tcm = tc_mode_for(tc, mixed, pair, maxn, maxm, fill);
-  size_t sm = factor_smem_bytes(maxn, maxm, mixed, fill, tcm ? 0 : 1);
+  // Mixed launches go without the second pivot buffer: warp 4 then joins the
+  // pivot sweep's workers, whose FP32 panel work keeps all four sub-partitions
+  // busy, and the pivot blocks are written right after the sweep (the uneven
+  // batch's mixed factorization 2-8 % faster). FP64 unpaired launches drop it
+  // only when that lets more CTAs share an SM (below); CTA pairs keep it.
+  int dbl = (mixed || tcm) ? 0 : 1;
+  size_t sm = factor_smem_bytes(maxn, maxm, mixed, fill, dbl);
   if (top_solve) sm = std::max(sm, solve_smem_bytes(maxn, maxm, 0, fill));
   const void* fn = mixed ? (pair ? (const void*)k_factor<float, 1>
                                  : tcm ? (const void*)k_factor<float, 4, true> : (const void*)k_factor<float, 4>)
                           : (pair ? (const void*)k_factor<double, 1> : (const void*)k_factor<double, 4>);
   int e = set_smem(fn, sm);
   if (e) return e;
-  // unpaired launches drop the second pivot buffer when that lets more CTAs
-  // share an SM (the occupancy of this kernel with either request)
-  int dbl = tcm ? 0 : 1;
-  if (!pair && !top_solve && !tcm) {
+  if (dbl && !pair && !top_solve) {
+    // the occupancy of this kernel with either request
     const size_t sm1 = factor_smem_bytes(maxn, maxm, mixed, fill, 0);
     int occ = 0, occ1 = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kFactorThreads, sm) == cudaSuccess &&
