@@ -907,7 +907,9 @@ kkt_status build_persistent(kkt_handle* h) {
   const int wpc = any_w ? std::max(1, std::min(8, (200 * 1024) / slice)) : 8;
   int dbl = 1, best_occ = -1;
   size_t smem = 0;
-  for (int db = 1; db >= 0; --db) {
+  // mixed levels without the second pivot buffer (warp 4 joins the sweep's
+  // workers), FP64 with it unless dropping it lets more CTAs share an SM
+  for (int db = mixed ? 0 : 1; db >= 0; --db) {
     const size_t sc = any_cta ? kkt::factor_smem_bytes(cn, cm, mixed, cfill, db) : 0;
     const size_t sm = std::max(sc, (size_t)wpc * slice);
     const int occ = kkt::persist_occupancy(mixed, sm);
