@@ -11,6 +11,13 @@ forward substitution); L2 is flushed (a 256 MiB write) before every timed
 step. The level plan (segments per level of the recursive partition) is
 picked on the device among a few candidates before the warm-up.
 
+In the same run the line's `batched` object measures the comparison the
+metric names on the uneven 4096-system batch: the plain FP64 path against the
+FP32-mixed path refined to the FP64 path's accuracy (eta <= 1e-16 or the
+rounding floor; residuals of 64 sampled systems checked on the host against
+the FP64 path's), each with per-level launches and with the persistent
+schedule, plus the dominant batched launch's roofline.
+
 `--impl reference` times the FP64 CPU oracle (the sequential block method)
 on the host cores instead, on a bounded sample of the same workload.
 
@@ -481,7 +488,7 @@ def _factor_launch_groups(Ns, ns, ms):
     return [(n, groups[n]) for n in sorted(groups)]
 
 
-def measure_batch(name, args, world, rank, local, host_check=64):
+def measure_batch(name, args, world, rank, local, host_check=64, paths=None):
     """Time one batched workload, FP64 and (where listed) mixed, each step a
     CUDA graph of factor + solve (FP64) or factor + refinement (mixed).
     Returns (results per path, shapes). Besides the step time: the device's
@@ -512,7 +519,7 @@ def measure_batch(name, args, world, rank, local, host_check=64):
                             R[off["R"][s]:off["R"][s + 1]].cpu().numpy().reshape(m, m),
                             b0[off["b"][s]:off["b"][s + 1]].cpu().numpy()))
     results = {}
-    for path in (args.paths.split(",") if args.paths else spec["paths"]):
+    for path in (paths or (args.paths.split(",") if args.paths else spec["paths"])):
         persist = path.endswith("_persist")
         base = path[:-len("_persist")] if persist else path
         prec = {"mixed": kkt.KKT_MIXED_FP32_ALL, "mixed_tf32": kkt.KKT_MIXED_TF32,
@@ -1058,7 +1065,11 @@ def main():
     # plain FP64 path at equal accuracy), measured in the same run
     batched = None
     if not args.no_batched:
-        bres, (bN, bn, bm) = measure_batch("uneven4096", args, world, rank, local)
+        # FP64 and FP32 mixed, each with per-level launches and with the
+        # persistent schedule (the tensor-core variants are in the
+        # --workload uneven4096 line)
+        bres, (bN, bn, bm) = measure_batch("uneven4096", args, world, rank, local,
+                                           paths=("fp64", "fp64_persist", "mixed", "mixed_persist"))
         batched = {"workload": BATCHES["uneven4096"]["desc"], "systems": len(bN) * world,
                    "paths": bres, "comparison": compare_paths(bres),
                    "roofline": next((r["roofline"] for r in bres.values() if r.get("roofline")), None)}
