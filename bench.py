@@ -415,9 +415,9 @@ BATCHES = {
         kind="ipm", sigma=6.0, psd=True,
         paths=("fp64", "fp64_persist", "mixed", "mixed_persist", "mixed_tf32", "mixed_bf16")),
     "adjoint512": dict(
-        desc="512 ipm-shaped KKT systems N=256, n=32, m=8, FP64; loss 1/2 ||x||^2: factor + solve + "
-             "adjoint (dL/db and every block gradient)",
-        kind="ipm", sigma=8.0, paths=("fp64_adjoint",)),
+        desc="512 ipm-shaped KKT systems N=256, n=32, m=8; loss 1/2 ||x||^2: factor + solve + adjoint "
+             "(dL/db and every block gradient), FP64 vs FP32 mixed with both solves refined in FP64",
+        kind="ipm", sigma=8.0, paths=("fp64_adjoint", "mixed_adjoint")),
     "raceline64": dict(
         desc="64 race-line-shaped KKT systems N=8192, n=6, m=2; FP64 vs FP32 mixed + FP64 refinement",
         kind="raceline", sigma=8.0, paths=("fp64", "fp64_persist", "mixed")),
@@ -440,7 +440,8 @@ def batch_shapes(name: str, seed: int = 0):
 def batch_cpu_baseline(name: str, Ns, ns, ms, budget_s: float):
     """The oracle's sequential factor + solve over the host cores (one system
     per thread at a time) on a bounded sample of the batch's systems,
-    generated on the host with the same recipe (gen)."""
+    generated on the host with the same recipe (gen); for the differentiable
+    workload also the oracle's adjoint (which factors the system again)."""
     from concurrent.futures import ThreadPoolExecutor
     import oracle
     oracle.build()
@@ -457,9 +458,13 @@ def batch_cpu_baseline(name: str, Ns, ns, ms, budget_s: float):
             sy = gen.raceline(N, n, m, seed=int(i), sigma_decades=spec["sigma"])
         systems.append((sy, gen.rhs(N * n + m, 1, seed=int(i) + 1)))
 
+    adjoint = name == "adjoint512"
+
     def one(sy):
         (D, E, G, R), b = sy
-        oracle.seq_solve(oracle.seq_factor(D, E, G, R), b)
+        x = oracle.seq_solve(oracle.seq_factor(D, E, G, R), b)
+        if adjoint:     # the same step as the GPU's: loss 1/2 ||x||^2, xbar = x
+            oracle.adjoint(D, E, G, R, x, x)
 
     with ThreadPoolExecutor(max_workers=cores) as ex:
         t0 = time.perf_counter()
@@ -471,7 +476,8 @@ def batch_cpu_baseline(name: str, Ns, ns, ms, budget_s: float):
             list(ex.map(one, systems))
         dt = time.perf_counter() - t0
     return dict(value=reps * len(systems) / dt, unit=UNIT, cores=cores, kind="oracle", cpu=host_cpu(),
-                sample=f"{reps} x {len(systems)} systems drawn from the batch on {cores} threads ({dt:.1f} s)")
+                sample=f"{reps} x {len(systems)} systems drawn from the batch on {cores} threads ({dt:.1f} s)"
+                + ("; factor + solve + oracle.adjoint (a second factorization)" if adjoint else ""))
 
 
 def _plan_is_sequential(kkt, h, count):
@@ -522,8 +528,9 @@ def measure_batch(name, args, world, rank, local, host_check=64, paths=None):
     for path in (paths or (args.paths.split(",") if args.paths else spec["paths"])):
         persist = path.endswith("_persist")
         base = path[:-len("_persist")] if persist else path
+        adjoint = base.endswith("_adjoint")
         prec = {"mixed": kkt.KKT_MIXED_FP32_ALL, "mixed_tf32": kkt.KKT_MIXED_TF32,
-                "mixed_bf16": kkt.KKT_MIXED_BF16}.get(base, kkt.KKT_FP64)
+                "mixed_bf16": kkt.KKT_MIXED_BF16}.get(base.replace("_adjoint", ""), kkt.KKT_FP64)
         mixed = path.startswith("mixed")
         t0 = time.perf_counter()
         if args.P:
@@ -548,9 +555,12 @@ def measure_batch(name, args, world, rank, local, host_check=64, paths=None):
                 kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=args.sweeps, tol=args.tol)
             else:
                 kkt.kkt_solve(h, b)
-                if path == "fp64_adjoint":
-                    # loss 1/2 ||x||^2: xbar = x
-                    kkt.kkt_solve_adjoint(h, b, b, bb, gD, gE, gG, gR, D=D, E=E, G=G, R=R, sweeps=1)
+            if adjoint:
+                # loss 1/2 ||x||^2: xbar = x; on a mixed factor bbar is refined
+                # like x (to the rounding floor, at most `sweeps` sweeps)
+                xs_ = x if mixed else b
+                kkt.kkt_solve_adjoint(h, xs_, xs_, bb, gD, gE, gG, gR, D=D, E=E, G=G, R=R,
+                                      sweeps=args.sweeps if mixed else 1)
 
         def reset():
             if not mixed:
@@ -635,7 +645,14 @@ def measure_batch(name, args, world, rank, local, host_check=64, paths=None):
         # error of the returned solution: the device's eta per system, and a
         # host FP64 residual of the sampled systems
         xs = (x if mixed else b).cpu().numpy()
-        if mixed:
+        if mixed and adjoint:
+            # the step's last refinement is the adjoint's: refine x once more
+            # on its own (same factor and input, the same sweeps) for x's eta
+            x1 = torch.zeros_like(b0)
+            kkt.kkt_solve_refined(h, D, E, G, R, b0, x1, sweeps=args.sweeps, tol=args.tol)
+            eta_dev = kkt.kkt_refine_eta(h, args.sweeps - 1, count)
+            eta_raw = kkt.kkt_refine_eta(h, 0, count)
+        elif mixed:
             eta_dev = kkt.kkt_refine_eta(h, args.sweeps - 1, count)
             eta_raw = kkt.kkt_refine_eta(h, 0, count)
         else:
@@ -643,9 +660,18 @@ def measure_batch(name, args, world, rank, local, host_check=64, paths=None):
             kkt.kkt_solve_refined(h, D, E, G, R, b0, x1, sweeps=1, tol=0.0)
             eta_dev = kkt.kkt_refine_eta(h, 0, count)
             eta_raw = eta_dev
-        host = []
+        host, host_adj, grads = [], [], []
+        if adjoint:
+            bbs = bb.cpu().numpy()
+            gh = [t.cpu().numpy() for t in (gD, gE, gG, gR)]
         for s, (Dh, Eh, Gh, Rh, bh) in zip(sample, host_blocks):
-            host.append(backward_error(Dh, Eh, Gh, Rh, xs[off["b"][s]:off["b"][s + 1]], bh))
+            xsl = xs[off["b"][s]:off["b"][s + 1]]
+            host.append(backward_error(Dh, Eh, Gh, Rh, xsl, bh))
+            if adjoint:
+                # the adjoint solve Psi bbar = xbar (= x) and the sampled
+                # system's block gradients
+                host_adj.append(backward_error(Dh, Eh, Gh, Rh, bbs[off["b"][s]:off["b"][s + 1]], xsl))
+                grads.append([g[off[k][s]:off[k][s + 1]] for g, k in zip(gh, ("D", "E", "G", "R"))])
         fl = kkt.kkt_flops(h)
         t_ms, max_eta = max_over_ranks([statistics.median(ms_list), float(np.max(eta_dev))])
         P1 = [len(kkt.kkt_partition(h, s, 1)) for s in range(count)]
@@ -656,6 +682,10 @@ def measure_batch(name, args, world, rank, local, host_check=64, paths=None):
                  levels_max=int(max(lv)), level1_segments_total=int(sum(P1)), tune_s=tune_s,
                  factor_flops=fl["factor"], sequential_factor_flops=fl["sequential_factor"],
                  clocks=clk.summary())
+        if adjoint:
+            r["host_check"]["adjoint_max_backward_error"] = max(e for e, _ in host_adj)
+            r["host_check"]["adjoint_relres"] = [rr for _, rr in host_adj]
+            r["_grads"] = grads     # sampled gradients, compared across paths and then dropped
         if mixed:
             r["refinement"] = {"sweeps_max": args.sweeps, "tol": args.tol,
                                "stop": "eta <= tol, or eta <= 4 u and a sweep that cuts it by less than 10 % (rounding floor)"}
@@ -692,7 +722,8 @@ def compare_paths(results):
     over FP64; worst and median system) and of the step rates. `best` is the
     fastest mixed path at equal accuracy (residuals within 10x the FP64
     path's, eta <= 1e-14)."""
-    fp = {p: r for p, r in results.items() if p in ("fp64", "fp64_persist")}
+    fp = {p: r for p, r in results.items() if p.startswith("fp64")}
+    grads = {p: r.pop("_grads", None) for p, r in results.items()}
     if not fp:
         return None
     ref, a = min(fp.items(), key=lambda kv: kv[1]["ms_per_step"])   # the faster plain FP64 schedule
@@ -704,8 +735,21 @@ def compare_paths(results):
         out[p] = {"rate_over_fp64": m["value"] / a["value"], "ms_fp64": a["ms_per_step"],
                   "ms_mixed": m["ms_per_step"], "worst_relres_ratio_over_fp64": max(ratios),
                   "median_relres_ratio_over_fp64": statistics.median(ratios),
-                  "max_eta_fp64": a["max_eta"], "max_eta_mixed": m["max_eta"],
-                  "equal_accuracy": bool(max(ratios) <= 10.0 and m["max_eta"] <= 1e-14)}
+                  "max_eta_fp64": a["max_eta"], "max_eta_mixed": m["max_eta"]}
+        equal = max(ratios) <= 10.0 and m["max_eta"] <= 1e-14
+        if "adjoint_relres" in m["host_check"] and "adjoint_relres" in a["host_check"]:
+            # the adjoint solve at equal accuracy too; the gradients' largest
+            # difference from the FP64 path's, relative to their largest entry
+            ar = [rm / ra for rm, ra in zip(m["host_check"]["adjoint_relres"], a["host_check"]["adjoint_relres"])]
+            out[p]["worst_adjoint_relres_ratio_over_fp64"] = max(ar)
+            out[p]["adjoint_max_backward_error"] = m["host_check"]["adjoint_max_backward_error"]
+            equal = equal and max(ar) <= 10.0 and m["host_check"]["adjoint_max_backward_error"] <= 1e-14
+            if grads.get(p) and grads.get(ref):
+                out[p]["gradient_max_rel_diff_vs_fp64"] = {
+                    k: max(float(np.abs(gm[i] - gf[i]).max() / max(np.abs(gf[i]).max(), 1e-300))
+                           for gm, gf in zip(grads[p], grads[ref]) if gf[i].size)
+                    for i, k in enumerate(("dD", "dE", "dG", "dR"))}
+        out[p]["equal_accuracy"] = bool(equal)
     if len(out) == 1:
         return None
     ok = [p for p, c in out.items() if p != "fp64_reference_path" and c["equal_accuracy"]]
@@ -738,7 +782,8 @@ def run_batch(args):
         "metric": METRIC, "value": br["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": br["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if not bp.startswith("mixed") else
-        {"mixed": "f32+f64", "mixed_tf32": "tf32+f32+f64", "mixed_bf16": "bf16+f32+f64"}[bp.replace("_persist", "")],
+        {"mixed": "f32+f64", "mixed_tf32": "tf32+f32+f64", "mixed_bf16": "bf16+f32+f64"}[
+            bp.replace("_persist", "").replace("_adjoint", "")],
         "data": "synthetic",
         "config": {"workload": spec["desc"], "name": name, "path": bp, "systems": count * world,
                    "systems_per_rank": count,
@@ -765,6 +810,8 @@ PROFILE_CASES = {
                "sequential plan: factor + 2 refinement sweeps",
     "fp64_48": "the same systems, FP64: factor + solve",
     "adjoint128": "128 ipm-shaped systems N=256, n=32, m=8 (Sigma +-8 decades), FP64: factor + solve + adjoint",
+    "adjoint128_mixed": "the same systems, FP32 mixed: factor + refined solve + refined adjoint (tol 1e-16, "
+                        "at most 8 sweeps each)",
     "uneven512": "512 systems of the uneven workload's shapes, FP64, persistent factorization + solve",
 }
 
@@ -778,7 +825,7 @@ def run_profile_case(name):
         c = 304
         Ns, ns, ms = [60] * c, [48] * c, [4] * c
         D, E, G, R = gdev.batch(Ns, ns, ms, seed=1, kind="ipm", sigma_decades=6.0, psd_couplings=True)
-    elif name == "adjoint128":
+    elif name in ("adjoint128", "adjoint128_mixed"):
         c = 128
         Ns, ns, ms = [256] * c, [32] * c, [8] * c
         D, E, G, R = gdev.batch(Ns, ns, ms, seed=1, kind="ipm", sigma_decades=8.0)
@@ -789,7 +836,7 @@ def run_profile_case(name):
     else:
         raise ValueError(name)
     b = gdev.rhs(int(sum(N * n + m for N, n, m in zip(Ns, ns, ms))), 1, seed=2)
-    prec = kkt.KKT_MIXED_FP32_ALL if name == "mixed48" else kkt.KKT_FP64
+    prec = kkt.KKT_MIXED_FP32_ALL if name in ("mixed48", "adjoint128_mixed") else kkt.KKT_FP64
     h = kkt.kkt_batch_create(Ns, ns, ms, [1] * c, prec)
     if name == "uneven512":
         kkt.kkt_set_persistent(h, True)
@@ -800,6 +847,9 @@ def run_profile_case(name):
         kkt.kkt_factor(h, D, E, G, R)
         if name == "mixed48":
             kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=2, tol=0.0)
+        elif name == "adjoint128_mixed":
+            kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=8, tol=1e-16)
+            kkt.kkt_solve_adjoint(h, x, x, bb, gD, gE, gG, gR, D=D, E=E, G=G, R=R, sweeps=8)
         else:
             x.copy_(b)
             kkt.kkt_solve(h, x)

@@ -391,13 +391,18 @@ kkt_status kkt_set_pairing(kkt_handle* h, int policy);
  * kkt_factor_solve and kkt_factor_solve_host keep the per-level launches. */
 kkt_status kkt_set_persistent(kkt_handle* h, int on);
 
-/* Bounded waits of the persistent schedule: a task gives up waiting for its
- * feeders after `cycles` SM clock cycles (default 2^31, about a second),
- * records KKT_ERR_TIMEOUT (system, natural stage and level of the waiting
- * task) and carries on without its own work, so nothing hangs. unmet != 0
- * adds one unsatisfiable dependency to every waiting task (a counter no task
- * ever releases), which makes every wait run out: a test of the timeout path
- * on the device; unmet = 0 restores the real counts. */
+/* Bounded waits of the persistent schedule and of the one-warp substitution
+ * of sequential systems (one level, P = 1, one right-hand side), whose stage
+ * blocks arrive by bulk copies counted on an mbarrier: a task gives up
+ * waiting for its feeders (or its copies) after `cycles` SM clock cycles
+ * (default 2^31, about a second), records KKT_ERR_TIMEOUT (system, natural
+ * stage and level of the waiting task) and carries on without its own work,
+ * so nothing hangs; the substitution first waits, with the same bound, for
+ * its copies still in flight. unmet != 0 adds one unsatisfiable dependency
+ * to every waiting task (a counter no task ever releases) and makes every
+ * stage of the substitution expect 16 bytes more than its copies deliver,
+ * which makes every wait run out: a test of the timeout path on the device;
+ * unmet = 0 restores the real counts. */
 kkt_status kkt_set_wait_limit(kkt_handle* h, long long cycles, int unmet);
 
 /* Number of kernel launches one kkt_factor / one kkt_solve (per chunk of up

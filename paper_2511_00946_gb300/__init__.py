@@ -325,8 +325,9 @@ def kkt_set_persistent(h: int, on: bool = True) -> None:
 
 
 def kkt_set_wait_limit(h: int, cycles: int, unmet: bool = False) -> None:
-    """Clock-cycle bound of the persistent schedule's dependency waits;
-    `unmet` injects an unsatisfiable dependency (tests the timeout path)."""
+    """Clock-cycle bound of the persistent schedule's dependency waits and of
+    the one-warp substitution's bulk-copy waits; `unmet` makes every such
+    wait run out (tests the timeout path)."""
     _check(_lib.kkt_set_wait_limit(h, int(cycles), int(bool(unmet))), "kkt_set_wait_limit")
 
 

@@ -157,6 +157,9 @@ struct kkt_handle {
     int off, cnt, n, m;
     bool warp;
     bool fill;  // some task has fill-in rows (its system has P > 1 at this level)
+    // every system's blocks suit the bulk copies of the one-warp substitution
+    // (k_seq_solve): n even, and m n a multiple of 4 for the FP32 copies
+    bool even = true, mn4 = true;
   };
   std::vector<std::vector<Group>> fac_groups, bwd_groups;
   std::vector<int> bwd_off, bwd_cnt;         // task ranges per level (backward)
@@ -446,6 +449,8 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       kkt_handle::Group& gr = groups.back();
       for (int k = 0; k < sp.lv[l].P; ++k) tasks.push_back(Task{h->desc_of[s][l], k});
       gr.cnt += sp.lv[l].P;
+      gr.even = gr.even && sp.n % 2 == 0;
+      gr.mn4 = gr.mn4 && (sp.m * sp.n) % 4 == 0;
       gr.n = std::max(gr.n, sp.n);
       gr.m = std::max(gr.m, sp.m);
     }
@@ -980,19 +985,17 @@ kkt_status build_persistent(kkt_handle* h) {
     }
   }
   std::vector<kkt::PCons> cons;
-  for (size_t i = 0, pos = 0; i < items.size(); ++i) {
+  for (size_t i = 0; i < items.size(); ++i) {
     items[i].cons0 = (int)cons.size();
     auto itr = w.lower_bound({(int)i, -1});
     for (; itr != w.end() && itr->first.first == (int)i; ++itr) cons.push_back(kkt::PCons{itr->first.second, itr->second});
     items[i].ncons = (int)cons.size() - items[i].cons0;
-    (void)pos;
   }
   const size_t n_it = items.size(), n_c = std::max<size_t>(cons.size(), 1), n_t = ptasks.size();
   Carver cv;
   const size_t o_it = cv.take(sizeof(kkt::PItem) * n_it), o_c = cv.take(sizeof(kkt::PCons) * n_c),
                o_t = cv.take(sizeof(Task) * n_t), o_r = cv.take(sizeof(int) * (n_it + 1));
   if (h->pmem) cudaFree(h->pmem);
-  if (h->cg_mem) cudaFree(h->cg_mem);
   h->pmem = nullptr;
   if (cudaMalloc(&h->pmem, cv.off) != cudaSuccess) {
     h->pmem = nullptr;
@@ -1087,6 +1090,7 @@ namespace {
 // with the descriptors of the current factor. fwd_done: the factorization
 // carried the forward sweep (bordered pass), so only the top levels' corner
 // and backward sweep run among the forward launches.
+constexpr int kSeqSmemMax = 227 * 1024;  // shared memory a CTA can opt in to
 kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* skip, void* stream, int* li,
                        int fwd_done = 0) {
   const LevelDesc* dd = h->cur_b ? h->ddesc_b : h->ddesc;
@@ -1102,7 +1106,15 @@ kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* ski
       // the CTAs fit one wave (three substitution CTAs per SM)
       const int slots = 3 * std::max(h->sms, 1);
       const int split = std::max(1, std::min(nr / 4, slots / std::max(gr.cnt, 1)));
-      const int e = gr.warp ? kkt::launch_solve_w(backward, dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip,
+      // whole systems (level 1 with P = 1) and one right-hand side: one warp
+      // per system solves forward, corner and backward with the stage blocks
+      // streamed by bulk copies
+      const bool seq = l == 0 && !backward && !gr.fill && nr == 1 && !fwd_done && gr.even &&
+                       (!mx || (gr.mn4 && !dm)) && gr.n <= kkt::kMaxN && gm <= kkt::kMaxM &&
+                       kkt::seq_slice_bytes(gr.n, gm, mx ? 4 : 8) <= kSeqSmemMax;
+      const int e = seq ? kkt::launch_seq_solve(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, skip, h->dinfo, h->pwait,
+                                                h->punmet, stream)
+                    : gr.warp ? kkt::launch_solve_w(backward, dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip,
                                                   stream, fwd_done, gr.fill)
                     : backward ? kkt::launch_backward(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip, stream, split,
                                                       gr.fill)

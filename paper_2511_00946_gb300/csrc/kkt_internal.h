@@ -212,6 +212,24 @@ __host__ __device__ inline SolLayout sol_layout(int n, int m, int sb, bool fill 
   return L;
 }
 
+// Substitution of a system whose plan is one level with P = 1, one
+// right-hand side, one warp per system (k_seq_solve): two mbarriers, then
+// two buffers each holding one stage's n x n multipliers (unpadded; the
+// forward ones transposed) and its n + m panel rows, both filled by bulk
+// copies. sb = bytes per element (8 FP64, 4 FP32).
+__host__ __device__ inline int seq_zoff_bytes(int n, int sb) { return kkt_align16(sb * n * n); }
+__host__ __device__ inline int seq_buf_bytes(int n, int m, int sb) {
+  return seq_zoff_bytes(n, sb) + kkt_align16(sb * (n + m) * n);
+}
+__host__ __device__ inline int seq_slice_bytes(int n, int m, int sb) { return 16 + 2 * seq_buf_bytes(n, m, sb); }
+// Bulk copies move whole 16-byte units from 16-byte aligned addresses: every
+// block a stage copies starts and ends on such a boundary when n is even and,
+// for FP32 blocks, m n is a multiple of 4 (the panel of stage j starts at
+// element j (2n + m) n).
+__host__ __device__ inline bool seq_shape_ok(int n, int m, int sb) {
+  return n >= 2 && n % 2 == 0 && n <= kMaxN && m <= kMaxM && (sb == 8 || (m * n) % 4 == 0);
+}
+
 // Residual pass of iterative refinement: one CTA per chunk of kResChunk
 // stages of one system.
 constexpr int kResChunk = 8;
@@ -256,6 +274,14 @@ int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
 // one warp per task (blocks n <= kWarpMaxN), forward or backward substitution
 int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
                    double* b, int ldb, int nrhs, const int* skip, void* stream, int fwd_done = 0, int fill = 1);
+// whole substitution (Algorithms 2 and 3, corner of Eq. (7)) of systems
+// whose level plan is one level with P = 1, one right-hand side, one warp per
+// system; every system of the launch satisfies seq_shape_ok. A bulk copy
+// that has not arrived within `wait` clock cycles records KKT_ERR_TIMEOUT in
+// `info` and ends the system's task (`unmet`: every stage expects 16 bytes
+// more than its copies deliver, so that every wait runs out).
+int launch_seq_solve(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single, double* b,
+                     int ldb, const int* skip, Info* info, long long wait, int unmet, void* stream);
 // bordered inputs of a fused factor-and-solve pass, for every system: Gb_j =
 // [G_j; b_j^T] ((m+1) x n per stage), Rb = [[R, b_g], [b_g^T, 0]] ((m+1)^2)
 // (stages [j0, j1) of every system's arrow, and with `corner` the bordered corners)

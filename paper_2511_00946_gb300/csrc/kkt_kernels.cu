@@ -24,6 +24,7 @@
 #include <unordered_map>
 
 #include "kkt_internal.h"
+#include "kkt_bulk.cuh"
 #include "kkt_numerics.cuh"
 #include "kkt_tc.cuh"
 
@@ -765,17 +766,19 @@ struct FacCtx {
 
   // factor blocks of stage j from the pivot factor L (Dp_, ld ldD) and
   // rv = 1/diag: Ld = L, LdR = L with its rows divided by their diagonal
-  // (backward substitution), LdM = L with its columns divided by their
-  // diagonal (forward substitution: the panel operand Ms when given, else
-  // formed here with the same rounding), Lri = rv. Strict lower triangles are
-  // computed and the rest zero-filled, so that no FP64 multiply is issued for
-  // an upper half.
+  // (backward substitution, row-major), LdM = L with its columns divided by
+  // their diagonal (forward substitution: the panel operand Ms when given,
+  // else formed here with the same rounding), stored transposed so that
+  // column c of L is the contiguous row c of LdM, Lri = rv. Strict lower
+  // triangles are computed (no FP64 multiply for an upper half), the
+  // diagonals of LdR and LdM hold rv (a substitution reads the reciprocal
+  // from the block it streams in) and the rest is zero.
   __device__ void store_pivot(int j, const double* Dp_, const double* rv, const TZ* Ms, Grp G) const {
     store_blk(d->Ld + (size_t)j * nn, Dp_, ldD, n, n, false, true, G);
     TZ* LdRj = mixed ? (TZ*)(d->LdRf + (size_t)j * nn) : (TZ*)(d->LdR + (size_t)j * nn);
     TZ* LdMj = mixed ? (TZ*)(d->LdMf + (size_t)j * nn) : (TZ*)(d->LdM + (size_t)j * nn);
     for (int e = G.tid; e < n * n; e += G.nt) LdRj[e] = TZ(0);
-    if (Ms) store_blk(LdMj, Ms, ldD, n, n, false, true, G);
+    if (Ms) store_blk(LdMj, Ms, ldD, n, n, true, true, G);
     else
       for (int e = G.tid; e < n * n; e += G.nt) LdMj[e] = TZ(0);
     gsync(G);
@@ -784,7 +787,11 @@ struct FacCtx {
       tri_rc(e, a, b);
       const int r = a + 1, c = b;
       LdRj[r * n + c] = (TZ)(Dp_[r * ldD + c] * rv[r]);
-      if (!Ms) LdMj[r * n + c] = (TZ)(Dp_[r * ldD + c] * rv[c]);
+      if (!Ms) LdMj[c * n + r] = (TZ)(Dp_[r * ldD + c] * rv[c]);
+    }
+    for (int e = G.tid; e < n; e += G.nt) {
+      LdRj[e * n + e] = (TZ)rv[e];
+      LdMj[e * n + e] = (TZ)rv[e];
     }
     if (mixed)
       for (int e = G.tid; e < n; e += G.nt) d->Lrif[(size_t)j * n + e] = (float)rv[e];
@@ -1539,10 +1546,11 @@ __device__ void prefetch_stage_factor(const SolveSmem<TS>& S, int q, const Level
                                       int r1, bool backward, Grp G) {
   const int n = d.n, R = 2 * n + d.m;
   const FactorView<TS> F = factor_view(d, TS(0));
+  // (the forward multipliers are stored transposed: element e is (e % n, e / n))
   const TS* Lg = (backward ? F.MR : F.M) + (size_t)j * n * n;
   for (int e = G.tid; e < n * n; e += G.nt) {
-    const int r = e / n, c = e - r * n;
-    cp_async_elem(S.L(q) + r * S.ldL + c, Lg + e);
+    const int a = e / n, c = e - a * n;
+    cp_async_elem(S.L(q) + (backward ? a * S.ldL + c : c * S.ldL + a), Lg + e);
   }
   for (int e = G.tid; e < n; e += G.nt) cp_async_elem(S.rinv(q) + e, F.ri + (size_t)j * n + e);
   const TS* P = F.P + (size_t)j * R * n;
@@ -1823,6 +1831,374 @@ __global__ void __launch_bounds__(256) k_backward_w(const LevelDesc* __restrict_
   if (t >= ntasks) return;  // whole warp
   backward_task<TS>(tasks[t], descs, b, ldb, nr, skip, smraw + (size_t)wid * slice,
                     Grp{(int)(threadIdx.x & 31), 32, -1});
+}
+
+// ---------------------------------------------------------------------------
+// Whole substitution of a system whose level plan is one level with P = 1
+// (the sequential method), one right-hand side, one warp per system:
+// Algorithm 2 over the N stages, the corner of Eq. (7), Algorithm 3 back.
+// Stage j's n x n multipliers and its panel rows (the E-hat rows when a next
+// stage exists, then the arrow rows) arrive by two bulk copies into one of
+// two shared-memory buffers, the next stage's while this one is solved. A
+// lane owns rows `lane` (and `lane + 32` when RPL = 2) of a stage, so the
+// warp needs no block barrier. Every shared-memory read is free of bank
+// conflicts on the unpadded blocks: the forward multipliers are stored
+// transposed (column c of L contiguous), the backward ones row-major, the
+// backward panel product reads columns and the forward one walks a skewed
+// diagonal (lane r reads column (r + kk) mod n of row r at step kk). The
+// arrow rows' sums sum_j G-hat_j y_j stay in registers over the forward
+// sweep (per lane, over its own rows) and are reduced across the warp once,
+// before the corner. b is read two stages ahead.
+// ---------------------------------------------------------------------------
+
+// forward chain u_r -= (L_rc / L_cc) u_c for c < r; MT holds column c of L
+// (divided by its diagonal) as row c
+template <typename TS, int RPL>
+__device__ __forceinline__ void seq_fwd_chain(TS& u0, TS& u1, const TS* MT, int n, int lane) {
+  if (RPL == 1) {
+    const int r0 = lane < n ? lane : n - 1;
+    int c = 0;
+    for (; c + 4 < n; c += 4) {  // multipliers of four steps loaded ahead
+      const TS m0 = MT[c * n + r0], m1 = MT[(c + 1) * n + r0], m2 = MT[(c + 2) * n + r0],
+               m3 = MT[(c + 3) * n + r0];
+      TS uc = shfl_idx(u0, c);
+      if (lane > c) u0 = fma(-m0, uc, u0);
+      uc = shfl_idx(u0, c + 1);
+      if (lane > c + 1) u0 = fma(-m1, uc, u0);
+      uc = shfl_idx(u0, c + 2);
+      if (lane > c + 2) u0 = fma(-m2, uc, u0);
+      uc = shfl_idx(u0, c + 3);
+      if (lane > c + 3) u0 = fma(-m3, uc, u0);
+    }
+    for (; c < n - 1; ++c) {
+      const TS uc = shfl_idx(u0, c);
+      if (lane > c) u0 = fma(-MT[c * n + r0], uc, u0);
+    }
+  } else {
+    const int r1 = lane + 32 < n ? lane + 32 : n - 1;
+#pragma unroll 4
+    for (int c = 0; c < n - 1; ++c) {
+      const TS m0 = MT[c * n + lane], m1 = MT[c * n + r1];
+      const TS uc = shfl_idx(c < 32 ? u0 : u1, c & 31);
+      if (lane > c) u0 = fma(-m0, uc, u0);
+      if (lane + 32 > c && lane + 32 < n) u1 = fma(-m1, uc, u1);
+    }
+  }
+}
+
+// backward chain u_r -= (L_cr / L_cc) u_c for c > r; MR holds row c of L
+// (divided by its diagonal)
+template <typename TS, int RPL>
+__device__ __forceinline__ void seq_bwd_chain(TS& u0, TS& u1, const TS* MR, int n, int lane) {
+  if (RPL == 1) {
+    const int r0 = lane < n ? lane : n - 1;
+    int c = n - 1;
+    for (; c - 3 > 0; c -= 4) {
+      const TS m0 = MR[c * n + r0], m1 = MR[(c - 1) * n + r0], m2 = MR[(c - 2) * n + r0],
+               m3 = MR[(c - 3) * n + r0];
+      TS uc = shfl_idx(u0, c);
+      if (lane < c) u0 = fma(-m0, uc, u0);
+      uc = shfl_idx(u0, c - 1);
+      if (lane < c - 1) u0 = fma(-m1, uc, u0);
+      uc = shfl_idx(u0, c - 2);
+      if (lane < c - 2) u0 = fma(-m2, uc, u0);
+      uc = shfl_idx(u0, c - 3);
+      if (lane < c - 3) u0 = fma(-m3, uc, u0);
+    }
+    for (; c > 0; --c) {
+      const TS uc = shfl_idx(u0, c);
+      if (lane < c) u0 = fma(-MR[c * n + r0], uc, u0);
+    }
+  } else {
+    const int r1 = lane + 32 < n ? lane + 32 : n - 1;
+#pragma unroll 4
+    for (int c = n - 1; c > 0; --c) {
+      const TS m0 = MR[c * n + lane], m1 = MR[c * n + r1];
+      const TS uc = shfl_idx(c < 32 ? u0 : u1, c & 31);
+      if (lane < c) u0 = fma(-m0, uc, u0);
+      if (lane + 32 < c) u1 = fma(-m1, uc, u1);
+    }
+  }
+}
+
+// a_r = sum_k Z[r][k] y_k for the rows r = lane (a0) and lane + 32 (a1) of
+// an n x n block, y_k held by lane k (k < 32, y0) or lane k - 32 (y1);
+// lane r starts its walk over k at column r, so that the warp's reads of
+// one step fall in distinct banks
+template <typename TS, int RPL>
+__device__ __forceinline__ void seq_fwd_panel(TS& a0, TS& a1, const TS* Z, TS y0, TS y1, int n, int lane) {
+  if (RPL == 1) {
+    const int r0 = lane < n ? lane : n - 1;
+    const TS* zr = Z + r0 * n;
+    int k = r0;
+    TS s0 = TS(0), s1 = TS(0);
+    int kk = 0;
+    for (; kk + 1 < n; kk += 2) {
+      const TS ya = shfl_idx(y0, k);
+      const TS za = zr[k];
+      k = k + 1 == n ? 0 : k + 1;
+      const TS yb = shfl_idx(y0, k);
+      const TS zb = zr[k];
+      k = k + 1 == n ? 0 : k + 1;
+      s0 = fma(za, ya, s0);
+      s1 = fma(zb, yb, s1);
+    }
+    if (kk < n) s0 = fma(zr[k], shfl_idx(y0, k), s0);
+    a0 = s0 + s1;
+    a1 = TS(0);
+  } else {
+    const int r1 = lane + 32 < n ? lane + 32 : n - 1, h = n - 32;
+    const TS *z0 = Z + lane * n, *z1 = Z + r1 * n;
+    TS s0 = TS(0), s1 = TS(0);
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {  // columns 0..31: y from y0
+      const int k = (lane + kk) & 31;
+      const TS yk = shfl_idx(y0, k);
+      s0 = fma(z0[k], yk, s0);
+      s1 = fma(z1[k], yk, s1);
+    }
+    int k = lane % h;
+    for (int kk = 0; kk < h; ++kk) {  // columns 32..n-1: y from y1
+      const TS yk = shfl_idx(y1, k);
+      s0 = fma(z0[32 + k], yk, s0);
+      s1 = fma(z1[32 + k], yk, s1);
+      k = k + 1 == h ? 0 : k + 1;
+    }
+    a0 = s0;
+    a1 = s1;
+  }
+}
+
+template <typename TS, int RPL>
+__global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ descs,
+                                                  const Task* __restrict__ tasks, double* b, int ldb,
+                                                  const int* skip, Info* info, long long wait_cycles,
+                                                  int unmet) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int sb = (int)sizeof(TS);
+  const int lane = threadIdx.x;
+  const Task tk = tasks[blockIdx.x];
+  const LevelDesc& d = descs[tk.desc];
+  if (skip && skip[d.sys]) return;
+  const int n = d.n, m = d.m, N = d.N, R = 2 * n + m, mg = m - d.mr;
+#ifdef KKT_DEBUG
+  {
+    unsigned dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    if (!dbg_ok(d.is_top && d.P == 1 && d.level == 1 && tk.seg == 0 && N >= 1 && seq_shape_ok(n, m, sb) &&
+                    n <= 32 * RPL && mg >= 0 && d.nyg_all >= 0 && seq_slice_bytes(n, m, sb) <= (int)dyn,
+                d))
+      return;
+  }
+#endif
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
+  TS* const buf0 = reinterpret_cast<TS*>(smraw + 16);
+  TS* const buf1 = reinterpret_cast<TS*>(smraw + 16 + seq_buf_bytes(n, m, sb));
+  const int zo = seq_zoff_bytes(n, sb) / sb;  // panel rows follow the multipliers
+  const size_t nn = (size_t)n * n;
+  const FactorView<TS> F = factor_view(d, TS(0));
+  double* const bs = b + (size_t)d.offB * ldb;  // the system's stage rows
+  const bool own0 = lane < n, own1 = RPL == 2 && lane + 32 < n;
+  const int c0 = own0 ? lane : n - 1, c1 = own1 ? lane + 32 : n - 1;  // rows for addresses
+  if (lane == 0) {
+    bulk::init(bar);
+    bulk::init(bar + 1);
+    bulk::fence_async();
+  }
+  __syncwarp();
+  uint32_t phase = 0, pend = 0;  // bit q: parity of buffer q's next phase; buffer q's copies in flight
+  // lane 0: stage j's multipliers and panel rows into buffer q
+  auto issue = [&](int j, int q, bool backward) {
+    const int e0 = j < N - 1 ? 0 : n;  // E-hat rows exist above the last stage only
+    const uint32_t bM = (uint32_t)(nn * sb), bZ = (uint32_t)((n + m - e0) * n * sb);
+    TS* B = q ? buf1 : buf0;
+    bulk::fence_async();
+    bulk::expect_tx(bar + q, bM + bZ + (unmet ? 16u : 0u));  // unmet: a phase that never completes
+    bulk::g2s(B, (backward ? F.MR : F.M) + (size_t)j * nn, bM, bar + q);
+    if (bZ) bulk::g2s(B + zo, F.P + ((size_t)j * R + e0) * n, bZ, bar + q);
+  };
+  auto wait_buf = [&](int q) -> bool {
+    const bool got = __all_sync(0xffffffffu, bulk::wait(bar + q, (phase >> q) & 1u, wait_cycles));
+    if (got) {
+      phase ^= 1u << q;
+      pend &= ~(1u << q);
+    }
+    return got;
+  };
+  // a copy that did not arrive: record it; the copies still in flight land
+  // in this warp's buffers, so wait for them (bounded) before returning
+  auto fail = [&](int stage) {
+    if (lane == 0) record_timeout(info, d.sys, stage, 1);
+    for (int q = 0; q < 2; ++q)
+      if ((pend >> q) & 1u) (void)bulk::wait(bar + q, (phase >> q) & 1u, wait_cycles);
+  };
+  auto bval = [&](int j, int r) -> double { return bs[((size_t)j * n + r) * ldb]; };
+
+  // ---- forward sweep (Algorithm 2): L y = b
+  TS t0 = own0 ? (TS)bval(0, lane) : TS(0), t1 = own1 ? (TS)bval(0, lane + 32) : TS(0);
+  double bn0 = 0.0, bn1 = 0.0, bm0 = 0.0, bm1 = 0.0;  // b of stages j + 1 and j + 2
+  if (N > 1) {
+    if (own0) bn0 = bval(1, lane);
+    if (own1) bn1 = bval(1, lane + 32);
+  }
+  if (N > 2) {
+    if (own0) bm0 = bval(2, lane);
+    if (own1) bm1 = bval(2, lane + 32);
+  }
+  TS pg[kMaxM];  // this lane's terms of sum_j G-hat_j y_j, per arrow row
+#pragma unroll
+  for (int g = 0; g < kMaxM; ++g) pg[g] = TS(0);
+  if (lane == 0) issue(0, 0, false);
+  pend |= 1u;
+  for (int j = 0; j < N; ++j) {
+    const int q = j & 1;
+    if (!wait_buf(q)) {
+      fail(j);
+      return;
+    }
+    __syncwarp();  // every lane is done with the other buffer (stage j - 1)
+    // next: stage j + 1, or after the last stage the backward sweep's first
+    if (lane == 0) {
+      if (j + 1 < N) issue(j + 1, q ^ 1, false);
+      else issue(N - 1, q ^ 1, true);
+    }
+    pend |= 1u << (q ^ 1);
+    const TS* MT = q ? buf1 : buf0;
+    const TS* Z = MT + zo;
+    TS u0 = t0, u1 = t1;
+    seq_fwd_chain<TS, RPL>(u0, u1, MT, n, lane);
+    const TS y0 = own0 ? u0 * MT[c0 * n + c0] : TS(0);
+    const TS y1 = own1 ? u1 * MT[c1 * n + c1] : TS(0);
+    if (own0) bs[((size_t)j * n + lane) * ldb] = (double)y0;
+    if (own1) bs[((size_t)j * n + lane + 32) * ldb] = (double)y1;
+    const int e0 = j < N - 1 ? 0 : n;
+    const TS* ZG = Z + (size_t)(n - e0) * n;  // arrow rows
+#pragma unroll
+    for (int g = 0; g < kMaxM; ++g) {
+      if (g >= m) break;  // warp-uniform; full unrolling keeps pg in registers
+      pg[g] = fma(ZG[g * n + c0], y0, pg[g]);
+      if (RPL == 2) pg[g] = fma(ZG[g * n + c1], y1, pg[g]);
+    }
+    if (j + 1 < N) {  // t_{j+1} = b_{j+1} - E-hat_j y_j
+      TS a0, a1;
+      seq_fwd_panel<TS, RPL>(a0, a1, Z, y0, y1, n, lane);
+      t0 = (TS)bn0 - a0;
+      t1 = (TS)bn1 - a1;
+      bn0 = bm0;
+      bn1 = bm1;
+      if (j + 3 < N) {
+        if (own0) bm0 = bval(j + 3, lane);
+        if (own1) bm1 = bval(j + 3, lane + 32);
+      }
+    }
+  }
+
+  // ---- corner (Eq. (7)): R-hat R-hat^T x_g = b_g - sum_j G-hat_j y_j
+  TS vg = TS(0);  // lane g: sum_j G-hat_j y_j of arrow row g
+#pragma unroll
+  for (int g = 0; g < kMaxM; ++g) {
+    if (g >= m) break;
+    TS v = pg[g];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == g) vg = v;
+  }
+  TS xgl = TS(0);  // lane g: x_g of arrow row g (0 for a bordered row)
+  if (mg > 0) {
+    const int gl = lane < mg ? lane : 0;
+    double bsum = 0.0;
+    if (lane < mg) {
+      double v = 0.0;
+      for (int p = 0; p < d.nyg_all; ++p) v += d.yg_all[((size_t)p * m + lane) * kRhsChunk];
+      bsum = b[(size_t)(d.rowG + lane) * ldb] + v;
+    }
+    TS u = lane < mg ? (TS)(bsum + (double)(-vg)) : TS(0);
+    double rrow[kMaxM], rcol[kMaxM];  // row and column gl of R-hat
+#pragma unroll
+    for (int p = 0; p < kMaxM; ++p) {
+      rrow[p] = p < mg ? d.Rhat[gl * m + p] : 0.0;
+      rcol[p] = p < mg ? d.Rhat[p * m + gl] : 0.0;
+    }
+    // R-hat y = u: u_g -= (R_gp / R_pp) u_p for p < g, y_g = u_g / R_gg
+#pragma unroll
+    for (int p = 0; p < kMaxM - 1; ++p) {
+      if (p >= mg - 1) break;
+      const TS up = shfl_idx(u, p);
+      if (lane > p && lane < mg) u = fma(-(TS)(rrow[p] * d.Rri[p]), up, u);
+    }
+    u = u * (TS)d.Rri[gl];
+    // R-hat^T x = y: u_g -= (R_pg / R_pp) u_p for p > g, x_g = u_g / R_gg
+#pragma unroll
+    for (int p = kMaxM - 1; p >= 1; --p) {
+      if (p >= mg) continue;
+      const TS up = shfl_idx(u, p);
+      if (lane < p) u = fma(-(TS)(rcol[p] * d.Rri[p]), up, u);
+    }
+    const TS x = u * (TS)d.Rri[gl];
+    if (lane < mg) b[(size_t)(d.rowG + lane) * ldb] = (double)x;
+    xgl = lane < mg ? x : TS(0);
+  }
+  TS xg[kMaxM];  // x_g, every lane
+#pragma unroll
+  for (int g = 0; g < kMaxM; ++g) xg[g] = g < m ? shfl_idx(xgl, g) : TS(0);
+
+  // ---- backward sweep (Algorithm 3): L^T x = y
+  TS xn0 = TS(0), xn1 = TS(0);  // x of stage j + 1
+  TS yc0 = own0 ? (TS)bval(N - 1, lane) : TS(0), yc1 = own1 ? (TS)bval(N - 1, lane + 32) : TS(0);
+  double yn0 = 0.0, yn1 = 0.0, ym0 = 0.0, ym1 = 0.0;  // y of stages j - 1 and j - 2
+  if (N > 1) {
+    if (own0) yn0 = bval(N - 2, lane);
+    if (own1) yn1 = bval(N - 2, lane + 32);
+  }
+  if (N > 2) {
+    if (own0) ym0 = bval(N - 3, lane);
+    if (own1) ym1 = bval(N - 3, lane + 32);
+  }
+  for (int s = 0; s < N; ++s) {
+    const int j = N - 1 - s, q = (N + s) & 1;
+    if (!wait_buf(q)) {
+      fail(j);
+      return;
+    }
+    __syncwarp();
+    if (s + 1 < N) {
+      if (lane == 0) issue(j - 1, q ^ 1, true);
+      pend |= 1u << (q ^ 1);
+    }
+    const TS* MR = q ? buf1 : buf0;
+    const TS* Z = MR + zo;
+    const int e0 = j < N - 1 ? 0 : n;
+    const TS* ZG = Z + (size_t)(n - e0) * n;
+    // t_c = y_c - sum_g G-hat_j[g][c] x_g - sum_r E-hat_j[r][c] x_{j+1, r}
+    TS s0 = TS(0), s1 = TS(0), s0b = TS(0), s1b = TS(0);
+#pragma unroll
+    for (int g = 0; g < kMaxM; ++g) {
+      if (g >= m) break;
+      s0 = fma(ZG[g * n + c0], xg[g], s0);
+      if (RPL == 2) s1 = fma(ZG[g * n + c1], xg[g], s1);
+    }
+    if (e0 == 0) {
+#pragma unroll 4
+      for (int r = 0; r < n; ++r) {
+        const TS xr = shfl_idx(RPL == 2 && r >= 32 ? xn1 : xn0, r & 31);
+        s0b = fma(Z[r * n + c0], xr, s0b);
+        if (RPL == 2) s1b = fma(Z[r * n + c1], xr, s1b);
+      }
+    }
+    TS u0 = yc0 - (s0 + s0b), u1 = yc1 - (s1 + s1b);
+    seq_bwd_chain<TS, RPL>(u0, u1, MR, n, lane);
+    xn0 = u0 * MR[c0 * n + c0];
+    xn1 = u1 * MR[c1 * n + c1];
+    if (own0) bs[((size_t)j * n + lane) * ldb] = (double)xn0;
+    if (own1) bs[((size_t)j * n + lane + 32) * ldb] = (double)xn1;
+    yc0 = (TS)yn0;
+    yc1 = (TS)yn1;
+    yn0 = ym0;
+    yn1 = ym1;
+    if (j - 3 >= 0) {
+      if (own0) ym0 = bval(j - 3, lane);
+      if (own1) ym1 = bval(j - 3, lane + 32);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -2465,6 +2841,28 @@ int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks,
   } else {
     if (single) k_forward_w<float><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice, fwd_done);
     else k_forward_w<double><<<grid, 32 * wpc, sm, st>>>(d, t, ntasks, b, ldb, nrhs, skip, slice, fwd_done);
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_seq_solve(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single, double* b,
+                     int ldb, const int* skip, Info* info, long long wait, int unmet, void* stream) {
+  if (ntasks <= 0) return 0;
+  const int sb = single ? 4 : 8;
+  if (maxn < 2 || maxn % 2 || maxn > kMaxN || maxm < 0 || maxm > kMaxM) return (int)cudaErrorInvalidValue;
+  const size_t sm = (size_t)seq_slice_bytes(maxn, maxm, sb);
+  const bool two = maxn > 32;
+  const void* fn = single ? (two ? (const void*)k_seq_solve<float, 2> : (const void*)k_seq_solve<float, 1>)
+                          : (two ? (const void*)k_seq_solve<double, 2> : (const void*)k_seq_solve<double, 1>);
+  int e = set_smem(fn, sm);
+  if (e) return e;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (single) {
+    if (two) k_seq_solve<float, 2><<<ntasks, 32, sm, st>>>(d, t, b, ldb, skip, info, wait, unmet);
+    else k_seq_solve<float, 1><<<ntasks, 32, sm, st>>>(d, t, b, ldb, skip, info, wait, unmet);
+  } else {
+    if (two) k_seq_solve<double, 2><<<ntasks, 32, sm, st>>>(d, t, b, ldb, skip, info, wait, unmet);
+    else k_seq_solve<double, 1><<<ntasks, 32, sm, st>>>(d, t, b, ldb, skip, info, wait, unmet);
   }
   return (int)cudaGetLastError();
 }

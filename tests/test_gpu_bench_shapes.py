@@ -163,26 +163,30 @@ def test_uneven_batch_slice(kkt, orc, path):
 
 # ------------------------------------------------------------ differentiable solve (N = 256, n = 32, m = 8)
 
-def test_adjoint_bench_shape_full_sigma(kkt, orc):
+@pytest.mark.parametrize("path", ["fp64", "mixed"])
+def test_adjoint_bench_shape_full_sigma(kkt, orc, path):
     """The differentiable workload's systems (N = 256, n = 32, m = 8, Sigma
     over 16 decades, kappa ~ 1e9) in the sequential plan the tuner picks for
     that batch, loss 1/2 ||x||^2 (xbar = x): bbar and every block gradient
     against the oracle's FP64 adjoint on the same x, within 10 u kappa_est of
-    each output's largest entry."""
+    each output's largest entry. The mixed path (FP32 factor, both solves
+    refined to the rounding floor, as the benchmark runs it) meets the same
+    bound as the FP64 path."""
     import torch
     count, N, n, m = 4, 256, 32, 8
-    h, lv = kkt.kkt_batch_create_tuned([N] * 512, [n] * 512, [m] * 512)
+    prec = kkt.KKT_MIXED_FP32_ALL if path == "mixed" else kkt.KKT_FP64
+    h, lv = kkt.kkt_batch_create_tuned([N] * 512, [n] * 512, [m] * 512, prec)
     kkt.kkt_destroy(h)
     assert max(lv) == 1
     systems = [gen.ipm(N, n, m, seed=300 + s, sigma_decades=8.0) for s in range(count)]
     bs = [gen.rhs(N * n + m, 1, seed=400 + s) for s in range(count)]
-    h = kkt.kkt_batch_create([N] * count, [n] * count, [m] * count, [1] * count)
+    h = kkt.kkt_batch_create([N] * count, [n] * count, [m] * count, [1] * count, prec)
     try:
-        x, (D, E, G, R, b) = run_batch(kkt, h, systems, bs, "fp64")
+        x, (D, E, G, R, b) = run_batch(kkt, h, systems, bs, path)
         xd = dev(x)
         bbar = torch.empty_like(xd)
         gD, gE, gG, gR = (torch.empty_like(t) for t in (D, E, G, R))
-        kkt.kkt_solve_adjoint(h, xd, xd, bbar, gD, gE, gG, gR, D, E, G, R, sweeps=1)
+        kkt.kkt_solve_adjoint(h, xd, xd, bbar, gD, gE, gG, gR, D, E, G, R, sweeps=8 if path == "mixed" else 1)
         torch.cuda.synchronize()
         off = kkt.kkt_batch_offsets(h, count)
         got = dict(bbar=bbar.cpu().numpy(), dD=gD.cpu().numpy(), dE=gE.cpu().numpy(), dG=gG.cpu().numpy(),

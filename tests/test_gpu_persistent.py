@@ -164,3 +164,34 @@ def test_persistent_wait_runs_out_and_reports(kkt, orc):
         kkt.kkt_destroy(h)
     xo = orc.seq_solve(orc.seq_factor(Dh, Eh, Gh, Rh), bh)
     assert np.abs(x - xo).max() <= 1e-10 * np.abs(xo).max()
+
+
+def test_persistent_keeps_refine_fallback_buffers(kkt, orc):
+    """The refinement fallback's buffers survive enabling the persistent
+    schedule after them: a mixed handle with the fallback set first and the
+    persistent schedule second refines a stalling system (Sigma over 20
+    decades) to the same x, bit for bit, as a handle with the fallback alone,
+    meets the FP64 backward-error gate, and is destroyed cleanly."""
+    import torch
+    N, n, m = 2048, 6, 2
+    D, E, G, R = gen.raceline(N, n, m, seed=5, sigma_decades=10.0)
+    b = gen.rhs(N * n + m, 1, seed=6)
+    Dd, Ed, Gd, Rd, bd = dev(D), dev(E), dev(G), dev(R), dev(b)
+    xs = {}
+    for persist in (False, True):
+        h = kkt.kkt_create_plan(N, n, m, [1], kkt.KKT_PARTITION_BALANCED, kkt.KKT_MIXED_FP32_ALL)
+        try:
+            kkt.kkt_set_refine_fallback(h, 12)
+            if persist:
+                kkt.kkt_set_persistent(h, True)
+                assert kkt.kkt_launch_counts(h)[0] == 1
+            kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+            x = torch.zeros(N * n + m, dtype=torch.float64, device="cuda")
+            kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, bd, x, sweeps=10, tol=1e-16)
+            torch.cuda.synchronize()
+            assert kkt.kkt_get_info(h)["status"] == 0
+            xs[persist] = x.cpu().numpy()
+        finally:
+            kkt.kkt_destroy(h)
+    np.testing.assert_array_equal(xs[True], xs[False])
+    assert orc.block_backward_error(D, E, G, R, xs[True], b) <= 1e-14
