@@ -812,6 +812,8 @@ PROFILE_CASES = {
     "adjoint128": "128 ipm-shaped systems N=256, n=32, m=8 (Sigma +-8 decades), FP64: factor + solve + adjoint",
     "adjoint128_mixed": "the same systems, FP32 mixed: factor + refined solve + refined adjoint (tol 1e-16, "
                         "at most 8 sweeps each)",
+    "adjoint512_mixed": "the differentiable workload's 512 systems, FP32 mixed: factor + refined solve + refined "
+                        "adjoint (tol 1e-16, at most 8 sweeps each)",
     "uneven512": "512 systems of the uneven workload's shapes, FP64, persistent factorization + solve",
 }
 
@@ -825,8 +827,8 @@ def run_profile_case(name):
         c = 304
         Ns, ns, ms = [60] * c, [48] * c, [4] * c
         D, E, G, R = gdev.batch(Ns, ns, ms, seed=1, kind="ipm", sigma_decades=6.0, psd_couplings=True)
-    elif name in ("adjoint128", "adjoint128_mixed"):
-        c = 128
+    elif name in ("adjoint128", "adjoint128_mixed", "adjoint512_mixed"):
+        c = 512 if name == "adjoint512_mixed" else 128
         Ns, ns, ms = [256] * c, [32] * c, [8] * c
         D, E, G, R = gdev.batch(Ns, ns, ms, seed=1, kind="ipm", sigma_decades=8.0)
     elif name == "uneven512":
@@ -836,7 +838,7 @@ def run_profile_case(name):
     else:
         raise ValueError(name)
     b = gdev.rhs(int(sum(N * n + m for N, n, m in zip(Ns, ns, ms))), 1, seed=2)
-    prec = kkt.KKT_MIXED_FP32_ALL if name in ("mixed48", "adjoint128_mixed") else kkt.KKT_FP64
+    prec = kkt.KKT_MIXED_FP32_ALL if name in ("mixed48", "adjoint128_mixed", "adjoint512_mixed") else kkt.KKT_FP64
     h = kkt.kkt_batch_create(Ns, ns, ms, [1] * c, prec)
     if name == "uneven512":
         kkt.kkt_set_persistent(h, True)
@@ -847,7 +849,7 @@ def run_profile_case(name):
         kkt.kkt_factor(h, D, E, G, R)
         if name == "mixed48":
             kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=2, tol=0.0)
-        elif name == "adjoint128_mixed":
+        elif name in ("adjoint128_mixed", "adjoint512_mixed"):
             kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=8, tol=1e-16)
             kkt.kkt_solve_adjoint(h, x, x, bb, gD, gE, gG, gR, D=D, E=E, G=G, R=R, sweeps=8)
         else:

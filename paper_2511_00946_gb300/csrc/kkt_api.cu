@@ -160,6 +160,7 @@ struct kkt_handle {
     // every system's blocks suit the bulk copies of the one-warp substitution
     // (k_seq_solve): n even, and m n a multiple of 4 for the FP32 copies
     bool even = true, mn4 = true;
+    int nmin = 1 << 30;  // smallest block size (the group's n is the largest)
   };
   std::vector<std::vector<Group>> fac_groups, bwd_groups;
   std::vector<int> bwd_off, bwd_cnt;         // task ranges per level (backward)
@@ -205,6 +206,7 @@ struct kkt_handle {
   // refinement fallback (kkt_set_refine_fallback): preconditioned conjugate
   // gradients for stalled systems, its vectors and per-system scalars
   int cg_iters = 0;
+  int res_two = 0;  // some system has n > 32 (two rows per lane in the residual)
   void* cg_mem = nullptr;
   double *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_rho0 = nullptr, *cg_rho1 = nullptr,
          *cg_pq = nullptr, *cg_eta = nullptr;
@@ -450,6 +452,7 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       for (int k = 0; k < sp.lv[l].P; ++k) tasks.push_back(Task{h->desc_of[s][l], k});
       gr.cnt += sp.lv[l].P;
       gr.even = gr.even && sp.n % 2 == 0;
+      gr.nmin = std::min(gr.nmin, sp.n);
       gr.mn4 = gr.mn4 && (sp.m * sp.n) % 4 == 0;
       gr.n = std::max(gr.n, sp.n);
       gr.m = std::max(gr.m, sp.m);
@@ -592,7 +595,10 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
     ok = ok && cudaMemcpy(h->ddesc_b, hdesc_b.data(), sizeof(LevelDesc) * hdesc_b.size(),
                           cudaMemcpyHostToDevice) == cudaSuccess;
   h->level_top.assign(h->maxL, 0);
-  for (const SysPlan& sp : h->sys) h->level_top[sp.lv.size() - 1] = 1;
+  for (const SysPlan& sp : h->sys) {
+    h->level_top[sp.lv.size() - 1] = 1;
+    h->res_two = h->res_two || sp.n > 32;
+  }
   if (!tasks.empty())
     ok = ok && cudaMemcpy(h->dtasks, tasks.data(), sizeof(Task) * tasks.size(),
                           cudaMemcpyHostToDevice) == cudaSuccess;
@@ -1111,9 +1117,9 @@ kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* ski
       // streamed by bulk copies
       const bool seq = l == 0 && !backward && !gr.fill && nr == 1 && !fwd_done && gr.even &&
                        (!mx || (gr.mn4 && !dm)) && gr.n <= kkt::kMaxN && gm <= kkt::kMaxM &&
-                       kkt::seq_slice_bytes(gr.n, gm, mx ? 4 : 8) <= kSeqSmemMax;
+                       kkt::seq_slice_bytes(gr.n, gm, mx ? 4 : 8, 2) <= kSeqSmemMax;
       const int e = seq ? kkt::launch_seq_solve(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, skip, h->dinfo, h->pwait,
-                                                h->punmet, stream)
+                                                h->punmet, h->sms, gr.nmin == gr.n, stream)
                     : gr.warp ? kkt::launch_solve_w(backward, dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip,
                                                   stream, fwd_done, gr.fill)
                     : backward ? kkt::launch_backward(dd, t, gr.cnt, gr.n, gm, mx, b, ldb, nr, skip, stream, split,
@@ -1367,7 +1373,7 @@ kkt_status refine_fallback(kkt_handle* h, const double* D, const double* E, cons
   const size_t vec = sizeof(double) * h->tot_B * CH;
   auto matvec = [&](const double* v, double* out) {  // out = -Psi v (b = 0)
     return kkt::launch_residual(h->ddesc, h->dres, nres, D, E, G, nullptr, 1, v, CH, out, nr, h->dparts,
-                                h->cg_skip, 0, stream) == 0 &&
+                                h->cg_skip, 0, stream, h->res_two, h->maxm) == 0 &&
            kkt::launch_residual_final(h->ddesc, h->dsys_desc, h->dpart0, cnt, G, R, nullptr, 1, v, CH, out, nr,
                                       h->dparts, -1.0, h->cg_eta, nullptr, h->cg_skip, stream) == 0;
   };
@@ -1394,7 +1400,7 @@ kkt_status refine_fallback(kkt_handle* h, const double* D, const double* E, cons
   // the true residual and eta of the fallback's systems
   ok = ok &&
        kkt::launch_residual(h->ddesc, h->dres, nres, D, E, G, b, ldb, x, ldx, h->dcorr, nr, h->dparts, h->cg_skip, 0,
-                            stream) == 0 &&
+                            stream, h->res_two, h->maxm) == 0 &&
        kkt::launch_residual_final(h->ddesc, h->dsys_desc, h->dpart0, cnt, G, R, b, ldb, x, ldx, h->dcorr, nr,
                                   h->dparts, -1.0, h->deta + (size_t)(sweeps - 1) * cnt, nullptr, h->cg_skip,
                                   stream) == 0;
@@ -1449,7 +1455,7 @@ kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, co
       if (s2 != KKT_OK) return s2;
       if (kkt::launch_axpy(h->ddesc, h->dres, nres, x + c0, ldx, h->dcorr, nr, h->dconv, stream) ||
           kkt::launch_residual(h->ddesc, h->dres, nres, D, E, G, b + c0, ldb, x + c0, ldx, h->dcorr, nr,
-                               h->dparts, h->dconv, c0 == 0 && sw == 0, stream) ||
+                               h->dparts, h->dconv, c0 == 0 && sw == 0, stream, h->res_two, h->maxm) ||
           kkt::launch_residual_final(h->ddesc, h->dsys_desc, h->dpart0, h->count, G, R, b + c0, ldb,
                                      x + c0, ldx, h->dcorr, nr, h->dparts, tol,
                                      h->deta + (size_t)sw * h->count,

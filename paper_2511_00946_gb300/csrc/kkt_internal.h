@@ -213,15 +213,29 @@ __host__ __device__ inline SolLayout sol_layout(int n, int m, int sb, bool fill 
 }
 
 // Substitution of a system whose plan is one level with P = 1, one
-// right-hand side, one warp per system (k_seq_solve): two mbarriers, then
-// two buffers each holding one stage's n x n multipliers (unpadded; the
-// forward ones transposed) and its n + m panel rows, both filled by bulk
-// copies. sb = bytes per element (8 FP64, 4 FP32).
+// right-hand side, one warp per system (k_seq_solve): up to kSeqMaxBuf
+// mbarriers, then `nbuf` buffers each holding one stage's n x n multipliers
+// (unpadded; the forward ones transposed) and its n + m panel rows, both
+// filled by bulk copies. sb = bytes per element (8 FP64, 4 FP32).
+constexpr int kSeqMaxBuf = 4;
+constexpr int kSeqHeader = 8 * kSeqMaxBuf;
 __host__ __device__ inline int seq_zoff_bytes(int n, int sb) { return kkt_align16(sb * n * n); }
 __host__ __device__ inline int seq_buf_bytes(int n, int m, int sb) {
   return seq_zoff_bytes(n, sb) + kkt_align16(sb * (n + m) * n);
 }
-__host__ __device__ inline int seq_slice_bytes(int n, int m, int sb) { return 16 + 2 * seq_buf_bytes(n, m, sb); }
+__host__ __device__ inline int seq_slice_bytes(int n, int m, int sb, int nbuf) {
+  return kSeqHeader + nbuf * seq_buf_bytes(n, m, sb);
+}
+// Copies in flight: the deepest pipeline (up to kSeqMaxBuf buffers) with
+// which every task of the launch still finds a place in the first wave
+// (about 228 KB of shared memory per SM, one warp per CTA, at most 32 CTAs
+// per SM), at least double buffering.
+__host__ __device__ inline int seq_nbuf(int n, int m, int sb, int ntasks, int sms) {
+  const int per_sm = (ntasks + (sms > 0 ? sms : 1) - 1) / (sms > 0 ? sms : 1);
+  const int want = per_sm < 32 ? per_sm : 32;
+  if ((228 * 1024) / (seq_slice_bytes(n, m, sb, kSeqMaxBuf) + 1024) >= want) return kSeqMaxBuf;
+  return 2;  // (a power of two: buffer = visit & (nbuf - 1))
+}
 // Bulk copies move whole 16-byte units from 16-byte aligned addresses: every
 // block a stage copies starts and ends on such a boundary when n is even and,
 // for FP32 blocks, m n is a multiple of 4 (the panel of stage j starts at
@@ -280,8 +294,11 @@ int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks,
 // that has not arrived within `wait` clock cycles records KKT_ERR_TIMEOUT in
 // `info` and ends the system's task (`unmet`: every stage expects 16 bytes
 // more than its copies deliver, so that every wait runs out).
+// (sms: the device's SM count, for the pipeline depth; uniform: every system
+// of the launch has n = maxn)
 int launch_seq_solve(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single, double* b,
-                     int ldb, const int* skip, Info* info, long long wait, int unmet, void* stream);
+                     int ldb, const int* skip, Info* info, long long wait, int unmet, int sms, int uniform,
+                     void* stream);
 // bordered inputs of a fused factor-and-solve pass, for every system: Gb_j =
 // [G_j; b_j^T] ((m+1) x n per stage), Rb = [[R, b_g], [b_g^T, 0]] ((m+1)^2)
 // (stages [j0, j1) of every system's arrow, and with `corner` the bordered corners)
@@ -294,9 +311,11 @@ int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int
 // c = b - Psi x over the stage rows of each task (+ partials for the g rows
 // and the max norms; the row sums of |Psi| only when `norms`, otherwise the
 // values of an earlier call stay in `parts`); c has leading dimension kRhsChunk
+// (`two`: some system has n > 32; maxm: the largest m over the systems)
 int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, const double* D, const double* E,
                     const double* G, const double* b, int ldb, const double* x, int ldx, double* c, int nr,
-                    double* parts, const int* skip, int norms, void* stream);
+                    double* parts, const int* skip, int norms, void* stream, int two = 1,
+                    int maxm = kMaxM);
 // g rows of c, eta per system, converged[s] = (eta <= tol); a system that had
 // converged before copies its eta from eta_prev (the previous sweep's; may be null)
 // (stall: mark systems whose refinement stalls with flag 3 for the fallback)

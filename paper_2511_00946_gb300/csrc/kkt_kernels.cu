@@ -1839,7 +1839,10 @@ __global__ void __launch_bounds__(256) k_backward_w(const LevelDesc* __restrict_
 // Algorithm 2 over the N stages, the corner of Eq. (7), Algorithm 3 back.
 // Stage j's n x n multipliers and its panel rows (the E-hat rows when a next
 // stage exists, then the arrow rows) arrive by two bulk copies into one of
-// two shared-memory buffers, the next stage's while this one is solved. A
+// `nbuf` (2 to 4) shared-memory buffers; the 2N stage visits (forward, then
+// backward) form one sequence whose next nbuf - 1 visits are in flight while
+// one is solved (the backward sweep's first stages arrive during the last
+// forward stages and the corner). A
 // lane owns rows `lane` (and `lane + 32` when RPL = 2) of a stage, so the
 // warp needs no block barrier. Every shared-memory read is free of bank
 // conflicts on the unpadded blocks: the forward multipliers are stored
@@ -1858,6 +1861,7 @@ __device__ __forceinline__ void seq_fwd_chain(TS& u0, TS& u1, const TS* MT, int 
   if (RPL == 1) {
     const int r0 = lane < n ? lane : n - 1;
     int c = 0;
+#pragma unroll
     for (; c + 4 < n; c += 4) {  // multipliers of four steps loaded ahead
       const TS m0 = MT[c * n + r0], m1 = MT[(c + 1) * n + r0], m2 = MT[(c + 2) * n + r0],
                m3 = MT[(c + 3) * n + r0];
@@ -1870,13 +1874,14 @@ __device__ __forceinline__ void seq_fwd_chain(TS& u0, TS& u1, const TS* MT, int 
       uc = shfl_idx(u0, c + 3);
       if (lane > c + 3) u0 = fma(-m3, uc, u0);
     }
+#pragma unroll
     for (; c < n - 1; ++c) {
       const TS uc = shfl_idx(u0, c);
       if (lane > c) u0 = fma(-MT[c * n + r0], uc, u0);
     }
   } else {
     const int r1 = lane + 32 < n ? lane + 32 : n - 1;
-#pragma unroll 4
+#pragma unroll
     for (int c = 0; c < n - 1; ++c) {
       const TS m0 = MT[c * n + lane], m1 = MT[c * n + r1];
       const TS uc = shfl_idx(c < 32 ? u0 : u1, c & 31);
@@ -1893,6 +1898,7 @@ __device__ __forceinline__ void seq_bwd_chain(TS& u0, TS& u1, const TS* MR, int 
   if (RPL == 1) {
     const int r0 = lane < n ? lane : n - 1;
     int c = n - 1;
+#pragma unroll
     for (; c - 3 > 0; c -= 4) {
       const TS m0 = MR[c * n + r0], m1 = MR[(c - 1) * n + r0], m2 = MR[(c - 2) * n + r0],
                m3 = MR[(c - 3) * n + r0];
@@ -1905,13 +1911,14 @@ __device__ __forceinline__ void seq_bwd_chain(TS& u0, TS& u1, const TS* MR, int 
       uc = shfl_idx(u0, c - 3);
       if (lane < c - 3) u0 = fma(-m3, uc, u0);
     }
+#pragma unroll
     for (; c > 0; --c) {
       const TS uc = shfl_idx(u0, c);
       if (lane < c) u0 = fma(-MR[c * n + r0], uc, u0);
     }
   } else {
     const int r1 = lane + 32 < n ? lane + 32 : n - 1;
-#pragma unroll 4
+#pragma unroll
     for (int c = n - 1; c > 0; --c) {
       const TS m0 = MR[c * n + lane], m1 = MR[c * n + r1];
       const TS uc = shfl_idx(c < 32 ? u0 : u1, c & 31);
@@ -1933,6 +1940,7 @@ __device__ __forceinline__ void seq_fwd_panel(TS& a0, TS& a1, const TS* Z, TS y0
     int k = r0;
     TS s0 = TS(0), s1 = TS(0);
     int kk = 0;
+#pragma unroll
     for (; kk + 1 < n; kk += 2) {
       const TS ya = shfl_idx(y0, k);
       const TS za = zr[k];
@@ -1950,7 +1958,7 @@ __device__ __forceinline__ void seq_fwd_panel(TS& a0, TS& a1, const TS* Z, TS y0
     const int r1 = lane + 32 < n ? lane + 32 : n - 1, h = n - 32;
     const TS *z0 = Z + lane * n, *z1 = Z + r1 * n;
     TS s0 = TS(0), s1 = TS(0);
-#pragma unroll 4
+#pragma unroll
     for (int kk = 0; kk < 32; ++kk) {  // columns 0..31: y from y0
       const int k = (lane + kk) & 31;
       const TS yk = shfl_idx(y0, k);
@@ -1958,6 +1966,7 @@ __device__ __forceinline__ void seq_fwd_panel(TS& a0, TS& a1, const TS* Z, TS y0
       s1 = fma(z1[k], yk, s1);
     }
     int k = lane % h;
+#pragma unroll
     for (int kk = 0; kk < h; ++kk) {  // columns 32..n-1: y from y1
       const TS yk = shfl_idx(y1, k);
       s0 = fma(z0[32 + k], yk, s0);
@@ -1969,31 +1978,34 @@ __device__ __forceinline__ void seq_fwd_panel(TS& a0, TS& a1, const TS* Z, TS y0
   }
 }
 
-template <typename TS, int RPL>
+// NT > 0: every system of the launch has n = NT (the loops unroll with
+// constant offsets); NT = 0: n from the descriptor, RPL rows per lane
+template <typename TS, int RPL, int NT>
 __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ descs,
                                                   const Task* __restrict__ tasks, double* b, int ldb,
                                                   const int* skip, Info* info, long long wait_cycles,
-                                                  int unmet) {
+                                                  int unmet, int nbuf) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int sb = (int)sizeof(TS);
   const int lane = threadIdx.x;
   const Task tk = tasks[blockIdx.x];
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
-  const int n = d.n, m = d.m, N = d.N, R = 2 * n + m, mg = m - d.mr;
+  const int n = NT > 0 ? NT : d.n, m = d.m, N = d.N, R = 2 * n + m, mg = m - d.mr;
 #ifdef KKT_DEBUG
   {
     unsigned dyn;
     asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
-    if (!dbg_ok(d.is_top && d.P == 1 && d.level == 1 && tk.seg == 0 && N >= 1 && seq_shape_ok(n, m, sb) &&
-                    n <= 32 * RPL && mg >= 0 && d.nyg_all >= 0 && seq_slice_bytes(n, m, sb) <= (int)dyn,
+    if (!dbg_ok(d.n == n && d.is_top && d.P == 1 && d.level == 1 && tk.seg == 0 && N >= 1 && seq_shape_ok(n, m, sb) &&
+                    n <= 32 * RPL && mg >= 0 && d.nyg_all >= 0 && nbuf >= 2 && nbuf <= kSeqMaxBuf &&
+                    seq_slice_bytes(n, m, sb, nbuf) <= (int)dyn,
                 d))
       return;
   }
 #endif
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);
-  TS* const buf0 = reinterpret_cast<TS*>(smraw + 16);
-  TS* const buf1 = reinterpret_cast<TS*>(smraw + 16 + seq_buf_bytes(n, m, sb));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smraw);  // one mbarrier per buffer
+  const int bufB = seq_buf_bytes(n, m, sb);
+  auto bufp = [&](int q) { return reinterpret_cast<TS*>(smraw + kSeqHeader + q * bufB); };
   const int zo = seq_zoff_bytes(n, sb) / sb;  // panel rows follow the multipliers
   const size_t nn = (size_t)n * n;
   const FactorView<TS> F = factor_view(d, TS(0));
@@ -2001,21 +2013,27 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
   const bool own0 = lane < n, own1 = RPL == 2 && lane + 32 < n;
   const int c0 = own0 ? lane : n - 1, c1 = own1 ? lane + 32 : n - 1;  // rows for addresses
   if (lane == 0) {
-    bulk::init(bar);
-    bulk::init(bar + 1);
+    for (int q = 0; q < nbuf; ++q) bulk::init(bar + q);
     bulk::fence_async();
   }
   __syncwarp();
   uint32_t phase = 0, pend = 0;  // bit q: parity of buffer q's next phase; buffer q's copies in flight
-  // lane 0: stage j's multipliers and panel rows into buffer q
-  auto issue = [&](int j, int q, bool backward) {
-    const int e0 = j < N - 1 ? 0 : n;  // E-hat rows exist above the last stage only
-    const uint32_t bM = (uint32_t)(nn * sb), bZ = (uint32_t)((n + m - e0) * n * sb);
-    TS* B = q ? buf1 : buf0;
-    bulk::fence_async();
-    bulk::expect_tx(bar + q, bM + bZ + (unmet ? 16u : 0u));  // unmet: a phase that never completes
-    bulk::g2s(B, (backward ? F.MR : F.M) + (size_t)j * nn, bM, bar + q);
-    if (bZ) bulk::g2s(B + zo, F.P + ((size_t)j * R + e0) * n, bZ, bar + q);
+  // visit t of the sequence (t < N: forward stage t; else backward stage
+  // 2N - 1 - t) into buffer t % nbuf: lane 0 copies the stage's multipliers
+  // and panel rows; every lane notes the copies in flight
+  auto issue = [&](int t) {
+    const bool backward = t >= N;
+    const int j = backward ? 2 * N - 1 - t : t, q = t & (nbuf - 1);
+    if (lane == 0) {
+      const int e0 = j < N - 1 ? 0 : n;  // E-hat rows exist above the last stage only
+      const uint32_t bM = (uint32_t)(nn * sb), bZ = (uint32_t)((n + m - e0) * n * sb);
+      TS* B = bufp(q);
+      bulk::fence_async();
+      bulk::expect_tx(bar + q, bM + bZ + (unmet ? 16u : 0u));  // unmet: a phase that never completes
+      bulk::g2s(B, (backward ? F.MR : F.M) + (size_t)j * nn, bM, bar + q);
+      if (bZ) bulk::g2s(B + zo, F.P + ((size_t)j * R + e0) * n, bZ, bar + q);
+    }
+    pend |= 1u << q;
   };
   auto wait_buf = [&](int q) -> bool {
     const bool got = __all_sync(0xffffffffu, bulk::wait(bar + q, (phase >> q) & 1u, wait_cycles));
@@ -2029,7 +2047,7 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
   // in this warp's buffers, so wait for them (bounded) before returning
   auto fail = [&](int stage) {
     if (lane == 0) record_timeout(info, d.sys, stage, 1);
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < nbuf; ++q)
       if ((pend >> q) & 1u) (void)bulk::wait(bar + q, (phase >> q) & 1u, wait_cycles);
   };
   auto bval = [&](int j, int r) -> double { return bs[((size_t)j * n + r) * ldb]; };
@@ -2048,22 +2066,16 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
   TS pg[kMaxM];  // this lane's terms of sum_j G-hat_j y_j, per arrow row
 #pragma unroll
   for (int g = 0; g < kMaxM; ++g) pg[g] = TS(0);
-  if (lane == 0) issue(0, 0, false);
-  pend |= 1u;
+  for (int t = 0; t < nbuf - 1 && t < 2 * N; ++t) issue(t);
   for (int j = 0; j < N; ++j) {
-    const int q = j & 1;
+    const int q = j & (nbuf - 1);
     if (!wait_buf(q)) {
       fail(j);
       return;
     }
-    __syncwarp();  // every lane is done with the other buffer (stage j - 1)
-    // next: stage j + 1, or after the last stage the backward sweep's first
-    if (lane == 0) {
-      if (j + 1 < N) issue(j + 1, q ^ 1, false);
-      else issue(N - 1, q ^ 1, true);
-    }
-    pend |= 1u << (q ^ 1);
-    const TS* MT = q ? buf1 : buf0;
+    __syncwarp();  // every lane is done with the buffer of the previous visit
+    if (j + nbuf - 1 < 2 * N) issue(j + nbuf - 1);
+    const TS* MT = bufp(q);
     const TS* Z = MT + zo;
     TS u0 = t0, u1 = t1;
     seq_fwd_chain<TS, RPL>(u0, u1, MT, n, lane);
@@ -2154,17 +2166,14 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
     if (own1) ym1 = bval(N - 3, lane + 32);
   }
   for (int s = 0; s < N; ++s) {
-    const int j = N - 1 - s, q = (N + s) & 1;
+    const int j = N - 1 - s, t = N + s, q = t & (nbuf - 1);
     if (!wait_buf(q)) {
       fail(j);
       return;
     }
     __syncwarp();
-    if (s + 1 < N) {
-      if (lane == 0) issue(j - 1, q ^ 1, true);
-      pend |= 1u << (q ^ 1);
-    }
-    const TS* MR = q ? buf1 : buf0;
+    if (t + nbuf - 1 < 2 * N) issue(t + nbuf - 1);
+    const TS* MR = bufp(q);
     const TS* Z = MR + zo;
     const int e0 = j < N - 1 ? 0 : n;
     const TS* ZG = Z + (size_t)(n - e0) * n;
@@ -2177,7 +2186,7 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
       if (RPL == 2) s1 = fma(ZG[g * n + c1], xg[g], s1);
     }
     if (e0 == 0) {
-#pragma unroll 4
+#pragma unroll
       for (int r = 0; r < n; ++r) {
         const TS xr = shfl_idx(RPL == 2 && r >= 32 ? xn1 : xn0, r & 31);
         s0b = fma(Z[r * n + c0], xr, s0b);
@@ -2244,6 +2253,8 @@ __global__ void k_axpy(const LevelDesc* __restrict__ descs, const ResTask* __res
 // writes the g-row partials sum_j G_j x_j (m x nr), max|c|, max|x|, max|b|
 // and, with `norms`, the largest stage-row sum of |Psi| and the |G| sums of
 // the g rows; k_residual_final combines them per system.
+// MB: registers for up to MB arrow rows; TWO: some system has n > 32.
+template <int MB, bool TWO>
 __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict__ descs,
                                                   const ResTask* __restrict__ tasks, int ntasks,
                                                   const double* __restrict__ uD, const double* __restrict__ uE,
@@ -2256,7 +2267,8 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
   const ResTask tk = tasks[t];
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
-  if (!dbg_ok(tk.j0 >= 0 && tk.j0 < d.N && d.n <= kMaxN && d.m <= kMaxM && tk.part < tk.nparts, d)) return;
+  if (!dbg_ok(tk.j0 >= 0 && tk.j0 < d.N && d.n <= (TWO ? kMaxN : 32) && d.m <= MB && tk.part < tk.nparts, d))
+    return;
   const int n = d.n, m = d.m, N = d.N;
   const int j0 = tk.j0, j1 = min(tk.j0 + kResChunk, N);
   const size_t nn = (size_t)n * n, mn = (size_t)m * n;
@@ -2269,16 +2281,16 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
   const int sj = packed ? lane / n : 0;   // this lane's stage within a pass
   const int i0 = packed ? lane - sj * n : lane, i1 = lane + 32;
   const bool lane_ok = packed ? sj < spw : lane < n;
-  const bool two = n > 32;  // warp-uniform: a second row per lane
+  const bool two = TWO && n > 32;  // warp-uniform: a second row per lane
   const int src0 = packed ? sj * n : 0;  // lane holding row 0 of this lane's stage
   double mr = 0.0, mx = 0.0, mb = 0.0;
   float mrow = 0.0f;
   auto xat = [&](long long row, int col) { return x[(size_t)row * ldx + col]; };
   for (int col = 0; col < nr; ++col) {
     const double xg_l = lane < m ? xat(d.rowG + lane, col) : 0.0;  // x_g, lane q holds row q
-    double gacc[kMaxM];  // this lane's terms of sum_j G_j x_j per g row
+    double gacc[MB];  // this lane's terms of sum_j G_j x_j per g row
 #pragma unroll
-    for (int q = 0; q < kMaxM; ++q) gacc[q] = 0.0;
+    for (int q = 0; q < MB; ++q) gacc[q] = 0.0;
     for (int jb = j0; jb < j1; jb += spw) {
       const int j = jb + sj;
       const bool ok0 = lane_ok && j < j1, ok1 = two && j < j1 && i1 < n;
@@ -2292,9 +2304,10 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
       const double xc0 = ok0 ? xat(rb + i0, col) : 0.0, xc1 = ok1 ? xat(rb + i1, col) : 0.0;
       const double xp0 = (ok0 && hp) ? xat(rb - n + i0, col) : 0.0, xp1 = (ok1 && hp) ? xat(rb - n + i1, col) : 0.0;
       const double xn0 = (ok0 && hn) ? xat(rb + n + i0, col) : 0.0, xn1 = (ok1 && hn) ? xat(rb + n + i1, col) : 0.0;
-      double acc0 = 0.0, acc1 = 0.0;
+      // E_{j-1} x_{j-1}, D_j x_j (lower triangle by symmetry) and E_j^T
+      // x_{j+1} as three independent chains over k, then summed
+      double aP0 = 0.0, aD0 = 0.0, aN0 = 0.0, aP1 = 0.0, aD1 = 0.0, aN1 = 0.0;
       float rs0 = 0.0f, rs1 = 0.0f;
-      // D_j x_j (lower triangle by symmetry), E_{j-1} x_{j-1}, E_j^T x_{j+1}
       for (int k = 0; k < n; ++k) {
         const int sl = packed ? src0 + k : (k & 31);
         const double xk = __shfl_sync(0xffffffffu, k < 32 ? xc0 : xc1, sl);
@@ -2302,23 +2315,24 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
         const double xnk = __shfl_sync(0xffffffffu, k < 32 ? xn0 : xn1, sl);
         const double d0 = k <= a0 ? Dj[a0 * n + k] : Dj[k * n + a0];
         const double p0 = hp ? Ep[a0 * n + k] : 0.0, q0 = hn ? En[k * n + a0] : 0.0;
-        acc0 = fma(d0, xk, acc0);
-        acc0 = fma(p0, xpk, acc0);
-        acc0 = fma(q0, xnk, acc0);
+        aP0 = fma(p0, xpk, aP0);
+        aD0 = fma(d0, xk, aD0);
+        aN0 = fma(q0, xnk, aN0);
         if (norms) rs0 += (abs_lo(d0) + abs_lo(p0)) + abs_lo(q0);
         if (two) {
           const double d1 = k <= a1 ? Dj[a1 * n + k] : Dj[k * n + a1];
           const double p1 = hp ? Ep[a1 * n + k] : 0.0, q1 = hn ? En[k * n + a1] : 0.0;
-          acc1 = fma(d1, xk, acc1);
-          acc1 = fma(p1, xpk, acc1);
-          acc1 = fma(q1, xnk, acc1);
+          aP1 = fma(p1, xpk, aP1);
+          aD1 = fma(d1, xk, aD1);
+          aN1 = fma(q1, xnk, aN1);
           if (norms) rs1 += (abs_lo(d1) + abs_lo(p1)) + abs_lo(q1);
         }
       }
+      double acc0 = (aP0 + aD0) + aN0, acc1 = (aP1 + aD1) + aN1;
       if (m) {
         const double* Gj = G + (size_t)jc * mn;
 #pragma unroll
-        for (int q = 0; q < kMaxM; ++q) {
+        for (int q = 0; q < MB; ++q) {
           if (q >= m) break;  // warp-uniform; full unrolling keeps gacc in registers
           const double xq = __shfl_sync(0xffffffffu, xg_l, q);
           const double g0 = Gj[q * n + a0];
@@ -2348,7 +2362,7 @@ __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict
     }
     // g-row partials of this column: lane sums, then a shuffle tree
 #pragma unroll
-    for (int q = 0; q < kMaxM; ++q) {
+    for (int q = 0; q < MB; ++q) {
       if (q >= m) break;
       double v = gacc[q];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -2846,25 +2860,39 @@ int launch_solve_w(bool backward, const LevelDesc* d, const Task* t, int ntasks,
 }
 
 int launch_seq_solve(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single, double* b,
-                     int ldb, const int* skip, Info* info, long long wait, int unmet, void* stream) {
+                     int ldb, const int* skip, Info* info, long long wait, int unmet, int sms, int uniform,
+                     void* stream) {
   if (ntasks <= 0) return 0;
   const int sb = single ? 4 : 8;
   if (maxn < 2 || maxn % 2 || maxn > kMaxN || maxm < 0 || maxm > kMaxM) return (int)cudaErrorInvalidValue;
-  const size_t sm = (size_t)seq_slice_bytes(maxn, maxm, sb);
+  const int nbuf = seq_nbuf(maxn, maxm, sb, ntasks, sms);
+  const size_t sm = (size_t)seq_slice_bytes(maxn, maxm, sb, nbuf);
+  // block sizes with their own unrolled kernel (every system of the launch the same n)
+  const int nt = uniform && (maxn == 12 || maxn == 24 || maxn == 32 || maxn == 48) ? maxn : 0;
   const bool two = maxn > 32;
-  const void* fn = single ? (two ? (const void*)k_seq_solve<float, 2> : (const void*)k_seq_solve<float, 1>)
-                          : (two ? (const void*)k_seq_solve<double, 2> : (const void*)k_seq_solve<double, 1>);
-  int e = set_smem(fn, sm);
-  if (e) return e;
   cudaStream_t st = (cudaStream_t)stream;
+  auto go = [&](auto kern) -> int {
+    const int e = set_smem((const void*)kern, sm);
+    if (e) return e;
+    kern<<<ntasks, 32, sm, st>>>(d, t, b, ldb, skip, info, wait, unmet, nbuf);
+    return (int)cudaGetLastError();
+  };
   if (single) {
-    if (two) k_seq_solve<float, 2><<<ntasks, 32, sm, st>>>(d, t, b, ldb, skip, info, wait, unmet);
-    else k_seq_solve<float, 1><<<ntasks, 32, sm, st>>>(d, t, b, ldb, skip, info, wait, unmet);
-  } else {
-    if (two) k_seq_solve<double, 2><<<ntasks, 32, sm, st>>>(d, t, b, ldb, skip, info, wait, unmet);
-    else k_seq_solve<double, 1><<<ntasks, 32, sm, st>>>(d, t, b, ldb, skip, info, wait, unmet);
+    switch (nt) {
+      case 12: return go(k_seq_solve<float, 1, 12>);
+      case 24: return go(k_seq_solve<float, 1, 24>);
+      case 32: return go(k_seq_solve<float, 1, 32>);
+      case 48: return go(k_seq_solve<float, 2, 48>);
+      default: return two ? go(k_seq_solve<float, 2, 0>) : go(k_seq_solve<float, 1, 0>);
+    }
   }
-  return (int)cudaGetLastError();
+  switch (nt) {
+    case 12: return go(k_seq_solve<double, 1, 12>);
+    case 24: return go(k_seq_solve<double, 1, 24>);
+    case 32: return go(k_seq_solve<double, 1, 32>);
+    case 48: return go(k_seq_solve<double, 2, 48>);
+    default: return two ? go(k_seq_solve<double, 2, 0>) : go(k_seq_solve<double, 1, 0>);
+  }
 }
 
 int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int ldx, const double* c,
@@ -2922,10 +2950,20 @@ int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const 
 
 int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, const double* D, const double* E,
                     const double* G, const double* b, int ldb, const double* x, int ldx, double* c, int nr,
-                    double* parts, const int* skip, int norms, void* stream) {
+                    double* parts, const int* skip, int norms, void* stream, int two, int maxm) {
   if (ntasks <= 0) return 0;
-  k_residual<<<(ntasks + 7) / 8, 256, 0, (cudaStream_t)stream>>>(d, t, ntasks, D, E, G, b, ldb, x, ldx, c,
-                                                                 nr, parts, skip, norms);
+  cudaStream_t st = (cudaStream_t)stream;
+  const unsigned grid = (unsigned)((ntasks + 7) / 8);
+#define KKT_RES(MB, TW) \
+  k_residual<MB, TW><<<grid, 256, 0, st>>>(d, t, ntasks, D, E, G, b, ldb, x, ldx, c, nr, parts, skip, norms)
+  if (maxm <= 4) {
+    if (two) KKT_RES(4, true); else KKT_RES(4, false);
+  } else if (maxm <= 8) {
+    if (two) KKT_RES(8, true); else KKT_RES(8, false);
+  } else {
+    if (two) KKT_RES(kMaxM, true); else KKT_RES(kMaxM, false);
+  }
+#undef KKT_RES
   return (int)cudaGetLastError();
 }
 

@@ -258,3 +258,64 @@ def test_refinement_stall_falls_back_to_pcg(kkt, orc, kind, N, n, m, sigma):
             assert eta_dev <= 1e-14
     assert ratios[0] > 10.0, ratios      # the classic sweeps stall
     assert ratios[12] <= 10.0, ratios    # the fallback reaches the FP64 path's residual
+
+
+@pytest.mark.parametrize("N,n,m,levels", [(60, 6, 2, [6, 1]), (80, 12, 4, [8, 1]), (30, 16, 0, [3, 1]),
+                                          (40, 48, 4, [4, 1]), (50, 33, 3, [5, 1])])
+def test_one_column_residual_matches_chunked(kkt, orc, N, n, m, levels):
+    """A one-column refinement (the residual kernel that stages the blocks in
+    shared memory) and the same column inside a chunk of three (the kernel
+    for several columns) run the same substitutions on plans with fill-in
+    rows and the same residual arithmetic term for term: x and every sweep's
+    eta agree bit for bit, for packed small blocks (several stages per warp),
+    two rows per lane (n > 32) and m = 0."""
+    import torch
+    D, E, G, R = gen.ipm(N, n, m, seed=N + n, sigma_decades=4.0)
+    b = gen.rhs(N * n + m, 3, seed=5).reshape(N * n + m, 3)
+    h = kkt.kkt_create_plan(N, n, m, levels, kkt.KKT_PARTITION_BALANCED, kkt.KKT_MIXED_FP32_ALL)
+    try:
+        Dd, Ed = dev(D), dev(E)
+        Gd, Rd = (dev(G), dev(R)) if m else (None, None)
+        kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+        x3 = torch.zeros((N * n + m, 3), dtype=torch.float64, device="cuda")
+        kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, dev(b), x3, sweeps=4, tol=-1.0)
+        x1 = torch.zeros(N * n + m, dtype=torch.float64, device="cuda")
+        kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, dev(np.ascontiguousarray(b[:, 1])), x1, sweeps=4, tol=-1.0)
+        torch.cuda.synchronize()
+        assert kkt.kkt_get_info(h)["status"] == 0
+        x3, x1 = x3.cpu().numpy(), x1.cpu().numpy()
+    finally:
+        kkt.kkt_destroy(h)
+    np.testing.assert_array_equal(x3[:, 1], x1)
+    assert orc.block_backward_error(D, E, G, R, x1, b[:, 1]) <= 1e-14
+
+
+def test_one_column_residual_uneven_batch(kkt, orc):
+    """The one-column residual on an uneven batch (block sizes 6 to 48, one
+    launch over every system's chunks) against the chunked kernel, bit for
+    bit, and the oracle's backward error."""
+    import torch
+    shapes = [(40, 6, 2, 4), (33, 12, 0, 3), (25, 48, 4, 3), (60, 24, 4, 6), (17, 33, 3, 2), (9, 16, 1, 2)]
+    systems = [gen.ipm(N, n, m, seed=70 + i, sigma_decades=4.0) for i, (N, n, m, _) in enumerate(shapes)]
+    Ns, ns, ms, Ps = (list(v) for v in zip(*shapes))
+    cat = lambda i: dev(np.concatenate([s[i].ravel() for s in systems] + [np.zeros(1)]))
+    D, E, G, R = cat(0), cat(1), cat(2), cat(3)
+    rows = sum(N * n + m for N, n, m, _ in shapes)
+    b = gen.rhs(rows, 3, seed=9).reshape(rows, 3)
+    h = kkt.kkt_batch_create(Ns, ns, ms, Ps, kkt.KKT_MIXED_FP32_ALL)
+    try:
+        kkt.kkt_factor(h, D, E, G, R)
+        x3 = torch.zeros((rows, 3), dtype=torch.float64, device="cuda")
+        kkt.kkt_solve_refined(h, D, E, G, R, dev(b), x3, sweeps=4, tol=-1.0)
+        x1 = torch.zeros(rows, dtype=torch.float64, device="cuda")
+        kkt.kkt_solve_refined(h, D, E, G, R, dev(np.ascontiguousarray(b[:, 2])), x1, sweeps=4, tol=-1.0)
+        torch.cuda.synchronize()
+        assert kkt.kkt_get_info(h)["status"] == 0
+        off = kkt.kkt_batch_offsets(h, len(shapes))["b"]
+        x3, x1 = x3.cpu().numpy(), x1.cpu().numpy()
+    finally:
+        kkt.kkt_destroy(h)
+    np.testing.assert_array_equal(x3[:, 2], x1)
+    for i, s in enumerate(systems):
+        xi, bi = x1[off[i]:off[i + 1]], b[off[i]:off[i + 1], 2]
+        assert orc.block_backward_error(*s, xi, bi) <= 1e-14
