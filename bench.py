@@ -542,6 +542,8 @@ def measure_batch(name, args, world, rank, local, host_check=64, paths=None):
         tune_s = time.perf_counter() - t0
         if persist:     # one persistent launch for the factorization (ticket queue, longest first)
             kkt.kkt_set_persistent(h, True)
+        if mixed and adjoint:   # the adjoint's refinement stops at the forward solve's tolerance
+            kkt.kkt_set_refine_tol(h, args.tol)
         b = b0.clone()
         x = torch.zeros_like(b0)
         bb = torch.empty_like(b0)
@@ -851,6 +853,7 @@ def run_profile_case(name):
             kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=2, tol=0.0)
         elif name in ("adjoint128_mixed", "adjoint512_mixed"):
             kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=8, tol=1e-16)
+            kkt.kkt_set_refine_tol(h, 1e-16)
             kkt.kkt_solve_adjoint(h, x, x, bb, gD, gE, gG, gR, D=D, E=E, G=G, R=R, sweeps=8)
         else:
             x.copy_(b)

@@ -297,6 +297,13 @@ kkt_status kkt_solve_adjoint(kkt_handle* h, const double* D, const double* E, co
                              double* bbar, int ldbb, int nrhs, double* dD, double* dE, double* dG,
                              double* dR, int sweeps, void* stream);
 
+/* Refinement tolerance of kkt_solve_adjoint on a mixed factor (its tol
+ * argument to kkt_solve_refined; same meaning): 0, the default, refines each
+ * system until its eta stops falling; a value such as 1e-16 stops a system
+ * as soon as its eta is at or below it, which saves the sweep that only
+ * confirms the floor. NaN gives KKT_ERR_ARG. */
+kkt_status kkt_set_refine_tol(kkt_handle* h, double tol);
+
 /* Fallback of kkt_solve_refined for systems whose refinement stalls:
  * cg_iters > 0 enables it. A system whose eta, still above the rounding
  * level, is not at least halved by a sweep is taken out of the classic sweeps

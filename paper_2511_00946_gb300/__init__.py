@@ -29,7 +29,7 @@ RHS_CHUNK = 16
 
 EXPORTED = [
     "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_batch_create_tuned", "kkt_destroy",
-    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_factor_solve", "kkt_factor_solve_host", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta",
+    "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_factor_solve", "kkt_factor_solve_host", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta", "kkt_set_refine_tol",
     "kkt_get_info",
     "kkt_get_factor", "kkt_set_pairing", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
     "kkt_set_persistent", "kkt_set_wait_limit", "kkt_set_refine_fallback",
@@ -84,6 +84,7 @@ _sig = {
     "kkt_set_persistent": [_vp, _i],
     "kkt_set_wait_limit": [_vp, ctypes.c_longlong, _i],
     "kkt_set_refine_fallback": [_vp, _i],
+    "kkt_set_refine_tol": [_vp, ctypes.c_double],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -331,6 +332,12 @@ def kkt_set_wait_limit(h: int, cycles: int, unmet: bool = False) -> None:
     _check(_lib.kkt_set_wait_limit(h, int(cycles), int(bool(unmet))), "kkt_set_wait_limit")
 
 
+def kkt_set_refine_tol(h: int, tol: float) -> None:
+    """Refinement tolerance of kkt_solve_adjoint on a mixed factor (0: until
+    eta stops falling)."""
+    _check(_lib.kkt_set_refine_tol(h, float(tol)), "kkt_set_refine_tol")
+
+
 def kkt_set_refine_fallback(h: int, cg_iters: int) -> None:
     """Preconditioned conjugate-gradient fallback of kkt_solve_refined for
     systems whose refinement stalls (cg_iters = 0 disables it)."""
@@ -398,7 +405,7 @@ def _autograd_function():
             kkt_factor(solver.h, D, E, G, R)
             x = torch.empty_like(b)
             if solver.mixed:
-                kkt_solve_refined(solver.h, D, E, G, R, b, x, sweeps=solver.sweeps, tol=0.0)
+                kkt_solve_refined(solver.h, D, E, G, R, b, x, sweeps=solver.sweeps, tol=solver.tol)
             else:
                 x.copy_(b)
                 kkt_solve(solver.h, x)
@@ -443,14 +450,16 @@ class KKTSolver:
     torch stream."""
 
     def __init__(self, N, n, m, P=1, precision=KKT_FP64, levels=None, partition=KKT_PARTITION_BALANCED,
-                 sweeps=4):
+                 sweeps=4, tol=0.0):
         self.N, self.n, self.m = N, n, m
         self.mixed = precision != KKT_FP64
         self.sweeps = sweeps
+        self.tol = tol  # refinement tolerance of the forward and adjoint solves (mixed)
         if levels is not None:
             self.h = kkt_create_plan(N, n, m, levels, partition, precision)
         else:
             self.h = kkt_create(N, n, m, P, precision)
+        kkt_set_refine_tol(self.h, tol)
 
     def factor(self, D, E, G=None, R=None, stream=None):
         kkt_factor(self.h, D, E, G, R, stream)

@@ -207,6 +207,7 @@ struct kkt_handle {
   // gradients for stalled systems, its vectors and per-system scalars
   int cg_iters = 0;
   int res_two = 0;  // some system has n > 32 (two rows per lane in the residual)
+  double adj_tol = 0.0;  // refinement tolerance of kkt_solve_adjoint on a mixed factor
   void* cg_mem = nullptr;
   double *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_rho0 = nullptr, *cg_rho1 = nullptr,
          *cg_pq = nullptr, *cg_eta = nullptr;
@@ -1408,6 +1409,12 @@ kkt_status refine_fallback(kkt_handle* h, const double* D, const double* E, cons
 }
 }  // namespace
 
+kkt_status kkt_set_refine_tol(kkt_handle* h, double tol) {
+  if (!h || !(tol == tol)) return KKT_ERR_ARG;
+  h->adj_tol = tol;
+  return KKT_OK;
+}
+
 kkt_status kkt_set_refine_fallback(kkt_handle* h, int cg_iters) {
   if (!h || cg_iters < 0 || cg_iters > 256) return KKT_ERR_ARG;
   if (cg_iters > 0 && !h->cg_mem) {
@@ -1486,7 +1493,7 @@ kkt_status kkt_solve_adjoint(kkt_handle* h, const double* D, const double* E, co
   if (mixed) {
     if (!D || (h->tot_E > 0 && !E) || (h->maxm > 0 && (!G || !R))) return KKT_ERR_ARG;
     const kkt_status st = kkt_solve_refined(h, D, E, G, R, xbar, ldxb, bbar, ldbb, nrhs,
-                                            sweeps < 1 ? 4 : sweeps, 0.0, stream);
+                                            sweeps < 1 ? 4 : sweeps, h->adj_tol, stream);
     if (st != KKT_OK) return st;
   } else {
     if (cudaMemcpy2DAsync(bbar, sizeof(double) * ldbb, xbar, sizeof(double) * ldxb, sizeof(double) * nrhs,

@@ -113,6 +113,11 @@ def test_invalid_arguments(kkt):
     with pytest.raises(kkt.KKTError):
         kkt.kkt_plan_flops(0, 4, 0, [1])
     assert kkt.status_string(kkt.KKT_ERR_NOT_SPD).startswith("pivot")
+    for setter, args in ((kkt.kkt_set_refine_tol, (1e-16,)), (kkt.kkt_set_refine_fallback, (4,)),
+                         (kkt.kkt_set_persistent, (True,)), (kkt.kkt_set_wait_limit, (1 << 20,))):
+        with pytest.raises(kkt.KKTError) as ei:   # no handle: refused before any device work
+            setter(None, *args)
+        assert ei.value.status == kkt.KKT_ERR_ARG
 
 
 def test_recursive_plan_flops(kkt):
