@@ -219,12 +219,13 @@ __host__ __device__ inline SolLayout sol_layout(int n, int m, int sb, bool fill 
 // filled by bulk copies. sb = bytes per element (8 FP64, 4 FP32).
 constexpr int kSeqMaxBuf = 4;
 constexpr int kSeqHeader = 8 * kSeqMaxBuf;
+constexpr int kSeqRing = 4;  // slots of right-hand-side rows (64 doubles each) after the buffers
 __host__ __device__ inline int seq_zoff_bytes(int n, int sb) { return kkt_align16(sb * n * n); }
 __host__ __device__ inline int seq_buf_bytes(int n, int m, int sb) {
   return seq_zoff_bytes(n, sb) + kkt_align16(sb * (n + m) * n);
 }
 __host__ __device__ inline int seq_slice_bytes(int n, int m, int sb, int nbuf) {
-  return kSeqHeader + nbuf * seq_buf_bytes(n, m, sb);
+  return kSeqHeader + nbuf * seq_buf_bytes(n, m, sb) + kSeqRing * 64 * 8;
 }
 // Copies in flight: the deepest pipeline (up to kSeqMaxBuf buffers) with
 // which every task of the launch still finds a place in the first wave

@@ -1421,6 +1421,8 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// every group but the two most recent ones complete
+__device__ __forceinline__ void cp_async_wait_2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
 // t <- L^{-1} t (forward) or t <- L^{-T} t (backward) for nr columns, one
 // warp per column (warp-synchronous: shuffles, no block barriers). Rows i
@@ -1851,7 +1853,9 @@ __global__ void __launch_bounds__(256) k_backward_w(const LevelDesc* __restrict_
 // diagonal (lane r reads column (r + kk) mod n of row r at step kk). The
 // arrow rows' sums sum_j G-hat_j y_j stay in registers over the forward
 // sweep (per lane, over its own rows) and are reduced across the warp once,
-// before the corner. b is read two stages ahead.
+// before the corner. The right-hand side (forward) and y (backward) rows of
+// the stages three ahead stream into a ring of shared-memory slots by
+// cp.async, so no register waits on a load in flight.
 // ---------------------------------------------------------------------------
 
 // forward chain u_r -= (L_rc / L_cc) u_c for c < r; MT holds column c of L
@@ -2049,20 +2053,31 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
     if (lane == 0) record_timeout(info, d.sys, stage, 1);
     for (int q = 0; q < nbuf; ++q)
       if ((pend >> q) & 1u) (void)bulk::wait(bar + q, (phase >> q) & 1u, wait_cycles);
+    cp_async_wait_all();  // the ring's copies too
   };
-  auto bval = [&](int j, int r) -> double { return bs[((size_t)j * n + r) * ldb]; };
+  // ring of kSeqRing slots (rows lane and lane + 32 of one stage each);
+  // stage j's rows of bs go to slot j % kSeqRing, one commit group per stage
+  double* const ring = reinterpret_cast<double*>(smraw + kSeqHeader + nbuf * bufB);
+  auto ring_load = [&](int j) {
+    if (j >= 0 && j < N) {
+      double* sl = ring + (j & (kSeqRing - 1)) * 64;
+      if (own0) cp_async_elem(sl + lane, bs + ((size_t)j * n + lane) * ldb);
+      if (own1) cp_async_elem(sl + 32 + lane, bs + ((size_t)j * n + lane + 32) * ldb);
+    }
+    cp_async_commit();
+  };
+  auto ring_get = [&](int j, TS& v0, TS& v1) {  // after the wait for stage j's group
+    const double* sl = ring + (j & (kSeqRing - 1)) * 64;
+    v0 = own0 ? (TS)sl[lane] : TS(0);
+    v1 = own1 ? (TS)sl[32 + lane] : TS(0);
+  };
+  constexpr int kAhead = kSeqRing - 1;  // stages in flight besides the one read
 
   // ---- forward sweep (Algorithm 2): L y = b
-  TS t0 = own0 ? (TS)bval(0, lane) : TS(0), t1 = own1 ? (TS)bval(0, lane + 32) : TS(0);
-  double bn0 = 0.0, bn1 = 0.0, bm0 = 0.0, bm1 = 0.0;  // b of stages j + 1 and j + 2
-  if (N > 1) {
-    if (own0) bn0 = bval(1, lane);
-    if (own1) bn1 = bval(1, lane + 32);
-  }
-  if (N > 2) {
-    if (own0) bm0 = bval(2, lane);
-    if (own1) bm1 = bval(2, lane + 32);
-  }
+  for (int jj = 0; jj < kAhead; ++jj) ring_load(jj);
+  cp_async_wait_2();
+  TS t0, t1;
+  ring_get(0, t0, t1);
   TS pg[kMaxM];  // this lane's terms of sum_j G-hat_j y_j, per arrow row
 #pragma unroll
   for (int g = 0; g < kMaxM; ++g) pg[g] = TS(0);
@@ -2075,6 +2090,7 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
     }
     __syncwarp();  // every lane is done with the buffer of the previous visit
     if (j + nbuf - 1 < 2 * N) issue(j + nbuf - 1);
+    ring_load(j + kAhead);
     const TS* MT = bufp(q);
     const TS* Z = MT + zo;
     TS u0 = t0, u1 = t1;
@@ -2094,14 +2110,11 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
     if (j + 1 < N) {  // t_{j+1} = b_{j+1} - E-hat_j y_j
       TS a0, a1;
       seq_fwd_panel<TS, RPL>(a0, a1, Z, y0, y1, n, lane);
-      t0 = (TS)bn0 - a0;
-      t1 = (TS)bn1 - a1;
-      bn0 = bm0;
-      bn1 = bm1;
-      if (j + 3 < N) {
-        if (own0) bm0 = bval(j + 3, lane);
-        if (own1) bm1 = bval(j + 3, lane + 32);
-      }
+      cp_async_wait_2();  // stage j + 1's group (two newer ones may be in flight)
+      TS bn0, bn1;
+      ring_get(j + 1, bn0, bn1);
+      t0 = bn0 - a0;
+      t1 = bn1 - a1;
     }
   }
 
@@ -2155,16 +2168,11 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
 
   // ---- backward sweep (Algorithm 3): L^T x = y
   TS xn0 = TS(0), xn1 = TS(0);  // x of stage j + 1
-  TS yc0 = own0 ? (TS)bval(N - 1, lane) : TS(0), yc1 = own1 ? (TS)bval(N - 1, lane + 32) : TS(0);
-  double yn0 = 0.0, yn1 = 0.0, ym0 = 0.0, ym1 = 0.0;  // y of stages j - 1 and j - 2
-  if (N > 1) {
-    if (own0) yn0 = bval(N - 2, lane);
-    if (own1) yn1 = bval(N - 2, lane + 32);
-  }
-  if (N > 2) {
-    if (own0) ym0 = bval(N - 3, lane);
-    if (own1) ym1 = bval(N - 3, lane + 32);
-  }
+  __threadfence_block();  // this lane's y stores before its asynchronous reads of them
+  for (int jj = 0; jj < kAhead; ++jj) ring_load(N - 1 - jj);
+  cp_async_wait_2();
+  TS yc0, yc1;
+  ring_get(N - 1, yc0, yc1);
   for (int s = 0; s < N; ++s) {
     const int j = N - 1 - s, t = N + s, q = t & (nbuf - 1);
     if (!wait_buf(q)) {
@@ -2173,6 +2181,7 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
     }
     __syncwarp();
     if (t + nbuf - 1 < 2 * N) issue(t + nbuf - 1);
+    ring_load(j - kAhead);
     const TS* MR = bufp(q);
     const TS* Z = MR + zo;
     const int e0 = j < N - 1 ? 0 : n;
@@ -2199,15 +2208,12 @@ __global__ void __launch_bounds__(32) k_seq_solve(const LevelDesc* __restrict__ 
     xn1 = u1 * MR[c1 * n + c1];
     if (own0) bs[((size_t)j * n + lane) * ldb] = (double)xn0;
     if (own1) bs[((size_t)j * n + lane + 32) * ldb] = (double)xn1;
-    yc0 = (TS)yn0;
-    yc1 = (TS)yn1;
-    yn0 = ym0;
-    yn1 = ym1;
-    if (j - 3 >= 0) {
-      if (own0) ym0 = bval(j - 3, lane);
-      if (own1) ym1 = bval(j - 3, lane + 32);
+    if (j > 0) {
+      cp_async_wait_2();  // stage j - 1's group
+      ring_get(j - 1, yc0, yc1);
     }
   }
+  cp_async_wait_all();  // (only empty groups remain)
 }
 
 // ---------------------------------------------------------------------------
