@@ -392,8 +392,11 @@ def per_launch_flops(kkt, plan, partition, nrhs=1):
 
 
 def candidate_plans(kkt, partition):
+    # four-fold reductions per level, and halving ones (more levels, two stages per deep segment)
     plans = [[304, 76, 19, 6, 2, 1], [256, 64, 16, 4, 1], [304, 76, 19, 5, 1], [256, 64, 16, 4, 2, 1],
-             [304, 76, 19, 9, 3, 1], [304, 76, 25, 8, 2, 1], [152, 38, 10, 3, 1], [228, 57, 14, 3, 1]]
+             [304, 76, 19, 9, 3, 1], [304, 76, 25, 8, 2, 1], [152, 38, 10, 3, 1], [228, 57, 14, 3, 1],
+             [256, 128, 64, 32, 16, 8, 4, 2, 1], [288, 144, 72, 36, 18, 9, 4, 2, 1],
+             [320, 160, 80, 40, 20, 10, 5, 2, 1], [256, 128, 64, 32, 16, 8, 4, 1]]
     ok = []
     for p in plans:
         try:
