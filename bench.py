@@ -396,7 +396,9 @@ def candidate_plans(kkt, partition):
     plans = [[304, 76, 19, 6, 2, 1], [256, 64, 16, 4, 1], [304, 76, 19, 5, 1], [256, 64, 16, 4, 2, 1],
              [304, 76, 19, 9, 3, 1], [304, 76, 25, 8, 2, 1], [152, 38, 10, 3, 1], [228, 57, 14, 3, 1],
              [256, 128, 64, 32, 16, 8, 4, 2, 1], [288, 144, 72, 36, 18, 9, 4, 2, 1],
-             [320, 160, 80, 40, 20, 10, 5, 2, 1], [256, 128, 64, 32, 16, 8, 4, 1]]
+             [320, 160, 80, 40, 20, 10, 5, 2, 1], [256, 128, 64, 32, 16, 8, 4, 1],
+             [304, 152, 76, 38, 19, 9, 4, 2, 1], [304, 152, 76, 38, 19, 9, 4, 1],
+             [304, 152, 76, 38, 19, 9, 3, 1]]
     ok = []
     for p in plans:
         try:
@@ -820,6 +822,8 @@ PROFILE_CASES = {
     "adjoint512_mixed": "the differentiable workload's 512 systems, FP32 mixed: factor + refined solve + refined "
                         "adjoint (tol 1e-16, at most 8 sweeps each)",
     "uneven512": "512 systems of the uneven workload's shapes, FP64, persistent factorization + solve",
+    "uneven4096_mixed": "the uneven workload's 4096 systems, FP32 mixed, persistent factorization + refined "
+                        "solve (tol 1e-16, at most 8 sweeps)",
 }
 
 
@@ -836,16 +840,17 @@ def run_profile_case(name):
         c = 512 if name == "adjoint512_mixed" else 128
         Ns, ns, ms = [256] * c, [32] * c, [8] * c
         D, E, G, R = gdev.batch(Ns, ns, ms, seed=1, kind="ipm", sigma_decades=8.0)
-    elif name == "uneven512":
-        Ns, ns, ms = (v[:512] for v in batch_shapes("uneven4096"))
+    elif name in ("uneven512", "uneven4096_mixed"):
+        Ns, ns, ms = (v[:512] if name == "uneven512" else v for v in batch_shapes("uneven4096"))
         c = len(Ns)
         D, E, G, R = gdev.batch(Ns, ns, ms, seed=1, kind="ipm", sigma_decades=6.0, psd_couplings=True)
     else:
         raise ValueError(name)
     b = gdev.rhs(int(sum(N * n + m for N, n, m in zip(Ns, ns, ms))), 1, seed=2)
-    prec = kkt.KKT_MIXED_FP32_ALL if name in ("mixed48", "adjoint128_mixed", "adjoint512_mixed") else kkt.KKT_FP64
+    prec = (kkt.KKT_MIXED_FP32_ALL if name in ("mixed48", "adjoint128_mixed", "adjoint512_mixed", "uneven4096_mixed")
+            else kkt.KKT_FP64)
     h = kkt.kkt_batch_create(Ns, ns, ms, [1] * c, prec)
-    if name == "uneven512":
+    if name in ("uneven512", "uneven4096_mixed"):
         kkt.kkt_set_persistent(h, True)
     x = torch.zeros_like(b)
     gD, gE, gG, gR = (torch.empty_like(t) for t in (D, E, G, R))
@@ -854,6 +859,8 @@ def run_profile_case(name):
         kkt.kkt_factor(h, D, E, G, R)
         if name == "mixed48":
             kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=2, tol=0.0)
+        elif name == "uneven4096_mixed":
+            kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=8, tol=1e-16)
         elif name in ("adjoint128_mixed", "adjoint512_mixed"):
             kkt.kkt_solve_refined(h, D, E, G, R, b, x, sweeps=8, tol=1e-16)
             kkt.kkt_set_refine_tol(h, 1e-16)

@@ -206,7 +206,7 @@ struct kkt_handle {
   // refinement fallback (kkt_set_refine_fallback): preconditioned conjugate
   // gradients for stalled systems, its vectors and per-system scalars
   int cg_iters = 0;
-  int res_two = 0;  // some system has n > 32 (two rows per lane in the residual)
+  int res_xs = 1;  // x rows the residual kernel stages per warp (the largest res_xs_doubles)
   double adj_tol = 0.0;  // refinement tolerance of kkt_solve_adjoint on a mixed factor
   void* cg_mem = nullptr;
   double *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_rho0 = nullptr, *cg_rho1 = nullptr,
@@ -598,7 +598,7 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
   h->level_top.assign(h->maxL, 0);
   for (const SysPlan& sp : h->sys) {
     h->level_top[sp.lv.size() - 1] = 1;
-    h->res_two = h->res_two || sp.n > 32;
+    h->res_xs = std::max(h->res_xs, kkt::res_xs_doubles(sp.n));
   }
   if (!tasks.empty())
     ok = ok && cudaMemcpy(h->dtasks, tasks.data(), sizeof(Task) * tasks.size(),
@@ -1374,7 +1374,7 @@ kkt_status refine_fallback(kkt_handle* h, const double* D, const double* E, cons
   const size_t vec = sizeof(double) * h->tot_B * CH;
   auto matvec = [&](const double* v, double* out) {  // out = -Psi v (b = 0)
     return kkt::launch_residual(h->ddesc, h->dres, nres, D, E, G, nullptr, 1, v, CH, out, nr, h->dparts,
-                                h->cg_skip, 0, stream, h->res_two, h->maxm) == 0 &&
+                                h->cg_skip, 0, stream, h->res_xs, h->maxm) == 0 &&
            kkt::launch_residual_final(h->ddesc, h->dsys_desc, h->dpart0, cnt, G, R, nullptr, 1, v, CH, out, nr,
                                       h->dparts, -1.0, h->cg_eta, nullptr, h->cg_skip, stream) == 0;
   };
@@ -1401,7 +1401,7 @@ kkt_status refine_fallback(kkt_handle* h, const double* D, const double* E, cons
   // the true residual and eta of the fallback's systems
   ok = ok &&
        kkt::launch_residual(h->ddesc, h->dres, nres, D, E, G, b, ldb, x, ldx, h->dcorr, nr, h->dparts, h->cg_skip, 0,
-                            stream, h->res_two, h->maxm) == 0 &&
+                            stream, h->res_xs, h->maxm) == 0 &&
        kkt::launch_residual_final(h->ddesc, h->dsys_desc, h->dpart0, cnt, G, R, b, ldb, x, ldx, h->dcorr, nr,
                                   h->dparts, -1.0, h->deta + (size_t)(sweeps - 1) * cnt, nullptr, h->cg_skip,
                                   stream) == 0;
@@ -1462,7 +1462,7 @@ kkt_status kkt_solve_refined(kkt_handle* h, const double* D, const double* E, co
       if (s2 != KKT_OK) return s2;
       if (kkt::launch_axpy(h->ddesc, h->dres, nres, x + c0, ldx, h->dcorr, nr, h->dconv, stream) ||
           kkt::launch_residual(h->ddesc, h->dres, nres, D, E, G, b + c0, ldb, x + c0, ldx, h->dcorr, nr,
-                               h->dparts, h->dconv, c0 == 0 && sw == 0, stream, h->res_two, h->maxm) ||
+                               h->dparts, h->dconv, c0 == 0 && sw == 0, stream, h->res_xs, h->maxm) ||
           kkt::launch_residual_final(h->ddesc, h->dsys_desc, h->dpart0, h->count, G, R, b + c0, ldb,
                                      x + c0, ldx, h->dcorr, nr, h->dparts, tol,
                                      h->deta + (size_t)sw * h->count,

@@ -245,9 +245,24 @@ __host__ __device__ inline bool seq_shape_ok(int n, int m, int sb) {
   return n >= 2 && n % 2 == 0 && n <= kMaxN && m <= kMaxM && (sb == 8 || (m * n) % 4 == 0);
 }
 
+// Residual kernel: stages per pass, as many (up to kResChunk) as fill the
+// most lanes with up to three rows each (an FP64 instruction costs its issue
+// slot with or without a row in the lane), and the x rows it stages per warp
+// (the pass and one stage on either side).
+constexpr int kResChunkStages = 8;  // (= kResChunk, defined below)
+__host__ __device__ inline int res_spw(int n) {
+  int best = 1, bn = 0, bd = 1;  // utilisation bn / bd of the best count so far
+  for (int s = 1; s <= kResChunkStages && s * n <= 96; ++s) {
+    const int rows = s * n, cap = 32 * ((rows + 31) / 32);
+    if (rows * bd > bn * cap) { best = s; bn = rows; bd = cap; }
+  }
+  return best;
+}
+__host__ __device__ inline int res_xs_doubles(int n) { return (res_spw(n) + 2) * n; }
+
 // Residual pass of iterative refinement: one CTA per chunk of kResChunk
 // stages of one system.
-constexpr int kResChunk = 8;
+constexpr int kResChunk = kResChunkStages;
 struct ResTask {
   int desc;   // level-1 descriptor of the system
   int j0;     // first stage of the chunk
@@ -312,10 +327,11 @@ int launch_axpy(const LevelDesc* d, const ResTask* t, int ntasks, double* x, int
 // c = b - Psi x over the stage rows of each task (+ partials for the g rows
 // and the max norms; the row sums of |Psi| only when `norms`, otherwise the
 // values of an earlier call stay in `parts`); c has leading dimension kRhsChunk
-// (`two`: some system has n > 32; maxm: the largest m over the systems)
+// (xs_doubles: the largest res_xs_doubles over the systems, per warp; maxm:
+// the largest m over the systems)
 int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, const double* D, const double* E,
                     const double* G, const double* b, int ldb, const double* x, int ldx, double* c, int nr,
-                    double* parts, const int* skip, int norms, void* stream, int two = 1,
+                    double* parts, const int* skip, int norms, void* stream, int xs_doubles,
                     int maxm = kMaxM);
 // g rows of c, eta per system, converged[s] = (eta <= tol); a system that had
 // converged before copies its eta from eta_prev (the previous sweep's; may be null)

@@ -2245,134 +2245,129 @@ __global__ void k_axpy(const LevelDesc* __restrict__ descs, const ResTask* __res
 }
 
 // FP64 residual c = b - Psi x (blocks of Eq. (3)) over the stage rows of one
-// residual task (kResChunk consecutive stages of one system) per warp: a lane
-// owns one row of a stage (row i and i + 32 when n > 32; for n <= 16 the warp
-// takes floor(32/n) stages at a time, lane = (stage, row)) and forms
+// residual task (kResChunk consecutive stages of one system) per warp. A
+// pass takes res_spw(n) consecutive stages, chosen so that their rows fill
+// whole warps (up to three rows per lane: row r of the pass is lane r % 32,
+// slot r / 32), since an FP64 instruction costs its issue slot whether a
+// lane has a row or not. Each lane forms, for each of its rows,
 //   (E_{j-1} x_{j-1} + D_j x_j + E_j^T x_{j+1} + G_j^T x_g)_i
-// from the blocks in global memory (lower triangle of D_j by symmetry), with
-// x_k broadcast by shuffles, so every FP64 instruction has a lane per row
-// and Psi is read once. A matrix-vector product does 2 flop per 8-byte
-// element, more than the FP64 units sustain at full HBM bandwidth on this
-// part, so the kernel keeps FP64 work to the products themselves: the row
-// sums of |Psi| (for eta) are only formed when `norms` is set (the first
-// sweep of a refinement; they depend on the matrix alone). Per task it
-// writes the g-row partials sum_j G_j x_j (m x nr), max|c|, max|x|, max|b|
-// and, with `norms`, the largest stage-row sum of |Psi| and the |G| sums of
-// the g rows; k_residual_final combines them per system.
-// MB: registers for up to MB arrow rows; TWO: some system has n > 32.
-template <int MB, bool TWO>
+// from the blocks in global memory (lower triangle of D_j by symmetry) as
+// three independent FMA chains, with the pass's x rows (and its neighbour
+// stages') staged in shared memory, so Psi is read once. A matrix-vector
+// product does 2 flop per 8-byte element, more than the FP64 units sustain
+// at full HBM bandwidth on this part, so the kernel keeps FP64 work to the
+// products themselves: the row sums of |Psi| (for eta) are only formed when
+// `norms` is set (the first sweep of a refinement; they depend on the matrix
+// alone). Per task it writes the g-row partials sum_j G_j x_j (m x nr),
+// max|c|, max|x|, max|b| and, with `norms`, the largest stage-row sum of
+// |Psi| and the |G| sums of the g rows; k_residual_final combines them per
+// system. MB: registers for up to MB arrow rows.
+template <int MB>
 __global__ void __launch_bounds__(256, 3) k_residual(const LevelDesc* __restrict__ descs,
                                                   const ResTask* __restrict__ tasks, int ntasks,
                                                   const double* __restrict__ uD, const double* __restrict__ uE,
                                                   const double* __restrict__ uG, const double* __restrict__ b,
                                                   int ldb, const double* __restrict__ x, int ldx, double* c,
-                                                  int nr, double* parts, const int* skip, int norms) {
+                                                  int nr, double* parts, const int* skip, int norms,
+                                                  int xs_doubles) {
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31;
   const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (t >= ntasks) return;  // whole warp
   const ResTask tk = tasks[t];
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
-  if (!dbg_ok(tk.j0 >= 0 && tk.j0 < d.N && d.n <= (TWO ? kMaxN : 32) && d.m <= MB && tk.part < tk.nparts, d))
-    return;
   const int n = d.n, m = d.m, N = d.N;
+  const int spw = res_spw(n);  // stages per pass
+  if (!dbg_ok(tk.j0 >= 0 && tk.j0 < d.N && d.n <= kMaxN && d.m <= MB && tk.part < tk.nparts &&
+                  (spw + 2) * n <= xs_doubles,
+              d))
+    return;
   const int j0 = tk.j0, j1 = min(tk.j0 + kResChunk, N);
   const size_t nn = (size_t)n * n, mn = (size_t)m * n;
   const double* D = uD + d.offD;
   const double* E = uE ? uE + d.offE : nullptr;
   const double* G = m ? uG + d.offG : nullptr;
   double* part = parts + (size_t)t * kResPartDoubles;
-  const bool packed = n <= 16;            // several stages per pass
-  const int spw = packed ? 32 / n : 1;    // stages per pass
-  const int sj = packed ? lane / n : 0;   // this lane's stage within a pass
-  const int i0 = packed ? lane - sj * n : lane, i1 = lane + 32;
-  const bool lane_ok = packed ? sj < spw : lane < n;
-  const bool two = TWO && n > 32;  // warp-uniform: a second row per lane
-  const int src0 = packed ? sj * n : 0;  // lane holding row 0 of this lane's stage
+  // x rows of stages jb-1 .. jb+spw of the current pass: xs[(s + 1) n + k] is
+  // row k of stage jb + s (zero outside 0..N-1)
+  double* const xs = reinterpret_cast<double*>(smraw) + (size_t)(threadIdx.x >> 5) * xs_doubles;
+  // this lane's rows of a pass: slot q is pass row lane + 32 q, i.e. row ri[q] of stage si[q]
+  const int rows = spw * n, slots = (rows + 31) >> 5;
+  int si[3], ri[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int r = lane + 32 * q;
+    si[q] = r < rows ? r / n : 0;
+    ri[q] = r < rows ? r - si[q] * n : 0;
+  }
   double mr = 0.0, mx = 0.0, mb = 0.0;
   float mrow = 0.0f;
-  auto xat = [&](long long row, int col) { return x[(size_t)row * ldx + col]; };
   for (int col = 0; col < nr; ++col) {
-    const double xg_l = lane < m ? xat(d.rowG + lane, col) : 0.0;  // x_g, lane q holds row q
+    const double xg_l = lane < m ? x[(size_t)(d.rowG + lane) * ldx + col] : 0.0;  // x_g, lane q holds row q
     double gacc[MB];  // this lane's terms of sum_j G_j x_j per g row
 #pragma unroll
     for (int q = 0; q < MB; ++q) gacc[q] = 0.0;
     for (int jb = j0; jb < j1; jb += spw) {
-      const int j = jb + sj;
-      const bool ok0 = lane_ok && j < j1, ok1 = two && j < j1 && i1 < n;
-      const int jc = ok0 ? j : jb;                 // a valid stage for the addresses
-      const int a0 = ok0 ? i0 : 0, a1 = ok1 ? i1 : 0;
-      const long long rb = d.offB + (long long)jc * n;
-      const double* Dj = D + (size_t)jc * nn;
-      const bool hp = E && jc > 0, hn = E && jc < N - 1;
-      const double* Ep = hp ? E + (size_t)(jc - 1) * nn : D;
-      const double* En = hn ? E + (size_t)jc * nn : D;
-      const double xc0 = ok0 ? xat(rb + i0, col) : 0.0, xc1 = ok1 ? xat(rb + i1, col) : 0.0;
-      const double xp0 = (ok0 && hp) ? xat(rb - n + i0, col) : 0.0, xp1 = (ok1 && hp) ? xat(rb - n + i1, col) : 0.0;
-      const double xn0 = (ok0 && hn) ? xat(rb + n + i0, col) : 0.0, xn1 = (ok1 && hn) ? xat(rb + n + i1, col) : 0.0;
-      // E_{j-1} x_{j-1}, D_j x_j (lower triangle by symmetry) and E_j^T
-      // x_{j+1} as three independent chains over k, then summed
-      double aP0 = 0.0, aD0 = 0.0, aN0 = 0.0, aP1 = 0.0, aD1 = 0.0, aN1 = 0.0;
-      float rs0 = 0.0f, rs1 = 0.0f;
-      for (int k = 0; k < n; ++k) {
-        const int sl = packed ? src0 + k : (k & 31);
-        const double xk = __shfl_sync(0xffffffffu, k < 32 ? xc0 : xc1, sl);
-        const double xpk = __shfl_sync(0xffffffffu, k < 32 ? xp0 : xp1, sl);
-        const double xnk = __shfl_sync(0xffffffffu, k < 32 ? xn0 : xn1, sl);
-        const double d0 = k <= a0 ? Dj[a0 * n + k] : Dj[k * n + a0];
-        const double p0 = hp ? Ep[a0 * n + k] : 0.0, q0 = hn ? En[k * n + a0] : 0.0;
-        aP0 = fma(p0, xpk, aP0);
-        aD0 = fma(d0, xk, aD0);
-        aN0 = fma(q0, xnk, aN0);
-        if (norms) rs0 += (abs_lo(d0) + abs_lo(p0)) + abs_lo(q0);
-        if (two) {
-          const double d1 = k <= a1 ? Dj[a1 * n + k] : Dj[k * n + a1];
-          const double p1 = hp ? Ep[a1 * n + k] : 0.0, q1 = hn ? En[k * n + a1] : 0.0;
-          aP1 = fma(p1, xpk, aP1);
-          aD1 = fma(d1, xk, aD1);
-          aN1 = fma(q1, xnk, aN1);
-          if (norms) rs1 += (abs_lo(d1) + abs_lo(p1)) + abs_lo(q1);
-        }
+      const int cnt = min(spw, j1 - jb);
+      __syncwarp();  // the previous pass is done with xs
+      for (int e = lane; e < (cnt + 2) * n; e += 32) {
+        const int s = e / n - 1, k = e - (s + 1) * n, jj = jb + s;
+        xs[e] = (jj >= 0 && jj < N) ? x[(size_t)(d.offB + (long long)jj * n + k) * ldx + col] : 0.0;
       }
-      double acc0 = (aP0 + aD0) + aN0, acc1 = (aP1 + aD1) + aN1;
-      if (m) {
-        const double* Gj = G + (size_t)jc * mn;
+      __syncwarp();
 #pragma unroll
-        for (int q = 0; q < MB; ++q) {
-          if (q >= m) break;  // warp-uniform; full unrolling keeps gacc in registers
-          const double xq = __shfl_sync(0xffffffffu, xg_l, q);
-          const double g0 = Gj[q * n + a0];
-          acc0 = fma(g0, xq, acc0);
-          gacc[q] = fma(g0, xc0, gacc[q]);  // xc0 = 0 on idle lanes
-          if (norms) rs0 += abs_lo(g0);
-          if (two) {
-            const double g1 = Gj[q * n + a1];
-            acc1 = fma(g1, xq, acc1);
-            gacc[q] = fma(g1, xc1, gacc[q]);
-            if (norms) rs1 += abs_lo(g1);
+      for (int q = 0; q < 3; ++q) {
+        if (q >= slots) break;  // warp-uniform
+        const bool ok = lane + 32 * q < cnt * n;
+        const int s = ok ? si[q] : 0, i = ok ? ri[q] : 0, j = jb + s;
+        const long long rb = d.offB + (long long)j * n;
+        const double* Dj = D + (size_t)j * nn;
+        const bool hp = E && j > 0, hn = E && j < N - 1;
+        const double* Ep = hp ? E + (size_t)(j - 1) * nn : D;
+        const double* En = hn ? E + (size_t)j * nn : D;
+        const double* xp = xs + (size_t)s * n;  // x_{j-1}, x_j, x_{j+1} follow at n apart
+        // E_{j-1} x_{j-1}, D_j x_j (lower triangle by symmetry) and E_j^T
+        // x_{j+1} as three independent chains over k, then summed
+        double aP = 0.0, aD = 0.0, aN = 0.0;
+        float rs = 0.0f;
+        for (int k = 0; k < n; ++k) {
+          const double dv = k <= i ? Dj[i * n + k] : Dj[k * n + i];
+          const double pv = hp ? Ep[i * n + k] : 0.0, qv = hn ? En[k * n + i] : 0.0;
+          aP = fma(pv, xp[k], aP);
+          aD = fma(dv, xp[n + k], aD);
+          aN = fma(qv, xp[2 * n + k], aN);
+          if (norms) rs += (abs_lo(dv) + abs_lo(pv)) + abs_lo(qv);
+        }
+        double acc = (aP + aD) + aN;
+        const double xo = ok ? xp[n + i] : 0.0;  // this row's x
+        if (m) {
+          const double* Gj = G + (size_t)j * mn;
+#pragma unroll
+          for (int g = 0; g < MB; ++g) {
+            if (g >= m) break;  // warp-uniform; full unrolling keeps gacc in registers
+            const double xq = __shfl_sync(0xffffffffu, xg_l, g);
+            const double gv = Gj[g * n + i];
+            acc = fma(gv, xq, acc);
+            gacc[g] = fma(gv, xo, gacc[g]);  // xo = 0 on lanes without a row
+            if (norms) rs += abs_lo(gv);
           }
         }
-      }
-      if (ok0) {
-        const double bv = b ? b[(size_t)(rb + i0) * ldb + col] : 0.0, r = bv - acc0;
-        c[(size_t)(rb + i0) * kRhsChunk + col] = r;
-        mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xc0));
-        if (norms) mrow = fmaxf(mrow, rs0);
-      }
-      if (ok1) {
-        const double bv = b ? b[(size_t)(rb + i1) * ldb + col] : 0.0, r = bv - acc1;
-        c[(size_t)(rb + i1) * kRhsChunk + col] = r;
-        mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xc1));
-        if (norms) mrow = fmaxf(mrow, rs1);
+        if (ok) {
+          const double bv = b ? b[(size_t)(rb + i) * ldb + col] : 0.0, r = bv - acc;
+          c[(size_t)(rb + i) * kRhsChunk + col] = r;
+          mr = fmax(mr, fabs(r)); mb = fmax(mb, fabs(bv)); mx = fmax(mx, fabs(xo));
+          if (norms) mrow = fmaxf(mrow, rs);
+        }
       }
     }
     // g-row partials of this column: lane sums, then a shuffle tree
 #pragma unroll
-    for (int q = 0; q < MB; ++q) {
-      if (q >= m) break;
-      double v = gacc[q];
+    for (int g = 0; g < MB; ++g) {
+      if (g >= m) break;
+      double v = gacc[g];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) part[q * kRhsChunk + col] = v;
+      if (lane == 0) part[g * kRhsChunk + col] = v;
     }
   }
   float gab = 0.0f;  // |G| sum of g row `lane` (lane < m) over the task's stages
@@ -2956,21 +2951,20 @@ int launch_adjoint_grad(const LevelDesc* d, const ResTask* t, int ntasks, const 
 
 int launch_residual(const LevelDesc* d, const ResTask* t, int ntasks, const double* D, const double* E,
                     const double* G, const double* b, int ldb, const double* x, int ldx, double* c, int nr,
-                    double* parts, const int* skip, int norms, void* stream, int two, int maxm) {
+                    double* parts, const int* skip, int norms, void* stream, int xs_doubles, int maxm) {
   if (ntasks <= 0) return 0;
   cudaStream_t st = (cudaStream_t)stream;
   const unsigned grid = (unsigned)((ntasks + 7) / 8);
-#define KKT_RES(MB, TW) \
-  k_residual<MB, TW><<<grid, 256, 0, st>>>(d, t, ntasks, D, E, G, b, ldb, x, ldx, c, nr, parts, skip, norms)
-  if (maxm <= 4) {
-    if (two) KKT_RES(4, true); else KKT_RES(4, false);
-  } else if (maxm <= 8) {
-    if (two) KKT_RES(8, true); else KKT_RES(8, false);
-  } else {
-    if (two) KKT_RES(kMaxM, true); else KKT_RES(kMaxM, false);
-  }
-#undef KKT_RES
-  return (int)cudaGetLastError();
+  const size_t sm = (size_t)8 * xs_doubles * sizeof(double);
+  auto go = [&](auto kern) -> int {
+    const int e = set_smem((const void*)kern, sm);
+    if (e) return e;
+    kern<<<grid, 256, sm, st>>>(d, t, ntasks, D, E, G, b, ldb, x, ldx, c, nr, parts, skip, norms, xs_doubles);
+    return (int)cudaGetLastError();
+  };
+  if (maxm <= 4) return go(k_residual<4>);
+  if (maxm <= 8) return go(k_residual<8>);
+  return go(k_residual<kMaxM>);
 }
 
 int launch_residual_final(const LevelDesc* d, const int* sys_desc, const int* part0, int count,
