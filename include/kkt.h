@@ -206,7 +206,14 @@ kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const dou
 /* Solve Psi x = b with the current factor (Algorithms 2 and 3): b is a
  * device pointer to (N*n+m) rows of ldb >= nrhs doubles (for batches the
  * packed rows of every system), overwritten with x in its first nrhs
- * columns. nrhs >= 1. Asynchronous on `stream`. */
+ * columns. nrhs >= 1. Asynchronous on `stream`.
+ * Systems planned as one level (P = 1) are solved with one right-hand side
+ * by one warp each (forward sweep, corner and backward sweep, the stage
+ * blocks streamed by bulk copies; their waits are bounded as described at
+ * kkt_set_wait_limit and a timeout is reported through kkt_get_info); with
+ * several right-hand sides, for odd n, or for other plans by the segment
+ * kernels, whose panel products sum in another order: a column solved alone
+ * and in a chunk of several then agree to rounding, not bit for bit. */
 kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream);
 
 /* Factor Psi and solve Psi x = b in one pass (kkt_factor followed by
