@@ -744,6 +744,11 @@ struct FacCtx {
   __device__ const double* Dp(const double* b, int j) const { return b ? b + (size_t)j * nn : nullptr; }
   __device__ const double* Gp(const double* b, int j) const { return b ? b + (size_t)j * mn : nullptr; }
 
+  // the pivot block D_j (on levels >= 2 the sum of its two slots) into dst (ld ldD)
+  __device__ void load_D(double* dst, int j, Grp G) const {
+    load_blk<LU>(dst, ldD, Dp(Din, j), Dp(D2, j), n, n, false, G);
+  }
+
   // the first stage's inputs: pivot block, E- and G-rows and the next D, G
   // (eg); the fill-in rows W_1 = E[s]^T, A_k and Q_k^T (wr)
   __device__ void load_first(bool eg, bool wr, Grp G) const {
@@ -918,9 +923,17 @@ __device__ __forceinline__ void factor_task(const Task tk, const LevelDesc* __re
       tc::fence_before();
     }
   }
+  // An FP64 pair's consumer factors the first stage's pivot block as well,
+  // in the second pivot buffer (no hand-off ever writes there), so that its
+  // W-rows' panel solve of that stage runs while the producer's sweep and
+  // hand-off are still under way; the result is bitwise the producer's
+  // (potrf_sm + panel_operand is the fused sweep's arithmetic).
+  const bool own0 = mode == kPair && rank == 1 && g.hasW && dbl && !mixed;
+  double* const Dfac2c = (double*)(smraw + lay.oDfac2);
+  double* const rinv2c = (double*)(smraw + lay.oRinv2);
   if (threadIdx.x == 0) bad = 0;
   for (int e = threadIdx.x; e < lay.Rs * ldT; e += blockDim.x) T[e] = 0.0;
-  if (eg) potrf_table(tab, n);
+  if (eg || own0) potrf_table(tab, n);
   __syncthreads();
   if constexpr (TC) {
     if (use_tc) {
@@ -929,6 +942,7 @@ __device__ __forceinline__ void factor_task(const Task tk, const LevelDesc* __re
     }
   }
   cx.load_first(eg, wr, cta_grp());
+  if (own0) cx.load_D(Dfac2c, g.f, cta_grp());
   __syncthreads();
   if (mode == kPair) {
     // both CTAs have started before any remote store
@@ -1064,13 +1078,22 @@ __device__ __forceinline__ void factor_task(const Task tk, const LevelDesc* __re
       const bool eRows = (i < g.len - 1) || g.hasF;
       const int r0 = eRows ? 0 : n;
       const int b = mode == kPair ? (i & 1) : 0;
+      const bool own = i == 0 && own0;
       if (mode == kSplit) {
         group_bar(kBarFullM, kFactorThreads);
+      } else if (own) {
+        cluster_arrive();  // (stage -1)
+        int bad0 = 0;      // a breakdown is the producer's to report
+        potrf_sm(Dfac2c, ldD, n, rinv2c, tab, &bad0);
+        panel_operand(Dfac2c, Dfac2c, ldD, n, rinv2c, cta_grp());  // in place: M_cj = L_cj / L_jj
+        __syncthreads();
+        trsm_panel(Z, ldZ, oW, R, (const TZ*)Dfac2c, ldD, n, (const TZ*)rinv2c, cta_grp());
+        cluster_wait();    // stage 0's E- and G-rows are in buffer 0
       } else {
         cluster_arrive();  // done with stage i-1
         cluster_wait();    // stage i's blocks are in buffer b
       }
-      trsm_panel(Z, ldZ, oW, R, Mbuf(b), ldD, n, rinvbuf(b), C);
+      if (!own) trsm_panel(Z, ldZ, oW, R, Mbuf(b), ldD, n, rinvbuf(b), C);
       if (mode == kSplit && i + 1 < g.len) group_arrive(kBarFreeM, kFactorThreads);
       {
         double* Pd = d.Lp + (size_t)j * R * n + (size_t)oW * n;
