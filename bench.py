@@ -398,7 +398,7 @@ def candidate_plans(kkt, partition):
              [256, 128, 64, 32, 16, 8, 4, 2, 1], [288, 144, 72, 36, 18, 9, 4, 2, 1],
              [320, 160, 80, 40, 20, 10, 5, 2, 1], [256, 128, 64, 32, 16, 8, 4, 1],
              [304, 152, 76, 38, 19, 9, 4, 2, 1], [304, 152, 76, 38, 19, 9, 4, 1],
-             [304, 152, 76, 38, 19, 9, 3, 1]]
+             [304, 152, 76, 38, 19, 9, 3, 1], [256, 64, 32, 16, 8, 4, 2, 1]]
     ok = []
     for p in plans:
         try:
