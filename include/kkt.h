@@ -375,12 +375,25 @@ kkt_status kkt_set_launch_events(kkt_handle* h, void* const* events, int count);
  * Systems with blocks n <= 16 run one warp per segment task (several tasks
  * per CTA) in every case and never pair: at that size what counts is how
  * many independent stage chains an SM interleaves.
+ * On FP64 levels whose segments are all single stages with fill-in rows
+ * (the deep levels of a recursive plan), KKT_PAIR_AUTO runs each task on a
+ * cluster of 2, 4 or 8 CTAs instead (the largest size whose clusters all
+ * fit on the device at once, at most two CTAs per SM): every CTA factors
+ * the pivot block, solves a band of the panel rows and applies the Schur
+ * update (Alg. 1) to a band of about 1/C of its elements, the bands
+ * exchanged through distributed shared memory. KKT_PAIR_AUTO_PAIRS is the
+ * automatic choice without these clusters.
  * KKT_PAIR_OFF and KKT_PAIR_ON force one layout on every level (the
  * partition chosen at creation is kept). The layouts give bitwise identical
  * results: each element is computed by the same operations in the same
  * order; only the assignment to threads differs. Returns KKT_ERR_ARG for a
  * NULL handle or an unknown policy. Takes effect at the next kkt_factor. */
-typedef enum { KKT_PAIR_AUTO = 0, KKT_PAIR_OFF = 1, KKT_PAIR_ON = 2 } kkt_pair_policy;
+typedef enum {
+  KKT_PAIR_AUTO = 0,
+  KKT_PAIR_OFF = 1,
+  KKT_PAIR_ON = 2,
+  KKT_PAIR_AUTO_PAIRS = 3
+} kkt_pair_policy;
 kkt_status kkt_set_pairing(kkt_handle* h, int policy);
 
 /* Schedule of kkt_factor. on = 0 (the default): one launch per level and
@@ -422,6 +435,14 @@ kkt_status kkt_set_wait_limit(kkt_handle* h, long long cycles, int unmet);
 /* Number of kernel launches one kkt_factor / one kkt_solve (per chunk of up
  * to 16 right-hand sides) enqueues for this handle. */
 kkt_status kkt_launch_counts(const kkt_handle* h, int* factor_launches, int* solve_launches);
+
+/* CTAs per segment task in the per-level factor launches of level `level`
+ * (0-based) under the current pairing policy: 1 (one CTA per task, or one
+ * warp per task for blocks n <= 16), 2 (CTA pairs, or clusters of two), 4 or
+ * 8 (clusters of one-stage segments); the largest over the level's launch
+ * groups. *ctas is written on success; KKT_ERR_ARG for a NULL handle or
+ * pointer or a level outside [0, number of levels). */
+kkt_status kkt_factor_ctas_per_task(const kkt_handle* h, int level, int* ctas);
 
 /* Algorithmic FP64 flops of one kkt_factor and of one kkt_solve with one
  * right-hand side for this handle, in the standard counting convention

@@ -24,14 +24,14 @@ LIB_PATH = os.path.join(_HERE, "_build_debug" if DEBUG else "_build", "libkkt.so
  KKT_ERR_CAPACITY, KKT_ERR_BOUNDS) = range(9)
 KKT_FP64, KKT_MIXED_FP32, KKT_MIXED_FP32_ALL, KKT_MIXED_TF32, KKT_MIXED_BF16 = 0, 1, 2, 3, 4
 KKT_PARTITION_PAPER, KKT_PARTITION_BALANCED = 0, 1
-KKT_PAIR_AUTO, KKT_PAIR_OFF, KKT_PAIR_ON = 0, 1, 2
+KKT_PAIR_AUTO, KKT_PAIR_OFF, KKT_PAIR_ON, KKT_PAIR_AUTO_PAIRS = 0, 1, 2, 3
 RHS_CHUNK = 16
 
 EXPORTED = [
     "kkt_create", "kkt_create_levels", "kkt_create_plan", "kkt_batch_create", "kkt_batch_create_tuned", "kkt_destroy",
     "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_factor_solve", "kkt_factor_solve_host", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta", "kkt_set_refine_tol",
     "kkt_get_info",
-    "kkt_get_factor", "kkt_set_pairing", "kkt_set_launch_events", "kkt_launch_counts", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
+    "kkt_get_factor", "kkt_set_pairing", "kkt_set_launch_events", "kkt_launch_counts", "kkt_factor_ctas_per_task", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
     "kkt_set_persistent", "kkt_set_wait_limit", "kkt_set_refine_fallback",
 ]
 
@@ -77,6 +77,7 @@ _sig = {
     "kkt_set_pairing": [_vp, _i],
     "kkt_set_launch_events": [_vp, ctypes.POINTER(_vp), _i],
     "kkt_launch_counts": [_vp, _ip, _ip],
+    "kkt_factor_ctas_per_task": [_vp, ctypes.c_int, _ip],
     "kkt_flops": [_vp, _dp, _dp, _dp],
     "kkt_plan_flops": [_i, _i, _i, _i, _ip, _i, _i, _dp, _dp, _dp],
     "kkt_solve_noalloc": [_i, _i, _i, _i, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp, _vp],
@@ -304,8 +305,10 @@ def kkt_get_factor(h: int, N: int, n: int, m: int, system: int = 0) -> dict:
 
 
 def kkt_set_pairing(h: int, policy: int) -> None:
-    """KKT_PAIR_AUTO (default), KKT_PAIR_OFF or KKT_PAIR_ON: whether factor
-    tasks run on clusters of two CTAs (see the C header)."""
+    """KKT_PAIR_AUTO (default), KKT_PAIR_OFF, KKT_PAIR_ON or
+    KKT_PAIR_AUTO_PAIRS: whether factor tasks run on one CTA, a pair of CTAs
+    or (the deep levels' one-stage segments, automatic policy only) a
+    cluster of up to eight (see the C header)."""
     _check(_lib.kkt_set_pairing(h, int(policy)), "kkt_set_pairing")
 
 
@@ -342,6 +345,14 @@ def kkt_set_refine_fallback(h: int, cg_iters: int) -> None:
     """Preconditioned conjugate-gradient fallback of kkt_solve_refined for
     systems whose refinement stalls (cg_iters = 0 disables it)."""
     _check(_lib.kkt_set_refine_fallback(h, int(cg_iters)), "kkt_set_refine_fallback")
+
+
+def kkt_factor_ctas_per_task(h: int, level: int) -> int:
+    """CTAs per segment task of level `level`'s per-level factor launches:
+    1, 2 (pairs), 4 or 8 (clusters of one-stage segments)."""
+    c = ctypes.c_int(0)
+    _check(_lib.kkt_factor_ctas_per_task(h, int(level), ctypes.byref(c)), "kkt_factor_ctas_per_task")
+    return c.value
 
 
 def kkt_launch_counts(h: int) -> tuple[int, int]:

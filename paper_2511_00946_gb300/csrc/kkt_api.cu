@@ -161,6 +161,8 @@ struct kkt_handle {
     // (k_seq_solve): n even, and m n a multiple of 4 for the FP32 copies
     bool even = true, mn4 = true;
     int nmin = 1 << 30;  // smallest block size (the group's n is the largest)
+    bool len1 = true;    // every task is a segment of one stage
+    int clus = 0;        // cluster size of its FP64 factor launch (k_factor_clus), 0: one or two CTAs
   };
   std::vector<std::vector<Group>> fac_groups, bwd_groups;
   std::vector<int> bwd_off, bwd_cnt;         // task ranges per level (backward)
@@ -450,7 +452,10 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
           groups.back().fill != fill)
         groups.push_back(kkt_handle::Group{(int)tasks.size(), 0, sp.n, sp.m, warp, fill});
       kkt_handle::Group& gr = groups.back();
-      for (int k = 0; k < sp.lv[l].P; ++k) tasks.push_back(Task{h->desc_of[s][l], k});
+      for (int k = 0; k < sp.lv[l].P; ++k) {
+        tasks.push_back(Task{h->desc_of[s][l], k});
+        gr.len1 = gr.len1 && seg_len(sp.lv[l], k) == 1;
+      }
       gr.cnt += sp.lv[l].P;
       gr.even = gr.even && sp.n % 2 == 0;
       gr.nmin = std::min(gr.nmin, sp.n);
@@ -471,6 +476,13 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
     build_groups(l, true, h->bwd_groups[l]);
     h->bwd_cnt[l] = (int)tasks.size() - h->bwd_off[l];
   }
+  // FP64 levels whose segments are single stages with fill-in rows (the deep
+  // levels of a recursive plan): clusters of up to eight CTAs per task where
+  // they all fit at once (sized for the bordered arrow too)
+  for (int l = 0; l < h->maxL; ++l)
+    for (kkt_handle::Group& gr : h->fac_groups[l])
+      if (!gr.warp && gr.fill && gr.len1 && !h->level_mixed[l])
+        gr.clus = kkt::factor_clus_size(gr.cnt, gr.n, gr.m + bc, sms);
   const size_t task_off = cv.take(sizeof(Task) * std::max<size_t>(tasks.size(), 1));
   // refinement: residual tasks (chunks of kResChunk stages per system)
   std::vector<int> sys_desc(count), part0(count);
@@ -857,8 +869,14 @@ namespace {
 // unless the caller forced one.
 int level_paired(const kkt_handle* h, int l) {
   if (h->pair_policy == KKT_PAIR_OFF) return 0;
-  if (h->pair_policy == KKT_PAIR_ON) return 1;
+  if (h->pair_policy == KKT_PAIR_ON) return 1;  // (KKT_PAIR_AUTO_PAIRS: the automatic choice)
   return h->level_pair[l];
+}
+
+// Cluster size of a group's FP64 factor launch (0: the one- and two-CTA
+// layouts); the automatic policy only.
+int clus_of(const kkt_handle* h, int l, const kkt_handle::Group& gr) {
+  return h->pair_policy == KKT_PAIR_AUTO && !h->level_mixed[l] ? gr.clus : 0;
 }
 
 // A bordered pass runs the top level's corner solve and backward sweep at the
@@ -871,7 +889,7 @@ bool top_in_factor(const kkt_handle* h, int l, const kkt_handle::Group& gr) {
 }  // namespace
 
 kkt_status kkt_set_pairing(kkt_handle* h, int policy) {
-  if (!h || policy < KKT_PAIR_AUTO || policy > KKT_PAIR_ON) return KKT_ERR_ARG;
+  if (!h || policy < KKT_PAIR_AUTO || policy > KKT_PAIR_AUTO_PAIRS) return KKT_ERR_ARG;
   h->pair_policy = policy;
   return KKT_OK;
 }
@@ -1078,7 +1096,10 @@ kkt_status kkt_factor(kkt_handle* h, const double* D, const double* E, const dou
   int li = 0;
   for (int l = 0; l < h->maxL; ++l)
     for (const kkt_handle::Group& gr : h->fac_groups[l]) {
-      const int e = gr.warp ? kkt::launch_factor_w(h->ddesc, h->dtasks + gr.off, gr.cnt, gr.n, gr.m,
+      const int C = clus_of(h, l, gr);
+      const int e = C ? kkt::launch_factor_clus(h->ddesc, h->dtasks + gr.off, gr.cnt, gr.n, gr.m, C, D, E, G,
+                                                h->dinfo, stream)
+                    : gr.warp ? kkt::launch_factor_w(h->ddesc, h->dtasks + gr.off, gr.cnt, gr.n, gr.m,
                                                    h->level_mixed[l], D, E, G, R, h->dinfo, stream, nullptr, 1,
                                                    gr.fill)
                             : kkt::launch_factor(h->ddesc, h->dtasks + gr.off, gr.cnt, gr.n, gr.m,
@@ -1171,7 +1192,10 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
     return KKT_ERR_CUDA;
   for (int l = 0; l < h->maxL; ++l)
     for (const kkt_handle::Group& gr : h->fac_groups[l]) {
-      const int e = gr.warp ? kkt::launch_factor_w(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0, D, E,
+      const int C = clus_of(h, l, gr);
+      const int e = C ? kkt::launch_factor_clus(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, C, D, E,
+                                                h->Gb, h->dinfo, stream, b, ldb)
+                    : gr.warp ? kkt::launch_factor_w(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0, D, E,
                                                    h->Gb, h->Rb, h->dinfo, stream, b, ldb, gr.fill)
                             : kkt::launch_factor(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0,
                                                  level_paired(h, l), D, E, h->Gb, h->Rb, h->dinfo, stream, b, ldb,
@@ -1345,7 +1369,10 @@ kkt_status kkt_factor_solve_host(kkt_handle* h, const double* D, const double* E
   }
   for (int l = 1; l < h->maxL; ++l)
     for (const kkt_handle::Group& gr : h->fac_groups[l]) {
-      const int e = gr.warp ? kkt::launch_factor_w(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0,
+      const int C = clus_of(h, l, gr);
+      const int e = C ? kkt::launch_factor_clus(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, C, h->hsD,
+                                                h->hsE, h->Gb, h->dinfo, stream, h->hsB, 1)
+                    : gr.warp ? kkt::launch_factor_w(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0,
                                                    h->hsD, h->hsE, h->Gb, h->Rb, h->dinfo, stream, h->hsB, 1,
                                                    gr.fill)
                             : kkt::launch_factor(h->ddesc_b, h->dtasks + gr.off, gr.cnt, gr.n, gr.m + 1, 0,
@@ -1591,6 +1618,18 @@ kkt_status kkt_set_launch_events(kkt_handle* h, void* const* events, int count) 
   h->events.clear();
   if (events)
     for (int i = 0; i < count; ++i) h->events.push_back((cudaEvent_t)events[i]);
+  return KKT_OK;
+}
+
+kkt_status kkt_factor_ctas_per_task(const kkt_handle* h, int level, int* ctas) {
+  if (!h || !ctas || level < 0 || level >= h->maxL) return KKT_ERR_ARG;
+  int c = 1;
+  for (const kkt_handle::Group& gr : h->fac_groups[level])
+    if (!gr.warp) {
+      const int C = clus_of(h, level, gr);
+      c = std::max(c, C ? C : level_paired(h, level) ? 2 : 1);
+    }
+  *ctas = c;
   return KKT_OK;
 }
 

@@ -293,6 +293,14 @@ int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
                   void* stream, double* b = nullptr, int ldb = 1, int fill = 1, int top_solve = 0, int tc = 0);
+// One-stage segment tasks (FP64, fill-in rows) on clusters of C CTAs, 2 <= C
+// <= 8 (k_factor_clus): bitwise the results of launch_factor.
+// factor_clus_size: the largest C of 8, 4, 2 for which every cluster of the
+// launch is resident at once (at most two CTAs per SM), 0 if none.
+int factor_clus_size(int ntasks, int maxn, int maxm, int sms);
+int launch_factor_clus(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int C, const double* D,
+                       const double* E, const double* G, Info* info, void* stream, double* b = nullptr,
+                       int ldb = 1);
 // (split: CTAs per task, each on its own group of right-hand-side columns)
 // (fill: some task's level has P > 1; 0 sizes shared memory for the compact
 // layout of levels with P = 1)

@@ -1195,6 +1195,152 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
                       top_solve, dbl, tcm, smraw, bad, tslot, tbar);
 }
 
+// ---------------------------------------------------------------------------
+// One-stage segments on a cluster of C CTAs (2 <= C <= 8), FP64. On the deep
+// levels of a recursive plan every segment is a single stage (its pivot
+// block with the E-, G- and W-rows of its panel), and the levels have few
+// tasks: one or two CTAs per task leave most SMs idle while the stage's
+// panel solve and Schur update (Alg. 1) run at two FP64 FMAs per clock per
+// SM. Here the stage is spread over the cluster:
+//   - every CTA factors the pivot block itself and solves a contiguous band
+//     of about 1/C of the panel rows with the fused sweep (potrf_trsm_sm),
+//     then stores its solved rows into every other CTA's shared memory;
+//   - every CTA applies the Schur update to a band of trapezoid rows holding
+//     about 1/C of the elements and stores the results into the shared
+//     memory of the CTA that writes that block's slots for the next level
+//     (rank 0: E- and G-rows, rank 1: W-rows);
+//   - rank 0 writes the pivot blocks, each CTA its panel rows.
+// Three split-phase cluster barriers order the exchanges. Every element is
+// computed by the same operations in the same order as in the one- and
+// two-CTA layouts, so the results are bitwise theirs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void clus_task(const Task tk, const LevelDesc* __restrict__ descs,
+                                          const double* __restrict__ uD, const double* __restrict__ uE,
+                                          const double* __restrict__ uG, Info* info, double* yb, int ldyb, int C,
+                                          unsigned char* smraw, int& bad) {
+  const int rank = (int)cluster_rank();
+  const LevelDesc& d = descs[tk.desc];
+  const FacLayout lay = fac_layout(d.n, d.m, 8, true, false);
+  if (!task_geometry_ok(d, tk.seg, smraw, lay.total)) return;  // debug build only (every CTA alike)
+  const FacCtx<double, 4> cx(d, tk.seg, smraw, lay, uD, uE, uG);
+  const int n = cx.n, m = cx.m, ldD = cx.ldD, ldZ = cx.ldZ, ldT = cx.ldT, oG = cx.oG, oW = cx.oW;
+  const SegGeom g = cx.g;
+  const int j = g.f, s = cx.s, tid = threadIdx.x, nt = blockDim.x;
+  double* const Dfac = cx.Dfac;
+  double* const rinv = cx.rinv;
+  double* const T = cx.T;
+  double* const M = cx.M;
+  double* const Z = cx.Z;
+  // panel rows [r0, r1): the E-rows when a next separator exists, the G-rows,
+  // the W-rows when a previous one does
+  const int r0 = g.hasF ? 0 : n, r1 = g.hasW ? cx.R : n + m, h = r1 - r0;
+  // this CTA's band of the panel solve: equal row counts
+  const int t0 = r0 + h * rank / C, t1 = r0 + h * (rank + 1) / C;
+  // its band of the Schur update: row r0 + a holds a + 1 elements; band q
+  // starts at the first row whose preceding rows hold >= q/C of the total
+  const int tot = h * (h + 1) / 2;
+  auto band0 = [&](int q) {
+    const int want = (tot * q + C - 1) / C;
+    int a = 0;
+    while (a < h && a * (a + 1) / 2 < want) ++a;
+    return r0 + a;
+  };
+  const int s0 = band0(rank), s1 = band0(rank + 1);
+  cluster_arrive();  // this CTA runs: the others may store into its shared memory after their wait
+  if (tid == 0) bad = 0;
+  potrf_table(cx.tab, n);
+  // inputs: the pivot block, the panel rows of the solve band, and the
+  // initial values of the Schur band (A_k and Q_k^T in the W-rows, else 0)
+  cx.load_D(Dfac, j, cta_grp());
+  for (int e = tid; e < (t1 - t0) * n; e += nt) {
+    const int r = t0 + e / n, c = e - (r - t0) * n;
+    double v;
+    if (r < n) v = cx.Ein[(size_t)j * cx.nn + r * n + c];  // E_j
+    else if (r < oW) {                                      // G_j (+ its second slot)
+      const size_t o = (size_t)j * cx.mn + (r - oG) * n + c;
+      v = cx.G2 ? cx.Gin[o] + cx.G2[o] : cx.Gin[o];
+    } else v = cx.Ein[(size_t)s * cx.nn + c * n + (r - oW)];  // W_1 = E[s]^T
+    Z[r * ldZ + c] = v;
+  }
+  for (int e = tid; e < (s1 - s0) * ldT; e += nt) {
+    const int a = s0 + e / ldT, b = e - (a - s0) * ldT;
+    double v = 0.0;
+    if (a >= oW && b >= oW && b < cx.R) {  // A_k = D_s (+ its second slot)
+      const size_t o = (size_t)s * cx.nn + (a - oW) * n + (b - oW);
+      v = cx.D2 ? cx.Din[o] + cx.D2[o] : cx.Din[o];
+    } else if (a >= oW && b >= oG && b < oW) {  // Q_k^T = G_s^T
+      const size_t o = (size_t)s * cx.mn + (b - oG) * n + (a - oW);
+      v = cx.G2 ? cx.Gin[o] + cx.G2[o] : cx.Gin[o];
+    }
+    T[a * ldT + b] = v;
+  }
+  __syncthreads();
+  potrf_trsm_sm(Dfac, ldD, n, rinv, M, cx.tab, &bad, Z, ldZ, t0, t1, true);
+  __syncthreads();
+  if (d.mr) {
+    const int ry = oG + m - d.mr;  // the bordered row: y_j of the forward substitution
+    if (ry >= t0 && ry < t1) cx.store_y(j, yb, ldyb, cta_grp());
+  }
+  cluster_wait();  // every CTA of the cluster runs
+  {
+    for (int q = 1; q < C; ++q) {
+      const unsigned az = cluster_addr(Z, (unsigned)((rank + q) % C));
+      for (int e = tid; e < (t1 - t0) * n; e += nt) {
+        const int r = t0 + e / n, c = e - (r - t0) * n;
+        const unsigned off = (unsigned)(r * ldZ + c) * 8u;
+        st_cluster(az + off, Z[r * ldZ + c]);
+      }
+    }
+  }
+  cluster_arrive();
+  if (rank == 0) {
+    if (tid == 0 && bad) record_breakdown(info, d.sys, d.nat[j], d.level);
+    cx.store_pivot(j, Dfac, rinv, M, cta_grp());
+  }
+  {
+    double* Pd = d.Lp + (size_t)j * cx.R * n;
+    const int p0 = rank == 0 ? 0 : t0;  // rank 0 also writes the zero rows [0, r0)
+    for (int e = tid; e < (t1 - p0) * n; e += nt) {
+      const int r = p0 + e / n, c = e - (r - p0) * n;
+      Pd[(size_t)r * n + c] = r >= r0 ? Z[r * ldZ + c] : 0.0;
+    }
+  }
+  cluster_wait();  // every solved panel row is here
+  syrk_trap(T, ldT, Z, Z, 0, ldZ, s0, s1, r0, n, cta_grp());
+  {
+    const unsigned a0 = cluster_addr(T, 0u), a1 = cluster_addr(T, 1u);
+    const int w0 = s0 - r0;  // row s0 + i holds w0 + i + 1 elements
+    const int cnt = (s1 - s0) * w0 + (s1 - s0) * (s1 - s0 + 1) / 2;
+    // (a, b) of element tid of the band, then advanced by nt along the rows
+    int a = s0, b = r0 + tid;
+    while (a < s1 && b > a) { b -= a - r0 + 1; ++a; }
+    for (int e = tid; e < cnt; e += nt) {
+      if (e != tid) {
+        b += nt;
+        while (b > a) { b -= a - r0 + 1; ++a; }
+      }
+      const int owner = a < oW ? 0 : 1;
+      if (owner != rank)
+        st_cluster((owner ? a1 : a0) + (unsigned)(a * ldT + b) * 8u, T[a * ldT + b]);
+    }
+  }
+  cluster_arrive();
+  cluster_wait();  // the slot owners hold their rows of the update
+  if (rank == 0) cx.store_slots(tk.seg, true, false, cta_grp());
+  else if (rank == 1) cx.store_slots(tk.seg, false, g.hasW, cta_grp());
+}
+
+__global__ void __launch_bounds__(kFactorThreads, 2) k_factor_clus(const LevelDesc* __restrict__ descs,
+                                                                   const Task* __restrict__ tasks,
+                                                                   const double* __restrict__ uD,
+                                                                   const double* __restrict__ uE,
+                                                                   const double* __restrict__ uG, Info* info,
+                                                                   double* yb, int ldyb, int C) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int bad;
+  clus_task(tasks[blockIdx.x / C], descs, uD, uE, uG, info, yb, ldyb, C, smraw, bad);
+}
+
 
 // ---------------------------------------------------------------------------
 // Small blocks (n <= kWarpMaxN): one warp per segment task, every step of a
@@ -2826,6 +2972,56 @@ int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int m
                                         dbl, 0)
               : (int)cudaLaunchKernelEx(&cfg, k_factor<double, 4>, d, t, D, E, G, R, info, p, b, ldb, top_solve,
                                         dbl, 0);
+}
+
+int factor_clus_size(int ntasks, int maxn, int maxm, int sms) {
+  if (ntasks <= 0) return 0;
+  const size_t sm = factor_smem_bytes(maxn, maxm, 0, 1, 0);
+  if (set_smem((const void*)k_factor_clus, sm)) return 0;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor_clus, kFactorThreads, sm) != cudaSuccess ||
+      occ < 1)
+    return 0;
+  occ = std::min(occ, 2);
+  for (int C = 8; C >= 2; C /= 2) {
+    if ((long long)C * ntasks > (long long)occ * sms) continue;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)(C * ntasks));
+    cfg.blockDim = dim3(kFactorThreads);
+    cfg.dynamicSmemBytes = sm;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_factor_clus, &cfg) == cudaSuccess && ncl >= ntasks) return C;
+  }
+  return 0;
+}
+
+int launch_factor_clus(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int C, const double* D,
+                       const double* E, const double* G, Info* info, void* stream, double* b, int ldb) {
+  if (ntasks <= 0) return 0;
+  if (C < 2 || C > 8) return (int)cudaErrorInvalidValue;
+  const size_t sm = factor_smem_bytes(maxn, maxm, 0, 1, 0);
+  const int e = set_smem((const void*)k_factor_clus, sm);
+  if (e) return e;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(C * ntasks));
+  cfg.blockDim = dim3(kFactorThreads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = (cudaStream_t)stream;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, k_factor_clus, d, t, D, E, G, info, b, ldb, C);
 }
 
 int launch_forward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int single,
