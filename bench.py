@@ -348,7 +348,7 @@ def device_sms() -> int:
     return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
-def per_launch_flops(kkt, plan, partition, nrhs=1):
+def per_launch_flops(kkt, plan, partition, nrhs=1, chain=False):
     """Names and algorithmic FP64 flops (standard convention, as executed) of
     the launches of one factor-and-solve step, in launch order. With one
     right-hand side (kkt_factor_solve, the right-hand side bordered onto the
@@ -357,7 +357,8 @@ def per_launch_flops(kkt, plan, partition, nrhs=1):
     launch also runs the corner solve and the top level's backward sweep),
     backward levels L-1..1. With several (the two
     passes): factor levels 1..L, forward levels 1..L (the top one also solves
-    the corner and runs its backward sweep), backward levels L-1..1."""
+    the corner and runs its backward sweep), backward levels L-1..1 (with
+    `chain`, the backward levels L-1..1 in one launch)."""
     L = len(plan)
     Ns = [N_STAGES]
     for p in plan[:-1]:
@@ -385,9 +386,13 @@ def per_launch_flops(kkt, plan, partition, nrhs=1):
     else:
         names[-1] = f"k_factor level {L} (+forward, corner, corner solve, backward)"
         flops[-1] += sol[L - 1] / 2.0
-    for l in range(L - 2, -1, -1):
-        names.append(f"k_backward level {l + 1}")
-        flops.append(sol[l] / 2.0)
+    if chain:
+        names.append(f"k_backward_chain (levels {L - 1}..1)")
+        flops.append(sum(sol[l] / 2.0 for l in range(L - 1)))
+    else:
+        for l in range(L - 2, -1, -1):
+            names.append(f"k_backward level {l + 1}")
+            flops.append(sol[l] / 2.0)
     return names, flops
 
 
@@ -954,7 +959,10 @@ def main():
         plan = best[1]
     h = kkt.kkt_create_plan(N_STAGES, N_BLOCK, M_ARROW, plan, part)
     fl = kkt.kkt_flops(h)
-    launch_names, launch_flops = per_launch_flops(kkt, plan, part, args.nrhs)
+    # one group per level: L forward launches, then one backward launch per
+    # level below the top or a single one for all of them
+    chain = kkt.kkt_launch_counts(h)[1] == len(plan) + 1 and len(plan) >= 3
+    launch_names, launch_flops = per_launch_flops(kkt, plan, part, args.nrhs, chain)
     nl = len(launch_names)
 
     def launch_step():

@@ -418,7 +418,23 @@ kkt_status kkt_set_pairing(kkt_handle* h, int policy);
  * kkt_factor_solve and kkt_factor_solve_host keep the per-level launches. */
 kkt_status kkt_set_persistent(kkt_handle* h, int on);
 
-/* Bounded waits of the persistent schedule and of the one-warp substitution
+/* The backward substitution of the levels below the top (Algorithm 3,
+ * parallel phase of each level) as ONE launch (on = 1, the default where it
+ * applies) or one launch per level and block-size class (on = 0). It applies
+ * to handles with at least three levels whose backward tasks all have blocks
+ * n > 16 and whose levels below the top share one precision; elsewhere the
+ * per-level launches run whatever `on` says. In the single launch CTAs take
+ * (task, column group) items by ticket, top level first; an item requests
+ * its stage's factor blocks at once, then waits until every item of the
+ * level above has released its counter (a bounded wait, see
+ * kkt_set_wait_limit), solves, and releases its own level's counter.
+ * Results are bitwise those of the per-level launches (the same operations
+ * per element). kkt_launch_counts reflects the setting. Returns KKT_ERR_ARG
+ * for a NULL handle. Takes effect at the next solve. */
+kkt_status kkt_set_backward_chain(kkt_handle* h, int on);
+
+/* Bounded waits of the persistent schedule, of the single-launch backward
+ * substitution and of the one-warp substitution
  * of sequential systems (one level, P = 1, one right-hand side), whose stage
  * blocks arrive by bulk copies counted on an mbarrier: a task gives up
  * waiting for its feeders (or its copies) after `cycles` SM clock cycles

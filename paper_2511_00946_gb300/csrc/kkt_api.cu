@@ -166,6 +166,11 @@ struct kkt_handle {
   };
   std::vector<std::vector<Group>> fac_groups, bwd_groups;
   std::vector<int> bwd_off, bwd_cnt;         // task ranges per level (backward)
+  // the backward levels in one launch (k_backward_chain): every backward
+  // task has blocks n > 16 and every level below the top the same precision
+  bool chain = false;
+  bool chain_on = true;                      // kkt_set_backward_chain
+  int* dchain = nullptr;                     // its counters (maxL ints)
   void* dmem = nullptr;                      // one allocation for everything
   size_t dbytes = 0;
   LevelDesc* ddesc = nullptr;
@@ -484,6 +489,13 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
       if (!gr.warp && gr.fill && gr.len1 && !h->level_mixed[l])
         gr.clus = kkt::factor_clus_size(gr.cnt, gr.n, gr.m + bc, sms);
   const size_t task_off = cv.take(sizeof(Task) * std::max<size_t>(tasks.size(), 1));
+  // the backward chain: at least two backward levels
+  h->chain = h->maxL >= 3 && h->maxL - 1 <= kkt::kChainMax;
+  for (int l = 0; l + 1 < h->maxL && h->chain; ++l) {
+    h->chain = h->level_mixed[l] == h->level_mixed[0];
+    for (const kkt_handle::Group& gr : h->bwd_groups[l]) h->chain = h->chain && !gr.warp;
+  }
+  const size_t chain_off = cv.take(sizeof(int) * (h->maxL + 1));
   // refinement: residual tasks (chunks of kResChunk stages per system)
   std::vector<int> sys_desc(count), part0(count);
   for (int s = 0; s < count; ++s) {
@@ -600,6 +612,7 @@ kkt_status build_handle(int count, const int* N, const int* n, const int* m,
     h->Rb = dp(rb_off);
   }
   h->dtasks = (Task*)(base + task_off);
+  h->dchain = (int*)(base + chain_off);
   h->dinfo = (kkt::Info*)(base + info_off);
   bool ok = cudaMemset(h->dmem, 0, h->dbytes) == cudaSuccess;
   ok = ok && cudaMemcpy(h->ddesc, h->hdesc.data(), sizeof(LevelDesc) * h->hdesc.size(),
@@ -1062,6 +1075,12 @@ kkt_status kkt_set_persistent(kkt_handle* h, int on) {
   return KKT_OK;
 }
 
+kkt_status kkt_set_backward_chain(kkt_handle* h, int on) {
+  if (!h) return KKT_ERR_ARG;
+  h->chain_on = on != 0;
+  return KKT_OK;
+}
+
 kkt_status kkt_set_wait_limit(kkt_handle* h, long long cycles, int unmet) {
   if (!h || cycles < 1) return KKT_ERR_ARG;
   h->pwait = cycles;
@@ -1154,6 +1173,30 @@ kkt_status solve_chunk(kkt_handle* h, double* b, int ldb, int nr, const int* ski
   };
   for (int l = 0; l < h->maxL; ++l)
     if ((!fwd_done || h->level_top[l]) && !run(false, l, h->fac_groups[l])) return KKT_ERR_CUDA;
+  if (h->chain && h->chain_on) {
+    // every backward level in one launch, top down; the column split of each
+    // level as in the per-level launches
+    kkt::ChainPlan cp{};
+    int acc = 0, maxn = 1, maxm = 0;
+    const int slots = 3 * std::max(h->sms, 1);
+    for (int l = h->maxL - 2; l >= 0; --l) {
+      const int cnt = h->bwd_cnt[l];
+      const int split = std::max(1, std::min(nr / 4, slots / std::max(cnt, 1)));
+      acc += cnt * split;
+      cp.off[cp.nlev] = h->bwd_off[l];
+      cp.end[cp.nlev] = acc;
+      cp.split[cp.nlev] = split;
+      ++cp.nlev;
+      for (const kkt_handle::Group& gr : h->bwd_groups[l]) {
+        maxn = std::max(maxn, gr.n);
+        maxm = std::max(maxm, gr.m + dm);
+      }
+    }
+    const int e = kkt::launch_backward_chain(dd, h->dtasks, cp, h->dchain, maxn, maxm, h->level_mixed[0], b, ldb, nr,
+                                             skip, h->dinfo, h->pwait, h->punmet, h->sms, stream);
+    if (e || (li && !mark(h, (*li)++, stream))) return KKT_ERR_CUDA;
+    return KKT_OK;
+  }
   for (int l = h->maxL - 2; l >= 0; --l)
     if (!run(true, l, h->bwd_groups[l])) return KKT_ERR_CUDA;
   return KKT_OK;
@@ -1638,8 +1681,9 @@ kkt_status kkt_launch_counts(const kkt_handle* h, int* fl, int* sl) {
   int f = 0, sv = 0;
   for (int l = 0; l < h->maxL; ++l) {
     f += (int)h->fac_groups[l].size();
-    sv += (int)h->fac_groups[l].size() + (int)h->bwd_groups[l].size();
+    sv += (int)h->fac_groups[l].size() + (h->chain && h->chain_on ? 0 : (int)h->bwd_groups[l].size());
   }
+  if (h->chain && h->chain_on) sv += 1;
   if (h->persistent) f = 1;
   if (fl) *fl = f;
   if (sl) *sl = sv;

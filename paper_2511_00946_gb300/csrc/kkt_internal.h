@@ -293,6 +293,22 @@ int launch_factor_w(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
 int launch_factor(const LevelDesc* d, const Task* t, int ntasks, int maxn, int maxm, int mixed, int pair,
                   const double* D, const double* E, const double* G, const double* R, Info* info,
                   void* stream, double* b = nullptr, int ldb = 1, int fill = 1, int top_solve = 0, int tc = 0);
+// The backward levels below the top in one launch (k_backward_chain): chain
+// level li (0 = the level below the top, then down to level 1) holds the
+// tasks [off[li], off[li] + its count) of the task array, each split into
+// split[li] column groups; end[li] is the cumulative item count. ctr: nlev +
+// 1 device ints (zeroed by the launcher); sms: the device's SM count (the
+// grid is at most the CTAs resident at once).
+constexpr int kChainMax = 32;
+struct ChainPlan {
+  int nlev;
+  int off[kChainMax];
+  int end[kChainMax];
+  int split[kChainMax];
+};
+int launch_backward_chain(const LevelDesc* d, const Task* t, const ChainPlan& cp, int* ctr, int maxn, int maxm,
+                          int single, double* b, int ldb, int nrhs, const int* skip, Info* info, long long wait,
+                          int unmet, int sms, void* stream);
 // One-stage segment tasks (FP64, fill-in rows) on clusters of C CTAs, 2 <= C
 // <= 8 (k_factor_clus): bitwise the results of launch_factor.
 // factor_clus_size: the largest C of 8, 4, 2 for which every cluster of the

@@ -1742,13 +1742,15 @@ __device__ __forceinline__ void stage_rows(const SegGeom& g, int i, int n, int m
 // parallel phase; for the top level the whole sequential sweep). On entry
 // S.V holds [x_next (E rows); x_g (G rows); x_sep (W rows)]. The factor
 // blocks of the next stage stream in while the current one is solved.
+// (prefetched: the last stage's factor blocks were already requested into
+// buffer 0, see backward_prefetch)
 template <typename TS>
 __device__ void backward_segment(const SolveSmem<TS>& S, const LevelDesc& d, const SegGeom& g,
-                                 double* b, int ldb, int nr, int c0, Grp G) {
+                                 double* b, int ldb, int nr, int c0, Grp G, bool prefetched = false) {
   const int n = d.n, m = d.m;
   int r0, r1;
   stage_rows(g, g.len - 1, n, m, r0, r1);
-  prefetch_stage_factor(S, 0, d, g.f + g.len - 1, r0, r1, true, G);
+  if (!prefetched) prefetch_stage_factor(S, 0, d, g.f + g.len - 1, r0, r1, true, G);
   for (int i = g.len - 1; i >= 0; --i) {
     const int j = g.f + i, q = (g.len - 1 - i) & 1;
     stage_rows(g, i, n, m, r0, r1);
@@ -1935,7 +1937,7 @@ __device__ void forward_task(const Task tk, const LevelDesc* __restrict__ descs,
 // next level (x at s_k and s_{k+1}), and this level's y.
 template <typename TS>
 __device__ void backward_task(const Task tk, const LevelDesc* __restrict__ descs, double* b, int ldb, int nr,
-                              const int* skip, unsigned char* smraw, Grp G, int c0 = 0) {
+                              const int* skip, unsigned char* smraw, Grp G, int c0 = 0, bool prefetched = false) {
   const LevelDesc& d = descs[tk.desc];
   if (skip && skip[d.sys]) return;
   if (!task_geometry_ok(d, tk.seg, smraw, sol_layout(d.n, d.m, (int)sizeof(TS), d.P > 1).total)) return;
@@ -1957,7 +1959,19 @@ __device__ void backward_task(const Task tk, const LevelDesc* __restrict__ descs
     store_vec(xs.p, xs.ld, S.V + oW * S.ldV, S.ldV, n, nr, G);
   }
   gsync(G);
-  backward_segment(S, d, g, b, ldb, nr, c0, G);
+  backward_segment(S, d, g, b, ldb, nr, c0, G, prefetched);
+}
+
+// The factor blocks of the backward sweep's first stage (the segment's last)
+// into buffer 0: they do not depend on x, so a task can request them before
+// the solutions it needs exist.
+template <typename TS>
+__device__ void backward_prefetch(const Task tk, const LevelDesc& d, unsigned char* smraw, Grp G) {
+  const SolveSmem<TS> S = solve_smem<TS>(smraw, d.n, d.m, d.P > 1);
+  const SegGeom g = seg_geom(d, tk.seg);
+  int r0, r1;
+  stage_rows(g, g.len - 1, d.n, d.m, r0, r1);
+  prefetch_stage_factor(S, 0, d, g.f + g.len - 1, r0, r1, true, G);
 }
 
 
@@ -2002,6 +2016,75 @@ __global__ void __launch_bounds__(256) k_backward_w(const LevelDesc* __restrict_
   if (t >= ntasks) return;  // whole warp
   backward_task<TS>(tasks[t], descs, b, ldb, nr, skip, smraw + (size_t)wid * slice,
                     Grp{(int)(threadIdx.x & 31), 32, -1});
+}
+
+// Every backward level below the top (Algorithm 3, parallel phase of each
+// level, top down) in one launch. Items are (segment task, column group)
+// pairs in chain order: the levels from the one below the top down to level
+// 1, each level's items together. CTAs take items by ticket, so a CTA only
+// ever waits for items taken before its own, which running CTAs hold. An
+// item first requests its stage's factor blocks (they do not depend on x),
+// then waits until every item of the level above has released its counter
+// (thread 0 polls with ld.acquire.gpu, bounded by `wait` clock cycles; a
+// wait that runs out records KKT_ERR_TIMEOUT and skips the item), solves,
+// and releases its own level's counter. ctr[0] is the ticket, ctr[1 + li]
+// the finished items of chain level li; the host zeroes them before the
+// launch. unmet: every wait expects one item more than its level has (a
+// test of the timeout path).
+template <typename TS>
+__global__ void __launch_bounds__(kSolveThreads) k_backward_chain(const LevelDesc* __restrict__ descs,
+                                                                  const Task* __restrict__ tasks, ChainPlan cp,
+                                                                  int* ctr, double* b, int ldb, int nr,
+                                                                  const int* skip, Info* info,
+                                                                  long long wait_cycles, int unmet) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int cur, ok;
+  const int total = cp.nlev > 0 ? cp.end[cp.nlev - 1] : 0;
+  for (;;) {
+    if (threadIdx.x == 0) cur = atomicAdd(ctr, 1);
+    __syncthreads();
+    const int t = cur;
+    if (t >= total) break;
+    int li = 0;
+    while (t >= cp.end[li]) ++li;
+    const int u = t - (li ? cp.end[li - 1] : 0), sp = cp.split[li];
+    const Task tk = tasks[cp.off[li] + u / sp];
+    const LevelDesc& d = descs[tk.desc];
+    const int nc = (nr + sp - 1) / sp, c0 = (u % sp) * nc, cn = min(nc, nr - c0);
+    bool work = cn > 0 && !(skip && skip[d.sys]) &&
+                task_geometry_ok(d, tk.seg, smraw, sol_layout(d.n, d.m, (int)sizeof(TS), d.P > 1).total);
+    if (work) backward_prefetch<TS>(tk, d, smraw, cta_grp());
+    if (threadIdx.x == 0) {
+      int good = 1;
+      if (li > 0) {
+        const int need = cp.end[li - 1] - (li >= 2 ? cp.end[li - 2] : 0) + unmet;
+        const long long t0 = clock64();
+        unsigned ns = 32;
+        while (ld_acquire_gpu(ctr + li) < need) {
+          if (clock64() - t0 > wait_cycles) {
+            good = 0;
+            break;
+          }
+          __nanosleep(ns);
+          if (ns < 1024) ns *= 2;
+        }
+        __threadfence();
+      }
+      ok = good;
+      if (!good) record_timeout(info, d.sys, d.nat[d.seg[tk.seg]], d.level);
+    }
+    __syncthreads();
+    work = work && ok;
+    if (work) backward_task<TS>(tk, descs, b + c0, ldb, cn, nullptr, smraw, cta_grp(), c0, true);
+    cp_async_wait_all();  // (a skipped item's requested blocks)
+    __syncthreads();
+    // release: the item's writes precede the barrier; the fence makes them
+    // visible device-wide before the counter moves
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(ctr + 1 + li, 1);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -3053,6 +3136,31 @@ int launch_backward(const LevelDesc* d, const Task* t, int ntasks, int maxn, int
     k_backward<float><<<grid, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip, split);
   else
     k_backward<double><<<grid, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, b, ldb, nrhs, skip, split);
+  return (int)cudaGetLastError();
+}
+
+int launch_backward_chain(const LevelDesc* d, const Task* t, const ChainPlan& cp, int* ctr, int maxn, int maxm,
+                          int single, double* b, int ldb, int nrhs, const int* skip, Info* info, long long wait,
+                          int unmet, int sms, void* stream) {
+  if (cp.nlev <= 0) return 0;
+  if (cp.nlev > kChainMax) return (int)cudaErrorInvalidValue;
+  const size_t sm = solve_smem_bytes(maxn, maxm, single, 1);
+  const void* fn = single ? (const void*)k_backward_chain<float> : (const void*)k_backward_chain<double>;
+  int e = set_smem(fn, sm);
+  if (e) return e;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kSolveThreads, sm) != cudaSuccess || occ < 1)
+    return (int)cudaErrorInvalidConfiguration;
+  const int total = cp.end[cp.nlev - 1];
+  const unsigned grid = (unsigned)std::max(1, std::min(total, occ * std::max(sms, 1)));
+  const cudaError_t me = cudaMemsetAsync(ctr, 0, sizeof(int) * (cp.nlev + 1), (cudaStream_t)stream);
+  if (me != cudaSuccess) return (int)me;
+  if (single)
+    k_backward_chain<float><<<grid, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, cp, ctr, b, ldb, nrhs, skip,
+                                                                               info, wait, unmet ? 1 : 0);
+  else
+    k_backward_chain<double><<<grid, kSolveThreads, sm, (cudaStream_t)stream>>>(d, t, cp, ctr, b, ldb, nrhs, skip,
+                                                                                info, wait, unmet ? 1 : 0);
   return (int)cudaGetLastError();
 }
 

@@ -114,10 +114,14 @@ def test_invalid_arguments(kkt):
         kkt.kkt_plan_flops(0, 4, 0, [1])
     assert kkt.status_string(kkt.KKT_ERR_NOT_SPD).startswith("pivot")
     for setter, args in ((kkt.kkt_set_refine_tol, (1e-16,)), (kkt.kkt_set_refine_fallback, (4,)),
-                         (kkt.kkt_set_persistent, (True,)), (kkt.kkt_set_wait_limit, (1 << 20,))):
+                         (kkt.kkt_set_persistent, (True,)), (kkt.kkt_set_wait_limit, (1 << 20,)),
+                         (kkt.kkt_set_backward_chain, (True,)), (kkt.kkt_set_pairing, (kkt.KKT_PAIR_AUTO_PAIRS,))):
         with pytest.raises(kkt.KKTError) as ei:   # no handle: refused before any device work
             setter(None, *args)
         assert ei.value.status == kkt.KKT_ERR_ARG
+    with pytest.raises(kkt.KKTError) as ei:
+        kkt.kkt_factor_ctas_per_task(None, 0)
+    assert ei.value.status == kkt.KKT_ERR_ARG
 
 
 def test_recursive_plan_flops(kkt):

@@ -117,3 +117,4 @@ def test_ctas_per_task_query(kkt):
         assert all(kkt.kkt_factor_ctas_per_task(h, l) == 2 for l in range(len(levels)))
     finally:
         kkt.kkt_destroy(h)
+
