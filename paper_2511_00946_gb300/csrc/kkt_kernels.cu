@@ -1462,6 +1462,9 @@ __global__ void __launch_bounds__(256, 4) k_factor_w(const LevelDesc* __restrict
 // task's system, natural stage and level), skips its task and still releases
 // its consumers, so nothing waits forever.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void red_release_gpu(int* p) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(p) : "memory");
+}
 __device__ __forceinline__ int ld_acquire_gpu(const int* p) {
   int v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -2059,16 +2062,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_chain(const LevelDes
       if (li > 0) {
         const int need = cp.end[li - 1] - (li >= 2 ? cp.end[li - 2] : 0) + unmet;
         const long long t0 = clock64();
-        unsigned ns = 32;
         while (ld_acquire_gpu(ctr + li) < need) {
           if (clock64() - t0 > wait_cycles) {
             good = 0;
             break;
           }
-          __nanosleep(ns);
-          if (ns < 1024) ns *= 2;
         }
-        __threadfence();
       }
       ok = good;
       if (!good) record_timeout(info, d.sys, d.nat[d.seg[tk.seg]], d.level);
@@ -2078,12 +2077,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_backward_chain(const LevelDes
     if (work) backward_task<TS>(tk, descs, b + c0, ldb, cn, nullptr, smraw, cta_grp(), c0, true);
     cp_async_wait_all();  // (a skipped item's requested blocks)
     __syncthreads();
-    // release: the item's writes precede the barrier; the fence makes them
-    // visible device-wide before the counter moves
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(ctr + 1 + li, 1);
-    }
+    // release: the item's writes precede the barrier, and the release
+    // reduction orders them (cumulatively) before the counter's increment
+    if (threadIdx.x == 0) red_release_gpu(ctr + 1 + li);
   }
 }
 
