@@ -551,6 +551,9 @@ __device__ __forceinline__ void st_cluster(unsigned addr, float v) {
 // called once per output. Many partials (one per segment of every lower
 // level) are summed with all FP64 sub-pipes instead of one dependent chain
 // per output.
+// The partials live in L2 (written by earlier launches); the loads of four
+// steps are issued before their adds, which keep the order above, so a lane
+// waits for one L2 round trip per four steps instead of one per step.
 template <typename Fpart, typename Fout>
 __device__ void sum_partials(Grp G, int nout, int np, Fpart part, Fout out) {
   int sp = 1;
@@ -561,6 +564,16 @@ __device__ void sum_partials(Grp G, int nout, int np, Fpart part, Fout out) {
     double a0 = 0.0, a1 = 0.0;
     if (o < nout) {
       int p = sub;
+      for (; p + 7 * sp < np; p += 8 * sp) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = part(p + u * sp, o);
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+          a0 += v[u];
+          a1 += v[u + 1];
+        }
+      }
       for (; p + sp < np; p += 2 * sp) {
         a0 += part(p, o);
         a1 += part(p + sp, o);
@@ -1209,7 +1222,7 @@ __global__ void __launch_bounds__(kFactorThreads, MINB) k_factor(const LevelDesc
 //     about 1/C of the elements and stores the results into the shared
 //     memory of the CTA that writes that block's slots for the next level
 //     (rank 0: E- and G-rows, rank 1: W-rows);
-//   - rank 0 writes the pivot blocks, each CTA its panel rows.
+//   - the last rank writes the pivot blocks, each CTA its panel rows.
 // Three split-phase cluster barriers order the exchanges. Every element is
 // computed by the same operations in the same order as in the one- and
 // two-CTA layouts, so the results are bitwise theirs.
@@ -1249,30 +1262,62 @@ __device__ __forceinline__ void clus_task(const Task tk, const LevelDesc* __rest
   cluster_arrive();  // this CTA runs: the others may store into its shared memory after their wait
   if (tid == 0) bad = 0;
   potrf_table(cx.tab, n);
-  // inputs: the pivot block, the panel rows of the solve band, and the
-  // initial values of the Schur band (A_k and Q_k^T in the W-rows, else 0)
-  cx.load_D(Dfac, j, cta_grp());
-  for (int e = tid; e < (t1 - t0) * n; e += nt) {
-    const int r = t0 + e / n, c = e - (r - t0) * n;
-    double v;
-    if (r < n) v = cx.Ein[(size_t)j * cx.nn + r * n + c];  // E_j
-    else if (r < oW) {                                      // G_j (+ its second slot)
-      const size_t o = (size_t)j * cx.mn + (r - oG) * n + c;
-      v = cx.G2 ? cx.Gin[o] + cx.G2[o] : cx.Gin[o];
-    } else v = cx.Ein[(size_t)s * cx.nn + c * n + (r - oW)];  // W_1 = E[s]^T
-    Z[r * ldZ + c] = v;
-  }
-  for (int e = tid; e < (s1 - s0) * ldT; e += nt) {
-    const int a = s0 + e / ldT, b = e - (a - s0) * ldT;
-    double v = 0.0;
-    if (a >= oW && b >= oW && b < cx.R) {  // A_k = D_s (+ its second slot)
-      const size_t o = (size_t)s * cx.nn + (a - oW) * n + (b - oW);
-      v = cx.D2 ? cx.Din[o] + cx.D2[o] : cx.Din[o];
-    } else if (a >= oW && b >= oG && b < oW) {  // Q_k^T = G_s^T
-      const size_t o = (size_t)s * cx.mn + (b - oG) * n + (a - oW);
-      v = cx.G2 ? cx.Gin[o] + cx.G2[o] : cx.Gin[o];
+  // inputs: the pivot block D_j, the panel rows of the solve band, and the
+  // initial values of the Schur band (A_k and Q_k^T in its W-rows, zero
+  // elsewhere). Every load is an L2 round trip, so the three sets form one
+  // list whose loads go out eight per thread before any store: element e
+  // of the list is D_j's (e < nD), then the band's panel rows (< nD + nZ),
+  // then the W-row part [oG, R) of the Schur band's rows (the rest of those
+  // rows is zeroed separately). Sums of two slots add in the order of
+  // load_blk, so the values are those of the other layouts.
+  {
+    const int nD = n * n, nZ = (t1 - t0) * n;
+    const int wa0 = max(s0, oW), nTr = max(0, s1 - wa0), nTc = m + n;
+    const int nIn = nD + nZ + nTr * nTc;
+    const double* const D1 = cx.Din + (size_t)j * cx.nn;
+    const double* const D2 = cx.D2 ? cx.D2 + (size_t)j * cx.nn : nullptr;
+    constexpr int U = 8;
+    for (int e0 = tid; e0 < nIn; e0 += U * nt) {
+      double v[U];
+      int dst[U];  // offset in doubles from smraw's Dfac (Dfac, Z and T are one allocation)
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = e0 + u * nt;
+        dst[u] = -1;
+        v[u] = 0.0;
+        if (e < nD) {
+          const int r = e / n, c = e - r * n;
+          v[u] = D2 ? D1[e] + D2[e] : D1[e];
+          dst[u] = (int)(&Dfac[r * ldD + c] - Dfac);
+        } else if (e < nD + nZ) {
+          const int f = e - nD, r = t0 + f / n, c = f - (r - t0) * n;
+          if (r < n) v[u] = cx.Ein[(size_t)j * cx.nn + r * n + c];  // E_j
+          else if (r < oW) {                                         // G_j (+ its second slot)
+            const size_t o = (size_t)j * cx.mn + (r - oG) * n + c;
+            v[u] = cx.G2 ? cx.Gin[o] + cx.G2[o] : cx.Gin[o];
+          } else v[u] = cx.Ein[(size_t)s * cx.nn + c * n + (r - oW)];  // W_1 = E[s]^T
+          dst[u] = (int)(&Z[r * ldZ + c] - Dfac);
+        } else if (e < nIn) {
+          const int f = e - nD - nZ, a = wa0 + f / nTc, b = oG + (f - (a - wa0) * nTc);
+          if (b >= oW) {  // A_k = D_s (+ its second slot)
+            const size_t o = (size_t)s * cx.nn + (a - oW) * n + (b - oW);
+            v[u] = cx.D2 ? cx.Din[o] + cx.D2[o] : cx.Din[o];
+          } else {        // Q_k^T = G_s^T
+            const size_t o = (size_t)s * cx.mn + (b - oG) * n + (a - oW);
+            v[u] = cx.G2 ? cx.Gin[o] + cx.G2[o] : cx.Gin[o];
+          }
+          dst[u] = (int)(&T[a * ldT + b] - Dfac);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (dst[u] >= 0) Dfac[dst[u]] = v[u];
     }
-    T[a * ldT + b] = v;
+    // the rest of the Schur band's rows: zero
+    for (int e = tid; e < (s1 - s0) * ldT; e += nt) {
+      const int a = s0 + e / ldT, b = e - (a - s0) * ldT;
+      if (!(a >= oW && b >= oG && b < cx.R)) T[a * ldT + b] = 0.0;
+    }
   }
   __syncthreads();
   potrf_trsm_sm(Dfac, ldD, n, rinv, M, cx.tab, &bad, Z, ldZ, t0, t1, true);
@@ -1293,7 +1338,8 @@ __device__ __forceinline__ void clus_task(const Task tk, const LevelDesc* __rest
     }
   }
   cluster_arrive();
-  if (rank == 0) {
+  // the pivot blocks: by the last rank, which stores no slots when C > 2
+  if (rank == C - 1) {
     if (tid == 0 && bad) record_breakdown(info, d.sys, d.nat[j], d.level);
     cx.store_pivot(j, Dfac, rinv, M, cta_grp());
   }
