@@ -941,6 +941,7 @@ def main():
         best = None
         for p in candidate_plans(kkt, part):
             h = kkt.kkt_create_plan(N_STAGES, N_BLOCK, M_ARROW, p, part)
+            kkt.kkt_set_code_warmup(h, True)
             ts = []
             for it in range(9):
                 bd.copy_(b0)
@@ -958,6 +959,14 @@ def main():
                 best = (t, p)
         plan = best[1]
     h = kkt.kkt_create_plan(N_STAGES, N_BLOCK, M_ARROW, plan, part)
+    # the code of the kernels that run once per step is brought into L2 by a
+    # companion system's pass on a forked side stream (kkt_set_code_warmup)
+    kkt.kkt_set_code_warmup(h, True)
+    # the companion's launches per step: its border copy, two factor levels,
+    # its top level and one backward launch
+    hw = kkt.kkt_create_plan(7, N_BLOCK, M_ARROW, [4, 2, 1], part)
+    warm_launches = 1 + kkt.kkt_launch_counts(hw)[0] + 1
+    kkt.kkt_destroy(hw)
     fl = kkt.kkt_flops(h)
     # one group per level: L forward launches, then one backward launch per
     # level below the top or a single one for all of them
@@ -1164,6 +1173,9 @@ def main():
             "config": {"workload": WORKLOAD.format(nrhs=args.nrhs), "levels": plan, "partition": args.partition,
                        "precision": "fp64",
                        "l2": "flushed before every timed step (256 MiB write)",
+                       "code_warmup": "on: each step forks a side stream on which a 7-stage companion system "
+                                      "runs its bordered pass, bringing the code of the once-per-step kernels "
+                                      "into L2 (its launches are counted in gpu_launches)",
                        "replicas": world},
             "error": {"backward_error": eta, "relative_residual": relres},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -1176,7 +1188,7 @@ def main():
                               "how": "the same call without a graph, host wall clock from the call to the "
                                      "stream synchronization that makes x readable (L2 flushed before)",
                               "same_x_as_device_path": eager_same}},
-            "gpu_launches": args.steps * nl,
+            "gpu_launches": args.steps * (nl + warm_launches),
             "launches_per_step": {names[i] if i < len(names) else f"launch {i}": round(a, 4)
                                   for i, a in enumerate(diag_avg)},
             "launches_per_step_note": "ms per launch from 27 diagnostic graph replays with an event after "

@@ -433,6 +433,25 @@ kkt_status kkt_set_persistent(kkt_handle* h, int on);
  * for a NULL handle. Takes effect at the next solve. */
 kkt_status kkt_set_backward_chain(kkt_handle* h, int on);
 
+/* Instruction warm-up of kkt_factor_solve's bordered pass (on = 1; default
+ * off). After an L2 flush, or when other work has evicted them, the code of
+ * the kernels that run once per call (the cluster kernel of the deep levels,
+ * the top level's corner factorization and corner solve, the single-launch
+ * backward substitution) is fetched from device memory the first time each
+ * runs, a cost of several microseconds per kernel on a latency-bound
+ * critical path. With the warm-up, each kkt_factor_solve first forks a side
+ * stream on which a companion system (7 stages with the handle's largest
+ * block sizes, identity blocks, plan [4, 2, 1]) runs its own bordered pass,
+ * concurrently with this call's border copy and first level, so that those
+ * kernels' code is in L2 when the call reaches them; the call joins the
+ * side stream before it returns (graph capture sees a fork and a join). The
+ * companion's results are discarded and do not touch this handle's factor,
+ * info record or events. Applies to FP64 handles with room for the bordered
+ * row; a no-op elsewhere. on = 1 allocates the companion (a few hundred KB)
+ * and a stream: call it outside any graph capture. Returns KKT_ERR_ARG for a
+ * NULL handle. */
+kkt_status kkt_set_code_warmup(kkt_handle* h, int on);
+
 /* Bounded waits of the persistent schedule, of the single-launch backward
  * substitution and of the one-warp substitution
  * of sequential systems (one level, P = 1, one right-hand side), whose stage

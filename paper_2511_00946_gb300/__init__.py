@@ -32,7 +32,8 @@ EXPORTED = [
     "kkt_partition", "kkt_partition_rule", "kkt_partition_balanced", "kkt_batch_offsets", "kkt_factor", "kkt_solve", "kkt_factor_solve", "kkt_factor_solve_host", "kkt_solve_refined", "kkt_solve_adjoint", "kkt_refine_eta", "kkt_set_refine_tol",
     "kkt_get_info",
     "kkt_get_factor", "kkt_set_pairing", "kkt_set_launch_events", "kkt_launch_counts", "kkt_factor_ctas_per_task", "kkt_flops", "kkt_plan_flops", "kkt_solve_noalloc", "kkt_status_string",
-    "kkt_set_persistent", "kkt_set_backward_chain", "kkt_set_wait_limit", "kkt_set_refine_fallback",
+    "kkt_set_persistent", "kkt_set_backward_chain", "kkt_set_code_warmup", "kkt_set_wait_limit",
+    "kkt_set_refine_fallback",
 ]
 
 
@@ -84,6 +85,7 @@ _sig = {
     "kkt_status_string": [_i],
     "kkt_set_persistent": [_vp, _i],
     "kkt_set_backward_chain": [_vp, _i],
+    "kkt_set_code_warmup": [_vp, _i],
     "kkt_set_wait_limit": [_vp, ctypes.c_longlong, _i],
     "kkt_set_refine_fallback": [_vp, _i],
     "kkt_set_refine_tol": [_vp, ctypes.c_double],
@@ -333,6 +335,12 @@ def kkt_set_backward_chain(h: int, on: bool = True) -> None:
     """The backward substitution of every level below the top in one launch
     (default where it applies) or one launch per level (see the C header)."""
     _check(_lib.kkt_set_backward_chain(h, int(bool(on))), "kkt_set_backward_chain")
+
+
+def kkt_set_code_warmup(h: int, on: bool = True) -> None:
+    """Instruction warm-up of kkt_factor_solve: a companion system's bordered
+    pass on a forked side stream (see the C header)."""
+    _check(_lib.kkt_set_code_warmup(h, int(bool(on))), "kkt_set_code_warmup")
 
 
 def kkt_set_wait_limit(h: int, cycles: int, unmet: bool = False) -> None:

@@ -168,6 +168,14 @@ struct kkt_handle {
   std::vector<int> bwd_off, bwd_cnt;         // task ranges per level (backward)
   // the backward levels in one launch (k_backward_chain): every backward
   // task has blocks n > 16 and every level below the top the same precision
+  // kkt_set_code_warmup: a companion handle (one small system with the
+  // same block sizes and a three-level plan) whose bordered pass runs on a
+  // side stream at the start of every kkt_factor_solve, its inputs, and the
+  // fork/join events
+  kkt_handle* warm = nullptr;
+  double* warm_mem = nullptr;
+  cudaStream_t warm_stream = nullptr;
+  cudaEvent_t warm_fork = nullptr, warm_join = nullptr;
   bool chain = false;
   bool chain_on = true;                      // kkt_set_backward_chain
   int* dchain = nullptr;                     // its counters (maxL ints)
@@ -817,8 +825,23 @@ kkt_status kkt_batch_create_tuned(int count, const int* N, const int* n, const i
   return st;
 }
 
+namespace {
+void warm_release(kkt_handle* h) {
+  if (h->warm) kkt_destroy(h->warm);
+  if (h->warm_mem) cudaFree(h->warm_mem);
+  if (h->warm_stream) cudaStreamDestroy(h->warm_stream);
+  if (h->warm_fork) cudaEventDestroy(h->warm_fork);
+  if (h->warm_join) cudaEventDestroy(h->warm_join);
+  h->warm = nullptr;
+  h->warm_mem = nullptr;
+  h->warm_stream = nullptr;
+  h->warm_fork = h->warm_join = nullptr;
+}
+}  // namespace
+
 kkt_status kkt_destroy(kkt_handle* h) {
   if (!h) return KKT_OK;
+  warm_release(h);
   if (h->dmem) cudaFree(h->dmem);
   if (h->pmem) cudaFree(h->pmem);
   if (h->cg_mem) cudaFree(h->cg_mem);
@@ -1075,6 +1098,44 @@ kkt_status kkt_set_persistent(kkt_handle* h, int on) {
   return KKT_OK;
 }
 
+// Companion system of the code warm-up: N = 7 stages with the handle's
+// largest block sizes, plan [4, 2, 1] (one-stage segments on both lower
+// levels, a top level of one stage), D_j = I, E_j = 0, G_j = 0, R = I, b = 0.
+kkt_status kkt_set_code_warmup(kkt_handle* h, int on) {
+  if (!h) return KKT_ERR_ARG;
+  if (!on) {
+    warm_release(h);
+    return KKT_OK;
+  }
+  if (h->warm) return KKT_OK;
+  if (!h->border || h->precision != KKT_FP64) return KKT_OK;  // nothing of the bordered pass to warm
+  const int N = 7, n = h->maxn, m = h->maxm, P[3] = {4, 2, 1};
+  kkt_handle* w = nullptr;
+  kkt_status st = kkt_create_plan(N, n, m, 3, P, KKT_PARTITION_BALANCED, KKT_FP64, &w);
+  if (st != KKT_OK) return st;
+  const size_t nD = (size_t)N * n * n, nE = (size_t)(N - 1) * n * n, nG = (size_t)N * m * n,
+               nR = (size_t)m * m, nB = (size_t)N * n + m;
+  std::vector<double> host(nD + nE + nG + nR + nB, 0.0);
+  for (int j = 0; j < N; ++j)
+    for (int i = 0; i < n; ++i) host[(size_t)j * n * n + (size_t)i * n + i] = 1.0;
+  for (int i = 0; i < m; ++i) host[nD + nE + nG + (size_t)i * m + i] = 1.0;
+  double* mem = nullptr;
+  if (cudaMalloc(&mem, sizeof(double) * host.size()) != cudaSuccess) {
+    kkt_destroy(w);
+    return KKT_ERR_CUDA;
+  }
+  h->warm = w;
+  h->warm_mem = mem;
+  if (cudaMemcpy(mem, host.data(), sizeof(double) * host.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->warm_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->warm_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->warm_join, cudaEventDisableTiming) != cudaSuccess) {
+    warm_release(h);
+    return KKT_ERR_CUDA;
+  }
+  return KKT_OK;
+}
+
 kkt_status kkt_set_backward_chain(kkt_handle* h, int on) {
   if (!h) return KKT_ERR_ARG;
   h->chain_on = on != 0;
@@ -1218,6 +1279,11 @@ kkt_status kkt_solve(kkt_handle* h, double* b, int nrhs, int ldb, void* stream) 
   return KKT_OK;
 }
 
+namespace {
+kkt_status factor_solve_bordered(kkt_handle* h, const double* D, const double* E, const double* G,
+                                 const double* R, double* b, int ldb, void* stream);
+}  // namespace
+
 kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, const double* G,
                             const double* R, double* b, int nrhs, int ldb, void* stream) {
   if (!h || !D || !b || nrhs < 1 || ldb < nrhs) return KKT_ERR_ARG;
@@ -1227,6 +1293,27 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
     const kkt_status st = kkt_factor(h, D, E, G, R, stream);
     return st != KKT_OK ? st : kkt_solve(h, b, nrhs, ldb, stream);
   }
+  // code warm-up: the companion system's bordered pass on the side stream,
+  // forked here and joined at the end of the call
+  if (h->warm) {
+    kkt_handle* w = h->warm;
+    const size_t nD = (size_t)w->tot_D, nE = (size_t)w->tot_E, nG = (size_t)w->tot_G, nR = (size_t)w->tot_R;
+    double* wm = h->warm_mem;
+    if (cudaEventRecord(h->warm_fork, (cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamWaitEvent(h->warm_stream, h->warm_fork, 0) != cudaSuccess)
+      return KKT_ERR_CUDA;
+    const kkt_status ws = kkt_factor_solve(w, wm, wm + nD, wm + nD + nE, wm + nD + nE + nG,
+                                           wm + nD + nE + nG + nR, 1, 1, h->warm_stream);
+    if (ws != KKT_OK || cudaEventRecord(h->warm_join, h->warm_stream) != cudaSuccess) return KKT_ERR_CUDA;
+  }
+  const kkt_status st = factor_solve_bordered(h, D, E, G, R, b, ldb, stream);
+  if (h->warm && cudaStreamWaitEvent((cudaStream_t)stream, h->warm_join, 0) != cudaSuccess) return KKT_ERR_CUDA;
+  return st;
+}
+
+namespace {
+kkt_status factor_solve_bordered(kkt_handle* h, const double* D, const double* E, const double* G,
+                                 const double* R, double* b, int ldb, void* stream) {
   // the right-hand side bordered onto the arrow: the factorization carries the
   // forward substitution and writes y where the backward sweep reads it
   int li = 0;
@@ -1249,6 +1336,7 @@ kkt_status kkt_factor_solve(kkt_handle* h, const double* D, const double* E, con
   h->cur_b = true;
   return solve_chunk(h, b, ldb, 1, nullptr, stream, &li, 1);
 }
+}  // namespace
 
 namespace {
 // Device buffers and the overlap streams of kkt_factor_solve_host: the copy

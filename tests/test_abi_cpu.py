@@ -115,7 +115,8 @@ def test_invalid_arguments(kkt):
     assert kkt.status_string(kkt.KKT_ERR_NOT_SPD).startswith("pivot")
     for setter, args in ((kkt.kkt_set_refine_tol, (1e-16,)), (kkt.kkt_set_refine_fallback, (4,)),
                          (kkt.kkt_set_persistent, (True,)), (kkt.kkt_set_wait_limit, (1 << 20,)),
-                         (kkt.kkt_set_backward_chain, (True,)), (kkt.kkt_set_pairing, (kkt.KKT_PAIR_AUTO_PAIRS,))):
+                         (kkt.kkt_set_backward_chain, (True,)), (kkt.kkt_set_pairing, (kkt.KKT_PAIR_AUTO_PAIRS,)),
+                         (kkt.kkt_set_code_warmup, (True,))):
         with pytest.raises(kkt.KKTError) as ei:   # no handle: refused before any device work
             setter(None, *args)
         assert ei.value.status == kkt.KKT_ERR_ARG

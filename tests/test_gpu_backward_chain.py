@@ -142,3 +142,45 @@ def test_chain_wait_runs_out_and_reports(kkt, orc):
     finally:
         kkt.kkt_destroy(h)
     assert orc.block_backward_error(D, E, G, R, x, b) <= 1e-14
+
+
+def test_code_warmup_same_bits_eager_and_graph(kkt, orc):
+    """kkt_set_code_warmup: the companion system's pass on the forked side
+    stream leaves this call's result bit for bit unchanged, eagerly and
+    replayed from a captured graph (fork and join inside the capture)."""
+    import torch
+    N, n, m = 1024, 32, 8
+    levels = halving(256)
+    D, E, G, R = gen.ipm(N, n, m, seed=21, sigma_decades=3.0)
+    b = gen.rhs(N * n + m, 1, seed=22)
+    Dd, Ed, Gd, Rd, bsrc = dev(D), dev(E), dev(G), dev(R), dev(b)
+    outs = []
+    for warm in (False, True):
+        h = kkt.kkt_create_plan(N, n, m, levels, kkt.KKT_PARTITION_BALANCED, kkt.KKT_FP64)
+        try:
+            kkt.kkt_set_code_warmup(h, warm)
+            x = bsrc.clone()
+            kkt.kkt_factor_solve(h, Dd, Ed, Gd, Rd, x)
+            torch.cuda.synchronize()
+            assert kkt.kkt_get_info(h)["status"] == 0
+            outs.append(x.cpu().numpy())
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(s):
+                xg = bsrc.clone()
+                with torch.cuda.graph(g, stream=s):
+                    kkt.kkt_factor_solve(h, Dd, Ed, Gd, Rd, xg, stream=s.cuda_stream)
+            torch.cuda.current_stream().wait_stream(s)
+            for _ in range(2):
+                xg.copy_(bsrc)
+                g.replay()
+            torch.cuda.synchronize()
+            assert kkt.kkt_get_info(h)["status"] == 0
+            outs.append(xg.cpu().numpy())
+            kkt.kkt_set_code_warmup(h, False)  # releases the companion
+        finally:
+            kkt.kkt_destroy(h)
+    for o in outs[1:]:
+        np.testing.assert_array_equal(outs[0], o)
+    assert orc.block_backward_error(D, E, G, R, outs[0], b) <= 1e-14
