@@ -935,6 +935,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     # --- level plan: fastest of a few candidates (untimed)
+    search = {}
     if args.levels:
         plan = [int(v) for v in args.levels.split(",")]
     else:
@@ -955,6 +956,7 @@ def main():
                     ts.append(e0.elapsed_time(e1))
             kkt.kkt_destroy(h)
             t = statistics.median(ts)
+            search[",".join(map(str, p))] = round(t, 4)
             if best is None or t < best[0]:
                 best = (t, p)
         plan = best[1]
@@ -1176,7 +1178,8 @@ def main():
                        "code_warmup": "on: each step forks a side stream on which a 7-stage companion system "
                                       "runs its bordered pass, bringing the code of the once-per-step kernels "
                                       "into L2 (its launches are counted in gpu_launches)",
-                       "replicas": world},
+                       "replicas": world,
+                       "plan_search_ms": search or None},
             "error": {"backward_error": eta, "relative_residual": relres},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "api": "kkt_factor_solve_host (page-locked host buffers, graph replay): the factor "
