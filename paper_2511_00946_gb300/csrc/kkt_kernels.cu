@@ -222,10 +222,10 @@ __device__ __forceinline__ void potrf_col0(double* A, int ld, int n, double* rin
   const double r = pivot_rsqrt(d);
   if (lane == 0) {
     if (not_positive(d) && *bad == 0) *bad = 1;
-    A[0] = d * r;
     rinv[0] = r;
   }
-  for (int i = 1 + lane; i < n; i += 32) A[i * ld] *= r;
+  // (lane 0 scales the diagonal: L_00 = d r)
+  for (int i = lane; i < n; i += 32) A[i * ld] *= r;
 }
 
 // warp 0 in the phase of column j: column j+1 updated, pivoted and scaled
@@ -243,11 +243,11 @@ __device__ __forceinline__ void potrf_lookahead(double* A, int ld, int n, double
   if (lane == 0) {  // v0 is the diagonal element (j+1, j+1)
     if (not_positive(v0) && *bad == 0) *bad = j + 2;
     r = pivot_rsqrt(v0);
-    A[(j + 1) * ld + j + 1] = v0 * r;
     rinv[j + 1] = r;
   }
   r = __shfl_sync(0xffffffffu, r, 0);
-  if (lane > 0 && i0 < n) A[i0 * ld + j + 1] = v0 * r;
+  // one FP64 multiply for the whole column, the diagonal L_{j+1,j+1} = v0 r on lane 0
+  if (i0 < n) A[i0 * ld + j + 1] = v0 * r;
   if (two) {
     if (i1 < n) A[i1 * ld + j + 1] = v1 * r;
   }

@@ -29,9 +29,14 @@ static __device__ __forceinline__ bool not_positive(double d) {
 // manipulation only, then refined by one step of Halley's method for
 // f(r) = r^-2 - d': with e = 1 - d' r^2, r <- r (1 + e/2 + 3 e^2 / 8), which
 // leaves an error of order e^3 (below 2^-62), so the result is within a few
-// units in the last place; finally r 2^-k. Zero, negative, NaN, subnormal or
-// huge d take an out-of-line path (NaN when d is not positive). The range
-// tests are integer tests: FP64 comparisons would occupy the FP64 pipe.
+// units in the last place; finally r 2^-k. The step is evaluated as
+// r + e (r/2 + (3r/8) e): r carries the estimate's 24 significant bits, so
+// r/2 and 3r/8 are exact and are formed on the bits with integer operations,
+// and the step costs two FP64 operations after e (a warp's FP64 instruction
+// holds the sub-partition's FP64 pipe for 64 cycles, so every instruction on
+// a pivot chain counts). Zero, negative, NaN, subnormal or huge d take an
+// out-of-line path (NaN when d is not positive). The range tests are integer
+// tests: FP64 comparisons would occupy the FP64 pipe.
 static __device__ __forceinline__ double pivot_rsqrt(double d) {
   const long long bits = __double_as_longlong(d);
   const int ef = (int)((bits >> 52) & 0x7ff);  // biased exponent; sign handled by bits > 0
@@ -46,8 +51,15 @@ static __device__ __forceinline__ double pivot_rsqrt(double d) {
   const int rb = __float_as_int(rf);  // in (0.5, 1]: normal
   double r = __longlong_as_double((long long)(((rb >> 23) & 0xff) - 127 + 1023) << 52 |
                                   (long long)(rb & 0x7fffff) << 29);
+  const long long rbits = __double_as_longlong(r), re = (rbits >> 52) & 0x7ff;  // r in (1/2, 1]
+  const double half_r = __longlong_as_double(rbits - (1LL << 52));
+  // 3r/8: the 53-bit significand times 3 (its low 29 bits are zero, so the
+  // renormalising shift by one or two places is exact)
+  const long long sig3 = 3 * ((rbits & ((1LL << 52) - 1)) | (1LL << 52));
+  const double c38_r = __longlong_as_double(sig3 >= (1LL << 54) ? ((re - 1) << 52) | ((sig3 >> 2) - (1LL << 52))
+                                                                 : ((re - 2) << 52) | ((sig3 >> 1) - (1LL << 52)));
   const double e = fma(-dp * r, r, 1.0);
-  r = fma(r * e, fma(0.375, e, 0.5), r);
+  r = fma(fma(c38_r, e, half_r), e, r);
   return __longlong_as_double(__double_as_longlong(r) - ((long long)k << 52));
 }
 
