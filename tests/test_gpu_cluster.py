@@ -118,3 +118,38 @@ def test_ctas_per_task_query(kkt):
     finally:
         kkt.kkt_destroy(h)
 
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_cluster_layout_mixed_levels(kkt, orc, precision):
+    """KKT_MIXED_FP32 (level 1 in FP32 panels, the deeper levels FP64: the
+    deep levels run on clusters, the backward levels one launch per level
+    since their precisions differ) and KKT_MIXED_FP32_ALL (every level mixed:
+    no clusters, the backward levels in one launch): the refined solution
+    agrees bit for bit with the pair layout's and meets the gates."""
+    import torch
+    N, n, m = 255, 32, 8
+    levels = halving(64)
+    D, E, G, R = gen.ipm(N, n, m, seed=77, sigma_decades=3.0)
+    b = gen.rhs(N * n + m, 1, seed=78)
+    Dd, Ed, Gd, Rd, bd = dev(D), dev(E), dev(G), dev(R), dev(b)
+    outs, ctas = [], []
+    for policy in (kkt.KKT_PAIR_AUTO, kkt.KKT_PAIR_AUTO_PAIRS):
+        h = kkt.kkt_create_plan(N, n, m, levels, kkt.KKT_PARTITION_BALANCED, precision)
+        try:
+            kkt.kkt_set_pairing(h, policy)
+            ctas.append([kkt.kkt_factor_ctas_per_task(h, l) for l in range(len(levels))])
+            x = torch.zeros_like(bd)
+            kkt.kkt_factor(h, Dd, Ed, Gd, Rd)
+            kkt.kkt_solve_refined(h, Dd, Ed, Gd, Rd, bd, x, sweeps=8, tol=1e-16)
+            torch.cuda.synchronize()
+            assert kkt.kkt_get_info(h)["status"] == 0
+            outs.append(x.cpu().numpy())
+        finally:
+            kkt.kkt_destroy(h)
+    if precision == 1:
+        assert max(ctas[0][1:-1]) >= 4, ctas[0]
+    else:
+        assert max(ctas[0]) <= 2, ctas[0]
+    np.testing.assert_array_equal(outs[0], outs[1])
+    assert orc.block_backward_error(D, E, G, R, outs[0], b) <= 1e-14
