@@ -1164,7 +1164,11 @@ __device__ __forceinline__ void factor_task(const Task tk, const LevelDesc* __re
       Rs[r * ldR + c] = (Ru[e] + Psum[e]) + T[(oG + r) * ldT + oG + c];
     }
     __syncthreads();
-    corner_factor<false>(Rs, ldR, m, d.mr, rinv, tab, d, info, &bad, cta_grp());
+    // by one warp: at m <= 16 a per-column block barrier costs more than the
+    // column's work (the operations per element are potrf_sm's)
+    if (threadIdx.x < 32)
+      corner_factor<true>(Rs, ldR, m, d.mr, rinv, tab, d, info, nullptr, Grp{(int)threadIdx.x, 32, -1});
+    __syncthreads();
   }
   if constexpr (!mixed) {
     // bordered pass, top level: the corner solve x_g = R-hat^{-T} y_g and the
