@@ -133,3 +133,22 @@ def test_recursive_plan_flops(kkt):
     three = kkt.kkt_plan_flops(1024, 32, 8, [152, 38, 1])
     assert one["factor"] == one["sequential_factor"]
     assert one["factor"] < two["factor"] < three["factor"] < 2.5 * one["factor"]
+
+
+def test_bench_launch_names_with_the_backward_chain(kkt, monkeypatch):
+    """The bench's per-launch split of a fused step: border copy, one factor
+    launch per level (the top one with the corner solve and its backward
+    sweep), then either one backward launch per level below the top or one
+    launch for all of them, carrying their summed flops."""
+    import bench
+    monkeypatch.setattr(bench, "device_sms", lambda: 152)
+    plan = [256, 128, 64, 32, 16, 8, 4, 2, 1]
+    part = kkt.KKT_PARTITION_BALANCED
+    n_lv, f_lv = bench.per_launch_flops(kkt, plan, part, 1, chain=False)
+    n_ch, f_ch = bench.per_launch_flops(kkt, plan, part, 1, chain=True)
+    L = len(plan)
+    assert len(n_lv) == 1 + L + (L - 1) and len(n_ch) == 1 + L + 1
+    assert n_ch[:1 + L] == n_lv[:1 + L] and f_ch[:1 + L] == f_lv[:1 + L]
+    assert n_ch[-1] == f"k_backward_chain (levels {L - 1}..1)"
+    assert f_ch[-1] == pytest.approx(sum(f_lv[1 + L:]), rel=1e-12)
+    assert all(f > 0 for f in f_lv[1:])
