@@ -992,7 +992,7 @@ def main():
     fl = kkt.kkt_flops(h)
     # one group per level: L forward launches, then one backward launch per
     # level below the top or a single one for all of them
-    chain = kkt.kkt_launch_counts(h)[1] == len(plan) + 1 and len(plan) >= 3
+    chain = kkt.kkt_launch_counts(h)[1] == len(plan) + 1 and len(plan) >= 3 and args.nrhs == 1
     launch_names, launch_flops = per_launch_flops(kkt, plan, part, args.nrhs, chain)
     nl = len(launch_names)
 

@@ -421,16 +421,19 @@ kkt_status kkt_set_persistent(kkt_handle* h, int on);
 /* The backward substitution of the levels below the top (Algorithm 3,
  * parallel phase of each level) as ONE launch (on = 1, the default where it
  * applies) or one launch per level and block-size class (on = 0). It applies
- * to handles with at least three levels whose backward tasks all have blocks
- * n > 16 and whose levels below the top share one precision; elsewhere the
- * per-level launches run whatever `on` says. In the single launch CTAs take
+ * to solves of one right-hand side (kkt_factor_solve, single-column
+ * kkt_solve and the refinement's correction solves) on handles with at
+ * least three levels whose backward tasks all have blocks n > 16 and whose
+ * levels below the top share one precision; elsewhere, and for chunks of
+ * several right-hand sides, the per-level launches run whatever `on` says. In the single launch CTAs take
  * (task, column group) items by ticket, top level first; an item requests
  * its stage's factor blocks at once, then waits until every item of the
  * level above has released its counter (a bounded wait, see
  * kkt_set_wait_limit), solves, and releases its own level's counter.
  * Results are bitwise those of the per-level launches (the same operations
- * per element). kkt_launch_counts reflects the setting. Returns KKT_ERR_ARG
- * for a NULL handle. Takes effect at the next solve. */
+ * per element). kkt_launch_counts reflects the setting for one right-hand
+ * side. Returns KKT_ERR_ARG for a NULL handle. Takes effect at the next
+ * solve. */
 kkt_status kkt_set_backward_chain(kkt_handle* h, int on);
 
 /* Instruction warm-up of kkt_factor_solve's bordered pass (on = 1; default
@@ -468,7 +471,10 @@ kkt_status kkt_set_code_warmup(kkt_handle* h, int on);
 kkt_status kkt_set_wait_limit(kkt_handle* h, long long cycles, int unmet);
 
 /* Number of kernel launches one kkt_factor / one kkt_solve (per chunk of up
- * to 16 right-hand sides) enqueues for this handle. */
+ * to 16 right-hand sides) enqueues for this handle. The solve count is that
+ * of a chunk with one right-hand side; where the backward levels run as one
+ * launch (kkt_set_backward_chain), a chunk of several right-hand sides runs
+ * them one launch per level and block-size class instead. */
 kkt_status kkt_launch_counts(const kkt_handle* h, int* factor_launches, int* solve_launches);
 
 /* CTAs per segment task in the per-level factor launches of level `level`

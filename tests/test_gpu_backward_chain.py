@@ -4,9 +4,9 @@ CTAs take (task, column group) items by ticket, request their stage's factor
 blocks, wait (bounded) for the level above's counter and release their own.
 Through the C interface:
 * bitwise the per-level launches (kkt_set_backward_chain(h, 0)) for the
-  bordered factor-and-solve pass, the two-pass solve with 3 and 16
-  right-hand sides (the 16-column solve splits the columns of deep levels
-  over several items), mixed precision with refinement, and plans with
+  bordered factor-and-solve pass, the two-pass solve with one right-hand
+  side and with 3 and 16 (chunks of several columns run the per-level
+  launches either way), mixed precision with refinement, and plans with
   multi-stage segments on every level;
 * the oracle's gates on the chained result;
 * kkt_launch_counts: one backward launch instead of L - 1;
@@ -73,6 +73,7 @@ def run(kkt, chain, N, n, m, levels, D, E, G, R, b, mode, precision=0):
 
 CASES = [
     (1024, 32, 8, halving(256), "bordered", 1, 0),
+    (1024, 32, 8, halving(256), "two-pass", 1, 0),
     (1024, 32, 8, halving(256), "two-pass", 3, 0),
     (1024, 32, 8, halving(256), "two-pass", 16, 0),
     (600, 24, 6, [60, 12, 3, 1], "two-pass", 2, 0),
